@@ -1,0 +1,116 @@
+"""CPU oracle for the GPU compute-actor path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg import this package.  It shares no code with the CUDA library: the
+numeric payloads live in ``oracle.c`` (plain single-threaded C, loaded
+through ctypes) and the actor semantics in ``actors.py`` (plain Python).
+
+Functions and the passages they follow:
+
+* ``factor`` / ``factor_batch`` -- trial division as the plain definition
+  of the factorization side load of the mixed benchmark (Sec. 5, "Mixed
+  Operations Under Work Load"): smallest d >= 2 with d*d <= n and d | n.
+* ``check_certificate`` / ``is_prime`` -- p*q == n, p <= q, p and q prime.
+* ``gemm_f64`` / ``gemm_entry`` -- the matrix product of the OpenCL actor
+  example (Sec. 3.6) in float64 from float32 inputs.
+* ``rel_frobenius`` -- relative Frobenius error in float64.
+* ``actors.simulate_mailboxes`` / ``actors.check_mailbox_log`` -- the
+  mailbox of Sec. 3.2 and Sec. 2 (FIFO, one reader, exactly-once handling).
+* ``actors.simulate_rings`` -- the token rings of Sec. 5.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``liboracle.so`` (gcc, -O2, no -march flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        L.oracle_factor.argtypes = [ctypes.c_uint64, u64p, u64p]
+        L.oracle_factor.restype = ctypes.c_int32
+        L.oracle_factor_batch.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_factor_batch.restype = None
+        L.oracle_is_prime.argtypes = [ctypes.c_uint64]
+        L.oracle_is_prime.restype = ctypes.c_int32
+        L.oracle_check_certificate.argtypes = [ctypes.c_uint64, ctypes.c_uint64,
+                                               ctypes.c_uint64, ctypes.c_int32]
+        L.oracle_check_certificate.restype = ctypes.c_int32
+        L.oracle_gemm_f64.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        L.oracle_gemm_f64.restype = None
+        L.oracle_gemm_entry.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_int64, ctypes.c_int64]
+        L.oracle_gemm_entry.restype = ctypes.c_double
+        L.oracle_rel_frobenius.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+        L.oracle_rel_frobenius.restype = ctypes.c_double
+        _lib = L
+    return _lib
+
+
+def factor(n: int):
+    """(status, p, q) for one n: status 0 -> n = p*q with p the smallest divisor >= 2
+    and p*p <= n; status 1 -> no such divisor, (p, q) = (1, n)."""
+    p = ctypes.c_uint64()
+    q = ctypes.c_uint64()
+    s = lib().oracle_factor(ctypes.c_uint64(int(n)), ctypes.byref(p), ctypes.byref(q))
+    return int(s), int(p.value), int(q.value)
+
+
+def factor_batch(n: np.ndarray):
+    """Vector form of ``factor``: returns (status int32, p uint64, q uint64)."""
+    n = np.ascontiguousarray(n, dtype=np.uint64)
+    p = np.empty_like(n)
+    q = np.empty_like(n)
+    st = np.empty(n.size, dtype=np.int32)
+    lib().oracle_factor_batch(n.ctypes.data, n.size, p.ctypes.data, q.ctypes.data, st.ctypes.data)
+    return st, p, q
+
+
+def is_prime(x: int) -> bool:
+    return bool(lib().oracle_is_prime(ctypes.c_uint64(int(x))))
+
+
+def check_certificate(n: int, p: int, q: int, status: int) -> bool:
+    return bool(lib().oracle_check_certificate(int(n), int(p), int(q), int(status)))
+
+
+def gemm_f64(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    n = A.shape[0]
+    assert A.shape == (n, n) and B.shape == (n, n)
+    C = np.empty((n, n), dtype=np.float64)
+    lib().oracle_gemm_f64(A.ctypes.data, B.ctypes.data, n, C.ctypes.data)
+    return C
+
+
+def gemm_entry(A: np.ndarray, B: np.ndarray, i: int, j: int) -> float:
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    return float(lib().oracle_gemm_entry(A.ctypes.data, B.ctypes.data, A.shape[0], i, j))
+
+
+def rel_frobenius(C: np.ndarray, C64: np.ndarray) -> float:
+    C = np.ascontiguousarray(C, dtype=np.float32)
+    C64 = np.ascontiguousarray(C64, dtype=np.float64)
+    assert C.size == C64.size
+    return float(lib().oracle_rel_frobenius(C.ctypes.data, C64.ctypes.data, C.size))

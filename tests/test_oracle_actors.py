@@ -1,0 +1,70 @@
+"""Pins for the sequential mailbox and token-ring readings."""
+import numpy as np
+
+from oracle import actors
+from paper_1505_07368_gb300 import workloads as W
+
+
+def test_simulate_mailboxes_hand_example():
+    actor = np.array([2, 0, 2, 1, 0, 2])
+    assert actors.simulate_mailboxes(actor) == {2: [0, 2, 5], 0: [1, 4], 1: [3]}
+
+
+def _valid_log(actor):
+    order = actors.simulate_mailboxes(actor)
+    la, lm = [], []
+    # interleave actors round robin: a valid global order
+    its = {a: iter(v) for a, v in order.items()}
+    while its:
+        for a in list(its):
+            try:
+                lm.append(next(its[a]))
+                la.append(a)
+            except StopIteration:
+                del its[a]
+    return np.array(la), np.array(lm), np.arange(len(lm))
+
+
+def test_checker_accepts_valid_and_rejects_planted_errors():
+    wl = W.config2(n_actors=16, max_messages=300)
+    la, lm, ls = _valid_log(wl.actor)
+    args = (wl.actor, wl.sender, wl.sender_seq)
+    assert actors.check_mailbox_log(*args, la, lm, ls, strict=True) == []
+    # duplicate handling
+    lm2 = lm.copy(); lm2[5] = lm2[6]
+    assert actors.check_mailbox_log(*args, la, lm2, ls)
+    # wrong actor
+    la2 = la.copy(); la2[3] = (la2[3] + 1) % 16
+    assert actors.check_mailbox_log(*args, la2, lm, ls)
+    # swap two messages of the same (sender, actor) pair
+    key = {}
+    for r, m in enumerate(lm.tolist()):
+        k = (int(wl.sender[m]), int(la[r]))
+        if k in key:
+            ls2 = ls.copy(); ls2[key[k]], ls2[r] = ls2[r], ls2[key[k]]
+            assert any("FIFO" in e for e in actors.check_mailbox_log(*args, la, lm, ls2))
+            break
+        key[k] = r
+    # missing row
+    assert actors.check_mailbox_log(*args, la[:-1], lm[:-1], ls[:-1])
+
+
+def test_rings_closed_form():
+    L, T = 128, 1000
+    rings = actors.simulate_rings(3, L, T)
+    for r in rings:
+        tr = r["trace"]
+        assert len(tr) == T + L                     # 1000 nonzero hops + one lap of 0
+        for k in range(T + 1):
+            assert tr[k] == ((k + 1) % L, T - k)
+        assert [v for _, v in tr].count(0) == L
+        assert r["requests"] == W.ring_rounds(L, T) == 8
+        # the master's nonzero receipts are the deliveries L, 2L, ..., 7L
+        assert r["request_after"] == [0] + [k * L for k in range(1, 8)]
+
+
+def test_rings_small_by_hand():
+    # ring of 3, token 2: deliveries a1:2, a2:1, a0:0, a1:0, a2:0
+    r = actors.simulate_rings(1, 3, 2)[0]
+    assert r["trace"] == [(1, 2), (2, 1), (0, 0), (1, 0), (2, 0)]
+    assert r["requests"] == 1
