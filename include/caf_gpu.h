@@ -1,0 +1,280 @@
+/*
+ * caf_gpu.h -- GPU compute actors on one GB300 (sm_103a).
+ *
+ * Actors live in device memory.  Each has a bounded lock-free mailbox in
+ * HBM; a persistent kernel drains the mailboxes, runs the message's
+ * data-parallel payload (64-bit trial-division factorization, or a dense
+ * matrix product on the tcgen05 tensor cores), and writes the reply to the
+ * request that asked for it.  The calls follow the actor model of
+ * "Revisiting Actor Programming in C++" (Charousset, Hiesgen, Schmidt):
+ *
+ *   caf_gpu_spawn    -- spawn an actor from a compiled-in GPU kernel
+ *                       (Sec. 3.6, spawn_cl: an actor facade over a kernel);
+ *   caf_gpu_send     -- asynchronous message, no reply (Sec. 4);
+ *   caf_gpu_request  -- message with a unique id whose reply is routed back
+ *                       to that id only (Sec. 4.3, sync_send);
+ *   caf_gpu_await    -- wait for that reply, with an optional timeout
+ *                       (Sec. 4.3, ".then" with timeout).
+ *
+ * All entry points are C, take plain pointers and sizes, and return 0 or a
+ * negative CAF_GPU_E* code (caf_gpu_strerror names it).  Nothing here takes
+ * or returns a PyTorch type.  Host pointers are ordinary process memory;
+ * "device pointer" means memory of the runtime's GPU (cudaMalloc, or a
+ * PyTorch CUDA tensor's data pointer).
+ *
+ * Threading: any host thread may call send/request/await concurrently on
+ * one runtime.  Order is kept per (sender, receiver) pair: messages that
+ * one sender id sends to one actor are handled in the order sent.
+ */
+#ifndef CAF_GPU_H
+#define CAF_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define CAF_GPU_OK          0
+#define CAF_GPU_EINVAL     (-1)  /* bad argument, unknown actor, kind mismatch, n out of range */
+#define CAF_GPU_ENOMEM     (-2)  /* device memory budget or an internal table is exhausted   */
+#define CAF_GPU_EAGAIN     (-3)  /* mailbox / ingress ring / reply table full: back off       */
+#define CAF_GPU_ETIMEDOUT  (-4)  /* await timed out; the handle stays valid                   */
+#define CAF_GPU_EDEAD      (-5)  /* the receiving actor has terminated                         */
+#define CAF_GPU_EWAITLIMIT (-6)  /* a bounded device wait expired; see caf_gpu_error_word      */
+#define CAF_GPU_ESTATE     (-7)  /* unknown or already-consumed handle, or runtime misuse      */
+#define CAF_GPU_ECUDA      (-8)  /* a CUDA call failed (no GPU, launch failure, ...)           */
+
+/* ---- kernel ids = message kinds (an actor accepts exactly one kind) ----- */
+#define CAF_GPU_FACTOR_U64          1u  /* u64 n -> (p, q), p <= q                   */
+#define CAF_GPU_GEMM_BF16           2u  /* C = A*B, BF16 operands, FP32 accumulate   */
+#define CAF_GPU_GEMM_SPLIT_BF16X3   3u  /* C = A*B, split-BF16x3 compensated         */
+#define CAF_GPU_RING_TOKEN          4u  /* token ring member (stateful)              */
+
+/* ---- backends ----------------------------------------------------------- */
+#define CAF_GPU_BACKEND_PERSISTENT          0  /* one persistent kernel drains all mailboxes */
+#define CAF_GPU_BACKEND_PER_MESSAGE_LAUNCH  1  /* one kernel launch per message (comparator)  */
+
+/* ---- reply status ------------------------------------------------------- */
+#define CAF_GPU_REPLY_OK        0  /* factor: n = r0 * r1 with r0 the smallest divisor >= 2 */
+#define CAF_GPU_REPLY_NOFACTOR  1  /* factor: no divisor d >= 2 with d*d <= n; (r0, r1) = (1, n) */
+#define CAF_GPU_REPLY_DEAD      2  /* the receiver had terminated; nothing was computed     */
+#define CAF_GPU_REPLY_REJECTED  3  /* device batch: unknown actor, kind mismatch or n too big */
+
+/* ---- message flags ------------------------------------------------------ */
+#define CAF_GPU_MSG_START  0x1u    /* RING_TOKEN: start the ring at this master   */
+
+/* ---- actor flags -------------------------------------------------------- */
+#define CAF_GPU_ACTOR_MASTER 0x1u  /* RING_TOKEN: ring master (emits factor requests) */
+
+typedef struct caf_gpu_runtime caf_gpu_runtime;   /* opaque */
+typedef uint64_t caf_gpu_actor;                   /* opaque actor id, 0 = invalid */
+typedef uint64_t caf_gpu_handle;                  /* request handle, 0 = invalid  */
+
+/*
+ * Runtime configuration (the scheduler knobs of Sec. 6.1, set_scheduler:
+ * number of workers and maximum messages per actor run).  Zero selects the
+ * default named after each field.
+ */
+typedef struct {
+    uint32_t max_actors;            /* actor table size (default 16384)                       */
+    uint32_t mailbox_capacity;      /* default mailbox slots per actor, power of two (64)     */
+    uint32_t max_inflight_requests; /* host reply slots (default 65536)                       */
+    uint32_t ingress_capacity;      /* host->device ring slots, power of two (65536)          */
+    uint32_t ctas_per_sm;           /* persistent CTAs per SM: the worker count (default 2)   */
+    uint32_t max_msgs_per_claim;    /* messages one claim of an actor may take; 0 = no limit  */
+    uint32_t factor_batch;          /* messages swept together by one work item (default 8)   */
+    uint32_t factor_warps;          /* warps sharing one factor batch (default 1)             */
+    uint64_t max_factor_n;          /* largest accepted n, < 2^62 (default 2^62 - 1)          */
+    uint64_t mem_budget_bytes;      /* serving admission budget (default 8 GiB)               */
+    uint64_t wait_limit_ns;         /* every device spin-wait gives up after this (200 ms)    */
+    uint64_t idle_exit_ns;          /* persistent kernel exits after this idle time (2 ms)    */
+    uint32_t validation_mode;       /* 1: record a handling log (caf_gpu_read_log)            */
+    uint32_t log_capacity;          /* log rows (default 1 << 20)                             */
+    void    *cuda_stream;           /* cudaStream_t for all work; NULL = runtime's own stream */
+} caf_gpu_runtime_cfg;
+
+/* Per-actor configuration for caf_gpu_spawn (may be NULL for defaults). */
+typedef struct {
+    uint32_t mailbox_capacity;      /* power of two; 0 = runtime default                       */
+    uint32_t flags;                 /* CAF_GPU_ACTOR_*                                         */
+    caf_gpu_actor next;             /* RING_TOKEN: successor in the ring                       */
+    caf_gpu_actor worker;           /* RING_TOKEN master: its factorization worker             */
+    int32_t  init_state;            /* RING_TOKEN: initial user state (0)                      */
+    uint32_t factor_count;          /* RING_TOKEN master: entries in factor_n                  */
+    const uint64_t *factor_n;       /* RING_TOKEN master: device array, n sent at round k      */
+    void *factor_replies;           /* RING_TOKEN master: device caf_gpu_dreply[factor_count]  */
+} caf_gpu_actor_cfg;
+
+/* A message.  Copied at the call (call-by-value, Sec. 3.3); GEMM operands
+ * are borrowed: A and B read-only, C written, all device pointers that must
+ * stay valid until the reply has been awaited (or caf_gpu_sync returned). */
+typedef struct {
+    uint32_t kind;                  /* CAF_GPU_* kernel id; must equal the actor's             */
+    uint32_t flags;                 /* CAF_GPU_MSG_*                                           */
+    uint32_t sender;                /* sender id: order is kept per (sender, receiver)         */
+    uint32_t n;                     /* GEMM: matrix size (n x n, row-major, leading dim n)     */
+    uint64_t u64;                   /* FACTOR_U64: the number; RING_TOKEN: the token value     */
+    uint64_t tag;                   /* caller's tag, echoed in the handling log                */
+    const float *A;                 /* GEMM operands (device)                                  */
+    const float *B;
+    float *C;                       /* GEMM result (device)                                    */
+} caf_gpu_msg;
+
+/* A reply. */
+typedef struct {
+    int32_t  status;                /* CAF_GPU_REPLY_*                                         */
+    uint32_t kind;
+    uint64_t r0, r1;                /* FACTOR_U64: (p, q) with p <= q; GEMM: (0, n)            */
+} caf_gpu_reply;
+
+/* Device-resident message for caf_gpu_request_batch_device (32 bytes). */
+typedef struct {
+    uint32_t actor;                 /* actor index: the caf_gpu_actor value minus one          */
+    uint32_t kind;                  /* kernel id | (CAF_GPU_MSG_* << 16)                       */
+    uint32_t sender;
+    uint32_t sender_seq;            /* position in that sender's stream (for the log)          */
+    uint64_t u64;                   /* FACTOR: n; TOKEN: value; GEMM: device address of a      */
+                                    /* caf_gpu_gemm_desc                                        */
+    uint64_t tag;
+} caf_gpu_dmsg;
+
+/* GEMM operand descriptor referenced by a caf_gpu_dmsg (device memory, 32 bytes). */
+typedef struct {
+    const float *A;
+    const float *B;
+    float *C;
+    uint32_t n;
+    uint32_t pad;
+} caf_gpu_gemm_desc;
+
+/* Device-resident reply written by the drain (32 bytes). */
+typedef struct {
+    int32_t  status;                /* CAF_GPU_REPLY_*                                         */
+    uint32_t done;                  /* 1 once written                                          */
+    uint64_t r0, r1;
+    uint64_t tag;
+} caf_gpu_dreply;
+
+/* One row of the validation-mode handling log. */
+typedef struct {
+    uint32_t actor;                 /* handling actor                                           */
+    uint32_t sender;
+    uint32_t sender_seq;
+    uint32_t kind;                  /* kind | flags << 16                                       */
+    uint64_t stamp;                 /* increases with handling order                            */
+    uint64_t tag;
+    uint64_t value;                 /* FACTOR: n; TOKEN: token value                            */
+} caf_gpu_log_row;
+
+/* Counters of the most recent drain. */
+typedef struct {
+    uint64_t launches;              /* kernels the runtime has launched                         */
+    uint64_t messages;              /* messages handled                                         */
+    uint64_t device_sends;          /* messages sent by actors on the device                    */
+    uint64_t claims;                /* actor claims                                             */
+    uint64_t factor_items;          /* factor work items run                                    */
+    uint64_t prime_tests;           /* (prime, n) divisibility tests run                        */
+    uint64_t gemm_tiles;            /* GEMM output tiles computed                               */
+    uint32_t error_word;            /* nonzero: a bounded wait expired (code | site << 8)      */
+    uint32_t pad;
+} caf_gpu_stats;
+
+/* Create a runtime on the current CUDA device.  Builds the prime table used by
+ * FACTOR_U64 actors (odd primes up to floor(sqrt(max_factor_n))).  `cfg` may be
+ * NULL.  Errors: EINVAL (bad cfg), ENOMEM, ECUDA. */
+int caf_gpu_runtime_create(const caf_gpu_runtime_cfg *cfg, caf_gpu_runtime **out);
+
+/* Drain outstanding work, stop the kernel and free everything.  Unawaited
+ * handles become invalid. */
+int caf_gpu_runtime_destroy(caf_gpu_runtime *rt);
+
+/* Spawn an actor that runs compiled-in kernel `kernel_id` (Sec. 3.6 spawn_cl:
+ * the kernel is fixed at spawn, the message carries the arguments).  No kernel
+ * launch.  Errors: EINVAL (unknown kernel id, bad cfg), ENOMEM (actor table or
+ * mailbox pool full). */
+int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_cfg *cfg,
+                  caf_gpu_actor *out);
+
+/* Asynchronous send (no reply).  EINVAL if msg->kind differs from the actor's
+ * kernel id (the runtime form of the paper's compile-time interface check,
+ * Sec. 4.3); EDEAD if the actor has terminated; EAGAIN if the ingress ring is full. */
+int caf_gpu_send(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *msg);
+
+/* Request: like send, but assigns a unique request id and reserves a reply
+ * slot; the reply goes to that id only (Sec. 4.3).  EAGAIN if no reply slot is free. */
+int caf_gpu_request(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *msg,
+                    caf_gpu_handle *out);
+
+/* Wait until the reply of `h` arrives, or `timeout_ns` passes (0 = wait
+ * forever).  On success copies it to *out and frees the handle.  ETIMEDOUT
+ * leaves the handle valid; ESTATE for an unknown or consumed handle;
+ * EWAITLIMIT if the device gave up a bounded wait. */
+int caf_gpu_await(caf_gpu_runtime *rt, caf_gpu_handle h, uint64_t timeout_ns,
+                  caf_gpu_reply *out);
+
+/* Batched host forms: `count` requests / awaits in one call (same semantics as
+ * the single calls, in array order; sender order is array order). */
+int caf_gpu_request_batch(caf_gpu_runtime *rt, const caf_gpu_actor *to, const caf_gpu_msg *msgs,
+                          uint32_t count, caf_gpu_handle *out);
+int caf_gpu_await_batch(caf_gpu_runtime *rt, const caf_gpu_handle *h, uint32_t count,
+                        uint64_t timeout_ns, caf_gpu_reply *out);
+
+/* Device-resident batch: `count` messages at device address `d_msgs`; the
+ * reply of message i is written to d_replies[i] (device).  Enqueued on the
+ * runtime stream, in stream order; it returns at once and the replies are
+ * complete when the stream reaches this point (caf_gpu_stream_sync).  Order per
+ * (sender, actor) is array order.  The kinds are checked on the device: a
+ * message whose kind does not match its actor, or whose actor is unknown or
+ * terminated, is not handled and gets reply status CAF_GPU_REPLY_DEAD. */
+int caf_gpu_request_batch_device(caf_gpu_runtime *rt, const caf_gpu_dmsg *d_msgs, uint32_t count,
+                                 caf_gpu_dreply *d_replies);
+
+/* Process everything sent so far and wait for it (both backends). */
+int caf_gpu_sync(caf_gpu_runtime *rt);
+
+/* Wait for the runtime stream. */
+int caf_gpu_stream_sync(caf_gpu_runtime *rt);
+
+/* Select the backend for subsequent messages (only while nothing is in flight). */
+int caf_gpu_set_backend(caf_gpu_runtime *rt, int backend);
+
+/* Reset every RING_TOKEN actor to its spawn state (lifecycle and user state),
+ * stream-ordered, so a ring workload can be replayed or captured in a CUDA graph. */
+int caf_gpu_reset_actors(caf_gpu_runtime *rt);
+
+/* Lifecycle (0 waiting, 1 ready, 2 running, 3 done) and user state of an actor. */
+int caf_gpu_actor_state(caf_gpu_runtime *rt, caf_gpu_actor a, uint32_t *lifecycle,
+                        int32_t *user_state);
+
+/* Counters and the device error word since the last call (which resets them). */
+int caf_gpu_stats_read(caf_gpu_runtime *rt, caf_gpu_stats *out);
+
+/* Copy up to `cap` rows of the validation-mode handling log and clear it. */
+int caf_gpu_read_log(caf_gpu_runtime *rt, caf_gpu_log_row *out, uint32_t cap, uint32_t *count);
+
+/* The runtime's CUDA stream (cudaStream_t). */
+void *caf_gpu_stream(caf_gpu_runtime *rt);
+
+/* Number of odd primes in the runtime's prime table and a device pointer to
+ * them (uint32_t, increasing). */
+int caf_gpu_prime_table(caf_gpu_runtime *rt, const uint32_t **d_primes, uint32_t *count);
+
+/* Fault-path test hook: launch a kernel whose bounded wait on a flag that
+ * nothing sets must give up after `limit_ns`.  Returns CAF_GPU_EWAITLIMIT when
+ * the expiry was reported through the error word (the expected result); no
+ * fault, trap or hang is involved.  caf_gpu_clear_error makes the runtime
+ * usable again. */
+int caf_gpu_debug_wait_expiry(caf_gpu_runtime *rt, uint64_t limit_ns);
+
+/* Clear the device error word after a reported bounded-wait expiry. */
+int caf_gpu_clear_error(caf_gpu_runtime *rt);
+
+const char *caf_gpu_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAF_GPU_H */

@@ -1,0 +1,277 @@
+"""Python binding of libcafgpu.so (the C ABI in include/caf_gpu.h).
+
+Argument marshalling only: every step of the actor path -- mailboxes,
+scheduling, payloads, replies -- runs in the library's CUDA kernels.  There
+is no fallback: if the library cannot be loaded, or no CUDA device is
+present, the calls raise.
+
+PyTorch is used by callers for device memory (``tensor.data_ptr()``) and
+streams; this module takes plain integers for device addresses.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+# ---- constants (caf_gpu.h) ------------------------------------------------
+OK, EINVAL, ENOMEM, EAGAIN, ETIMEDOUT, EDEAD, EWAITLIMIT, ESTATE, ECUDA = 0, -1, -2, -3, -4, -5, -6, -7, -8
+FACTOR_U64, GEMM_BF16, GEMM_SPLIT_BF16X3, RING_TOKEN = 1, 2, 3, 4
+BACKEND_PERSISTENT, BACKEND_PER_MESSAGE_LAUNCH = 0, 1
+REPLY_OK, REPLY_NOFACTOR, REPLY_DEAD, REPLY_REJECTED = 0, 1, 2, 3
+MSG_START = 1
+ACTOR_MASTER = 1
+
+DMSG_DTYPE = np.dtype([("actor", "<u4"), ("kind", "<u4"), ("sender", "<u4"), ("sender_seq", "<u4"),
+                       ("u64", "<u8"), ("tag", "<u8")])
+DREPLY_DTYPE = np.dtype([("status", "<i4"), ("done", "<u4"), ("r0", "<u8"), ("r1", "<u8"), ("tag", "<u8")])
+GEMM_DESC_DTYPE = np.dtype([("A", "<u8"), ("B", "<u8"), ("C", "<u8"), ("n", "<u4"), ("pad", "<u4")])
+LOG_DTYPE = np.dtype([("actor", "<u4"), ("sender", "<u4"), ("sender_seq", "<u4"), ("kind", "<u4"),
+                      ("stamp", "<u8"), ("tag", "<u8"), ("value", "<u8")])
+
+
+class CafGpuError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+class RuntimeCfg(ctypes.Structure):
+    _fields_ = [("max_actors", ctypes.c_uint32), ("mailbox_capacity", ctypes.c_uint32),
+                ("max_inflight_requests", ctypes.c_uint32), ("ingress_capacity", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("max_msgs_per_claim", ctypes.c_uint32),
+                ("factor_batch", ctypes.c_uint32), ("factor_warps", ctypes.c_uint32),
+                ("max_factor_n", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_uint64),
+                ("wait_limit_ns", ctypes.c_uint64), ("idle_exit_ns", ctypes.c_uint64),
+                ("validation_mode", ctypes.c_uint32), ("log_capacity", ctypes.c_uint32),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class ActorCfg(ctypes.Structure):
+    _fields_ = [("mailbox_capacity", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("next", ctypes.c_uint64), ("worker", ctypes.c_uint64), ("init_state", ctypes.c_int32),
+                ("factor_count", ctypes.c_uint32), ("factor_n", ctypes.c_void_p),
+                ("factor_replies", ctypes.c_void_p)]
+
+
+class Msg(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("sender", ctypes.c_uint32),
+                ("n", ctypes.c_uint32), ("u64", ctypes.c_uint64), ("tag", ctypes.c_uint64),
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p)]
+
+
+class Reply(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_uint32), ("r0", ctypes.c_uint64),
+                ("r1", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("messages", ctypes.c_uint64),
+                ("device_sends", ctypes.c_uint64), ("claims", ctypes.c_uint64),
+                ("factor_items", ctypes.c_uint64), ("prime_tests", ctypes.c_uint64),
+                ("gemm_tiles", ctypes.c_uint64), ("error_word", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+
+# Every symbol include/caf_gpu.h declares (checked by the CPU tests).
+EXPORTS = [
+    "caf_gpu_runtime_create", "caf_gpu_runtime_destroy", "caf_gpu_spawn", "caf_gpu_send",
+    "caf_gpu_request", "caf_gpu_await", "caf_gpu_request_batch", "caf_gpu_await_batch",
+    "caf_gpu_request_batch_device", "caf_gpu_sync", "caf_gpu_stream_sync", "caf_gpu_set_backend",
+    "caf_gpu_reset_actors", "caf_gpu_actor_state", "caf_gpu_stats_read", "caf_gpu_read_log",
+    "caf_gpu_stream", "caf_gpu_prime_table", "caf_gpu_debug_wait_expiry", "caf_gpu_clear_error",
+    "caf_gpu_strerror",
+]
+
+_lib = None
+
+
+def load(build: bool = True):
+    """Load libcafgpu.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise OSError(f"libcafgpu.so not built ({_build.LIB})")
+    L = ctypes.CDLL(_build.LIB)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
+    P = ctypes.POINTER
+    sig = {
+        "caf_gpu_runtime_create": [P(RuntimeCfg), P(vp)],
+        "caf_gpu_runtime_destroy": [vp],
+        "caf_gpu_spawn": [vp, u32, P(ActorCfg), P(u64)],
+        "caf_gpu_send": [vp, u64, P(Msg)],
+        "caf_gpu_request": [vp, u64, P(Msg), P(u64)],
+        "caf_gpu_await": [vp, u64, u64, P(Reply)],
+        "caf_gpu_request_batch": [vp, vp, vp, u32, vp],
+        "caf_gpu_await_batch": [vp, vp, u32, u64, vp],
+        "caf_gpu_request_batch_device": [vp, vp, u32, vp],
+        "caf_gpu_sync": [vp],
+        "caf_gpu_stream_sync": [vp],
+        "caf_gpu_set_backend": [vp, ctypes.c_int],
+        "caf_gpu_reset_actors": [vp],
+        "caf_gpu_actor_state": [vp, u64, P(u32), P(i32)],
+        "caf_gpu_stats_read": [vp, P(Stats)],
+        "caf_gpu_read_log": [vp, vp, u32, P(u32)],
+        "caf_gpu_prime_table": [vp, P(vp), P(u32)],
+        "caf_gpu_debug_wait_expiry": [vp, u64],
+        "caf_gpu_clear_error": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.caf_gpu_stream.argtypes = [vp]
+    L.caf_gpu_stream.restype = vp
+    L.caf_gpu_strerror.argtypes = [ctypes.c_int]
+    L.caf_gpu_strerror.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return load(build=False).caf_gpu_strerror(code).decode()
+    except OSError:
+        return f"error {code}"
+
+
+def _check(code: int, what: str) -> int:
+    if code != 0:
+        raise CafGpuError(code, what)
+    return code
+
+
+class Runtime:
+    """One caf_gpu runtime (actor table, mailboxes, prime table) on the current CUDA device."""
+
+    def __init__(self, **cfg):
+        self.L = load()
+        c = RuntimeCfg()
+        for k, v in cfg.items():
+            if not hasattr(c, k):
+                raise TypeError(f"unknown runtime cfg field {k}")
+            setattr(c, k, v)
+        h = ctypes.c_void_p()
+        _check(self.L.caf_gpu_runtime_create(ctypes.byref(c), ctypes.byref(h)), "caf_gpu_runtime_create")
+        self.h = h
+        self._keep = []
+
+    def close(self):
+        if self.h:
+            rc = self.L.caf_gpu_runtime_destroy(self.h)
+            self.h = None
+            _check(rc, "caf_gpu_runtime_destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- actors -------------------------------------------------------------
+    def spawn(self, kernel_id: int, mailbox_capacity: int = 0, flags: int = 0, next: int = 0,
+              worker: int = 0, init_state: int = 0, factor_n: int = 0, factor_count: int = 0,
+              factor_replies: int = 0) -> int:
+        c = ActorCfg(mailbox_capacity, flags, next, worker, init_state, factor_count, factor_n or None,
+                     factor_replies or None)
+        out = ctypes.c_uint64()
+        _check(self.L.caf_gpu_spawn(self.h, kernel_id, ctypes.byref(c), ctypes.byref(out)), "caf_gpu_spawn")
+        return out.value
+
+    def actor_state(self, actor: int):
+        lc = ctypes.c_uint32()
+        us = ctypes.c_int32()
+        _check(self.L.caf_gpu_actor_state(self.h, actor, ctypes.byref(lc), ctypes.byref(us)), "caf_gpu_actor_state")
+        return lc.value, us.value
+
+    # -- messages -----------------------------------------------------------
+    @staticmethod
+    def msg(kind: int, u64: int = 0, sender: int = 0, flags: int = 0, tag: int = 0, n: int = 0,
+            A: int = 0, B: int = 0, C: int = 0) -> Msg:
+        return Msg(kind, flags, sender, n, u64, tag, A or None, B or None, C or None)
+
+    def send(self, actor: int, m: Msg) -> None:
+        _check(self.L.caf_gpu_send(self.h, actor, ctypes.byref(m)), "caf_gpu_send")
+
+    def try_send(self, actor: int, m: Msg) -> int:
+        return self.L.caf_gpu_send(self.h, actor, ctypes.byref(m))
+
+    def request(self, actor: int, m: Msg) -> int:
+        out = ctypes.c_uint64()
+        _check(self.L.caf_gpu_request(self.h, actor, ctypes.byref(m), ctypes.byref(out)), "caf_gpu_request")
+        return out.value
+
+    def await_(self, handle: int, timeout_ns: int = 0):
+        r = Reply()
+        _check(self.L.caf_gpu_await(self.h, handle, timeout_ns, ctypes.byref(r)), "caf_gpu_await")
+        return r.status, r.r0, r.r1
+
+    def try_await(self, handle: int, timeout_ns: int = 0):
+        r = Reply()
+        rc = self.L.caf_gpu_await(self.h, handle, timeout_ns, ctypes.byref(r))
+        return rc, (r.status, r.r0, r.r1)
+
+    def request_batch(self, actors: np.ndarray, msgs) -> np.ndarray:
+        """actors: uint64 array of actor ids; msgs: ctypes array of Msg."""
+        actors = np.ascontiguousarray(actors, dtype=np.uint64)
+        n = actors.size
+        out = np.zeros(n, dtype=np.uint64)
+        _check(self.L.caf_gpu_request_batch(self.h, actors.ctypes.data, ctypes.addressof(msgs), n,
+                                            out.ctypes.data), "caf_gpu_request_batch")
+        return out
+
+    def await_batch(self, handles: np.ndarray, timeout_ns: int = 0):
+        handles = np.ascontiguousarray(handles, dtype=np.uint64)
+        out = (Reply * handles.size)()
+        _check(self.L.caf_gpu_await_batch(self.h, handles.ctypes.data, handles.size, timeout_ns,
+                                          ctypes.addressof(out)), "caf_gpu_await_batch")
+        a = np.frombuffer(out, dtype=np.dtype([("status", "<i4"), ("kind", "<u4"), ("r0", "<u8"), ("r1", "<u8")]))
+        return a.copy()
+
+    def request_batch_device(self, d_msgs: int, count: int, d_replies: int) -> None:
+        _check(self.L.caf_gpu_request_batch_device(self.h, d_msgs, count, d_replies),
+               "caf_gpu_request_batch_device")
+
+    # -- control --------------------------------------------------------------
+    def sync(self):
+        _check(self.L.caf_gpu_sync(self.h), "caf_gpu_sync")
+
+    def stream_sync(self):
+        _check(self.L.caf_gpu_stream_sync(self.h), "caf_gpu_stream_sync")
+
+    def set_backend(self, backend: int):
+        _check(self.L.caf_gpu_set_backend(self.h, backend), "caf_gpu_set_backend")
+
+    def reset_actors(self):
+        _check(self.L.caf_gpu_reset_actors(self.h), "caf_gpu_reset_actors")
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self.L.caf_gpu_stats_read(self.h, ctypes.byref(s)), "caf_gpu_stats_read")
+        return {k: getattr(s, k) for k, _ in Stats._fields_ if k != "pad"}
+
+    def read_log(self, cap: int = 1 << 22) -> np.ndarray:
+        out = np.zeros(cap, dtype=LOG_DTYPE)
+        cnt = ctypes.c_uint32()
+        _check(self.L.caf_gpu_read_log(self.h, out.ctypes.data, cap, ctypes.byref(cnt)), "caf_gpu_read_log")
+        return out[:cnt.value].copy()
+
+    def stream(self) -> int:
+        return self.L.caf_gpu_stream(self.h) or 0
+
+    def prime_table(self):
+        p = ctypes.c_void_p()
+        n = ctypes.c_uint32()
+        _check(self.L.caf_gpu_prime_table(self.h, ctypes.byref(p), ctypes.byref(n)), "caf_gpu_prime_table")
+        return p.value or 0, n.value
+
+    def debug_wait_expiry(self, limit_ns: int) -> int:
+        return self.L.caf_gpu_debug_wait_expiry(self.h, limit_ns)
+
+    def clear_error(self):
+        _check(self.L.caf_gpu_clear_error(self.h), "caf_gpu_clear_error")

@@ -1,0 +1,993 @@
+// The persistent drain kernel and the other device entry points of the
+// runtime (per-message launches, prime-table sieve, actor reset).
+//
+// Actor model mapping (Sec. 3.2 mailbox, Sec. 6 scheduler):
+//
+//  * Mailbox: each actor owns a power-of-two ring of 64-byte slots in HBM.
+//    Enqueue takes a ticket with one atomic add on the actor's tail, writes
+//    the slot and publishes it with a release store of seq = ticket + 1; a
+//    warp enqueueing several messages for one actor takes one ticket block,
+//    lanes in send order.  Only the current claim holder dequeues, so the
+//    head needs no atomics (the single-reader property of Sec. 3.2).
+//  * Scheduler: an actor that receives a message while WAITING becomes READY
+//    and its id is pushed to a global ready queue (the paper's
+//    central/internal enqueue).  A worker warp pops it, marks it RUNNING,
+//    dequeues up to the per-claim limit (the max_msgs knob of Sec. 6.1),
+//    and either re-queues it (resume_job_later) or parks it as WAITING.
+//  * Payloads: stateful ring actors are run by the claiming warp, one message
+//    at a time.  Factorization actors are pure: the claim moves up to K
+//    messages into a batch record and pushes W work items; any warp may run
+//    an item, and the last one to finish writes the replies in mailbox order.
+//
+// Every wait is bounded (WaitClock); when a limit expires the kernel records
+// an error code, sets the exit flag and all warps return.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "factor.cuh"
+#include "layout.h"
+
+namespace cafgpu {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+
+struct MsgData {
+    uint64_t payload;
+    uint64_t reply_addr;
+    uint64_t tag;
+    uint32_t sender, sender_seq, kind, reply_token;
+};
+
+__device__ __forceinline__ bool exit_requested(const DevCtl *ctl) {
+    return *((volatile const uint32_t *)&ctl->exit_flag) != 0 ||
+           *((volatile const uint32_t *)&ctl->error_word) != 0;
+}
+
+__device__ __forceinline__ void fail(const DrainParams &P, uint32_t code, uint32_t site) {
+    raise_error(P.ctl, code, site);
+    if (P.hctl) st_release_sys(&P.hctl->error_word, *((volatile uint32_t *)&P.ctl->error_word));
+    atomicExch(reinterpret_cast<unsigned int *>(&P.ctl->exit_flag), 1u);
+}
+
+__device__ __forceinline__ void heartbeat(const DrainParams &P) {
+    *((volatile uint64_t *)&P.ctl->heartbeat) = globaltimer();
+}
+
+// Warp-collective enqueue: every lane with `valid` holds one message for
+// actor `a`; lanes are in send order.  Returns false (all lanes) on a wait
+// that expired.
+__device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const MsgData &m) {
+    const uint32_t lane = lane_id();
+    const uint32_t vmask = __ballot_sync(FULL, valid);
+    if (!vmask) return true;
+    if (lane == 0) add_u64(&P.ctl->ingested, __popc(vmask));
+    __syncwarp();
+    const uint32_t key = valid ? a : 0xFFFFFFFFu;
+    uint32_t peers = __match_any_sync(FULL, key) & vmask;
+    const int leader = valid ? __ffs(peers) - 1 : (int)lane;
+    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    uint64_t t0 = 0;
+    ActorDesc *A = valid ? &P.actors[a] : nullptr;
+    if (valid && (int)lane == leader) t0 = add_u64(&A->tail, __popc(peers));
+    t0 = __shfl_sync(FULL, t0, leader);
+    bool ok = true;
+    if (valid) {
+        const uint64_t t = t0 + rank;
+        const uint32_t mask = A->cap_mask;
+        if (t - *((volatile uint64_t *)&A->head) > mask) {
+            WaitClock w(P.wait_limit_ns);
+            while (t - *((volatile uint64_t *)&A->head) > mask) {
+                if (!w.again()) { ok = false; break; }
+            }
+        }
+        if (ok) {
+            Slot *s = &P.slots[A->slot_base + (t & mask)];
+            s->payload = m.payload;
+            s->reply_addr = m.reply_addr;
+            s->tag = m.tag;
+            s->sender = m.sender;
+            s->sender_seq = m.sender_seq;
+            s->kind = m.kind;
+            s->reply_token = m.reply_token;
+            st_release_gpu(&s->seq, t + 1);
+        }
+    }
+    if (!__all_sync(FULL, ok)) {
+        if (lane == 0) fail(P, kErrWaitSpace, 1);
+        return false;
+    }
+    // wake the receiver after every peer has published (fence: Dekker pattern
+    // with the claim holder's park in release_actor)
+    asm volatile("fence.sc.gpu;" ::: "memory");
+    bool qok = true;
+    if (valid && (int)lane == leader) {
+        if (cas_u32(&A->state, kWaiting, kReady) == kWaiting)
+            qok = q_push(&P.ctl->readyq, P.readyq, a, P.wait_limit_ns);
+    }
+    if (!__all_sync(FULL, qok)) {
+        if (lane == 0) fail(P, kErrWaitQueue, 2);
+        return false;
+    }
+    return true;
+}
+
+// Park or re-queue an actor after its claim (warp-collective; lane 0 acts).
+__device__ void release_actor(const DrainParams &P, uint32_t a, uint64_t new_head) {
+    if (lane_id() == 0) {
+        ActorDesc *A = &P.actors[a];
+        *((volatile uint64_t *)&A->head) = new_head;
+        if (*((volatile uint32_t *)&A->state) != kDone) {
+            atomicExch(reinterpret_cast<unsigned int *>(&A->state), kWaiting);
+            asm volatile("fence.sc.gpu;" ::: "memory");
+            if (ld_relaxed_gpu(&A->tail) != new_head &&
+                cas_u32(&A->state, kWaiting, kReady) == kWaiting) {
+                if (!q_push(&P.ctl->readyq, P.readyq, a, P.wait_limit_ns)) fail(P, kErrWaitQueue, 3);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Dequeue up to `take` messages (<= 32) from the claimed actor: lane i reads
+// slot head + i.  Returns false if a slot was never published.
+__device__ bool warp_dequeue(const DrainParams &P, uint32_t a, uint64_t head, uint32_t take,
+                             MsgData &m) {
+    const uint32_t lane = lane_id();
+    ActorDesc *A = &P.actors[a];
+    bool ok = true;
+    if (lane < take) {
+        const uint64_t t = head + lane;
+        Slot *s = &P.slots[A->slot_base + (t & A->cap_mask)];
+        if (ld_acquire_gpu(&s->seq) != t + 1) {
+            WaitClock w(P.wait_limit_ns);
+            while (ld_acquire_gpu(&s->seq) != t + 1) {
+                if (!w.again()) { ok = false; break; }
+            }
+        }
+        if (ok) {
+            m.payload = s->payload;
+            m.reply_addr = s->reply_addr;
+            m.tag = s->tag;
+            m.sender = s->sender;
+            m.sender_seq = s->sender_seq;
+            m.kind = s->kind;
+            m.reply_token = s->reply_token;
+        }
+    }
+    if (!__all_sync(FULL, ok)) {
+        if (lane == 0) fail(P, kErrWaitSlot, 4);
+        return false;
+    }
+    if (P.validation) {
+        uint64_t base = 0;
+        if (lane == 0) base = add_u64(&P.ctl->log_count, take);
+        base = __shfl_sync(FULL, base, 0);
+        if (lane < take && base + lane < P.log_capacity) {
+            LogRow *r = &P.log[base + lane];
+            r->actor = a;
+            r->sender = m.sender;
+            r->sender_seq = m.sender_seq;
+            r->kind = m.kind;
+            r->stamp = base + lane;
+            r->tag = m.tag;
+            r->value = m.payload;
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Factorization batches
+// ---------------------------------------------------------------------------
+__device__ void finalize_batch(const DrainParams &P, uint32_t b) {
+    const uint32_t lane = lane_id();
+    FactorBatch *B = &P.batches[b];
+    __threadfence();
+    const uint32_t cnt = B->count;
+    if (lane < cnt) {
+        const uint64_t n = B->n[lane];
+        const uint32_t found = *((volatile uint32_t *)&B->found[lane]);
+        int32_t st;
+        uint64_t r0, r1;
+        factor_result(n, (B->even_mask >> lane) & 1u, found, B->pbound[lane], P.primes, &st, &r0, &r1);
+        write_reply(B->reply_addr[lane], st, r0, r1, B->tag[lane], B->reply_token[lane]);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();
+        add_u64(&P.ctl->messages, cnt);
+        add_u64(&P.ctl->completed, cnt);
+        if (!q_push(&P.ctl->freeq, P.freeq, b, P.wait_limit_ns)) fail(P, kErrWaitQueue, 5);
+    }
+    __syncwarp();
+}
+
+// Run work item (b, w): ranges w, w+W, w+2W, ... of kRangePrimes primes each.
+__device__ void factor_item(const DrainParams &P, uint32_t b, uint32_t w) {
+    const uint32_t lane = lane_id();
+    FactorBatch *B = &P.batches[b];
+    const uint32_t cnt = B->count;
+    SweepRegs s;
+    s.k = 0;
+#pragma unroll
+    for (int j = 0; j < (int)kFactorKMax; ++j) {
+        s.n[j] = 0; s.nl[j] = 0; s.pb[j] = 0; s.id[j] = 0;
+    }
+#pragma unroll
+    for (int j = 0; j < (int)kFactorKMax; ++j) {
+        if (j < (int)cnt) {
+            const uint32_t pb = B->pbound[j];
+            const bool even = (B->even_mask >> j) & 1u;
+            if (pb > 0 && !even) {
+                const uint64_t n = B->n[j];
+                // place at slot k (k <= j, static unrolled select)
+#pragma unroll
+                for (int i = 0; i <= j; ++i) {
+                    if (i == s.k) {
+                        s.n[i] = n;
+                        s.nl[i] = 0u - (uint32_t)n;
+                        s.pb[i] = pb;
+                        s.id[i] = (uint32_t)j;
+                    }
+                }
+                ++s.k;
+            }
+        }
+    }
+    const uint32_t W = P.factor_w;
+    uint64_t tests = 0;
+    for (uint32_t r = w; s.k > 0; r += W) {
+        const uint32_t start = r * kRangePrimes;
+        // drop messages decided below this range or whose bound ends before it
+        for (int j = s.k - 1; j >= 0; --j) {
+            uint32_t pbj = 0, idj = 0;
+#pragma unroll
+            for (int i = 0; i < (int)kFactorKMax; ++i)
+                if (i == j) { pbj = s.pb[i]; idj = s.id[i]; }
+            uint32_t f = 0;
+            if (lane == 0) f = *((volatile uint32_t *)&B->found[idj]);
+            f = __shfl_sync(FULL, f, 0);
+            if (f < start || pbj <= start) sweep_remove(s, j);
+        }
+        if (s.k == 0) break;
+        uint32_t end = 0;
+#pragma unroll
+        for (int i = 0; i < (int)kFactorKMax; ++i)
+            if (i < s.k) end = max(end, s.pb[i]);
+        end = min(end, start + kRangePrimes);
+        uint32_t next_drop = 0xFFFFFFFFu;
+#pragma unroll
+        for (int i = 0; i < (int)kFactorKMax; ++i)
+            if (i < s.k) next_drop = min(next_drop, s.pb[i]);
+        for (uint32_t c = start; c < end; c += 32) {
+            const uint32_t idx = c + lane;
+            const uint32_t p = __ldg(P.primes + idx);
+            const uint32_t pinv = __ldg(P.pinv + idx);
+            const uint32_t plim = __ldg(P.plim + idx);
+            const uint32_t hits = sweep_chunk(s, p, pinv, plim);
+            tests += (uint64_t)s.k * 32u;
+            if (__any_sync(FULL, hits != 0)) {
+                uint32_t any = __reduce_or_sync(FULL, hits);
+                // remove from the highest slot down so lower positions stay valid
+                for (int j = 31 - __clz(any); any; j = 31 - __clz(any)) {
+                    any &= ~(1u << j);
+                    const uint32_t mine = ((hits >> j) & 1u) ? idx : 0xFFFFFFFFu;
+                    const uint32_t mn = __reduce_min_sync(FULL, mine);
+                    uint32_t idj = 0;
+#pragma unroll
+                    for (int i = 0; i < (int)kFactorKMax; ++i)
+                        if (i == j) idj = s.id[i];
+                    if (lane == 0) atomicMin(reinterpret_cast<unsigned int *>(&B->found[idj]), mn);
+                    sweep_remove(s, j);
+                }
+                if (s.k == 0) break;
+            }
+            if (c + 32 >= next_drop) {
+                for (int j = s.k - 1; j >= 0; --j) {
+                    uint32_t pbj = 0;
+#pragma unroll
+                    for (int i = 0; i < (int)kFactorKMax; ++i)
+                        if (i == j) pbj = s.pb[i];
+                    if (pbj <= c + 32) sweep_remove(s, j);
+                }
+                if (s.k == 0) break;
+                next_drop = 0xFFFFFFFFu;
+                end = 0;
+#pragma unroll
+                for (int i = 0; i < (int)kFactorKMax; ++i)
+                    if (i < s.k) { next_drop = min(next_drop, s.pb[i]); end = max(end, s.pb[i]); }
+                end = min(end, start + kRangePrimes);
+            }
+        }
+        if ((r & 15u) == 0 && lane == 0) heartbeat(P);
+        if (exit_requested(P.ctl)) break;
+    }
+    if (lane == 0) {
+        add_u64(&P.ctl->prime_tests, tests);
+        add_u64(&P.ctl->factor_items, 1);
+    }
+    uint32_t left = 0;
+    if (lane == 0) {
+        __threadfence();
+        left = atomicSub(reinterpret_cast<unsigned int *>(&B->items_left), 1u);
+    }
+    left = __shfl_sync(FULL, left, 0);
+    if (left == 1) finalize_batch(P, b);
+}
+
+// Claim a factor actor: move up to K messages into batch b and schedule it.
+__device__ void claim_factor(const DrainParams &P, uint32_t a, uint32_t b) {
+    const uint32_t lane = lane_id();
+    ActorDesc *A = &P.actors[a];
+    if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
+    __syncwarp();
+    const uint64_t head = *((volatile uint64_t *)&A->head);
+    const uint64_t tail = ld_acquire_gpu(&A->tail);
+    uint32_t limit = P.factor_k;
+    if (P.max_claim && P.max_claim < limit) limit = P.max_claim;
+    const uint64_t avail = tail - head;
+    const uint32_t take = avail < limit ? (uint32_t)avail : limit;
+    MsgData m{};
+    if (take == 0 || !warp_dequeue(P, a, head, take, m)) {
+        release_actor(P, a, head);
+        if (lane == 0) q_push(&P.ctl->freeq, P.freeq, b, P.wait_limit_ns);
+        return;
+    }
+    release_actor(P, a, head + take);
+    FactorBatch *B = &P.batches[b];
+    uint32_t pb = 0;
+    bool even = false;
+    if (lane < take) {
+        const uint64_t n = m.payload;
+        even = (n >= 4) && !(n & 1u);
+        pb = even ? 0 : factor_bound(P.primes, P.nprimes, n);
+        B->n[lane] = n;
+        B->pbound[lane] = pb;
+        B->found[lane] = kNoFactor;
+        B->reply_addr[lane] = m.reply_addr;
+        B->reply_token[lane] = m.reply_token;
+        B->tag[lane] = m.tag;
+    }
+    const uint32_t even_mask = __ballot_sync(FULL, lane < take && even);
+    const uint32_t maxb = __reduce_max_sync(FULL, lane < take ? pb : 0u);
+    if (lane == 0) {
+        B->count = take;
+        B->even_mask = even_mask;
+        B->maxbound = maxb;
+        B->items_left = P.factor_w;
+        add_u64(&P.ctl->claims, 1);
+    }
+    __syncwarp();
+    if (maxb == 0) {
+        finalize_batch(P, b);
+        return;
+    }
+    if (lane == 0) {
+        __threadfence();
+        for (uint32_t w = 0; w < P.factor_w; ++w)
+            if (!q_push(&P.ctl->workq, P.workq, (b << 8) | w, P.wait_limit_ns)) {
+                fail(P, kErrWaitQueue, 6);
+                break;
+            }
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Ring token actors (stateful; the claiming warp runs them one message at a
+// time).  Reading of Sec. 5 "Mixed Operations Under Work Load": the token
+// loses one per hop; an actor receiving 0 terminates and forwards 0 once
+// unless its successor has terminated; the master sends one factorization
+// request to its worker at the start and on each token v > 0 it receives.
+// ---------------------------------------------------------------------------
+__device__ bool ring_emit_factor(const DrainParams &P, uint32_t a) {
+    ActorDesc *A = &P.actors[a];
+    MsgData m{};
+    bool valid = false;
+    uint32_t worker = 0;
+    if (lane_id() == 0 && (A->flags & kActorMaster)) {
+        const uint32_t k = A->round;
+        if (k < A->factor_count) {
+            A->round = k + 1;
+            valid = true;
+            worker = A->worker;
+            m.payload = reinterpret_cast<const uint64_t *>(A->factor_n)[k];
+            m.reply_addr = A->factor_replies + (uint64_t)k * sizeof(Reply);
+            m.reply_token = 1;
+            m.tag = k;
+            m.sender = 0x80000000u | a;
+            m.sender_seq = k;
+            m.kind = kFactor;
+        }
+    }
+    worker = __shfl_sync(FULL, worker, 0);
+    return warp_enqueue(P, valid, worker, m);
+}
+
+__device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v) {
+    ActorDesc *A = &P.actors[a];
+    const uint32_t next = A->next;
+    MsgData m{};
+    m.payload = (uint64_t)(uint32_t)v;
+    m.kind = kToken;
+    m.sender = 0x80000000u | a;
+    m.sender_seq = (uint32_t)v;
+    const bool send = lane_id() == 0;
+    if (lane_id() == 0) add_u64(&P.ctl->device_sends, 1);
+    return warp_enqueue(P, send, next, m);
+}
+
+__device__ void claim_ring(const DrainParams &P, uint32_t a) {
+    const uint32_t lane = lane_id();
+    ActorDesc *A = &P.actors[a];
+    if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
+    __syncwarp();
+    uint64_t head = *((volatile uint64_t *)&A->head);
+    const uint64_t tail = ld_acquire_gpu(&A->tail);
+    uint64_t take = tail - head;
+    if (P.max_claim && take > P.max_claim) take = P.max_claim;
+    if (lane == 0) add_u64(&P.ctl->claims, 1);
+    for (uint64_t i = 0; i < take; ++i) {
+        MsgData m{};
+        if (!warp_dequeue(P, a, head, 1, m)) return;
+        m.payload = __shfl_sync(FULL, m.payload, 0);
+        m.kind = __shfl_sync(FULL, m.kind, 0);
+        m.reply_addr = __shfl_sync(FULL, m.reply_addr, 0);
+        m.reply_token = __shfl_sync(FULL, m.reply_token, 0);
+        m.tag = __shfl_sync(FULL, m.tag, 0);
+        head += 1;
+        const int32_t v = (int32_t)(uint32_t)m.payload;
+        const bool dead = __shfl_sync(FULL, *((volatile uint32_t *)&A->state) == kDone, 0);
+        bool ok = true;
+        if (dead) {
+            if (lane == 0) write_reply(m.reply_addr, 2, 0, 0, m.tag, m.reply_token);
+        } else if ((m.kind >> 16) & kMsgStart) {
+            ok = ring_emit_factor(P, a) && ring_forward(P, a, v);
+        } else if (v > 0) {
+            ok = ring_emit_factor(P, a) && ring_forward(P, a, v - 1);
+        } else {
+            if (lane == 0) *((volatile uint32_t *)&A->state) = kDone;
+            uint32_t succ_state = 0;
+            if (lane == 0) succ_state = *((volatile uint32_t *)&P.actors[A->next].state);
+            succ_state = __shfl_sync(FULL, succ_state, 0);
+            if (succ_state != kDone) ok = ring_forward(P, a, 0);
+        }
+        if (!ok) return;
+        if (!dead && lane == 0) {
+            A->user_state = v;
+            write_reply(m.reply_addr, 0, (uint64_t)(uint32_t)v, 0, m.tag, m.reply_token);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            add_u64(&P.ctl->messages, 1);
+            add_u64(&P.ctl->completed, 1);
+        }
+    }
+    release_actor(P, a, head);
+}
+
+// Answer a message that cannot be handled (unknown actor, kind mismatch,
+// terminated receiver, n out of range).
+__device__ __forceinline__ void reject(uint64_t reply_addr, uint32_t token, uint64_t tag, int32_t status) {
+    write_reply(reply_addr, status, 0, 0, tag, token);
+}
+
+__device__ __forceinline__ bool message_ok(const DrainParams &P, uint32_t a, uint32_t kind, uint64_t payload,
+                                           int32_t *why) {
+    if (a >= P.n_actors) { *why = 3; return false; }
+    const ActorDesc *A = &P.actors[a];
+    if ((kind & 0xFFFFu) != A->kind) { *why = 3; return false; }
+    if (*((volatile const uint32_t *)&A->state) == kDone) { *why = 2; return false; }
+    if ((kind & 0xFFFFu) == kFactor && payload > P.max_n) { *why = 3; return false; }
+    return true;
+}
+
+// Device batch routing: router r takes the messages whose actor id is r
+// modulo the router count, scanning the batch in array order, so each
+// actor's messages enter its mailbox in array order.
+__device__ void route_batch(const DrainParams &P, uint32_t r) {
+    const uint32_t lane = lane_id();
+    const caf_dmsg_t *msgs = reinterpret_cast<const caf_dmsg_t *>(P.batch_msgs);
+    for (uint32_t base = 0; base < P.batch_count; base += 32) {
+        const uint32_t i = base + lane;
+        bool mine = false;
+        caf_dmsg_t d{};
+        if (i < P.batch_count) {
+            d = msgs[i];
+            mine = (d.actor % P.n_routers) == r;
+        }
+        if (!__any_sync(FULL, mine)) continue;
+        int32_t why = 0;
+        const bool ok = mine && message_ok(P, d.actor, d.kind, d.u64, &why);
+        Reply *rep = P.batch_replies ? &P.batch_replies[i] : nullptr;
+        if (mine && !ok) reject((uint64_t)rep, 1, d.tag, why);
+        MsgData m{};
+        m.payload = d.u64;
+        m.reply_addr = (uint64_t)rep;
+        m.reply_token = 1;
+        m.tag = d.tag;
+        m.sender = d.sender;
+        m.sender_seq = d.sender_seq;
+        m.kind = d.kind;
+        if (!warp_enqueue(P, ok, d.actor, m)) return;
+        if ((base & 4095u) == 0 && lane == 0) heartbeat(P);
+    }
+}
+
+// Live ingress: take the published prefix of the host ring (in ticket order)
+// and route it.  Returns true if anything was taken.
+__device__ bool poll_host_ring(const DrainParams &P) {
+    const uint32_t lane = lane_id();
+    const uint64_t head = P.ctl->ring_head;
+    IngressEntry *e = &P.ring[(head + lane) & P.ring_mask];
+    const bool pub = ld_acquire_sys(&e->seq) == head + lane + 1;
+    const uint32_t pm = __ballot_sync(FULL, pub);
+    const uint32_t n = (pm == FULL) ? 32u : (uint32_t)(__ffs(~pm) - 1);
+    if (n == 0) return false;
+    const bool take = lane < n;
+    MsgData m{};
+    uint32_t a = 0;
+    if (take) {
+        a = e->actor;
+        m.payload = e->payload;
+        m.reply_addr = e->reply_addr;
+        m.tag = e->tag;
+        m.sender = e->sender;
+        m.sender_seq = e->sender_seq;
+        m.kind = e->kind;
+        m.reply_token = e->reply_token;
+    }
+    int32_t why = 0;
+    const bool ok = take && message_ok(P, a, m.kind, m.payload, &why);
+    if (take && !ok) reject(m.reply_addr, m.reply_token, m.tag, why);
+    if (!warp_enqueue(P, ok, a, m)) return true;
+    if (lane == 0) {
+        P.ctl->ring_head = head + n;
+        st_release_sys(&P.hctl->ring_consumed, head + n);
+    }
+    __syncwarp();
+    return true;
+}
+
+__device__ __forceinline__ bool quiescent(const DrainParams &P) {
+    if (P.batch_count && *((volatile uint32_t *)&P.ctl->routers_done) < P.n_routers) return false;
+    const uint64_t c = ld_acquire_gpu(&P.ctl->completed);
+    const uint64_t i = ld_acquire_gpu(&P.ctl->ingested);
+    return c == i;
+}
+
+__global__ void __launch_bounds__(kThreads) k_drain(DrainParams P) {
+    const uint32_t lane = lane_id();
+    const uint32_t gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+    DevCtl *ctl = P.ctl;
+    const bool agent = P.live && gw == 0;
+    if (P.batch_count && gw < P.n_routers) {
+        route_batch(P, gw);
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            add_u32(&ctl->routers_done, 1);
+        }
+    }
+    bool idle = false;
+    uint64_t idle_start = 0;
+    while (!exit_requested(ctl)) {
+        bool did = false;
+        if (agent) {
+            did = poll_host_ring(P);
+        } else {
+            uint32_t item = 0;
+            bool got = false;
+            if (lane == 0) got = q_try_pop(&ctl->workq, P.workq, &item);
+            got = __shfl_sync(FULL, got, 0);
+            if (got) {
+                item = __shfl_sync(FULL, item, 0);
+                factor_item(P, item >> 8, item & 0xFFu);
+                did = true;
+            } else {
+                uint32_t a = 0;
+                if (lane == 0) got = q_try_pop(&ctl->readyq, P.readyq, &a);
+                got = __shfl_sync(FULL, got, 0);
+                if (got) {
+                    a = __shfl_sync(FULL, a, 0);
+                    const uint32_t kind = P.actors[a].kind;
+                    if (kind == kFactor) {
+                        uint32_t b = 0;
+                        bool gb = false;
+                        if (lane == 0) gb = q_try_pop(&ctl->freeq, P.freeq, &b);
+                        gb = __shfl_sync(FULL, gb, 0);
+                        if (gb) {
+                            claim_factor(P, a, __shfl_sync(FULL, b, 0));
+                            did = true;
+                        } else if (lane == 0) {
+                            // no batch record free: leave the actor READY for later
+                            if (!q_push(&ctl->readyq, P.readyq, a, P.wait_limit_ns)) fail(P, kErrWaitQueue, 7);
+                        }
+                    } else if (kind == kToken) {
+                        claim_ring(P, a);
+                        did = true;
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        if (did) {
+            idle = false;
+            continue;
+        }
+        const uint64_t now = globaltimer();
+        if (!idle) {
+            idle = true;
+            idle_start = now;
+        }
+        if (quiescent(P)) {
+            if (!P.live) {
+                if (lane == 0) atomicExch(reinterpret_cast<unsigned int *>(&ctl->exit_flag), 1u);
+                break;
+            }
+            if (agent) {
+                const bool stop = ld_acquire_sys(&P.hctl->stop) != 0;
+                const uint64_t head = ctl->ring_head;
+                const bool more = ld_acquire_sys(&P.ring[head & P.ring_mask].seq) == head + 1;
+                if (!more && (stop || now - idle_start > P.idle_exit_ns)) {
+                    if (lane == 0) atomicExch(reinterpret_cast<unsigned int *>(&ctl->exit_flag), 1u);
+                    break;
+                }
+            }
+        } else {
+            const uint64_t hb = *((volatile uint64_t *)&ctl->heartbeat);
+            const uint64_t last = hb > idle_start ? hb : idle_start;
+            if (now - last > P.wait_limit_ns) {
+                if (lane == 0) fail(P, kErrStall, 8);
+                break;
+            }
+        }
+        __nanosleep(256);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-message launch (the comparator): one kernel launch factors one n with
+// the whole grid.  Warp g tests chunks g, g + G, ... of 32 primes and
+// records the smallest dividing index with atomicMin in scratch[0]; the last
+// CTA to finish writes the reply and resets the scratch words for the next
+// launch.  scratch = {found, ctas_done} (two uint32 words, zero/kNoFactor at
+// rest).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_factor_one(uint64_t n, const uint32_t *primes,
+                                                          const uint32_t *pinv, const uint32_t *plim,
+                                                          uint32_t nprimes, uint64_t reply_addr,
+                                                          uint32_t reply_token, uint64_t tag,
+                                                          uint32_t *scratch, DevCtl *ctl) {
+    const uint32_t lane = lane_id();
+    const bool even = (n >= 4) && !(n & 1u);
+    const uint32_t bound = even ? 0 : factor_bound(primes, nprimes, n);
+    const uint32_t gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+    const uint32_t nw = gridDim.x * kWarpsPerCta;
+    const uint32_t nl = 0u - (uint32_t)n;
+    uint64_t tests = 0;
+    for (uint32_t c = gw * 32; c < bound; c += nw * 32) {
+        if (*((volatile uint32_t *)&scratch[0]) < c) break;
+        const uint32_t idx = c + lane;
+        const bool hit = idx < bound && mont_divides(n, nl, __ldg(primes + idx), __ldg(pinv + idx), __ldg(plim + idx));
+        tests += 32;
+        const uint32_t mn = __reduce_min_sync(FULL, hit ? idx : 0xFFFFFFFFu);
+        if (mn != 0xFFFFFFFFu) {
+            if (lane == 0) atomicMin(reinterpret_cast<unsigned int *>(&scratch[0]), mn);
+            break;
+        }
+    }
+    if (lane == 0 && tests) add_u64(&ctl->prime_tests, tests);
+    __syncthreads();
+    __shared__ uint32_t last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = (atomicAdd(reinterpret_cast<unsigned int *>(&scratch[1]), 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t found = *((volatile uint32_t *)&scratch[0]);
+        int32_t st;
+        uint64_t r0, r1;
+        factor_result(n, even, found, bound, primes, &st, &r0, &r1);
+        write_reply(reply_addr, st, r0, r1, tag, reply_token);
+        scratch[0] = kNoFactor;
+        scratch[1] = 0;
+        add_u64(&ctl->messages, 1);
+        __threadfence();
+    }
+}
+
+// Per-message launch of one ring-token message: the same handler as the
+// drain, run by one warp; its outgoing messages go to `outbox` (pinned host
+// memory) for the host to launch next.  outbox[0].seq counts entries.
+__global__ void k_token_one(ActorDesc *actors, uint32_t a, uint32_t kind, int32_t v,
+                            uint64_t reply_addr, uint32_t reply_token, IngressEntry *outbox,
+                            DevCtl *ctl) {
+    if (threadIdx.x != 0) return;
+    ActorDesc *A = &actors[a];
+    uint32_t nout = 0;
+    auto emit = [&](uint32_t to, uint32_t k, uint64_t payload, uint64_t raddr, uint32_t tok, uint64_t tag) {
+        IngressEntry *e = &outbox[1 + nout++];
+        e->actor = to;
+        e->kind = k;
+        e->payload = payload;
+        e->reply_addr = raddr;
+        e->reply_token = tok;
+        e->tag = tag;
+        e->sender = 0x80000000u | a;
+    };
+    auto emit_factor = [&]() {
+        if (!(A->flags & kActorMaster)) return;
+        const uint32_t k = A->round;
+        if (k >= A->factor_count) return;
+        A->round = k + 1;
+        emit(A->worker, kFactor, reinterpret_cast<const uint64_t *>(A->factor_n)[k],
+             A->factor_replies + (uint64_t)k * sizeof(Reply), 1, k);
+    };
+    if (A->state == kDone) {
+        write_reply(reply_addr, 2, 0, 0, 0, reply_token);
+    } else {
+        if ((kind >> 16) & kMsgStart) {
+            emit_factor();
+            emit(A->next, kToken, (uint32_t)v, 0, 0, 0);
+        } else if (v > 0) {
+            emit_factor();
+            emit(A->next, kToken, (uint32_t)(v - 1), 0, 0, 0);
+        } else {
+            A->state = kDone;
+            if (actors[A->next].state != kDone) emit(A->next, kToken, 0, 0, 0, 0);
+        }
+        A->user_state = v;
+        write_reply(reply_addr, 0, (uint32_t)v, 0, 0, reply_token);
+    }
+    add_u64(&ctl->messages, 1);
+    __threadfence_system();
+    st_release_sys(&outbox[0].seq, nout);
+}
+
+// Reset ring actors to their spawn state (stream-ordered; graph-capturable).
+__global__ void k_reset_actors(ActorDesc *actors, uint32_t n_actors) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_actors) return;
+    ActorDesc *A = &actors[i];
+    if (A->kind == kToken) {
+        A->state = kWaiting;
+        A->user_state = A->init_state;
+        A->round = 0;
+        A->head = A->tail;
+    }
+}
+
+// Reset the counters a drain launch reads (stream-ordered).
+__global__ void k_reset_ctl(DevCtl *ctl) {
+    ctl->exit_flag = 0;
+    ctl->routers_done = 0;
+    ctl->heartbeat = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Prime table: segmented sieve of Eratosthenes over the odd numbers.  Bit i
+// of the global bitmap stands for 2i + 1 and is set when composite (or 1).
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSegBits = 1u << 18;
+
+__global__ void k_sieve(uint32_t *bits, uint64_t nbits, const uint32_t *small, uint32_t nsmall) {
+    extern __shared__ uint32_t seg[];
+    const uint64_t i0 = (uint64_t)blockIdx.x * kSegBits;
+    const uint32_t words = kSegBits / 32;
+    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) seg[w] = 0;
+    __syncthreads();
+    const uint64_t lo = 2 * i0 + 1;                     // first odd number of the segment
+    const uint64_t hi = 2 * (i0 + kSegBits) - 1;        // last odd number
+    for (uint32_t k = threadIdx.x; k < nsmall; k += blockDim.x) {
+        const uint64_t p = small[k];
+        if (p * p > hi) break;
+        uint64_t m = (lo + p - 1) / p * p;
+        if (!(m & 1)) m += p;
+        if (m < p * p) m = p * p;
+        for (uint64_t x = m; x <= hi; x += 2 * p) {
+            const uint32_t b = (uint32_t)((x - lo) >> 1);
+            atomicOr(&seg[b >> 5], 1u << (b & 31));
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) seg[0] |= 1u;  // 1 is not prime
+    __syncthreads();
+    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) {
+        const uint64_t gbit = i0 + (uint64_t)w * 32;
+        if (gbit < nbits) {
+            uint32_t v = seg[w];
+            if (gbit + 32 > nbits) v |= ~0u << (uint32_t)(nbits - gbit);  // beyond the limit
+            bits[gbit >> 5] = v;
+        }
+    }
+}
+
+// Primes per segment (count of zero bits).
+__global__ void k_sieve_count(const uint32_t *bits, uint64_t nwords, uint32_t *counts) {
+    __shared__ uint32_t tot;
+    if (threadIdx.x == 0) tot = 0;
+    __syncthreads();
+    const uint64_t w0 = (uint64_t)blockIdx.x * (kSegBits / 32);
+    uint32_t c = 0;
+    for (uint32_t w = threadIdx.x; w < kSegBits / 32; w += blockDim.x)
+        if (w0 + w < nwords) c += __popc(~bits[w0 + w]);
+    atomicAdd(&tot, c);
+    __syncthreads();
+    if (threadIdx.x == 0) counts[blockIdx.x] = tot;
+}
+
+// Write the primes of each segment at its offset, with p^-1 mod 2^32 (Newton
+// iteration x <- x(2 - p x), 3 -> 6 -> 12 -> 24 -> 48 correct bits) and
+// floor((2^32 - 1) / p).
+__global__ void k_sieve_emit(const uint32_t *bits, uint64_t nwords, const uint32_t *offsets,
+                             uint32_t *primes, uint32_t *pinv, uint32_t *plim) {
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t running;
+    const uint64_t w0 = (uint64_t)blockIdx.x * (kSegBits / 32);
+    if (threadIdx.x == 0) running = offsets[blockIdx.x];
+    __syncthreads();
+    for (uint32_t base = 0; base < kSegBits / 32; base += blockDim.x) {
+        const uint64_t w = w0 + base + threadIdx.x;
+        uint32_t v = (base + threadIdx.x < kSegBits / 32 && w < nwords) ? ~bits[w] : 0u;
+        const uint32_t c = __popc(v);
+        // block exclusive scan of c
+        uint32_t incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, incl, o);
+            if ((threadIdx.x & 31) >= (uint32_t)o) incl += t;
+        }
+        if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = incl;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const uint32_t nwarps = blockDim.x >> 5;
+            uint32_t x = threadIdx.x < nwarps ? warp_tot[threadIdx.x] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULL, x, o);
+                if (threadIdx.x >= (uint32_t)o) x += t;
+            }
+            warp_tot[threadIdx.x] = x;  // inclusive over warps
+        }
+        __syncthreads();
+        const uint32_t warp_excl = (threadIdx.x >= 32) ? warp_tot[(threadIdx.x >> 5) - 1] : 0;
+        uint32_t pos = running + warp_excl + incl - c;
+        while (v) {
+            const uint32_t b = __ffs(v) - 1;
+            v &= v - 1;
+            const uint32_t p = (uint32_t)(2 * (w * 32 + b) + 1);
+            uint32_t x = p;  // p*p == 1 mod 8 for odd p: 3 correct bits
+            x *= 2u - p * x;
+            x *= 2u - p * x;
+            x *= 2u - p * x;
+            x *= 2u - p * x;
+            primes[pos] = p;
+            pinv[pos] = x;
+            plim[pos] = 0xFFFFFFFFu / p;
+            ++pos;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) running += warp_tot[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+}
+
+// A kernel that waits, bounded, for a flag that nothing sets, and reports
+// the expiry through the error word (exercises the bounded-wait path).
+__global__ void k_debug_wait(const uint32_t *flag, uint64_t limit_ns, DevCtl *ctl, HostCtl *hctl) {
+    if (threadIdx.x != 0) return;
+    WaitClock w(limit_ns);
+    while (ld_acquire_gpu(flag) == 0) {
+        if (!w.again()) {
+            raise_error(ctl, kErrDebugWait, 9);
+            st_release_sys(&hctl->error_word, *((volatile uint32_t *)&ctl->error_word));
+            return;
+        }
+    }
+}
+
+}  // namespace cafgpu
+
+// ---------------------------------------------------------------------------
+// Launch wrappers
+// ---------------------------------------------------------------------------
+#include <vector>
+
+#include "kernels.h"
+
+namespace cafgpu {
+
+cudaError_t launch_drain(const DrainParams &p, unsigned grid, cudaStream_t stream) {
+    k_drain<<<grid, kThreads, 0, stream>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_ctl(DevCtl *ctl, cudaStream_t stream) {
+    k_reset_ctl<<<1, 1, 0, stream>>>(ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_factor_one(uint64_t n, const uint32_t *primes, const uint32_t *pinv,
+                              const uint32_t *plim, uint32_t nprimes, uint64_t reply_addr,
+                              uint32_t reply_token, uint64_t tag, uint32_t *scratch, DevCtl *ctl,
+                              unsigned grid, cudaStream_t stream) {
+    k_factor_one<<<grid, kThreads, 0, stream>>>(n, primes, pinv, plim, nprimes, reply_addr, reply_token,
+                                                tag, scratch, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_token_one(ActorDesc *actors, uint32_t a, uint32_t kind, int32_t v,
+                             uint64_t reply_addr, uint32_t reply_token, IngressEntry *outbox,
+                             DevCtl *ctl, cudaStream_t stream) {
+    k_token_one<<<1, 32, 0, stream>>>(actors, a, kind, v, reply_addr, reply_token, outbox, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_actors(ActorDesc *actors, uint32_t n_actors, cudaStream_t stream) {
+    if (n_actors == 0) return cudaSuccess;
+    k_reset_actors<<<(n_actors + 255) / 256, 256, 0, stream>>>(actors, n_actors);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_wait(const uint32_t *flag, uint64_t limit_ns, DevCtl *ctl, HostCtl *hctl,
+                              cudaStream_t stream) {
+    k_debug_wait<<<1, 32, 0, stream>>>(flag, limit_ns, ctl, hctl);
+    return cudaGetLastError();
+}
+
+cudaError_t build_prime_table(uint64_t limit, uint32_t pad, uint32_t **primes, uint32_t **pinv,
+                              uint32_t **plim, uint32_t *count, cudaStream_t stream) {
+    *primes = *pinv = *plim = nullptr;
+    *count = 0;
+    if (limit < 3) limit = 3;
+    // small odd primes up to sqrt(limit), host sieve
+    uint64_t r = 1;
+    while ((r + 1) * (r + 1) <= limit) ++r;
+    std::vector<uint8_t> comp(r + 1, 0);
+    std::vector<uint32_t> small;
+    for (uint64_t i = 2; i <= r; ++i) {
+        if (comp[i]) continue;
+        if (i > 2) small.push_back((uint32_t)i);
+        for (uint64_t j = i * i; j <= r; j += i) comp[j] = 1;
+    }
+    const uint64_t nbits = (limit + 1) / 2;  // odd numbers 1, 3, ..., <= limit
+    const uint64_t nwords = (nbits + 31) / 32;
+    const uint32_t nseg = (uint32_t)((nbits + kSegBits - 1) / kSegBits);
+    uint32_t *d_small = nullptr, *d_bits = nullptr, *d_counts = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_small, sizeof(uint32_t) * (small.size() + 1))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&d_bits, sizeof(uint32_t) * nwords)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&d_counts, sizeof(uint32_t) * nseg)) != cudaSuccess) return e;
+    if (!small.empty())
+        cudaMemcpyAsync(d_small, small.data(), sizeof(uint32_t) * small.size(), cudaMemcpyHostToDevice, stream);
+    cudaFuncSetAttribute(k_sieve, cudaFuncAttributeMaxDynamicSharedMemorySize, kSegBits / 8);
+    k_sieve<<<nseg, 512, kSegBits / 8, stream>>>(d_bits, nbits, d_small, (uint32_t)small.size());
+    k_sieve_count<<<nseg, 256, 0, stream>>>(d_bits, nwords, d_counts);
+    std::vector<uint32_t> counts(nseg), offsets(nseg);
+    cudaMemcpyAsync(counts.data(), d_counts, sizeof(uint32_t) * nseg, cudaMemcpyDeviceToHost, stream);
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return e;
+    uint64_t total = 0;
+    for (uint32_t s = 0; s < nseg; ++s) {
+        offsets[s] = (uint32_t)total;
+        total += counts[s];
+    }
+    const size_t bytes = sizeof(uint32_t) * (total + pad);
+    if ((e = cudaMalloc(primes, bytes)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(pinv, bytes)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(plim, bytes)) != cudaSuccess) return e;
+    cudaMemsetAsync(*primes, 0, bytes, stream);
+    cudaMemsetAsync(*pinv, 0, bytes, stream);
+    cudaMemsetAsync(*plim, 0, bytes, stream);
+    cudaMemcpyAsync(d_counts, offsets.data(), sizeof(uint32_t) * nseg, cudaMemcpyHostToDevice, stream);
+    k_sieve_emit<<<nseg, 256, 0, stream>>>(d_bits, nwords, d_counts, *primes, *pinv, *plim);
+    e = cudaStreamSynchronize(stream);
+    cudaFree(d_small);
+    cudaFree(d_bits);
+    cudaFree(d_counts);
+    *count = (uint32_t)total;
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+}  // namespace cafgpu

@@ -1,0 +1,28 @@
+// Host-side launch wrappers for the kernels in drain.cu.  Each enqueues on
+// `stream` and returns the launch status.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "layout.h"
+
+namespace cafgpu {
+
+cudaError_t launch_drain(const DrainParams &p, unsigned grid, cudaStream_t stream);
+cudaError_t launch_reset_ctl(DevCtl *ctl, cudaStream_t stream);
+cudaError_t launch_factor_one(uint64_t n, const uint32_t *primes, const uint32_t *pinv,
+                              const uint32_t *plim, uint32_t nprimes, uint64_t reply_addr,
+                              uint32_t reply_token, uint64_t tag, uint32_t *scratch, DevCtl *ctl,
+                              unsigned grid, cudaStream_t stream);
+cudaError_t launch_token_one(ActorDesc *actors, uint32_t a, uint32_t kind, int32_t v,
+                             uint64_t reply_addr, uint32_t reply_token, IngressEntry *outbox,
+                             DevCtl *ctl, cudaStream_t stream);
+cudaError_t launch_reset_actors(ActorDesc *actors, uint32_t n_actors, cudaStream_t stream);
+cudaError_t launch_debug_wait(const uint32_t *flag, uint64_t limit_ns, DevCtl *ctl, HostCtl *hctl,
+                              cudaStream_t stream);
+// Prime table of the odd primes <= limit.  Allocates *primes/*pinv/*plim
+// (cudaMalloc, padded with zeros by `pad` entries) and returns their count.
+cudaError_t build_prime_table(uint64_t limit, uint32_t pad, uint32_t **primes, uint32_t **pinv,
+                              uint32_t **plim, uint32_t *count, cudaStream_t stream);
+
+}  // namespace cafgpu

@@ -1,0 +1,221 @@
+// Memory layout of the runtime's device-side state, shared by the host
+// runtime (which allocates and initialises it) and the kernels.
+//
+// Everything the drain touches lives in one device arena:
+//
+//   DevCtl            counters, error word, queue headers      (one per runtime)
+//   ActorDesc[A]      actor table, 128 B per actor
+//   Slot[S]           mailbox slots, 64 B each; actor a owns a power-of-two
+//                     ring of them starting at ActorDesc::slot_base
+//   QCell[...]        ready queue (actor ids), free-batch queue, work queue
+//   FactorBatch[B]    messages swept together against the prime table
+//   uint32_t x 3 x P  prime table: odd primes, their inverses mod 2^32 and
+//                     floor((2^32-1)/p), structure-of-arrays
+//   LogRow[L]         validation-mode handling log
+//
+// Host-visible state (pinned, mapped) holds the host->device ingress ring,
+// the reply slots that caf_gpu_await polls, and a small control block.
+#pragma once
+
+#include <cstdint>
+
+namespace cafgpu {
+
+constexpr uint32_t kWarpsPerCta = 8;
+constexpr uint32_t kThreads = kWarpsPerCta * 32;
+constexpr uint32_t kFactorKMax = 16;     // messages per factor batch, upper bound
+constexpr uint32_t kRangePrimes = 4096;  // primes per range of a factor work item
+constexpr uint32_t kNoFactor = 0xFFFFFFFFu;
+
+// actor lifecycle (Sec. 6: ready / waiting / running / done)
+enum : uint32_t { kWaiting = 0, kReady = 1, kRunning = 2, kDone = 3 };
+
+// kinds (mirror caf_gpu.h)
+enum : uint32_t { kFactor = 1, kGemmBf16 = 2, kGemmSplit = 3, kToken = 4 };
+enum : uint32_t { kMsgStart = 1 };
+enum : uint32_t { kActorMaster = 1 };
+
+// error codes in DevCtl::error_word (low byte) -- high bits carry the site
+enum : uint32_t {
+    kErrWaitQueue = 1,     // queue push waited too long
+    kErrWaitSlot = 2,      // mailbox slot never published
+    kErrWaitSpace = 3,     // mailbox stayed full
+    kErrBadMessage = 4,    // device batch named an unknown actor / wrong kind
+    kErrDebugWait = 5,     // the debug wait kernel's flag was never set
+    kErrGemm = 6,          // GEMM pipeline wait expired
+    kErrStall = 7,         // no progress anywhere while messages were in flight
+};
+
+// Device-resident message (same layout as caf_gpu_dmsg).
+struct caf_dmsg_t {
+    uint32_t actor;
+    uint32_t kind;
+    uint32_t sender;
+    uint32_t sender_seq;
+    uint64_t u64;
+    uint64_t tag;
+};
+static_assert(sizeof(caf_dmsg_t) == 32, "caf_dmsg_t is 32 bytes");
+
+struct QueueHdr {
+    uint64_t enq;
+    uint64_t pad0[15];
+    uint64_t deq;
+    uint64_t pad1[15];
+    uint32_t mask;
+    uint32_t pad2[31];
+};
+
+struct QCell {
+    uint64_t seq;
+    uint32_t val;
+    uint32_t pad;
+};
+
+struct ActorDesc {                 // 128 bytes
+    uint32_t kind;
+    uint32_t state;                // lifecycle
+    uint32_t cap_mask;             // mailbox capacity - 1
+    uint32_t flags;
+    uint64_t slot_base;            // first Slot of this actor's ring
+    uint64_t head;                 // consumer position (written by the claim holder only)
+    uint64_t pad_a[4];
+    uint64_t tail;                 // producer ticket (atomic add)
+    int32_t user_state;
+    uint32_t next;                 // ring successor
+    uint32_t worker;               // ring master: factor worker
+    uint32_t factor_count;         // ring master: number of n values
+    uint64_t factor_n;             // ring master: const uint64_t* (device)
+    uint64_t factor_replies;       // ring master: reply records (device)
+    int32_t init_state;
+    uint32_t round;                // ring master: next factor request index
+    uint64_t pad_b[2];
+};
+static_assert(sizeof(ActorDesc) == 128, "ActorDesc is 128 bytes");
+
+struct Slot {                      // 64 bytes
+    uint64_t seq;                  // ticket + 1 once published
+    uint64_t payload;              // FACTOR n / TOKEN value / GEMM desc address
+    uint64_t reply_addr;           // reply record (0: no reply)
+    uint64_t tag;
+    uint32_t sender;
+    uint32_t sender_seq;
+    uint32_t kind;                 // kind | flags << 16
+    uint32_t reply_token;          // value stored to the reply's done word
+    uint64_t pad[2];
+};
+static_assert(sizeof(Slot) == 64, "Slot is 64 bytes");
+
+// Reply record, same layout as caf_gpu_dreply (32 bytes).
+struct Reply {
+    int32_t status;
+    uint32_t done;
+    uint64_t r0, r1;
+    uint64_t tag;
+};
+static_assert(sizeof(Reply) == 32, "Reply is 32 bytes");
+
+// Host->device ingress entry (64 bytes, pinned memory).
+struct IngressEntry {
+    uint64_t seq;                  // ticket + 1 once published by the host
+    uint64_t payload;
+    uint64_t reply_addr;
+    uint64_t tag;
+    uint32_t actor;
+    uint32_t kind;
+    uint32_t sender;
+    uint32_t sender_seq;
+    uint32_t reply_token;
+    uint32_t pad[3];
+};
+static_assert(sizeof(IngressEntry) == 64, "IngressEntry is 64 bytes");
+
+struct FactorBatch {
+    uint32_t count;                // messages in the batch
+    uint32_t items_left;           // work items not yet finished
+    uint32_t maxbound;             // max over messages of pbound
+    uint32_t even_mask;            // messages answered by d = 2
+    uint64_t n[kFactorKMax];
+    uint32_t pbound[kFactorKMax];  // odd primes p in the table with p*p <= n
+    uint32_t found[kFactorKMax];   // index of the first dividing prime (atomicMin)
+    uint64_t reply_addr[kFactorKMax];
+    uint32_t reply_token[kFactorKMax];
+    uint64_t tag[kFactorKMax];
+};
+
+struct LogRow {                    // same layout as caf_gpu_log_row
+    uint32_t actor;
+    uint32_t sender;
+    uint32_t sender_seq;
+    uint32_t kind;
+    uint64_t stamp;
+    uint64_t tag;
+    uint64_t value;
+};
+static_assert(sizeof(LogRow) == 40, "LogRow is 40 bytes");
+
+struct DevCtl {
+    uint64_t ingested;             // messages put into mailboxes (host, batch, device sends)
+    uint64_t pad0[15];
+    uint64_t completed;            // messages fully handled
+    uint64_t pad1[15];
+    uint64_t log_count;
+    uint64_t ring_head;            // host ring entries taken by the ingress warp
+    uint32_t error_word;
+    uint32_t exit_flag;
+    uint32_t routers_done;
+    uint32_t pad2;
+    uint64_t heartbeat;            // %globaltimer of the last progress report
+    // statistics
+    uint64_t claims, factor_items, prime_tests, gemm_tiles, device_sends, messages;
+    uint64_t pad3[8];
+    QueueHdr readyq;
+    QueueHdr freeq;
+    QueueHdr workq;
+};
+
+// Host-visible control block (pinned, mapped).
+struct HostCtl {
+    uint64_t ring_consumed;        // written by the device: ring entries taken
+    uint32_t stop;                 // written by the host: leave once quiescent
+    uint32_t error_word;           // copy of DevCtl::error_word for the host
+    uint32_t pad[12];
+};
+
+// Everything a drain launch needs (kernel parameter).
+struct DrainParams {
+    DevCtl *ctl;
+    ActorDesc *actors;
+    uint32_t n_actors;
+    uint32_t pad0;
+    Slot *slots;
+    QCell *readyq;
+    QCell *freeq;
+    QCell *workq;
+    FactorBatch *batches;
+    const uint32_t *primes;
+    const uint32_t *pinv;
+    const uint32_t *plim;
+    uint32_t nprimes;
+    uint32_t factor_k;             // messages per batch (<= kFactorKMax)
+    uint32_t factor_w;             // work items per batch
+    uint32_t max_claim;            // messages per claim (0: unlimited)
+    uint64_t max_n;                // largest factor message accepted
+    uint64_t wait_limit_ns;
+    uint64_t idle_exit_ns;
+    LogRow *log;
+    uint32_t log_capacity;
+    uint32_t validation;
+    // device batch (may be empty)
+    const void *batch_msgs;        // caf_gpu_dmsg[count]
+    Reply *batch_replies;
+    uint32_t batch_count;
+    uint32_t n_routers;
+    // live host ring (may be absent)
+    IngressEntry *ring;
+    HostCtl *hctl;
+    uint32_t ring_mask;
+    uint32_t live;
+};
+
+}  // namespace cafgpu

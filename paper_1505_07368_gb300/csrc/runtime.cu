@@ -1,0 +1,766 @@
+// Host runtime behind caf_gpu.h: device arenas, actor table, host ingress
+// ring, reply slots, the two backends (persistent drain and one launch per
+// message) and the C entry points.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/caf_gpu.h"
+#include "kernels.h"
+#include "layout.h"
+
+using namespace cafgpu;
+
+namespace {
+
+uint32_t next_pow2(uint64_t x) {
+    uint32_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+bool is_pow2(uint32_t x) { return x && !(x & (x - 1)); }
+
+uint64_t now_ns() {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+template <class T>
+T load_acquire(const T *p) {
+    return __atomic_load_n(p, __ATOMIC_ACQUIRE);
+}
+
+}  // namespace
+
+struct caf_gpu_runtime {
+    caf_gpu_runtime_cfg cfg{};
+    int device = 0;
+    int n_sms = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t setup = nullptr;
+    bool own_stream = false;
+    unsigned grid = 0;
+
+    // device arena
+    DevCtl *d_ctl = nullptr;
+    ActorDesc *d_actors = nullptr;
+    Slot *d_slots = nullptr;
+    uint64_t n_slots = 0, slots_used = 0;
+    QCell *d_readyq = nullptr, *d_freeq = nullptr, *d_workq = nullptr;
+    uint32_t readyq_cap = 0, freeq_cap = 0, workq_cap = 0;
+    FactorBatch *d_batches = nullptr;
+    uint32_t n_batches = 0;
+    uint32_t *d_primes = nullptr, *d_pinv = nullptr, *d_plim = nullptr;
+    uint32_t nprimes = 0;
+    uint64_t prime_limit = 0;
+    LogRow *d_log = nullptr;
+    uint32_t *d_scratch = nullptr;
+    uint32_t *d_zero = nullptr;
+
+    // host mirror of the actor table
+    std::vector<ActorDesc> actors;
+    uint32_t n_actors = 0;
+
+    // pinned, device-visible
+    IngressEntry *ring = nullptr;
+    HostCtl *hctl = nullptr;
+    Reply *replies = nullptr;
+    IngressEntry *outbox = nullptr;
+    uint32_t outbox_per_msg = 4;
+    uint32_t outbox_msgs = 256;
+
+    std::mutex mu;                 // ring tickets, sender counters, reply slots, launches
+    uint64_t ring_tail = 0;
+    std::unordered_map<uint32_t, uint32_t> sender_seq;
+    std::vector<uint32_t> free_slots;
+    std::vector<uint32_t> gen;
+    std::vector<uint8_t> in_use;
+
+    int backend = CAF_GPU_BACKEND_PERSISTENT;
+    cudaEvent_t live_done = nullptr;
+    bool live_launched = false;
+    uint64_t launches = 0;
+    DevCtl last_stats{};
+
+    // per-message backend: messages produced by token kernels, waiting for a launch
+    std::deque<IngressEntry> pm_pending;
+};
+
+namespace {
+
+#define CK(x)                                  \
+    do {                                       \
+        cudaError_t e_ = (x);                  \
+        if (e_ != cudaSuccess) return CAF_GPU_ECUDA; \
+    } while (0)
+
+DrainParams make_params(caf_gpu_runtime *rt) {
+    DrainParams p{};
+    p.ctl = rt->d_ctl;
+    p.actors = rt->d_actors;
+    p.n_actors = rt->n_actors;
+    p.slots = rt->d_slots;
+    p.readyq = rt->d_readyq;
+    p.freeq = rt->d_freeq;
+    p.workq = rt->d_workq;
+    p.batches = rt->d_batches;
+    p.primes = rt->d_primes;
+    p.pinv = rt->d_pinv;
+    p.plim = rt->d_plim;
+    p.nprimes = rt->nprimes;
+    p.factor_k = rt->cfg.factor_batch;
+    p.factor_w = rt->cfg.factor_warps;
+    p.max_claim = rt->cfg.max_msgs_per_claim;
+    p.max_n = rt->cfg.max_factor_n;
+    p.wait_limit_ns = rt->cfg.wait_limit_ns;
+    p.idle_exit_ns = rt->cfg.idle_exit_ns;
+    p.log = rt->d_log;
+    p.log_capacity = rt->d_log ? rt->cfg.log_capacity : 0;
+    p.validation = rt->cfg.validation_mode ? 1 : 0;
+    p.ring = rt->ring;
+    p.hctl = rt->hctl;
+    p.ring_mask = rt->cfg.ingress_capacity - 1;
+    return p;
+}
+
+int init_queue(caf_gpu_runtime *rt, QCell **cells, uint32_t cap, QueueHdr *hdr_dev,
+               const std::vector<uint32_t> &initial) {
+    std::vector<QCell> h(cap);
+    for (uint32_t i = 0; i < cap; ++i) {
+        h[i].seq = i;
+        h[i].val = 0;
+        h[i].pad = 0;
+    }
+    for (size_t i = 0; i < initial.size(); ++i) {
+        h[i].seq = i + 1;
+        h[i].val = initial[i];
+    }
+    CK(cudaMalloc(cells, sizeof(QCell) * cap));
+    CK(cudaMemcpy(*cells, h.data(), sizeof(QCell) * cap, cudaMemcpyHostToDevice));
+    QueueHdr q{};
+    q.enq = initial.size();
+    q.deq = 0;
+    q.mask = cap - 1;
+    CK(cudaMemcpy(hdr_dev, &q, sizeof(q), cudaMemcpyHostToDevice));
+    return 0;
+}
+
+int launch_live(caf_gpu_runtime *rt) {
+    DrainParams p = make_params(rt);
+    p.live = 1;
+    CK(launch_reset_ctl(rt->d_ctl, rt->stream));
+    CK(launch_drain(p, rt->grid, rt->stream));
+    CK(cudaEventRecord(rt->live_done, rt->stream));
+    rt->live_launched = true;
+    rt->launches += 2;
+    return 0;
+}
+
+bool live_running(caf_gpu_runtime *rt) {
+    return rt->live_launched && cudaEventQuery(rt->live_done) == cudaErrorNotReady;
+}
+
+// Launch the persistent drain if host messages are waiting and no drain runs.
+// Caller holds rt->mu.
+int kick_locked(caf_gpu_runtime *rt) {
+    if (rt->backend != CAF_GPU_BACKEND_PERSISTENT) return 0;
+    if (live_running(rt)) return 0;
+    if (load_acquire(&rt->hctl->ring_consumed) == rt->ring_tail) return 0;
+    return launch_live(rt);
+}
+
+int kick(caf_gpu_runtime *rt) {
+    std::lock_guard<std::mutex> g(rt->mu);
+    return kick_locked(rt);
+}
+
+int check_msg(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *m, uint32_t *idx) {
+    if (!rt || !m) return CAF_GPU_EINVAL;
+    if (to == 0 || to > rt->n_actors) return CAF_GPU_EINVAL;
+    const uint32_t a = (uint32_t)(to - 1);
+    const ActorDesc &d = rt->actors[a];
+    if (m->kind != d.kind) return CAF_GPU_EINVAL;
+    if (m->kind == kFactor && m->u64 > rt->cfg.max_factor_n) return CAF_GPU_EINVAL;
+    if (m->kind == kGemmBf16 || m->kind == kGemmSplit) return CAF_GPU_EINVAL;  // GEMM not wired yet
+    if (m->kind == kToken) {
+        uint32_t state = 0;
+        if (cudaMemcpy(&state, &rt->d_actors[a].state, sizeof(state), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return CAF_GPU_ECUDA;
+        if (state == kDone) return CAF_GPU_EDEAD;
+    }
+    *idx = a;
+    return 0;
+}
+
+uint32_t factor_grid(caf_gpu_runtime *rt, uint64_t n) {
+    // about one chunk of 32 primes per warp: primes below sqrt(n) ~ s / ln s
+    const double s = std::sqrt((double)n);
+    const double np = s > 3 ? s / std::log(s) : 1.0;
+    uint64_t g = (uint64_t)(np / 32.0 / kWarpsPerCta) + 1;
+    return (uint32_t)std::min<uint64_t>(g, (uint64_t)rt->n_sms * 4);
+}
+
+// Launch the handler for one message (per-message backend).  Caller holds rt->mu.
+int pm_launch(caf_gpu_runtime *rt, const IngressEntry &e, uint32_t outbox_index) {
+    const uint32_t kind = e.kind & 0xFFFFu;
+    if (kind == kFactor) {
+        CK(launch_factor_one(e.payload, rt->d_primes, rt->d_pinv, rt->d_plim, rt->nprimes, e.reply_addr,
+                             e.reply_token, e.tag, rt->d_scratch, rt->d_ctl, factor_grid(rt, e.payload),
+                             rt->stream));
+    } else if (kind == kToken) {
+        IngressEntry *ob = rt->outbox + (size_t)outbox_index * rt->outbox_per_msg;
+        ob[0].seq = ~0ull;
+        CK(launch_token_one(rt->d_actors, e.actor, e.kind, (int32_t)(uint32_t)e.payload, e.reply_addr,
+                            e.reply_token, ob, rt->d_ctl, rt->stream));
+    } else {
+        return CAF_GPU_EINVAL;
+    }
+    rt->launches += 1;
+    return 0;
+}
+
+// Per-message backend: run every pending token message in waves until no
+// more are produced.  Caller holds rt->mu.
+int pm_pump(caf_gpu_runtime *rt) {
+    while (!rt->pm_pending.empty()) {
+        std::vector<IngressEntry> wave;
+        while (!rt->pm_pending.empty() && wave.size() < rt->outbox_msgs) {
+            wave.push_back(rt->pm_pending.front());
+            rt->pm_pending.pop_front();
+        }
+        for (uint32_t i = 0; i < wave.size(); ++i) {
+            int r = pm_launch(rt, wave[i], i);
+            if (r) return r;
+        }
+        CK(cudaStreamSynchronize(rt->stream));
+        for (uint32_t i = 0; i < wave.size(); ++i) {
+            if ((wave[i].kind & 0xFFFFu) != kToken) continue;
+            IngressEntry *ob = rt->outbox + (size_t)i * rt->outbox_per_msg;
+            const uint64_t nout = load_acquire(&ob[0].seq);
+            for (uint64_t k = 0; k < nout && k + 1 < rt->outbox_per_msg; ++k) rt->pm_pending.push_back(ob[1 + k]);
+        }
+    }
+    return 0;
+}
+
+// Put one message on its way (caller holds rt->mu).
+int submit_locked(caf_gpu_runtime *rt, uint32_t a, const caf_gpu_msg *m, uint64_t reply_addr, uint32_t token) {
+    IngressEntry e{};
+    e.actor = a;
+    e.kind = m->kind | (m->flags << 16);
+    e.sender = m->sender;
+    e.sender_seq = rt->sender_seq[m->sender]++;
+    e.payload = m->u64;
+    e.reply_addr = reply_addr;
+    e.reply_token = token;
+    e.tag = m->tag;
+    if (rt->backend == CAF_GPU_BACKEND_PER_MESSAGE_LAUNCH) {
+        if ((e.kind & 0xFFFFu) == kToken) {
+            // token messages may produce more messages: queued, run in waves by
+            // caf_gpu_sync / caf_gpu_await
+            rt->pm_pending.push_back(e);
+            return 0;
+        }
+        return pm_launch(rt, e, 0);
+    }
+    const uint32_t cap = rt->cfg.ingress_capacity;
+    const uint64_t t = rt->ring_tail;
+    if (t - load_acquire(&rt->hctl->ring_consumed) >= cap) {
+        int r = kick_locked(rt);
+        if (r) return r;
+        const uint64_t t0 = now_ns();
+        while (t - load_acquire(&rt->hctl->ring_consumed) >= cap) {
+            if (rt->hctl->error_word) return CAF_GPU_EWAITLIMIT;
+            if (now_ns() - t0 > rt->cfg.wait_limit_ns) return CAF_GPU_EAGAIN;
+            kick_locked(rt);
+            std::this_thread::yield();
+        }
+    }
+    IngressEntry *slot = &rt->ring[t & (cap - 1)];
+    slot->payload = e.payload;
+    slot->reply_addr = e.reply_addr;
+    slot->tag = e.tag;
+    slot->actor = e.actor;
+    slot->kind = e.kind;
+    slot->sender = e.sender;
+    slot->sender_seq = e.sender_seq;
+    slot->reply_token = e.reply_token;
+    __atomic_store_n(&slot->seq, t + 1, __ATOMIC_RELEASE);
+    rt->ring_tail = t + 1;
+    return 0;
+}
+
+int reserve_reply(caf_gpu_runtime *rt, uint32_t *slot, uint32_t *g) {
+    if (rt->free_slots.empty()) return CAF_GPU_EAGAIN;
+    *slot = rt->free_slots.back();
+    rt->free_slots.pop_back();
+    *g = ++rt->gen[*slot];
+    if (*g == 0) *g = ++rt->gen[*slot];
+    rt->in_use[*slot] = 1;
+    rt->replies[*slot].done = 0;
+    return 0;
+}
+
+void free_runtime(caf_gpu_runtime *rt) {
+    if (!rt) return;
+    cudaFree(rt->d_ctl);
+    cudaFree(rt->d_actors);
+    cudaFree(rt->d_slots);
+    cudaFree(rt->d_readyq);
+    cudaFree(rt->d_freeq);
+    cudaFree(rt->d_workq);
+    cudaFree(rt->d_batches);
+    cudaFree(rt->d_primes);
+    cudaFree(rt->d_pinv);
+    cudaFree(rt->d_plim);
+    cudaFree(rt->d_log);
+    cudaFree(rt->d_scratch);
+    cudaFree(rt->d_zero);
+    if (rt->ring) cudaFreeHost(rt->ring);
+    if (rt->hctl) cudaFreeHost(rt->hctl);
+    if (rt->replies) cudaFreeHost(rt->replies);
+    if (rt->outbox) cudaFreeHost(rt->outbox);
+    if (rt->live_done) cudaEventDestroy(rt->live_done);
+    if (rt->setup) cudaStreamDestroy(rt->setup);
+    if (rt->own_stream && rt->stream) cudaStreamDestroy(rt->stream);
+    delete rt;
+}
+
+int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
+    caf_gpu_runtime_cfg c{};
+    if (user) c = *user;
+    if (!c.max_actors) c.max_actors = 16384;
+    if (!c.mailbox_capacity) c.mailbox_capacity = 64;
+    if (!c.max_inflight_requests) c.max_inflight_requests = 65536;
+    if (!c.ingress_capacity) c.ingress_capacity = 65536;
+    if (!c.ctas_per_sm) c.ctas_per_sm = 2;
+    if (!c.factor_batch) c.factor_batch = 8;
+    if (!c.factor_warps) c.factor_warps = 1;
+    if (!c.max_factor_n) c.max_factor_n = (1ull << 62) - 1;
+    if (!c.mem_budget_bytes) c.mem_budget_bytes = 8ull << 30;
+    if (!c.wait_limit_ns) c.wait_limit_ns = 200000000ull;
+    if (!c.idle_exit_ns) c.idle_exit_ns = 2000000ull;
+    if (!c.log_capacity) c.log_capacity = 1u << 20;
+    if (!is_pow2(c.mailbox_capacity) || !is_pow2(c.ingress_capacity)) return CAF_GPU_EINVAL;
+    if (c.factor_batch > kFactorKMax || c.factor_warps > 255 || c.ctas_per_sm > 2) return CAF_GPU_EINVAL;
+    if (c.max_factor_n >= (1ull << 62)) return CAF_GPU_EINVAL;
+    if (c.max_actors > (1u << 24)) return CAF_GPU_EINVAL;
+    rt->cfg = c;
+
+    CK(cudaGetDevice(&rt->device));
+    CK(cudaDeviceGetAttribute(&rt->n_sms, cudaDevAttrMultiProcessorCount, rt->device));
+    rt->grid = (unsigned)rt->n_sms * c.ctas_per_sm;
+    if (c.cuda_stream) {
+        rt->stream = (cudaStream_t)c.cuda_stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&rt->stream, cudaStreamNonBlocking));
+        rt->own_stream = true;
+    }
+    CK(cudaStreamCreateWithFlags(&rt->setup, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&rt->live_done, cudaEventDisableTiming));
+
+    // device arena
+    CK(cudaMalloc(&rt->d_ctl, sizeof(DevCtl)));
+    CK(cudaMemset(rt->d_ctl, 0, sizeof(DevCtl)));
+    CK(cudaMalloc(&rt->d_actors, sizeof(ActorDesc) * (size_t)c.max_actors));
+    CK(cudaMemset(rt->d_actors, 0, sizeof(ActorDesc) * (size_t)c.max_actors));
+    rt->n_slots = (uint64_t)c.max_actors * c.mailbox_capacity;
+    CK(cudaMalloc(&rt->d_slots, sizeof(Slot) * rt->n_slots));
+    CK(cudaMemset(rt->d_slots, 0, sizeof(Slot) * rt->n_slots));
+    rt->n_batches = std::max<uint32_t>(4096, 2u * rt->grid * kWarpsPerCta);
+    CK(cudaMalloc(&rt->d_batches, sizeof(FactorBatch) * rt->n_batches));
+    CK(cudaMemset(rt->d_batches, 0, sizeof(FactorBatch) * rt->n_batches));
+    rt->readyq_cap = next_pow2((uint64_t)c.max_actors + 1);
+    rt->freeq_cap = next_pow2((uint64_t)rt->n_batches + 1);
+    rt->workq_cap = next_pow2((uint64_t)rt->n_batches * c.factor_warps + 1);
+    std::vector<uint32_t> none, all(rt->n_batches);
+    for (uint32_t i = 0; i < rt->n_batches; ++i) all[i] = i;
+    int r;
+    if ((r = init_queue(rt, &rt->d_readyq, rt->readyq_cap, &rt->d_ctl->readyq, none))) return r;
+    if ((r = init_queue(rt, &rt->d_freeq, rt->freeq_cap, &rt->d_ctl->freeq, all))) return r;
+    if ((r = init_queue(rt, &rt->d_workq, rt->workq_cap, &rt->d_ctl->workq, none))) return r;
+    if (c.validation_mode) {
+        CK(cudaMalloc(&rt->d_log, sizeof(LogRow) * (size_t)c.log_capacity));
+        CK(cudaMemset(rt->d_log, 0, sizeof(LogRow) * (size_t)c.log_capacity));
+    }
+    CK(cudaMalloc(&rt->d_scratch, 64));
+    const uint32_t scratch_init[2] = {kNoFactor, 0};
+    CK(cudaMemcpy(rt->d_scratch, scratch_init, sizeof(scratch_init), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&rt->d_zero, 64));
+    CK(cudaMemset(rt->d_zero, 0, 64));
+
+    // prime table: odd primes up to floor(sqrt(max_factor_n))
+    uint64_t lim = (uint64_t)std::sqrt((double)c.max_factor_n);
+    while (lim * lim > c.max_factor_n) --lim;
+    while ((lim + 1) * (lim + 1) <= c.max_factor_n) ++lim;
+    rt->prime_limit = lim;
+    CK(build_prime_table(lim, kRangePrimes + 64, &rt->d_primes, &rt->d_pinv, &rt->d_plim, &rt->nprimes,
+                         rt->setup));
+    rt->launches += 4;
+
+    // pinned, mapped host memory
+    CK(cudaHostAlloc(&rt->ring, sizeof(IngressEntry) * (size_t)c.ingress_capacity, cudaHostAllocMapped));
+    memset(rt->ring, 0, sizeof(IngressEntry) * (size_t)c.ingress_capacity);
+    CK(cudaHostAlloc(&rt->hctl, sizeof(HostCtl), cudaHostAllocMapped));
+    memset(rt->hctl, 0, sizeof(HostCtl));
+    CK(cudaHostAlloc(&rt->replies, sizeof(Reply) * (size_t)c.max_inflight_requests, cudaHostAllocMapped));
+    memset(rt->replies, 0, sizeof(Reply) * (size_t)c.max_inflight_requests);
+    CK(cudaHostAlloc(&rt->outbox, sizeof(IngressEntry) * rt->outbox_per_msg * rt->outbox_msgs,
+                     cudaHostAllocMapped));
+    memset(rt->outbox, 0, sizeof(IngressEntry) * rt->outbox_per_msg * rt->outbox_msgs);
+    rt->free_slots.resize(c.max_inflight_requests);
+    for (uint32_t i = 0; i < c.max_inflight_requests; ++i) rt->free_slots[i] = c.max_inflight_requests - 1 - i;
+    rt->gen.assign(c.max_inflight_requests, 0);
+    rt->in_use.assign(c.max_inflight_requests, 0);
+    rt->actors.reserve(1024);
+    CK(cudaDeviceSynchronize());
+    return 0;
+}
+
+// Wait until every host message sent so far has been handled (persistent backend).
+int sync_persistent(caf_gpu_runtime *rt) {
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> g(rt->mu);
+            int r = kick_locked(rt);
+            if (r) return r;
+            __atomic_store_n(&rt->hctl->stop, 1u, __ATOMIC_RELEASE);
+        }
+        CK(cudaStreamSynchronize(rt->stream));
+        __atomic_store_n(&rt->hctl->stop, 0u, __ATOMIC_RELEASE);
+        if (rt->hctl->error_word) return CAF_GPU_EWAITLIMIT;
+        std::lock_guard<std::mutex> g(rt->mu);
+        if (load_acquire(&rt->hctl->ring_consumed) == rt->ring_tail) return 0;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *caf_gpu_strerror(int code) {
+    switch (code) {
+        case CAF_GPU_OK: return "ok";
+        case CAF_GPU_EINVAL: return "invalid argument";
+        case CAF_GPU_ENOMEM: return "out of memory or table space";
+        case CAF_GPU_EAGAIN: return "resource temporarily full, retry";
+        case CAF_GPU_ETIMEDOUT: return "timed out";
+        case CAF_GPU_EDEAD: return "actor has terminated";
+        case CAF_GPU_EWAITLIMIT: return "a bounded device wait expired";
+        case CAF_GPU_ESTATE: return "unknown or consumed handle / invalid state";
+        case CAF_GPU_ECUDA: return "CUDA error";
+        default: return "unknown error";
+    }
+}
+
+int caf_gpu_runtime_create(const caf_gpu_runtime_cfg *cfg, caf_gpu_runtime **out) {
+    if (!out) return CAF_GPU_EINVAL;
+    *out = nullptr;
+    caf_gpu_runtime *rt = new caf_gpu_runtime();
+    int r = create_impl(cfg, rt);
+    if (r) {
+        free_runtime(rt);
+        return r;
+    }
+    *out = rt;
+    return 0;
+}
+
+int caf_gpu_runtime_destroy(caf_gpu_runtime *rt) {
+    if (!rt) return CAF_GPU_EINVAL;
+    int r = caf_gpu_sync(rt);
+    cudaStreamSynchronize(rt->stream);
+    free_runtime(rt);
+    return r == CAF_GPU_EWAITLIMIT ? 0 : r;
+}
+
+int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_cfg *cfg, caf_gpu_actor *out) {
+    if (!rt || !out) return CAF_GPU_EINVAL;
+    if (kernel_id < kFactor || kernel_id > kToken) return CAF_GPU_EINVAL;
+    caf_gpu_actor_cfg c{};
+    if (cfg) c = *cfg;
+    const uint32_t cap = c.mailbox_capacity ? c.mailbox_capacity : rt->cfg.mailbox_capacity;
+    if (!is_pow2(cap) || cap > (1u << 24)) return CAF_GPU_EINVAL;
+    std::lock_guard<std::mutex> g(rt->mu);
+    if (rt->n_actors >= rt->cfg.max_actors) return CAF_GPU_ENOMEM;
+    if (rt->slots_used + cap > rt->n_slots) return CAF_GPU_ENOMEM;
+    ActorDesc d{};
+    d.kind = kernel_id;
+    d.state = kWaiting;
+    d.cap_mask = cap - 1;
+    d.flags = c.flags;
+    d.slot_base = rt->slots_used;
+    if (kernel_id == kToken) {
+        if (c.next == 0 || c.next > rt->cfg.max_actors) return CAF_GPU_EINVAL;
+        d.next = (uint32_t)(c.next - 1);
+        if (c.flags & kActorMaster) {
+            if (c.worker == 0 || c.worker > rt->n_actors) return CAF_GPU_EINVAL;
+            if (rt->actors[c.worker - 1].kind != kFactor) return CAF_GPU_EINVAL;
+            d.worker = (uint32_t)(c.worker - 1);
+            d.factor_count = c.factor_count;
+            d.factor_n = (uint64_t)c.factor_n;
+            d.factor_replies = (uint64_t)c.factor_replies;
+            if (c.factor_count && (!c.factor_n || !c.factor_replies)) return CAF_GPU_EINVAL;
+        }
+        d.init_state = c.init_state;
+        d.user_state = c.init_state;
+    }
+    const uint32_t idx = rt->n_actors;
+    CK(cudaMemcpyAsync(&rt->d_actors[idx], &d, sizeof(d), cudaMemcpyHostToDevice, rt->setup));
+    CK(cudaStreamSynchronize(rt->setup));
+    rt->slots_used += cap;
+    rt->actors.push_back(d);
+    rt->n_actors = idx + 1;
+    *out = (caf_gpu_actor)idx + 1;
+    return 0;
+}
+
+int caf_gpu_send(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *msg) {
+    uint32_t a;
+    int r = check_msg(rt, to, msg, &a);
+    if (r) return r;
+    {
+        std::lock_guard<std::mutex> g(rt->mu);
+        r = submit_locked(rt, a, msg, 0, 0);
+        if (r) return r;
+        return kick_locked(rt);
+    }
+}
+
+int caf_gpu_request(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *msg, caf_gpu_handle *out) {
+    if (!out) return CAF_GPU_EINVAL;
+    uint32_t a;
+    int r = check_msg(rt, to, msg, &a);
+    if (r) return r;
+    std::lock_guard<std::mutex> g(rt->mu);
+    uint32_t slot, gen;
+    if ((r = reserve_reply(rt, &slot, &gen))) return r;
+    r = submit_locked(rt, a, msg, (uint64_t)&rt->replies[slot], gen);
+    if (r) {
+        rt->in_use[slot] = 0;
+        rt->free_slots.push_back(slot);
+        return r;
+    }
+    *out = ((uint64_t)gen << 32) | (slot + 1);
+    return kick_locked(rt);
+}
+
+int caf_gpu_request_batch(caf_gpu_runtime *rt, const caf_gpu_actor *to, const caf_gpu_msg *msgs, uint32_t count,
+                          caf_gpu_handle *out) {
+    if (!rt || (count && (!to || !msgs || !out))) return CAF_GPU_EINVAL;
+    for (uint32_t i = 0; i < count; ++i) {
+        uint32_t a;
+        int r = check_msg(rt, to[i], &msgs[i], &a);
+        if (r) return r;
+    }
+    std::lock_guard<std::mutex> g(rt->mu);
+    if (rt->free_slots.size() < count) return CAF_GPU_EAGAIN;
+    for (uint32_t i = 0; i < count; ++i) {
+        uint32_t slot, gen;
+        int r = reserve_reply(rt, &slot, &gen);
+        if (r) return r;
+        r = submit_locked(rt, (uint32_t)(to[i] - 1), &msgs[i], (uint64_t)&rt->replies[slot], gen);
+        if (r) {
+            rt->in_use[slot] = 0;
+            rt->free_slots.push_back(slot);
+            return r;
+        }
+        out[i] = ((uint64_t)gen << 32) | (slot + 1);
+        if ((i & 1023) == 1023) kick_locked(rt);
+    }
+    return kick_locked(rt);
+}
+
+int caf_gpu_await(caf_gpu_runtime *rt, caf_gpu_handle h, uint64_t timeout_ns, caf_gpu_reply *out) {
+    if (!rt || !out) return CAF_GPU_EINVAL;
+    const uint32_t slot = (uint32_t)(h & 0xFFFFFFFFu) - 1;
+    const uint32_t gen = (uint32_t)(h >> 32);
+    {
+        std::lock_guard<std::mutex> g(rt->mu);
+        if (h == 0 || slot >= rt->cfg.max_inflight_requests || !rt->in_use[slot] || rt->gen[slot] != gen)
+            return CAF_GPU_ESTATE;
+    }
+    if (rt->backend == CAF_GPU_BACKEND_PER_MESSAGE_LAUNCH) {
+        std::lock_guard<std::mutex> g(rt->mu);
+        int r = pm_pump(rt);
+        if (r) return r;
+    }
+    const uint64_t t0 = now_ns();
+    uint32_t spins = 0;
+    while (load_acquire(&rt->replies[slot].done) != gen) {
+        if (load_acquire(&rt->hctl->error_word)) return CAF_GPU_EWAITLIMIT;
+        if ((++spins & 255) == 0) {
+            int r = kick(rt);
+            if (r) return r;
+            if (rt->backend == CAF_GPU_BACKEND_PER_MESSAGE_LAUNCH && cudaStreamQuery(rt->stream) == cudaSuccess &&
+                load_acquire(&rt->replies[slot].done) != gen) {
+                // every launch finished and the reply is not there: nothing will write it
+                if (timeout_ns && now_ns() - t0 > timeout_ns) return CAF_GPU_ETIMEDOUT;
+            }
+            if (timeout_ns && now_ns() - t0 > timeout_ns) return CAF_GPU_ETIMEDOUT;
+            std::this_thread::yield();
+        }
+    }
+    const Reply &r = rt->replies[slot];
+    out->status = r.status;
+    out->kind = 0;
+    out->r0 = r.r0;
+    out->r1 = r.r1;
+    std::lock_guard<std::mutex> g(rt->mu);
+    rt->in_use[slot] = 0;
+    rt->free_slots.push_back(slot);
+    return 0;
+}
+
+int caf_gpu_await_batch(caf_gpu_runtime *rt, const caf_gpu_handle *h, uint32_t count, uint64_t timeout_ns,
+                        caf_gpu_reply *out) {
+    if (!rt || (count && (!h || !out))) return CAF_GPU_EINVAL;
+    for (uint32_t i = 0; i < count; ++i) {
+        int r = caf_gpu_await(rt, h[i], timeout_ns, &out[i]);
+        if (r) return r;
+    }
+    return 0;
+}
+
+int caf_gpu_request_batch_device(caf_gpu_runtime *rt, const caf_gpu_dmsg *d_msgs, uint32_t count,
+                                 caf_gpu_dreply *d_replies) {
+    if (!rt || (count && !d_msgs)) return CAF_GPU_EINVAL;
+    if (count == 0) return 0;
+    std::lock_guard<std::mutex> g(rt->mu);
+    if (rt->backend != CAF_GPU_BACKEND_PERSISTENT) return CAF_GPU_ESTATE;
+    DrainParams p = make_params(rt);
+    p.batch_msgs = d_msgs;
+    p.batch_replies = reinterpret_cast<Reply *>(d_replies);
+    p.batch_count = count;
+    p.n_routers = std::min<uint32_t>(rt->grid * kWarpsPerCta, 128);
+    CK(launch_reset_ctl(rt->d_ctl, rt->stream));
+    CK(launch_drain(p, rt->grid, rt->stream));
+    rt->launches += 2;
+    return 0;
+}
+
+int caf_gpu_sync(caf_gpu_runtime *rt) {
+    if (!rt) return CAF_GPU_EINVAL;
+    if (rt->backend == CAF_GPU_BACKEND_PER_MESSAGE_LAUNCH) {
+        std::lock_guard<std::mutex> g(rt->mu);
+        int r = pm_pump(rt);
+        if (r) return r;
+        CK(cudaStreamSynchronize(rt->stream));
+        return 0;
+    }
+    return sync_persistent(rt);
+}
+
+int caf_gpu_stream_sync(caf_gpu_runtime *rt) {
+    if (!rt) return CAF_GPU_EINVAL;
+    CK(cudaStreamSynchronize(rt->stream));
+    if (rt->hctl->error_word) return CAF_GPU_EWAITLIMIT;
+    uint32_t err = 0;
+    CK(cudaMemcpy(&err, &rt->d_ctl->error_word, sizeof(err), cudaMemcpyDeviceToHost));
+    return err ? CAF_GPU_EWAITLIMIT : 0;
+}
+
+int caf_gpu_set_backend(caf_gpu_runtime *rt, int backend) {
+    if (!rt) return CAF_GPU_EINVAL;
+    if (backend != CAF_GPU_BACKEND_PERSISTENT && backend != CAF_GPU_BACKEND_PER_MESSAGE_LAUNCH)
+        return CAF_GPU_EINVAL;
+    int r = caf_gpu_sync(rt);
+    if (r) return r;
+    std::lock_guard<std::mutex> g(rt->mu);
+    rt->backend = backend;
+    return 0;
+}
+
+int caf_gpu_reset_actors(caf_gpu_runtime *rt) {
+    if (!rt) return CAF_GPU_EINVAL;
+    std::lock_guard<std::mutex> g(rt->mu);
+    CK(launch_reset_actors(rt->d_actors, rt->n_actors, rt->stream));
+    rt->launches += 1;
+    return 0;
+}
+
+int caf_gpu_actor_state(caf_gpu_runtime *rt, caf_gpu_actor a, uint32_t *lifecycle, int32_t *user_state) {
+    if (!rt || a == 0 || a > rt->n_actors) return CAF_GPU_EINVAL;
+    ActorDesc d;
+    CK(cudaMemcpy(&d, &rt->d_actors[a - 1], sizeof(d), cudaMemcpyDeviceToHost));
+    if (lifecycle) *lifecycle = d.state;
+    if (user_state) *user_state = d.user_state;
+    return 0;
+}
+
+int caf_gpu_stats_read(caf_gpu_runtime *rt, caf_gpu_stats *out) {
+    if (!rt || !out) return CAF_GPU_EINVAL;
+    DevCtl c;
+    CK(cudaMemcpy(&c, rt->d_ctl, sizeof(c), cudaMemcpyDeviceToHost));
+    const DevCtl &l = rt->last_stats;
+    out->launches = rt->launches;
+    out->messages = c.messages - l.messages;
+    out->device_sends = c.device_sends - l.device_sends;
+    out->claims = c.claims - l.claims;
+    out->factor_items = c.factor_items - l.factor_items;
+    out->prime_tests = c.prime_tests - l.prime_tests;
+    out->gemm_tiles = c.gemm_tiles - l.gemm_tiles;
+    out->error_word = c.error_word;
+    out->pad = 0;
+    rt->last_stats = c;
+    rt->launches = 0;
+    return 0;
+}
+
+int caf_gpu_read_log(caf_gpu_runtime *rt, caf_gpu_log_row *out, uint32_t cap, uint32_t *count) {
+    if (!rt || !count) return CAF_GPU_EINVAL;
+    if (!rt->d_log) return CAF_GPU_ESTATE;
+    CK(cudaStreamSynchronize(rt->stream));
+    uint64_t n = 0;
+    CK(cudaMemcpy(&n, &rt->d_ctl->log_count, sizeof(n), cudaMemcpyDeviceToHost));
+    n = std::min<uint64_t>(n, rt->cfg.log_capacity);
+    const uint32_t m = (uint32_t)std::min<uint64_t>(n, cap);
+    if (m && out) CK(cudaMemcpy(out, rt->d_log, sizeof(LogRow) * m, cudaMemcpyDeviceToHost));
+    const uint64_t zero = 0;
+    CK(cudaMemcpy(&rt->d_ctl->log_count, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+    *count = m;
+    return 0;
+}
+
+void *caf_gpu_stream(caf_gpu_runtime *rt) { return rt ? (void *)rt->stream : nullptr; }
+
+int caf_gpu_prime_table(caf_gpu_runtime *rt, const uint32_t **d_primes, uint32_t *count) {
+    if (!rt) return CAF_GPU_EINVAL;
+    if (d_primes) *d_primes = rt->d_primes;
+    if (count) *count = rt->nprimes;
+    return 0;
+}
+
+// Test hook: a device wait on a flag that nothing sets must give up after
+// `limit_ns` and report CAF_GPU_EWAITLIMIT; the runtime stays usable after
+// caf_gpu_clear_error.
+int caf_gpu_debug_wait_expiry(caf_gpu_runtime *rt, uint64_t limit_ns) {
+    if (!rt) return CAF_GPU_EINVAL;
+    CK(launch_debug_wait(rt->d_zero, limit_ns, rt->d_ctl, rt->hctl, rt->stream));
+    rt->launches += 1;
+    CK(cudaStreamSynchronize(rt->stream));
+    return rt->hctl->error_word ? CAF_GPU_EWAITLIMIT : 0;
+}
+
+int caf_gpu_clear_error(caf_gpu_runtime *rt) {
+    if (!rt) return CAF_GPU_EINVAL;
+    CK(cudaStreamSynchronize(rt->stream));
+    const uint32_t zero = 0;
+    CK(cudaMemcpy(&rt->d_ctl->error_word, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+    rt->hctl->error_word = 0;
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,53 @@
+"""CPU checks of the C-ABI library: it builds, loads and exports every symbol
+that include/caf_gpu.h declares, and the binding's structs match the header."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1505_07368_gb300 import _build, cafgpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "caf_gpu.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(caf_gpu_\w+)\s*\(", src)))
+
+
+def test_header_declarations_match_binding():
+    assert _declared() == sorted(cafgpu.EXPORTS)
+
+
+def test_library_builds_and_exports_every_symbol():
+    lib_path = _build.build()
+    L = ctypes.CDLL(lib_path)
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_struct_sizes():
+    assert ctypes.sizeof(cafgpu.Msg) == 56
+    assert ctypes.sizeof(cafgpu.Reply) == 24
+    assert cafgpu.DMSG_DTYPE.itemsize == 32
+    assert cafgpu.DREPLY_DTYPE.itemsize == 32
+    assert cafgpu.GEMM_DESC_DTYPE.itemsize == 32
+    assert cafgpu.LOG_DTYPE.itemsize == 40
+    assert ctypes.sizeof(cafgpu.RuntimeCfg) == 80
+
+
+def test_strerror_without_gpu():
+    L = cafgpu.load()
+    assert L.caf_gpu_strerror(cafgpu.EDEAD) == b"actor has terminated"
+
+
+def test_create_without_gpu_fails_loudly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(cafgpu.CafGpuError) as e:
+        cafgpu.Runtime(max_factor_n=1 << 20)
+    assert e.value.code == cafgpu.ECUDA
