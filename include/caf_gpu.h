@@ -128,6 +128,7 @@ typedef struct {
     int32_t  status;                /* CAF_GPU_REPLY_*                                         */
     uint32_t kind;
     uint64_t r0, r1;                /* FACTOR_U64: (p, q) with p <= q; GEMM: (0, n)            */
+    uint64_t t_done;                /* device clock when the reply was written (ns)            */
 } caf_gpu_reply;
 
 /* Device-resident message for caf_gpu_request_batch_device (32 bytes). */
@@ -155,7 +156,7 @@ typedef struct {
     int32_t  status;                /* CAF_GPU_REPLY_*                                         */
     uint32_t done;                  /* 1 once written                                          */
     uint64_t r0, r1;
-    uint64_t tag;
+    uint64_t t_done;                /* device clock (%globaltimer, ns) when the reply was written */
 } caf_gpu_dreply;
 
 /* One row of the validation-mode handling log. */
@@ -180,6 +181,8 @@ typedef struct {
     uint64_t gemm_tiles;            /* GEMM output tiles computed                               */
     uint32_t error_word;            /* nonzero: a bounded wait expired (code | site << 8)      */
     uint32_t pad;
+    uint64_t diag[2];               /* values the expired wait saw (for diagnosis)              */
+    uint64_t t_mark;                /* device clock of the last caf_gpu_mark (ns)               */
 } caf_gpu_stats;
 
 /* Create a runtime on the current CUDA device.  Builds the prime table used by
@@ -254,6 +257,11 @@ int caf_gpu_stats_read(caf_gpu_runtime *rt, caf_gpu_stats *out);
 
 /* Copy up to `cap` rows of the validation-mode handling log and clear it. */
 int caf_gpu_read_log(caf_gpu_runtime *rt, caf_gpu_log_row *out, uint32_t cap, uint32_t *count);
+
+/* Record the device clock (%globaltimer, ns) on the runtime stream, in stream
+ * order; caf_gpu_stats_read returns it as t_mark.  Replies carry the same
+ * clock in t_done, so t_done - t_mark is a message's latency from the mark. */
+int caf_gpu_mark(caf_gpu_runtime *rt);
 
 /* The runtime's CUDA stream (cudaStream_t). */
 void *caf_gpu_stream(caf_gpu_runtime *rt);

@@ -27,7 +27,7 @@ ACTOR_MASTER = 1
 
 DMSG_DTYPE = np.dtype([("actor", "<u4"), ("kind", "<u4"), ("sender", "<u4"), ("sender_seq", "<u4"),
                        ("u64", "<u8"), ("tag", "<u8")])
-DREPLY_DTYPE = np.dtype([("status", "<i4"), ("done", "<u4"), ("r0", "<u8"), ("r1", "<u8"), ("tag", "<u8")])
+DREPLY_DTYPE = np.dtype([("status", "<i4"), ("done", "<u4"), ("r0", "<u8"), ("r1", "<u8"), ("t_done", "<u8")])
 GEMM_DESC_DTYPE = np.dtype([("A", "<u8"), ("B", "<u8"), ("C", "<u8"), ("n", "<u4"), ("pad", "<u4")])
 LOG_DTYPE = np.dtype([("actor", "<u4"), ("sender", "<u4"), ("sender_seq", "<u4"), ("kind", "<u4"),
                       ("stamp", "<u8"), ("tag", "<u8"), ("value", "<u8")])
@@ -65,14 +65,15 @@ class Msg(ctypes.Structure):
 
 class Reply(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_uint32), ("r0", ctypes.c_uint64),
-                ("r1", ctypes.c_uint64)]
+                ("r1", ctypes.c_uint64), ("t_done", ctypes.c_uint64)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("messages", ctypes.c_uint64),
                 ("device_sends", ctypes.c_uint64), ("claims", ctypes.c_uint64),
                 ("factor_items", ctypes.c_uint64), ("prime_tests", ctypes.c_uint64),
-                ("gemm_tiles", ctypes.c_uint64), ("error_word", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("gemm_tiles", ctypes.c_uint64), ("error_word", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("diag0", ctypes.c_uint64), ("diag1", ctypes.c_uint64), ("t_mark", ctypes.c_uint64)]
 
 
 # Every symbol include/caf_gpu.h declares (checked by the CPU tests).
@@ -81,7 +82,7 @@ EXPORTS = [
     "caf_gpu_request", "caf_gpu_await", "caf_gpu_request_batch", "caf_gpu_await_batch",
     "caf_gpu_request_batch_device", "caf_gpu_sync", "caf_gpu_stream_sync", "caf_gpu_set_backend",
     "caf_gpu_reset_actors", "caf_gpu_actor_state", "caf_gpu_stats_read", "caf_gpu_read_log",
-    "caf_gpu_stream", "caf_gpu_prime_table", "caf_gpu_debug_wait_expiry", "caf_gpu_clear_error",
+    "caf_gpu_stream", "caf_gpu_mark", "caf_gpu_prime_table", "caf_gpu_debug_wait_expiry", "caf_gpu_clear_error",
     "caf_gpu_strerror",
 ]
 
@@ -120,6 +121,7 @@ def load(build: bool = True):
         "caf_gpu_prime_table": [vp, P(vp), P(u32)],
         "caf_gpu_debug_wait_expiry": [vp, u64],
         "caf_gpu_clear_error": [vp],
+        "caf_gpu_mark": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -208,7 +210,7 @@ class Runtime:
 
     def await_(self, handle: int, timeout_ns: int = 0):
         r = Reply()
-        _check(self.L.caf_gpu_await(self.h, handle, timeout_ns, ctypes.byref(r)), "caf_gpu_await")
+        self._diag(self.L.caf_gpu_await(self.h, handle, timeout_ns, ctypes.byref(r)), "caf_gpu_await")
         return r.status, r.r0, r.r1
 
     def try_await(self, handle: int, timeout_ns: int = 0):
@@ -225,12 +227,19 @@ class Runtime:
                                             out.ctypes.data), "caf_gpu_request_batch")
         return out
 
+    def _diag(self, code: int, what: str):
+        if code == EWAITLIMIT:
+            s = self.stats()
+            what = f"{what} [error_word={s['error_word']:#x} diag=({s['diag0']}, {s['diag1']})]"
+        _check(code, what)
+
     def await_batch(self, handles: np.ndarray, timeout_ns: int = 0):
         handles = np.ascontiguousarray(handles, dtype=np.uint64)
         out = (Reply * handles.size)()
-        _check(self.L.caf_gpu_await_batch(self.h, handles.ctypes.data, handles.size, timeout_ns,
-                                          ctypes.addressof(out)), "caf_gpu_await_batch")
-        a = np.frombuffer(out, dtype=np.dtype([("status", "<i4"), ("kind", "<u4"), ("r0", "<u8"), ("r1", "<u8")]))
+        self._diag(self.L.caf_gpu_await_batch(self.h, handles.ctypes.data, handles.size, timeout_ns,
+                                              ctypes.addressof(out)), "caf_gpu_await_batch")
+        a = np.frombuffer(out, dtype=np.dtype([("status", "<i4"), ("kind", "<u4"), ("r0", "<u8"), ("r1", "<u8"),
+                                               ("t_done", "<u8")]))
         return a.copy()
 
     def request_batch_device(self, d_msgs: int, count: int, d_replies: int) -> None:
@@ -239,10 +248,10 @@ class Runtime:
 
     # -- control --------------------------------------------------------------
     def sync(self):
-        _check(self.L.caf_gpu_sync(self.h), "caf_gpu_sync")
+        self._diag(self.L.caf_gpu_sync(self.h), "caf_gpu_sync")
 
     def stream_sync(self):
-        _check(self.L.caf_gpu_stream_sync(self.h), "caf_gpu_stream_sync")
+        self._diag(self.L.caf_gpu_stream_sync(self.h), "caf_gpu_stream_sync")
 
     def set_backend(self, backend: int):
         _check(self.L.caf_gpu_set_backend(self.h, backend), "caf_gpu_set_backend")
@@ -260,6 +269,9 @@ class Runtime:
         cnt = ctypes.c_uint32()
         _check(self.L.caf_gpu_read_log(self.h, out.ctypes.data, cap, ctypes.byref(cnt)), "caf_gpu_read_log")
         return out[:cnt.value].copy()
+
+    def mark(self):
+        _check(self.L.caf_gpu_mark(self.h), "caf_gpu_mark")
 
     def stream(self) -> int:
         return self.L.caf_gpu_stream(self.h) or 0

@@ -30,6 +30,7 @@
 namespace cafgpu {
 
 constexpr uint32_t FULL = 0xFFFFFFFFu;
+constexpr int kPrefetch = 4;   // table chunks of 32 primes in flight per warp
 
 struct MsgData {
     uint64_t payload;
@@ -43,8 +44,12 @@ __device__ __forceinline__ bool exit_requested(const DevCtl *ctl) {
            *((volatile const uint32_t *)&ctl->error_word) != 0;
 }
 
-__device__ __forceinline__ void fail(const DrainParams &P, uint32_t code, uint32_t site) {
-    raise_error(P.ctl, code, site);
+__device__ __forceinline__ void fail(const DrainParams &P, uint32_t code, uint32_t site, uint64_t d0 = 0,
+                                     uint64_t d1 = 0) {
+    if (atomicCAS(reinterpret_cast<unsigned int *>(&P.ctl->error_word), 0u, code | (site << 8)) == 0u) {
+        P.ctl->diag[0] = d0;
+        P.ctl->diag[1] = d1;
+    }
     if (P.hctl) st_release_sys(&P.hctl->error_word, *((volatile uint32_t *)&P.ctl->error_word));
     atomicExch(reinterpret_cast<unsigned int *>(&P.ctl->exit_flag), 1u);
 }
@@ -54,8 +59,11 @@ __device__ __forceinline__ void heartbeat(const DrainParams &P) {
 }
 
 // Warp-collective enqueue: every lane with `valid` holds one message for
-// actor `a`; lanes are in send order.  Returns false (all lanes) on a wait
-// that expired.
+// actor `a`; lanes are in send order.  Messages that fit are published, the
+// receiver is woken, and only then do lanes whose slot is still occupied wait
+// for the receiver to make room (waking first keeps a full mailbox from
+// waiting on a consumer that was never scheduled).  Returns false (all
+// lanes) on a wait that expired.
 __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const MsgData &m) {
     const uint32_t lane = lane_id();
     const uint32_t vmask = __ballot_sync(FULL, valid);
@@ -70,17 +78,12 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
     ActorDesc *A = valid ? &P.actors[a] : nullptr;
     if (valid && (int)lane == leader) t0 = add_u64(&A->tail, __popc(peers));
     t0 = __shfl_sync(FULL, t0, leader);
-    bool ok = true;
-    if (valid) {
-        const uint64_t t = t0 + rank;
-        const uint32_t mask = A->cap_mask;
-        if (t - *((volatile uint64_t *)&A->head) > mask) {
-            WaitClock w(P.wait_limit_ns);
-            while (t - *((volatile uint64_t *)&A->head) > mask) {
-                if (!w.again()) { ok = false; break; }
-            }
-        }
-        if (ok) {
+    const uint64_t t = t0 + rank;
+    const uint32_t mask = valid ? A->cap_mask : 0;
+    bool pending = valid;
+    WaitClock w(P.wait_limit_ns);
+    for (;;) {
+        if (pending && t - *((volatile uint64_t *)&A->head) <= mask) {
             Slot *s = &P.slots[A->slot_base + (t & mask)];
             s->payload = m.payload;
             s->reply_addr = m.reply_addr;
@@ -90,25 +93,28 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
             s->kind = m.kind;
             s->reply_token = m.reply_token;
             st_release_gpu(&s->seq, t + 1);
+            pending = false;
+        }
+        __syncwarp();
+        // wake the receiver (fence: Dekker pattern with release_actor)
+        asm volatile("fence.sc.gpu;" ::: "memory");
+        bool qok = true;
+        if (valid && (int)lane == leader) {
+            if (cas_u32(&A->state, kWaiting, kReady) == kWaiting)
+                qok = q_push(&P.ctl->readyq, P.readyq, a, P.wait_limit_ns);
+        }
+        if (!__all_sync(FULL, qok)) {
+            if (!qok) fail(P, kErrWaitQueue, 2, P.ctl->readyq.enq, a);
+            return false;
+        }
+        if (!__any_sync(FULL, pending)) return true;
+        bool expired = false;
+        if (pending) expired = !w.again();
+        if (__any_sync(FULL, expired)) {
+            if (expired) fail(P, kErrWaitSpace, 1, t, ((uint64_t)a << 32) | 1);
+            return false;
         }
     }
-    if (!__all_sync(FULL, ok)) {
-        if (lane == 0) fail(P, kErrWaitSpace, 1);
-        return false;
-    }
-    // wake the receiver after every peer has published (fence: Dekker pattern
-    // with the claim holder's park in release_actor)
-    asm volatile("fence.sc.gpu;" ::: "memory");
-    bool qok = true;
-    if (valid && (int)lane == leader) {
-        if (cas_u32(&A->state, kWaiting, kReady) == kWaiting)
-            qok = q_push(&P.ctl->readyq, P.readyq, a, P.wait_limit_ns);
-    }
-    if (!__all_sync(FULL, qok)) {
-        if (lane == 0) fail(P, kErrWaitQueue, 2);
-        return false;
-    }
-    return true;
 }
 
 // Park or re-queue an actor after its claim (warp-collective; lane 0 acts).
@@ -128,35 +134,42 @@ __device__ void release_actor(const DrainParams &P, uint32_t a, uint64_t new_hea
     __syncwarp();
 }
 
-// Dequeue up to `take` messages (<= 32) from the claimed actor: lane i reads
-// slot head + i.  Returns false if a slot was never published.
-__device__ bool warp_dequeue(const DrainParams &P, uint32_t a, uint64_t head, uint32_t take,
-                             MsgData &m) {
+// Dequeue from the claimed actor: of the next `want` (<= 32) tickets, take
+// the run of consecutive published slots starting at `head` (lane i reads
+// slot head + i).  A ticket may be taken before its slot is published, and a
+// producer may be waiting for room behind it, so only published slots are
+// taken; if none is, wait (bounded) for the first.  Returns the number taken,
+// 0 after an expired wait.
+__device__ uint32_t warp_dequeue(const DrainParams &P, uint32_t a, uint64_t head, uint32_t want,
+                                 MsgData &m) {
     const uint32_t lane = lane_id();
     ActorDesc *A = &P.actors[a];
-    bool ok = true;
-    if (lane < take) {
-        const uint64_t t = head + lane;
-        Slot *s = &P.slots[A->slot_base + (t & A->cap_mask)];
-        if (ld_acquire_gpu(&s->seq) != t + 1) {
+    const uint64_t t = head + lane;
+    Slot *s = &P.slots[A->slot_base + (t & A->cap_mask)];
+    bool pub = lane < want && ld_acquire_gpu(&s->seq) == t + 1;
+    uint32_t pm = __ballot_sync(FULL, pub);
+    if (!(pm & 1u)) {
+        bool ok = true;
+        if (lane == 0) {
             WaitClock w(P.wait_limit_ns);
             while (ld_acquire_gpu(&s->seq) != t + 1) {
                 if (!w.again()) { ok = false; break; }
             }
+            if (!ok) fail(P, kErrWaitSlot, 4, t + 1, ld_acquire_gpu(&s->seq));
         }
-        if (ok) {
-            m.payload = s->payload;
-            m.reply_addr = s->reply_addr;
-            m.tag = s->tag;
-            m.sender = s->sender;
-            m.sender_seq = s->sender_seq;
-            m.kind = s->kind;
-            m.reply_token = s->reply_token;
-        }
+        if (!__shfl_sync(FULL, ok, 0)) return 0;
+        pub = lane < want && ld_acquire_gpu(&s->seq) == t + 1;
+        pm = __ballot_sync(FULL, pub) | 1u;
     }
-    if (!__all_sync(FULL, ok)) {
-        if (lane == 0) fail(P, kErrWaitSlot, 4);
-        return false;
+    const uint32_t take = (pm == FULL) ? 32u : (uint32_t)(__ffs(~pm) - 1);
+    if (lane < take) {
+        m.payload = s->payload;
+        m.reply_addr = s->reply_addr;
+        m.tag = s->tag;
+        m.sender = s->sender;
+        m.sender_seq = s->sender_seq;
+        m.kind = s->kind;
+        m.reply_token = s->reply_token;
     }
     if (P.validation) {
         uint64_t base = 0;
@@ -173,7 +186,7 @@ __device__ bool warp_dequeue(const DrainParams &P, uint32_t a, uint64_t head, ui
             r->value = m.payload;
         }
     }
-    return true;
+    return take;
 }
 
 // ---------------------------------------------------------------------------
@@ -202,6 +215,24 @@ __device__ void finalize_batch(const DrainParams &P, uint32_t b) {
     __syncwarp();
 }
 
+// Remove from the warp every slot whose bit is set in `mask` (highest first).
+__device__ __forceinline__ void sweep_remove_mask(SweepRegs &s, uint32_t mask) {
+    while (mask) {
+        const int j = 31 - __clz(mask);
+        mask &= ~(1u << j);
+        sweep_remove(s, j);
+    }
+}
+
+// Smallest bound (min) and largest bound (max) among the held slots.
+__device__ __forceinline__ void sweep_bounds(const SweepRegs &s, const FactorBatch *B, uint32_t *mn,
+                                             uint32_t *mx) {
+    const uint32_t lane = lane_id();
+    const uint32_t pb = (int)lane < s.k ? B->pbound[slot_id(s, lane)] : 0u;
+    *mn = __reduce_min_sync(FULL, (int)lane < s.k ? pb : 0xFFFFFFFFu);
+    *mx = __reduce_max_sync(FULL, pb);
+}
+
 // Run work item (b, w): ranges w, w+W, w+2W, ... of kRangePrimes primes each.
 __device__ void factor_item(const DrainParams &P, uint32_t b, uint32_t w) {
     const uint32_t lane = lane_id();
@@ -209,27 +240,26 @@ __device__ void factor_item(const DrainParams &P, uint32_t b, uint32_t w) {
     const uint32_t cnt = B->count;
     SweepRegs s;
     s.k = 0;
+    s.ids = 0;
 #pragma unroll
     for (int j = 0; j < (int)kFactorKMax; ++j) {
-        s.n[j] = 0; s.nl[j] = 0; s.pb[j] = 0; s.id[j] = 0;
+        s.n[j] = 0;
+        s.nl[j] = 0;
     }
 #pragma unroll
     for (int j = 0; j < (int)kFactorKMax; ++j) {
         if (j < (int)cnt) {
-            const uint32_t pb = B->pbound[j];
             const bool even = (B->even_mask >> j) & 1u;
-            if (pb > 0 && !even) {
+            if (B->pbound[j] > 0 && !even) {
                 const uint64_t n = B->n[j];
-                // place at slot k (k <= j, static unrolled select)
 #pragma unroll
                 for (int i = 0; i <= j; ++i) {
                     if (i == s.k) {
                         s.n[i] = n;
                         s.nl[i] = 0u - (uint32_t)n;
-                        s.pb[i] = pb;
-                        s.id[i] = (uint32_t)j;
                     }
                 }
+                s.ids |= (uint64_t)j << (4 * s.k);
                 ++s.k;
             }
         }
@@ -239,64 +269,62 @@ __device__ void factor_item(const DrainParams &P, uint32_t b, uint32_t w) {
     for (uint32_t r = w; s.k > 0; r += W) {
         const uint32_t start = r * kRangePrimes;
         // drop messages decided below this range or whose bound ends before it
-        for (int j = s.k - 1; j >= 0; --j) {
-            uint32_t pbj = 0, idj = 0;
-#pragma unroll
-            for (int i = 0; i < (int)kFactorKMax; ++i)
-                if (i == j) { pbj = s.pb[i]; idj = s.id[i]; }
-            uint32_t f = 0;
-            if (lane == 0) f = *((volatile uint32_t *)&B->found[idj]);
-            f = __shfl_sync(FULL, f, 0);
-            if (f < start || pbj <= start) sweep_remove(s, j);
+        {
+            bool rm = false;
+            if ((int)lane < s.k) {
+                const uint32_t id = slot_id(s, lane);
+                rm = *((volatile uint32_t *)&B->found[id]) < start || B->pbound[id] <= start;
+            }
+            sweep_remove_mask(s, __ballot_sync(FULL, rm));
         }
         if (s.k == 0) break;
-        uint32_t end = 0;
-#pragma unroll
-        for (int i = 0; i < (int)kFactorKMax; ++i)
-            if (i < s.k) end = max(end, s.pb[i]);
+        uint32_t next_drop, end;
+        sweep_bounds(s, B, &next_drop, &end);
         end = min(end, start + kRangePrimes);
-        uint32_t next_drop = 0xFFFFFFFFu;
+        // Software pipeline over the table: the (p, pinv, plim) of chunk
+        // c + kPrefetch*32 are loaded while chunk c is tested.  Loads run at
+        // most 2*kPrefetch*32 entries past `end` (<= nprimes); the table is
+        // padded beyond that with zeros.
+        uint32_t rp[kPrefetch], ri[kPrefetch], rl[kPrefetch];
 #pragma unroll
-        for (int i = 0; i < (int)kFactorKMax; ++i)
-            if (i < s.k) next_drop = min(next_drop, s.pb[i]);
-        for (uint32_t c = start; c < end; c += 32) {
-            const uint32_t idx = c + lane;
-            const uint32_t p = __ldg(P.primes + idx);
-            const uint32_t pinv = __ldg(P.pinv + idx);
-            const uint32_t plim = __ldg(P.plim + idx);
-            const uint32_t hits = sweep_chunk(s, p, pinv, plim);
-            tests += (uint64_t)s.k * 32u;
-            if (__any_sync(FULL, hits != 0)) {
-                uint32_t any = __reduce_or_sync(FULL, hits);
-                // remove from the highest slot down so lower positions stay valid
-                for (int j = 31 - __clz(any); any; j = 31 - __clz(any)) {
-                    any &= ~(1u << j);
-                    const uint32_t mine = ((hits >> j) & 1u) ? idx : 0xFFFFFFFFu;
-                    const uint32_t mn = __reduce_min_sync(FULL, mine);
-                    uint32_t idj = 0;
+        for (int u = 0; u < kPrefetch; ++u) {
+            const uint32_t idx = start + u * 32 + lane;
+            rp[u] = __ldg(P.primes + idx);
+            ri[u] = __ldg(P.pinv + idx);
+            rl[u] = __ldg(P.plim + idx);
+        }
+        bool stop = false;
+        for (uint32_t c0 = start; c0 < end && !stop; c0 += 32 * kPrefetch) {
 #pragma unroll
-                    for (int i = 0; i < (int)kFactorKMax; ++i)
-                        if (i == j) idj = s.id[i];
-                    if (lane == 0) atomicMin(reinterpret_cast<unsigned int *>(&B->found[idj]), mn);
-                    sweep_remove(s, j);
+            for (int u = 0; u < kPrefetch; ++u) {
+                const uint32_t c = c0 + u * 32;
+                const uint32_t p = rp[u], pinv = ri[u], plim = rl[u];
+                const uint32_t nidx = c + kPrefetch * 32 + lane;
+                rp[u] = __ldg(P.primes + nidx);
+                ri[u] = __ldg(P.pinv + nidx);
+                rl[u] = __ldg(P.plim + nidx);
+                if (stop || c >= end) continue;
+                const uint32_t hits = sweep_chunk(s, p, pinv, plim);
+                tests += (uint64_t)s.k * 32u;
+                if (__any_sync(FULL, hits != 0)) {
+                    const uint32_t any = __reduce_or_sync(FULL, hits);
+                    const uint32_t idx = c + lane;
+                    for (uint32_t m = any; m; m &= m - 1) {
+                        const int j = __ffs(m) - 1;
+                        const uint32_t mn = __reduce_min_sync(FULL, ((hits >> j) & 1u) ? idx : 0xFFFFFFFFu);
+                        if (lane == 0) atomicMin(reinterpret_cast<unsigned int *>(&B->found[slot_id(s, j)]), mn);
+                    }
+                    sweep_remove_mask(s, any);
+                    if (s.k == 0) { stop = true; continue; }
                 }
-                if (s.k == 0) break;
-            }
-            if (c + 32 >= next_drop) {
-                for (int j = s.k - 1; j >= 0; --j) {
-                    uint32_t pbj = 0;
-#pragma unroll
-                    for (int i = 0; i < (int)kFactorKMax; ++i)
-                        if (i == j) pbj = s.pb[i];
-                    if (pbj <= c + 32) sweep_remove(s, j);
+                if (c + 32 >= next_drop) {
+                    bool rm = false;
+                    if ((int)lane < s.k) rm = B->pbound[slot_id(s, lane)] <= c + 32;
+                    sweep_remove_mask(s, __ballot_sync(FULL, rm));
+                    if (s.k == 0) { stop = true; continue; }
+                    sweep_bounds(s, B, &next_drop, &end);
+                    end = min(end, start + kRangePrimes);
                 }
-                if (s.k == 0) break;
-                next_drop = 0xFFFFFFFFu;
-                end = 0;
-#pragma unroll
-                for (int i = 0; i < (int)kFactorKMax; ++i)
-                    if (i < s.k) { next_drop = min(next_drop, s.pb[i]); end = max(end, s.pb[i]); }
-                end = min(end, start + kRangePrimes);
             }
         }
         if ((r & 15u) == 0 && lane == 0) heartbeat(P);
@@ -326,9 +354,10 @@ __device__ void claim_factor(const DrainParams &P, uint32_t a, uint32_t b) {
     uint32_t limit = P.factor_k;
     if (P.max_claim && P.max_claim < limit) limit = P.max_claim;
     const uint64_t avail = tail - head;
-    const uint32_t take = avail < limit ? (uint32_t)avail : limit;
+    const uint32_t want = avail < limit ? (uint32_t)avail : limit;
     MsgData m{};
-    if (take == 0 || !warp_dequeue(P, a, head, take, m)) {
+    const uint32_t take = want ? warp_dequeue(P, a, head, want, m) : 0u;
+    if (take == 0) {
         release_actor(P, a, head);
         if (lane == 0) q_push(&P.ctl->freeq, P.freeq, b, P.wait_limit_ns);
         return;
@@ -429,7 +458,7 @@ __device__ void claim_ring(const DrainParams &P, uint32_t a) {
     if (lane == 0) add_u64(&P.ctl->claims, 1);
     for (uint64_t i = 0; i < take; ++i) {
         MsgData m{};
-        if (!warp_dequeue(P, a, head, 1, m)) return;
+        if (warp_dequeue(P, a, head, 1, m) == 0) return;
         m.payload = __shfl_sync(FULL, m.payload, 0);
         m.kind = __shfl_sync(FULL, m.kind, 0);
         m.reply_addr = __shfl_sync(FULL, m.reply_addr, 0);
@@ -557,7 +586,7 @@ __device__ __forceinline__ bool quiescent(const DrainParams &P) {
     return c == i;
 }
 
-__global__ void __launch_bounds__(kThreads) k_drain(DrainParams P) {
+__global__ void __launch_bounds__(kThreads, 2) k_drain(DrainParams P) {
     const uint32_t lane = lane_id();
     const uint32_t gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
     DevCtl *ctl = P.ctl;
@@ -638,8 +667,9 @@ __global__ void __launch_bounds__(kThreads) k_drain(DrainParams P) {
         } else {
             const uint64_t hb = *((volatile uint64_t *)&ctl->heartbeat);
             const uint64_t last = hb > idle_start ? hb : idle_start;
-            if (now - last > P.wait_limit_ns) {
-                if (lane == 0) fail(P, kErrStall, 8);
+            // another warp's heartbeat may be newer than `now`
+            if (last < now && now - last > P.wait_limit_ns) {
+                if (lane == 0) fail(P, kErrStall, 8, ld_acquire_gpu(&ctl->ingested), ld_acquire_gpu(&ctl->completed));
                 break;
             }
         }
@@ -760,6 +790,9 @@ __global__ void k_reset_actors(ActorDesc *actors, uint32_t n_actors) {
         A->head = A->tail;
     }
 }
+
+// Record the device clock in stream order.
+__global__ void k_mark(DevCtl *ctl) { ctl->t_mark = globaltimer(); }
 
 // Reset the counters a drain launch reads (stream-ordered).
 __global__ void k_reset_ctl(DevCtl *ctl) {
@@ -901,6 +934,11 @@ namespace cafgpu {
 
 cudaError_t launch_drain(const DrainParams &p, unsigned grid, cudaStream_t stream) {
     k_drain<<<grid, kThreads, 0, stream>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mark(DevCtl *ctl, cudaStream_t stream) {
+    k_mark<<<1, 1, 0, stream>>>(ctl);
     return cudaGetLastError();
 }
 

@@ -79,13 +79,13 @@ __device__ __forceinline__ void factor_result(uint64_t n, bool even, uint32_t fo
 }
 
 __device__ __forceinline__ void write_reply(uint64_t addr, int32_t status, uint64_t r0, uint64_t r1,
-                                            uint64_t tag, uint32_t token) {
+                                            uint64_t /*tag*/, uint32_t token) {
     if (!addr) return;
     Reply *r = reinterpret_cast<Reply *>(addr);
     r->status = status;
     r->r0 = r0;
     r->r1 = r1;
-    r->tag = tag;
+    r->t_done = globaltimer();
     st_release_sys(&r->done, token);
 }
 
@@ -101,10 +101,13 @@ __device__ __forceinline__ void write_reply(uint64_t addr, int32_t status, uint6
 struct SweepRegs {
     uint64_t n[kFactorKMax];
     uint32_t nl[kFactorKMax];   // -n mod 2^32
-    uint32_t pb[kFactorKMax];   // bound
-    uint32_t id[kFactorKMax];   // message index in the batch
+    uint64_t ids;               // 4 bits per slot: message index in the batch
     int k;
 };
+
+__device__ __forceinline__ uint32_t slot_id(const SweepRegs &s, int j) {
+    return (uint32_t)(s.ids >> (4 * j)) & 15u;
+}
 
 // Remove slot p (0 <= p < k) keeping the others in order.
 __device__ __forceinline__ void sweep_remove(SweepRegs &s, int p) {
@@ -113,10 +116,11 @@ __device__ __forceinline__ void sweep_remove(SweepRegs &s, int p) {
         if (i >= p) {
             s.n[i] = s.n[i + 1];
             s.nl[i] = s.nl[i + 1];
-            s.pb[i] = s.pb[i + 1];
-            s.id[i] = s.id[i + 1];
         }
     }
+    const uint64_t low = (p == 0) ? 0ull : (s.ids & ((1ull << (4 * p)) - 1ull));
+    const uint64_t high = (p >= 15) ? 0ull : ((s.ids >> (4 * (p + 1))) << (4 * p));
+    s.ids = low | high;
     --s.k;
 }
 

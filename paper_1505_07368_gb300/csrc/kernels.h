@@ -10,6 +10,7 @@ namespace cafgpu {
 
 cudaError_t launch_drain(const DrainParams &p, unsigned grid, cudaStream_t stream);
 cudaError_t launch_reset_ctl(DevCtl *ctl, cudaStream_t stream);
+cudaError_t launch_mark(DevCtl *ctl, cudaStream_t stream);
 cudaError_t launch_factor_one(uint64_t n, const uint32_t *primes, const uint32_t *pinv,
                               const uint32_t *plim, uint32_t nprimes, uint64_t reply_addr,
                               uint32_t reply_token, uint64_t tag, uint32_t *scratch, DevCtl *ctl,

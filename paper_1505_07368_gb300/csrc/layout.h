@@ -111,7 +111,7 @@ struct Reply {
     int32_t status;
     uint32_t done;
     uint64_t r0, r1;
-    uint64_t tag;
+    uint64_t t_done;               // %globaltimer when written
 };
 static_assert(sizeof(Reply) == 32, "Reply is 32 bytes");
 
@@ -166,9 +166,11 @@ struct DevCtl {
     uint32_t routers_done;
     uint32_t pad2;
     uint64_t heartbeat;            // %globaltimer of the last progress report
+    uint64_t diag[2];              // first failure: values seen by the expired wait
+    uint64_t t_mark;               // %globaltimer written by k_mark
     // statistics
     uint64_t claims, factor_items, prime_tests, gemm_tiles, device_sends, messages;
-    uint64_t pad3[8];
+    uint64_t pad3[5];
     QueueHdr readyq;
     QueueHdr freeq;
     QueueHdr workq;

@@ -618,6 +618,7 @@ int caf_gpu_await(caf_gpu_runtime *rt, caf_gpu_handle h, uint64_t timeout_ns, ca
     out->kind = 0;
     out->r0 = r.r0;
     out->r1 = r.r1;
+    out->t_done = r.t_done;
     std::lock_guard<std::mutex> g(rt->mu);
     rt->in_use[slot] = 0;
     rt->free_slots.push_back(slot);
@@ -714,6 +715,9 @@ int caf_gpu_stats_read(caf_gpu_runtime *rt, caf_gpu_stats *out) {
     out->gemm_tiles = c.gemm_tiles - l.gemm_tiles;
     out->error_word = c.error_word;
     out->pad = 0;
+    out->diag[0] = c.diag[0];
+    out->diag[1] = c.diag[1];
+    out->t_mark = c.t_mark;
     rt->last_stats = c;
     rt->launches = 0;
     return 0;
@@ -731,6 +735,14 @@ int caf_gpu_read_log(caf_gpu_runtime *rt, caf_gpu_log_row *out, uint32_t cap, ui
     const uint64_t zero = 0;
     CK(cudaMemcpy(&rt->d_ctl->log_count, &zero, sizeof(zero), cudaMemcpyHostToDevice));
     *count = m;
+    return 0;
+}
+
+int caf_gpu_mark(caf_gpu_runtime *rt) {
+    if (!rt) return CAF_GPU_EINVAL;
+    std::lock_guard<std::mutex> g(rt->mu);
+    CK(launch_mark(rt->d_ctl, rt->stream));
+    rt->launches += 1;
     return 0;
 }
 

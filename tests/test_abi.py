@@ -31,7 +31,7 @@ def test_library_builds_and_exports_every_symbol():
 
 def test_struct_sizes():
     assert ctypes.sizeof(cafgpu.Msg) == 56
-    assert ctypes.sizeof(cafgpu.Reply) == 24
+    assert ctypes.sizeof(cafgpu.Reply) == 32
     assert cafgpu.DMSG_DTYPE.itemsize == 32
     assert cafgpu.DREPLY_DTYPE.itemsize == 32
     assert cafgpu.GEMM_DESC_DTYPE.itemsize == 32

@@ -18,7 +18,9 @@ MAX32 = (1 << 32) - 1
 
 
 def _small_factor_workload(n_actors, count, seed=7):
-    wl = W.config2(seed=seed, n_actors=n_actors, lo=1 << 12, hi=1 << 16, max_messages=count)
+    wl = W.config2(seed=seed, n_actors=n_actors, lo=1 << 12, hi=1 << 16, max_messages=count,
+                   mean_len=max(64.0, 2.0 * count / n_actors))
+    assert wl.count == count
     return wl
 
 
