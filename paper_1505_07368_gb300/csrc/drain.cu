@@ -30,7 +30,6 @@
 namespace cafgpu {
 
 constexpr uint32_t FULL = 0xFFFFFFFFu;
-constexpr int kPrefetch = 4;   // table chunks of 32 primes in flight per warp
 
 struct MsgData {
     uint64_t payload;
@@ -224,89 +223,127 @@ __device__ __forceinline__ void sweep_remove_mask(SweepRegs &s, uint32_t mask) {
     }
 }
 
-// Smallest bound (min) and largest bound (max) among the held slots.
-__device__ __forceinline__ void sweep_bounds(const SweepRegs &s, const FactorBatch *B, uint32_t *mn,
-                                             uint32_t *mx) {
+// Smallest bound among the held slots.
+__device__ __forceinline__ uint32_t sweep_min_bound(const SweepRegs &s, const FactorBatch *B) {
     const uint32_t lane = lane_id();
-    const uint32_t pb = (int)lane < s.k ? B->pbound[slot_id(s, lane)] : 0u;
-    *mn = __reduce_min_sync(FULL, (int)lane < s.k ? pb : 0xFFFFFFFFu);
-    *mx = __reduce_max_sync(FULL, pb);
+    const uint32_t pb = (int)lane < s.k ? B->pbound[slot_id(s, lane)] : 0xFFFFFFFFu;
+    return __reduce_min_sync(FULL, pb);
 }
 
-// Run work item (b, w): ranges w, w+W, w+2W, ... of kRangePrimes primes each.
-__device__ void factor_item(const DrainParams &P, uint32_t b, uint32_t w) {
+__device__ __forceinline__ void named_bar_sync(uint32_t id, uint32_t nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait on an mbarrier phase; false (and an error recorded) on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(const DrainParams &P, uint64_t *bar, uint32_t parity,
+                                                  uint32_t site) {
+    if (mbar_try_wait(bar, parity)) return true;
+    WaitClock wc(P.wait_limit_ns);
+    while (!mbar_try_wait(bar, parity)) {
+        if (!wc.again()) {
+            fail(P, kErrWaitTable, site, parity, 0);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Table producer (one lane of the producer warp): streams tiles 0, 1, ... of
+// the prime table into the CTA ring until the group's bound is reached or no
+// consumer holds a message, then ends the stream with a tile that carries no
+// data (its full barrier is completed by a plain arrive; final_tile marks it).
+// `t` counts ring tiles over the whole kernel; stage = t % kStages, use = t / kStages.
+__device__ void group_produce(const DrainParams &P, GroupShared &G, uint32_t &t) {
+    const uint32_t limit = G.limit_tiles;
+    bool ok = true;
+    for (uint32_t i = 0;; ++i, ++t) {
+        const uint32_t st = t % kStages;
+        const uint32_t use = t / kStages;
+        if (use >= 1 && ok) ok = mbar_wait_bounded(P, &G.empty[st], (use - 1) & 1u, 12);
+        if (!ok || i >= limit || *((volatile uint32_t *)&G.active) == 0) {
+            *((volatile uint32_t *)&G.final_tile) = i;
+            mbar_arrive(&G.full[st]);
+            ++t;
+            return;
+        }
+        const uint32_t i0 = i * kTile;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&G.full[st], 3 * kTile * 4);
+        bulk_g2s(G.tile[st].p, P.primes + i0, kTile * 4, &G.full[st]);
+        bulk_g2s(G.tile[st].pinv, P.pinv + i0, kTile * 4, &G.full[st]);
+        bulk_g2s(G.tile[st].plim, P.plim + i0, kTile * 4, &G.full[st]);
+    }
+}
+
+// Consumer warp: sweep batch b (kNone: only keep the ring moving) over the
+// streamed tiles.  A team of `wpb` warps shares one batch; member `r` tests
+// the chunks u of each tile with u % wpb == r, and members drop messages that
+// another member has already decided below their position.
+__device__ void group_consume(const DrainParams &P, GroupShared &G, uint32_t &t, uint32_t b, uint32_t r,
+                              uint32_t wpb) {
     const uint32_t lane = lane_id();
-    FactorBatch *B = &P.batches[b];
-    const uint32_t cnt = B->count;
+    FactorBatch *B = (b != kNone) ? &P.batches[b] : nullptr;
     SweepRegs s;
-    s.k = 0;
-    s.ids = 0;
+    sweep_init(s);
+    if (B) {
+        const uint32_t cnt = B->count;
 #pragma unroll
-    for (int j = 0; j < (int)kFactorKMax; ++j) {
-        s.n[j] = 0;
-        s.nl[j] = 0;
-    }
+        for (int j = 0; j < (int)kFactorKMax; ++j) {
+            if (j < (int)cnt) {
+                const bool even = (B->even_mask >> j) & 1u;
+                if (B->pbound[j] > 0 && !even) {
+                    const uint64_t n = B->n[j];
 #pragma unroll
-    for (int j = 0; j < (int)kFactorKMax; ++j) {
-        if (j < (int)cnt) {
-            const bool even = (B->even_mask >> j) & 1u;
-            if (B->pbound[j] > 0 && !even) {
-                const uint64_t n = B->n[j];
-#pragma unroll
-                for (int i = 0; i <= j; ++i) {
-                    if (i == s.k) {
-                        s.n[i] = n;
-                        s.nl[i] = 0u - (uint32_t)n;
-                    }
+                    for (int i = 0; i <= j; ++i)
+                        if (i == s.k) sweep_set(s, i, n);
+                    s.ids |= (uint64_t)j << (4 * s.k);
+                    ++s.k;
                 }
-                s.ids |= (uint64_t)j << (4 * s.k);
-                ++s.k;
             }
         }
     }
-    const uint32_t W = P.factor_w;
+    bool counted = B != nullptr;   // included in G.active
+    if (counted && s.k == 0) {
+        if (lane == 0) atomicSub(&G.active, 1u);
+        counted = false;
+    }
+    uint32_t next_drop = s.k > 0 ? sweep_min_bound(s, B) : 0xFFFFFFFFu;
     uint64_t tests = 0;
-    for (uint32_t r = w; s.k > 0; r += W) {
-        const uint32_t start = r * kRangePrimes;
-        // drop messages decided below this range or whose bound ends before it
-        {
-            bool rm = false;
-            if ((int)lane < s.k) {
-                const uint32_t id = slot_id(s, lane);
-                rm = *((volatile uint32_t *)&B->found[id]) < start || B->pbound[id] <= start;
+    for (uint32_t i = 0;; ++i, ++t) {
+        const uint32_t st = t % kStages;
+        const bool ok = mbar_wait_bounded(P, &G.full[st], (t / kStages) & 1u, 13);
+        if (!__all_sync(FULL, ok)) break;
+        const uint32_t fin = *((volatile uint32_t *)&G.final_tile);
+        if (i >= fin) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&G.empty[st]);
+            ++t;
+            break;
+        }
+        if (s.k > 0) {
+            const uint32_t start = i * kTile;
+            if (wpb > 1 && (i & 3u) == 0) {
+                bool rm = false;
+                if ((int)lane < s.k) rm = *((volatile uint32_t *)&B->found[slot_id(s, lane)]) < start;
+                sweep_remove_mask(s, __ballot_sync(FULL, rm));
+                if (s.k > 0) next_drop = sweep_min_bound(s, B);
             }
-            sweep_remove_mask(s, __ballot_sync(FULL, rm));
-        }
-        if (s.k == 0) break;
-        uint32_t next_drop, end;
-        sweep_bounds(s, B, &next_drop, &end);
-        end = min(end, start + kRangePrimes);
-        // Software pipeline over the table: the (p, pinv, plim) of chunk
-        // c + kPrefetch*32 are loaded while chunk c is tested.  Loads run at
-        // most 2*kPrefetch*32 entries past `end` (<= nprimes); the table is
-        // padded beyond that with zeros.
-        uint32_t rp[kPrefetch], ri[kPrefetch], rl[kPrefetch];
-#pragma unroll
-        for (int u = 0; u < kPrefetch; ++u) {
-            const uint32_t idx = start + u * 32 + lane;
-            rp[u] = __ldg(P.primes + idx);
-            ri[u] = __ldg(P.pinv + idx);
-            rl[u] = __ldg(P.plim + idx);
-        }
-        bool stop = false;
-        for (uint32_t c0 = start; c0 < end && !stop; c0 += 32 * kPrefetch) {
-#pragma unroll
-            for (int u = 0; u < kPrefetch; ++u) {
-                const uint32_t c = c0 + u * 32;
-                const uint32_t p = rp[u], pinv = ri[u], plim = rl[u];
-                const uint32_t nidx = c + kPrefetch * 32 + lane;
-                rp[u] = __ldg(P.primes + nidx);
-                ri[u] = __ldg(P.pinv + nidx);
-                rl[u] = __ldg(P.plim + nidx);
-                if (stop || c >= end) continue;
-                const uint32_t hits = sweep_chunk(s, p, pinv, plim);
+            const TableTile &T = G.tile[st];
+            // one copy of the chunk body: the test switch is large, and an
+            // unrolled tile loop overflows the instruction cache
+#pragma unroll 1
+            for (uint32_t u = r; u < kTile / 32 && s.k > 0; u += wpb) {
+                const uint32_t c = start + u * 32;
+                const uint32_t p = T.p[u * 32 + lane];
+                const uint32_t pinv = T.pinv[u * 32 + lane];
+                const uint32_t plim = T.plim[u * 32 + lane];
                 tests += (uint64_t)s.k * 32u;
-                if (__any_sync(FULL, hits != 0)) {
+                if (__any_sync(FULL, sweep_chunk(s, p, pinv, plim))) {
+                    const uint32_t hits = sweep_which(s, p, pinv, plim);
                     const uint32_t any = __reduce_or_sync(FULL, hits);
                     const uint32_t idx = c + lane;
                     for (uint32_t m = any; m; m &= m - 1) {
@@ -315,36 +352,43 @@ __device__ void factor_item(const DrainParams &P, uint32_t b, uint32_t w) {
                         if (lane == 0) atomicMin(reinterpret_cast<unsigned int *>(&B->found[slot_id(s, j)]), mn);
                     }
                     sweep_remove_mask(s, any);
-                    if (s.k == 0) { stop = true; continue; }
                 }
-                if (c + 32 >= next_drop) {
+                if (s.k > 0 && c + 32 * wpb >= next_drop) {
                     bool rm = false;
-                    if ((int)lane < s.k) rm = B->pbound[slot_id(s, lane)] <= c + 32;
+                    if ((int)lane < s.k) rm = B->pbound[slot_id(s, lane)] <= c + 32 * wpb;
                     sweep_remove_mask(s, __ballot_sync(FULL, rm));
-                    if (s.k == 0) { stop = true; continue; }
-                    sweep_bounds(s, B, &next_drop, &end);
-                    end = min(end, start + kRangePrimes);
+                    if (s.k > 0) next_drop = sweep_min_bound(s, B);
                 }
             }
+            if (s.k == 0 && counted) {
+                if (lane == 0) atomicSub(&G.active, 1u);
+                counted = false;
+            }
+            if (lane == 0 && (i & 255u) == 0) heartbeat(P);
         }
-        if ((r & 15u) == 0 && lane == 0) heartbeat(P);
-        if (exit_requested(P.ctl)) break;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&G.empty[st]);
     }
-    if (lane == 0) {
-        add_u64(&P.ctl->prime_tests, tests);
-        add_u64(&P.ctl->factor_items, 1);
+    if (counted && lane == 0) atomicSub(&G.active, 1u);   // left early after an error
+    if (B) {
+        if (lane == 0) {
+            add_u64(&P.ctl->prime_tests, tests);
+            add_u64(&P.ctl->factor_items, 1);
+        }
+        uint32_t left = 0;
+        if (lane == 0) {
+            __threadfence();
+            left = atomicSub(reinterpret_cast<unsigned int *>(&B->items_left), 1u);
+        }
+        left = __shfl_sync(FULL, left, 0);
+        if (left == 1) finalize_batch(P, b);
     }
-    uint32_t left = 0;
-    if (lane == 0) {
-        __threadfence();
-        left = atomicSub(reinterpret_cast<unsigned int *>(&B->items_left), 1u);
-    }
-    left = __shfl_sync(FULL, left, 0);
-    if (left == 1) finalize_batch(P, b);
 }
 
-// Claim a factor actor: move up to K messages into batch b and schedule it.
-__device__ void claim_factor(const DrainParams &P, uint32_t a, uint32_t b) {
+// Claim a factor actor: move up to K messages into batch b.  Returns b when
+// the batch needs a sweep (the caller's team runs it), kNone when every
+// message was answered at once or nothing could be taken.
+__device__ uint32_t claim_factor(const DrainParams &P, uint32_t a, uint32_t b) {
     const uint32_t lane = lane_id();
     ActorDesc *A = &P.actors[a];
     if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
@@ -360,7 +404,7 @@ __device__ void claim_factor(const DrainParams &P, uint32_t a, uint32_t b) {
     if (take == 0) {
         release_actor(P, a, head);
         if (lane == 0) q_push(&P.ctl->freeq, P.freeq, b, P.wait_limit_ns);
-        return;
+        return kNone;
     }
     release_actor(P, a, head + take);
     FactorBatch *B = &P.batches[b];
@@ -389,17 +433,9 @@ __device__ void claim_factor(const DrainParams &P, uint32_t a, uint32_t b) {
     __syncwarp();
     if (maxb == 0) {
         finalize_batch(P, b);
-        return;
+        return kNone;
     }
-    if (lane == 0) {
-        __threadfence();
-        for (uint32_t w = 0; w < P.factor_w; ++w)
-            if (!q_push(&P.ctl->workq, P.workq, (b << 8) | w, P.wait_limit_ns)) {
-                fail(P, kErrWaitQueue, 6);
-                break;
-            }
-    }
-    __syncwarp();
+    return b;
 }
 
 // ---------------------------------------------------------------------------
@@ -586,62 +622,51 @@ __device__ __forceinline__ bool quiescent(const DrainParams &P) {
     return c == i;
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_drain(DrainParams P) {
+// A team leader looks for a factor batch to sweep: pop ready actors, claim
+// factor actors into a fresh batch record, and run ring-token actors on the
+// way (a few at most, so the group forms quickly).
+__device__ uint32_t find_batch(const DrainParams &P) {
     const uint32_t lane = lane_id();
-    const uint32_t gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
     DevCtl *ctl = P.ctl;
-    const bool agent = P.live && gw == 0;
-    if (P.batch_count && gw < P.n_routers) {
-        route_batch(P, gw);
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence();
-            add_u32(&ctl->routers_done, 1);
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        uint32_t a = 0;
+        bool got = false;
+        if (lane == 0) got = q_try_pop(&ctl->readyq, P.readyq, &a);
+        got = __shfl_sync(FULL, got, 0);
+        if (!got) return kNone;
+        a = __shfl_sync(FULL, a, 0);
+        const uint32_t kind = P.actors[a].kind;
+        if (kind == kFactor) {
+            uint32_t b = 0;
+            bool gb = false;
+            if (lane == 0) gb = q_try_pop(&ctl->freeq, P.freeq, &b);
+            gb = __shfl_sync(FULL, gb, 0);
+            if (!gb) {
+                // no batch record free: leave the actor READY for later
+                if (lane == 0 && !q_push(&ctl->readyq, P.readyq, a, P.wait_limit_ns)) fail(P, kErrWaitQueue, 7);
+                __syncwarp();
+                return kNone;
+            }
+            const uint32_t r = claim_factor(P, a, __shfl_sync(FULL, b, 0));
+            if (r != kNone) return r;
+        } else if (kind == kToken) {
+            claim_ring(P, a);
         }
+        if (exit_requested(ctl)) return kNone;
     }
+    return kNone;
+}
+
+// The live-ingress warp: move host messages into mailboxes until the drain
+// is quiescent, nothing is published and it has idled long enough (or the
+// host asked it to stop).
+__device__ void agent_loop(const DrainParams &P) {
+    DevCtl *ctl = P.ctl;
+    const uint32_t lane = lane_id();
     bool idle = false;
     uint64_t idle_start = 0;
     while (!exit_requested(ctl)) {
-        bool did = false;
-        if (agent) {
-            did = poll_host_ring(P);
-        } else {
-            uint32_t item = 0;
-            bool got = false;
-            if (lane == 0) got = q_try_pop(&ctl->workq, P.workq, &item);
-            got = __shfl_sync(FULL, got, 0);
-            if (got) {
-                item = __shfl_sync(FULL, item, 0);
-                factor_item(P, item >> 8, item & 0xFFu);
-                did = true;
-            } else {
-                uint32_t a = 0;
-                if (lane == 0) got = q_try_pop(&ctl->readyq, P.readyq, &a);
-                got = __shfl_sync(FULL, got, 0);
-                if (got) {
-                    a = __shfl_sync(FULL, a, 0);
-                    const uint32_t kind = P.actors[a].kind;
-                    if (kind == kFactor) {
-                        uint32_t b = 0;
-                        bool gb = false;
-                        if (lane == 0) gb = q_try_pop(&ctl->freeq, P.freeq, &b);
-                        gb = __shfl_sync(FULL, gb, 0);
-                        if (gb) {
-                            claim_factor(P, a, __shfl_sync(FULL, b, 0));
-                            did = true;
-                        } else if (lane == 0) {
-                            // no batch record free: leave the actor READY for later
-                            if (!q_push(&ctl->readyq, P.readyq, a, P.wait_limit_ns)) fail(P, kErrWaitQueue, 7);
-                        }
-                    } else if (kind == kToken) {
-                        claim_ring(P, a);
-                        did = true;
-                    }
-                    __syncwarp();
-                }
-            }
-        }
-        if (did) {
+        if (poll_host_ring(P)) {
             idle = false;
             continue;
         }
@@ -651,29 +676,126 @@ __global__ void __launch_bounds__(kThreads, 2) k_drain(DrainParams P) {
             idle_start = now;
         }
         if (quiescent(P)) {
-            if (!P.live) {
+            const bool stop = ld_acquire_sys(&P.hctl->stop) != 0;
+            const uint64_t head = ctl->ring_head;
+            const bool more = ld_acquire_sys(&P.ring[head & P.ring_mask].seq) == head + 1;
+            if (!more && (stop || now - idle_start > P.idle_exit_ns)) {
                 if (lane == 0) atomicExch(reinterpret_cast<unsigned int *>(&ctl->exit_flag), 1u);
                 break;
             }
-            if (agent) {
-                const bool stop = ld_acquire_sys(&P.hctl->stop) != 0;
-                const uint64_t head = ctl->ring_head;
-                const bool more = ld_acquire_sys(&P.ring[head & P.ring_mask].seq) == head + 1;
-                if (!more && (stop || now - idle_start > P.idle_exit_ns)) {
-                    if (lane == 0) atomicExch(reinterpret_cast<unsigned int *>(&ctl->exit_flag), 1u);
-                    break;
+        }
+        __nanosleep(128);
+    }
+}
+
+// The persistent drain.  Each CTA has kConsumerWarps consumer warps and one
+// producer warp.  In a loop, the consumer warps form a group (team leaders
+// claim actors; ring tokens are run on the way), then the producer streams
+// the prime table through the CTA's shared-memory ring while every team
+// sweeps its batch against it, so one pass over the table serves up to
+// kConsumerWarps * K messages.  With the live host ring, warp 0 of CTA 0 is
+// the ingress warp and takes no part in groups.
+__global__ void __launch_bounds__(kThreads, 2) k_drain(DrainParams P) {
+    extern __shared__ __align__(128) uint8_t drain_smem[];
+    GroupShared &G = *reinterpret_cast<GroupShared *>(drain_smem);
+    const uint32_t lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5;
+    const bool live0 = P.live && blockIdx.x == 0;
+    const bool producer = warp == kConsumerWarps;
+    const bool agent = live0 && warp == 0;
+    const uint32_t n_cons = live0 ? kConsumerWarps - 1 : kConsumerWarps;
+    const uint32_t ci = live0 ? warp - 1 : warp;             // consumer index (consumers only)
+    const uint32_t bar_threads = (n_cons + 1) * 32;
+    const uint32_t wpb = P.factor_w;
+    DevCtl *ctl = P.ctl;
+    if (agent) {
+        agent_loop(P);
+        return;
+    }
+    if (producer && lane == 0) {
+        for (uint32_t i = 0; i < kStages; ++i) {
+            mbar_init(&G.full[i], 1);
+            mbar_init(&G.empty[i], n_cons);
+        }
+        fence_barrier_init();
+    }
+    const uint32_t gw = blockIdx.x * kConsumerWarps + ci;
+    if (!producer && P.batch_count && gw < P.n_routers) {
+        route_batch(P, gw);
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            add_u32(&ctl->routers_done, 1);
+        }
+    }
+    named_bar_sync(1, bar_threads);
+    // teams: consumer warps [j*wpb, (j+1)*wpb); an incomplete last team idles
+    const uint32_t team = producer ? 0 : ci / wpb;
+    const uint32_t rank = producer ? 0 : ci % wpb;
+    const bool team_ok = !producer && (team + 1) * wpb <= n_cons;
+    uint32_t t = 0;
+    bool idle = false;
+    uint64_t idle_start = 0;
+    uint32_t idle_ns = 256;
+    for (;;) {
+        // ---- form a group
+        uint32_t mine = kNone;
+        if (!producer && team_ok && rank == 0) mine = find_batch(P);
+        if (!producer && lane == 0) G.batch[ci] = mine;
+        if (producer && lane == 0) G.exit = exit_requested(ctl) ? 1u : 0u;
+        named_bar_sync(1, bar_threads);
+        if (G.exit) break;
+        if (!producer) mine = team_ok ? G.batch[team * wpb] : kNone;
+        if (producer && lane == 0) {
+            uint32_t active = 0, limit = 0;
+            for (uint32_t i = 0; i < n_cons; ++i) {
+                const uint32_t tb = i / wpb;
+                if ((tb + 1) * wpb > n_cons) continue;
+                const uint32_t b = G.batch[tb * wpb];
+                if (b == kNone) continue;
+                ++active;
+                limit = max(limit, P.batches[b].maxbound);
+            }
+            G.active = active;
+            G.limit_tiles = (limit + kTile - 1) / kTile;
+            G.final_tile = 0xFFFFFFFFu;
+        }
+        named_bar_sync(1, bar_threads);
+        if (G.active == 0) {
+            // nothing to sweep in this CTA: exit when the drain is quiescent
+            if (producer && lane == 0) {
+                const uint64_t now = globaltimer();
+                if (!idle) {
+                    idle = true;
+                    idle_start = now;
+                }
+                if (quiescent(P)) {
+                    if (!P.live) atomicExch(reinterpret_cast<unsigned int *>(&ctl->exit_flag), 1u);
+                } else {
+                    const uint64_t hb = *((volatile uint64_t *)&ctl->heartbeat);
+                    const uint64_t last = hb > idle_start ? hb : idle_start;
+                    // another warp's heartbeat may be newer than `now`
+                    if (last < now && now - last > P.wait_limit_ns)
+                        fail(P, kErrStall, 8, ld_acquire_gpu(&ctl->ingested), ld_acquire_gpu(&ctl->completed));
                 }
             }
-        } else {
-            const uint64_t hb = *((volatile uint64_t *)&ctl->heartbeat);
-            const uint64_t last = hb > idle_start ? hb : idle_start;
-            // another warp's heartbeat may be newer than `now`
-            if (last < now && now - last > P.wait_limit_ns) {
-                if (lane == 0) fail(P, kErrStall, 8, ld_acquire_gpu(&ctl->ingested), ld_acquire_gpu(&ctl->completed));
-                break;
-            }
+            // back off: idle CTAs would otherwise take issue slots from
+            // sweeping CTAs on the same SM
+            __nanosleep(idle_ns);
+            idle_ns = min(idle_ns * 2, 2000u);
+            continue;
         }
-        __nanosleep(256);
+        idle = false;
+        idle_ns = 256;
+        // ---- sweep
+        if (producer) {
+            uint32_t tt = t;
+            if (lane == 0) group_produce(P, G, tt);
+            t = __shfl_sync(FULL, tt, 0);
+        } else {
+            group_consume(P, G, t, mine, rank, wpb);
+        }
+        named_bar_sync(1, bar_threads);
     }
 }
 
@@ -685,7 +807,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_drain(DrainParams P) {
 // launch.  scratch = {found, ctas_done} (two uint32 words, zero/kNoFactor at
 // rest).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_factor_one(uint64_t n, const uint32_t *primes,
+__global__ void __launch_bounds__(kOneThreads) k_factor_one(uint64_t n, const uint32_t *primes,
                                                           const uint32_t *pinv, const uint32_t *plim,
                                                           uint32_t nprimes, uint64_t reply_addr,
                                                           uint32_t reply_token, uint64_t tag,
@@ -693,8 +815,8 @@ __global__ void __launch_bounds__(kThreads) k_factor_one(uint64_t n, const uint3
     const uint32_t lane = lane_id();
     const bool even = (n >= 4) && !(n & 1u);
     const uint32_t bound = even ? 0 : factor_bound(primes, nprimes, n);
-    const uint32_t gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
-    const uint32_t nw = gridDim.x * kWarpsPerCta;
+    const uint32_t gw = blockIdx.x * (kOneThreads / 32) + (threadIdx.x >> 5);
+    const uint32_t nw = gridDim.x * (kOneThreads / 32);
     const uint32_t nl = 0u - (uint32_t)n;
     uint64_t tests = 0;
     for (uint32_t c = gw * 32; c < bound; c += nw * 32) {
@@ -932,8 +1054,24 @@ __global__ void k_debug_wait(const uint32_t *flag, uint64_t limit_ns, DevCtl *ct
 
 namespace cafgpu {
 
+static cudaError_t drain_attr() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_drain, cudaFuncAttributeMaxDynamicSharedMemorySize, kDrainSmem);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+cudaError_t drain_occupancy(int *ctas_per_sm) {
+    cudaError_t e = drain_attr();
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain, kThreads, kDrainSmem);
+}
+
 cudaError_t launch_drain(const DrainParams &p, unsigned grid, cudaStream_t stream) {
-    k_drain<<<grid, kThreads, 0, stream>>>(p);
+    cudaError_t e = drain_attr();
+    if (e != cudaSuccess) return e;
+    k_drain<<<grid, kThreads, kDrainSmem, stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -951,7 +1089,7 @@ cudaError_t launch_factor_one(uint64_t n, const uint32_t *primes, const uint32_t
                               const uint32_t *plim, uint32_t nprimes, uint64_t reply_addr,
                               uint32_t reply_token, uint64_t tag, uint32_t *scratch, DevCtl *ctl,
                               unsigned grid, cudaStream_t stream) {
-    k_factor_one<<<grid, kThreads, 0, stream>>>(n, primes, pinv, plim, nprimes, reply_addr, reply_token,
+    k_factor_one<<<grid, kOneThreads, 0, stream>>>(n, primes, pinv, plim, nprimes, reply_addr, reply_token,
                                                 tag, scratch, ctl);
     return cudaGetLastError();
 }

@@ -97,68 +97,107 @@ __device__ __forceinline__ void write_reply(uint64_t addr, int32_t status, uint6
 // among the lanes of that chunk is the first divisor, because the chunks run
 // in increasing order), when its bound is passed, or when another warp has
 // recorded a divisor below the current position.
+//
+// Per message the warp keeps nl = -n mod 2^32 and ch = floor(n / 2^32) +
+// [n mod 2^32 != 0].  Since n + m0*p == 0 (mod 2^32), the high word of the
+// 64-bit sum is umulhi(m0, p) + ch exactly, so the test needs only 32-bit
+// multiplies: m0 = nl*pinv, n1 = umulhi(m0, p) + ch, m1 = n1*pinv, m1 <= plim.
 // ---------------------------------------------------------------------------
 struct SweepRegs {
-    uint64_t n[kFactorKMax];
-    uint32_t nl[kFactorKMax];   // -n mod 2^32
+    uint32_t nl[kFactorKMax];
+    uint32_t ch[kFactorKMax];
     uint64_t ids;               // 4 bits per slot: message index in the batch
     int k;
 };
+
+// Slots at index >= k hold n = 1, which no prime divides, so the test can
+// run over whole blocks of four slots without checking k per slot.
+constexpr uint32_t kDummyNl = 0xFFFFFFFFu;   // -1 mod 2^32
+constexpr uint32_t kDummyCh = 1u;            // 0 + [1 != 0]
+
+__device__ __forceinline__ void sweep_init(SweepRegs &s) {
+    s.k = 0;
+    s.ids = 0;
+#pragma unroll
+    for (int j = 0; j < (int)kFactorKMax; ++j) {
+        s.nl[j] = kDummyNl;
+        s.ch[j] = kDummyCh;
+    }
+}
 
 __device__ __forceinline__ uint32_t slot_id(const SweepRegs &s, int j) {
     return (uint32_t)(s.ids >> (4 * j)) & 15u;
 }
 
-// Remove slot p (0 <= p < k) keeping the others in order.
+__device__ __forceinline__ void sweep_set(SweepRegs &s, int i, uint64_t n) {
+    const uint32_t lo = (uint32_t)n;
+    s.nl[i] = 0u - lo;
+    s.ch[i] = (uint32_t)(n >> 32) + (lo != 0u ? 1u : 0u);
+}
+
+// Remove slot p (0 <= p < k) keeping the others in order; the last slot
+// becomes a dummy.
 __device__ __forceinline__ void sweep_remove(SweepRegs &s, int p) {
 #pragma unroll
     for (int i = 0; i < (int)kFactorKMax - 1; ++i) {
         if (i >= p) {
-            s.n[i] = s.n[i + 1];
             s.nl[i] = s.nl[i + 1];
+            s.ch[i] = s.ch[i + 1];
         }
     }
+    s.nl[kFactorKMax - 1] = kDummyNl;
+    s.ch[kFactorKMax - 1] = kDummyCh;
     const uint64_t low = (p == 0) ? 0ull : (s.ids & ((1ull << (4 * p)) - 1ull));
     const uint64_t high = (p >= 15) ? 0ull : ((s.ids >> (4 * (p + 1))) << (4 * p));
     s.ids = low | high;
     --s.k;
 }
 
-#define CAFGPU_TEST_SLOT(J)                                                  \
-    case (J) + 1: {                                                          \
-        uint32_t m0 = s.nl[J] * pinv;                                        \
-        uint64_t t = (uint64_t)m0 * p + s.n[J];                              \
-        uint32_t m1 = (uint32_t)(t >> 32) * pinv;                            \
-        hits |= (m1 <= plim) ? (1u << (J)) : 0u;                             \
+__device__ __forceinline__ bool sweep_test(const SweepRegs &s, int j, uint32_t p, uint32_t pinv, uint32_t plim) {
+    const uint32_t m0 = s.nl[j] * pinv;
+    const uint32_t n1 = __umulhi(m0, p) + s.ch[j];
+    return n1 * pinv <= plim;
+}
+
+// Four independent tests (slots B..B+3), written so the multiplies of the
+// four chains interleave.
+#define CAFGPU_TEST_BLOCK(B)                                                              \
+    case (B) / 4 + 1: {                                                                   \
+        const uint32_t a0 = s.nl[(B) + 0] * pinv, a1 = s.nl[(B) + 1] * pinv;              \
+        const uint32_t a2 = s.nl[(B) + 2] * pinv, a3 = s.nl[(B) + 3] * pinv;              \
+        const uint32_t b0 = __umulhi(a0, p) + s.ch[(B) + 0];                              \
+        const uint32_t b1 = __umulhi(a1, p) + s.ch[(B) + 1];                              \
+        const uint32_t b2 = __umulhi(a2, p) + s.ch[(B) + 2];                              \
+        const uint32_t b3 = __umulhi(a3, p) + s.ch[(B) + 3];                              \
+        const bool h = (b0 * pinv <= plim) | (b1 * pinv <= plim) | (b2 * pinv <= plim) |   \
+                       (b3 * pinv <= plim);                                               \
+        hit |= h;                                                                         \
     }
 
-// Test the 32 primes at [c, c+32) (one per lane) against slots 0..k-1.
-__device__ __forceinline__ uint32_t sweep_chunk(const SweepRegs &s, uint32_t p, uint32_t pinv,
-                                                uint32_t plim) {
-    uint32_t hits = 0;
-    switch (s.k) {
-        CAFGPU_TEST_SLOT(15)
-        CAFGPU_TEST_SLOT(14)
-        CAFGPU_TEST_SLOT(13)
-        CAFGPU_TEST_SLOT(12)
-        CAFGPU_TEST_SLOT(11)
-        CAFGPU_TEST_SLOT(10)
-        CAFGPU_TEST_SLOT(9)
-        CAFGPU_TEST_SLOT(8)
-        CAFGPU_TEST_SLOT(7)
-        CAFGPU_TEST_SLOT(6)
-        CAFGPU_TEST_SLOT(5)
-        CAFGPU_TEST_SLOT(4)
-        CAFGPU_TEST_SLOT(3)
-        CAFGPU_TEST_SLOT(2)
-        CAFGPU_TEST_SLOT(1)
-        CAFGPU_TEST_SLOT(0)
+// True if any held message is divisible by this lane's prime.
+__device__ __forceinline__ bool sweep_chunk(const SweepRegs &s, uint32_t p, uint32_t pinv, uint32_t plim) {
+    bool hit = false;
+    switch ((s.k + 3) >> 2) {
+        CAFGPU_TEST_BLOCK(12)
+        CAFGPU_TEST_BLOCK(8)
+        CAFGPU_TEST_BLOCK(4)
+        CAFGPU_TEST_BLOCK(0)
         default:
             break;
     }
+    return hit;
+}
+#undef CAFGPU_TEST_BLOCK
+static_assert(kFactorKMax == 16, "sweep_chunk unrolls 16 slots in blocks of four");
+
+// Bit j set if this lane's prime divides the message in slot j (slow path,
+// run only for chunks where some lane hit).
+__device__ __forceinline__ uint32_t sweep_which(const SweepRegs &s, uint32_t p, uint32_t pinv, uint32_t plim) {
+    uint32_t hits = 0;
+#pragma unroll
+    for (int j = 0; j < (int)kFactorKMax; ++j)
+        if (j < s.k && sweep_test(s, j, p, pinv, plim)) hits |= 1u << j;
     return hits;
 }
-#undef CAFGPU_TEST_SLOT
-static_assert(kFactorKMax == 16, "sweep_chunk unrolls 16 slots");
 
 }  // namespace cafgpu

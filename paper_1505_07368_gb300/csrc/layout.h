@@ -21,11 +21,37 @@
 
 namespace cafgpu {
 
-constexpr uint32_t kWarpsPerCta = 8;
+constexpr uint32_t kConsumerWarps = 8;                     // warps that run actors and sweep
+constexpr uint32_t kWarpsPerCta = kConsumerWarps + 1;      // + one prime-table producer warp
 constexpr uint32_t kThreads = kWarpsPerCta * 32;
+constexpr uint32_t kOneThreads = 256;                      // per-message factor kernel
 constexpr uint32_t kFactorKMax = 16;     // messages per factor batch, upper bound
-constexpr uint32_t kRangePrimes = 4096;  // primes per range of a factor work item
+constexpr uint32_t kRangePrimes = 4096;  // table padding granule
 constexpr uint32_t kNoFactor = 0xFFFFFFFFu;
+constexpr uint32_t kTile = 512;          // primes per staged table tile (16 chunks of 32)
+constexpr uint32_t kStages = 8;          // tiles in flight per CTA
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+// One staged tile of the prime table (shared memory, 16-byte aligned).
+struct TableTile {
+    uint32_t p[kTile];
+    uint32_t pinv[kTile];
+    uint32_t plim[kTile];
+};
+
+// Per-CTA shared state of the cooperative sweep: the table ring and the
+// group (one factor batch per team of consumer warps) it serves.
+struct GroupShared {
+    TableTile tile[kStages];
+    uint64_t full[kStages];        // producer -> consumers (bulk copies landed)
+    uint64_t empty[kStages];       // consumers -> producer (stage free again)
+    uint32_t batch[kConsumerWarps];
+    uint32_t limit_tiles;          // tiles needed by the group's largest bound
+    uint32_t final_tile;           // tile index at which the group's stream ends
+    uint32_t active;               // consumer warps still holding messages
+    uint32_t exit;
+};
+constexpr uint32_t kDrainSmem = (uint32_t)sizeof(GroupShared);
 
 // actor lifecycle (Sec. 6: ready / waiting / running / done)
 enum : uint32_t { kWaiting = 0, kReady = 1, kRunning = 2, kDone = 3 };
@@ -44,6 +70,7 @@ enum : uint32_t {
     kErrDebugWait = 5,     // the debug wait kernel's flag was never set
     kErrGemm = 6,          // GEMM pipeline wait expired
     kErrStall = 7,         // no progress anywhere while messages were in flight
+    kErrWaitTable = 8,     // a prime-table bulk copy did not complete
 };
 
 // Device-resident message (same layout as caf_gpu_dmsg).

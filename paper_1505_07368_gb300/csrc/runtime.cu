@@ -208,7 +208,7 @@ uint32_t factor_grid(caf_gpu_runtime *rt, uint64_t n) {
     // about one chunk of 32 primes per warp: primes below sqrt(n) ~ s / ln s
     const double s = std::sqrt((double)n);
     const double np = s > 3 ? s / std::log(s) : 1.0;
-    uint64_t g = (uint64_t)(np / 32.0 / kWarpsPerCta) + 1;
+    uint64_t g = (uint64_t)(np / 32.0 / (kOneThreads / 32)) + 1;
     return (uint32_t)std::min<uint64_t>(g, (uint64_t)rt->n_sms * 4);
 }
 
@@ -346,22 +346,29 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     if (!c.max_inflight_requests) c.max_inflight_requests = 65536;
     if (!c.ingress_capacity) c.ingress_capacity = 65536;
     if (!c.ctas_per_sm) c.ctas_per_sm = 2;
-    if (!c.factor_batch) c.factor_batch = 8;
-    if (!c.factor_warps) c.factor_warps = 1;
+    if (!c.factor_batch) c.factor_batch = 16;
+    if (!c.factor_warps) c.factor_warps = 4;
     if (!c.max_factor_n) c.max_factor_n = (1ull << 62) - 1;
     if (!c.mem_budget_bytes) c.mem_budget_bytes = 8ull << 30;
     if (!c.wait_limit_ns) c.wait_limit_ns = 200000000ull;
     if (!c.idle_exit_ns) c.idle_exit_ns = 2000000ull;
     if (!c.log_capacity) c.log_capacity = 1u << 20;
     if (!is_pow2(c.mailbox_capacity) || !is_pow2(c.ingress_capacity)) return CAF_GPU_EINVAL;
-    if (c.factor_batch > kFactorKMax || c.factor_warps > 255 || c.ctas_per_sm > 2) return CAF_GPU_EINVAL;
+    if (c.factor_batch > kFactorKMax || c.ctas_per_sm > 4) return CAF_GPU_EINVAL;
+    if (c.factor_warps != 1 && c.factor_warps != 2 && c.factor_warps != 4 && c.factor_warps != 8)
+        return CAF_GPU_EINVAL;
     if (c.max_factor_n >= (1ull << 62)) return CAF_GPU_EINVAL;
     if (c.max_actors > (1u << 24)) return CAF_GPU_EINVAL;
     rt->cfg = c;
 
     CK(cudaGetDevice(&rt->device));
     CK(cudaDeviceGetAttribute(&rt->n_sms, cudaDevAttrMultiProcessorCount, rt->device));
-    rt->grid = (unsigned)rt->n_sms * c.ctas_per_sm;
+    // every drain CTA must be resident at once (router and ingress warps are
+    // waited on by the others), so the grid never exceeds the occupancy limit
+    int fit = 0;
+    CK(drain_occupancy(&fit));
+    if (fit < 1) return CAF_GPU_ECUDA;
+    rt->grid = (unsigned)rt->n_sms * std::min<uint32_t>(c.ctas_per_sm, (uint32_t)fit);
     if (c.cuda_stream) {
         rt->stream = (cudaStream_t)c.cuda_stream;
     } else {
@@ -379,7 +386,7 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     rt->n_slots = (uint64_t)c.max_actors * c.mailbox_capacity;
     CK(cudaMalloc(&rt->d_slots, sizeof(Slot) * rt->n_slots));
     CK(cudaMemset(rt->d_slots, 0, sizeof(Slot) * rt->n_slots));
-    rt->n_batches = std::max<uint32_t>(4096, 2u * rt->grid * kWarpsPerCta);
+    rt->n_batches = std::max<uint32_t>(4096, 2u * rt->grid * kConsumerWarps);
     CK(cudaMalloc(&rt->d_batches, sizeof(FactorBatch) * rt->n_batches));
     CK(cudaMemset(rt->d_batches, 0, sizeof(FactorBatch) * rt->n_batches));
     rt->readyq_cap = next_pow2((uint64_t)c.max_actors + 1);
@@ -645,7 +652,7 @@ int caf_gpu_request_batch_device(caf_gpu_runtime *rt, const caf_gpu_dmsg *d_msgs
     p.batch_msgs = d_msgs;
     p.batch_replies = reinterpret_cast<Reply *>(d_replies);
     p.batch_count = count;
-    p.n_routers = std::min<uint32_t>(rt->grid * kWarpsPerCta, 128);
+    p.n_routers = std::min<uint32_t>(rt->grid * kConsumerWarps, 128);
     CK(launch_reset_ctl(rt->d_ctl, rt->stream));
     CK(launch_drain(p, rt->grid, rt->stream));
     rt->launches += 2;

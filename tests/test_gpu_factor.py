@@ -53,7 +53,7 @@ def test_config1_per_message_launch():
     _assert_same(rep, wl.n)
 
 
-@pytest.mark.parametrize("k,w", [(8, 1), (16, 1), (3, 4), (1, 2)])
+@pytest.mark.parametrize("k,w", [(16, 8), (8, 1), (16, 1), (3, 4), (1, 2), (5, 8), (16, 2)])
 def test_config1_device_batch_batching_shapes(k, w):
     wl = W.config1()
     with C.Runtime(max_factor_n=MAX40, max_actors=8, factor_batch=k, factor_warps=w) as rt:
