@@ -280,6 +280,37 @@ int caf_gpu_debug_wait_expiry(caf_gpu_runtime *rt, uint64_t limit_ns);
 /* Clear the device error word after a reported bounded-wait expiry. */
 int caf_gpu_clear_error(caf_gpu_runtime *rt);
 
+/* ---- factorization without device allocation ----------------------------
+ *
+ * The paper has no counterpart to this call: it exists for callers of this
+ * library that cannot call cudaMalloc -- code inside a host framework whose
+ * allocator owns the GPU's memory, latency-critical paths that cannot take
+ * cudaMalloc's device-wide synchronisation, programs that forbid dynamic
+ * allocation after start-up.  Such callers cannot create a runtime (it
+ * allocates), so this call needs none.
+ *
+ * Factors d_n[0..count) (device memory) and writes reply i to d_replies[i]
+ * (device memory): status CAF_GPU_REPLY_OK with (r0, r1) = (smallest divisor
+ * d >= 2 with d*d <= n, n/d), CAF_GPU_REPLY_NOFACTOR with (1, n), or
+ * CAF_GPU_REPLY_REJECTED for n >= 2^62.  The results equal those of a
+ * FACTOR_U64 actor.  Work is enqueued on `stream` (cudaStream_t, NULL = the
+ * legacy default stream) and the call returns at once; the replies are
+ * complete when the stream reaches this point.  The caller owns both arrays.
+ *
+ * It allocates nothing: the two scratch words per number live in a fixed
+ * array of CAF_GPU_FACTOR_STATIC_MAX entries (32 KB) compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls share the array, so calls whose work overlaps
+ * on the GPU (other streams, other threads) race and must not be issued; each
+ * call resets the words it uses before its kernel runs.
+ *
+ * Errors: CAF_GPU_EINVAL if count > CAF_GPU_FACTOR_STATIC_MAX or a pointer is
+ * NULL (nothing is launched); CAF_GPU_ECUDA if the set-up or a launch fails. */
+#define CAF_GPU_FACTOR_STATIC_MAX 4096u
+int caf_gpu_factor_static(const uint64_t *d_n, uint32_t count, caf_gpu_dreply *d_replies, void *stream);
+
 const char *caf_gpu_strerror(int code);
 
 #ifdef __cplusplus

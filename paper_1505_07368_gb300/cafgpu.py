@@ -83,8 +83,9 @@ EXPORTS = [
     "caf_gpu_request_batch_device", "caf_gpu_sync", "caf_gpu_stream_sync", "caf_gpu_set_backend",
     "caf_gpu_reset_actors", "caf_gpu_actor_state", "caf_gpu_stats_read", "caf_gpu_read_log",
     "caf_gpu_stream", "caf_gpu_mark", "caf_gpu_prime_table", "caf_gpu_debug_wait_expiry", "caf_gpu_clear_error",
-    "caf_gpu_strerror",
+    "caf_gpu_factor_static", "caf_gpu_strerror",
 ]
+FACTOR_STATIC_MAX = 4096
 
 _lib = None
 
@@ -122,6 +123,7 @@ def load(build: bool = True):
         "caf_gpu_debug_wait_expiry": [vp, u64],
         "caf_gpu_clear_error": [vp],
         "caf_gpu_mark": [vp],
+        "caf_gpu_factor_static": [vp, u32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -133,6 +135,13 @@ def load(build: bool = True):
     L.caf_gpu_strerror.restype = ctypes.c_char_p
     _lib = L
     return L
+
+
+def factor_static(d_n: int, count: int, d_replies: int, stream: int = 0) -> int:
+    """caf_gpu_factor_static: factor `count` numbers at device address `d_n`
+    into the caf_gpu_dreply array at `d_replies`, allocating nothing.  Returns
+    the status code (0 on success)."""
+    return load().caf_gpu_factor_static(d_n, count, d_replies, stream or None)
 
 
 def strerror(code: int) -> str:
