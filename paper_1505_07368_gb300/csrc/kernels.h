@@ -21,6 +21,11 @@ cudaError_t launch_token_one(ActorDesc *actors, uint32_t a, uint32_t kind, int32
                              uint64_t reply_addr, uint32_t reply_token, IngressEntry *outbox,
                              DevCtl *ctl, cudaStream_t stream);
 cudaError_t launch_reset_actors(ActorDesc *actors, uint32_t n_actors, cudaStream_t stream);
+// One GEMM message, C = A * B (n x n FP32), BF16 or split-BF16x3 on tcgen05;
+// scratch[0] must be 0 at rest.
+cudaError_t launch_gemm_one(const float *A, const float *B, float *C, uint32_t n, bool split, uint64_t reply_addr,
+                            uint32_t reply_token, uint32_t *scratch, uint64_t limit_ns, DevCtl *ctl,
+                            cudaStream_t stream);
 cudaError_t launch_debug_wait(const uint32_t *flag, uint64_t limit_ns, DevCtl *ctl, HostCtl *hctl,
                               cudaStream_t stream);
 // Prime table of the odd primes <= limit.  Allocates *primes/*pinv/*plim

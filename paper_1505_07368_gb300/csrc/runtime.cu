@@ -31,6 +31,8 @@ uint32_t next_pow2(uint64_t x) {
 
 bool is_pow2(uint32_t x) { return x && !(x & (x - 1)); }
 
+constexpr uint32_t kMaxGemmN = 1u << 15;
+
 uint64_t now_ns() {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
                std::chrono::steady_clock::now().time_since_epoch())
@@ -193,7 +195,10 @@ int check_msg(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *m, uint3
     const ActorDesc &d = rt->actors[a];
     if (m->kind != d.kind) return CAF_GPU_EINVAL;
     if (m->kind == kFactor && m->u64 > rt->cfg.max_factor_n) return CAF_GPU_EINVAL;
-    if (m->kind == kGemmBf16 || m->kind == kGemmSplit) return CAF_GPU_EINVAL;  // GEMM not wired yet
+    if (m->kind == kGemmBf16 || m->kind == kGemmSplit) {
+        if (!m->A || !m->B || !m->C || m->n == 0 || m->n > kMaxGemmN) return CAF_GPU_EINVAL;
+        if (rt->backend == CAF_GPU_BACKEND_PERSISTENT) return CAF_GPU_EINVAL;  // drain path: see gemm jobs
+    }
     if (m->kind == kToken) {
         uint32_t state = 0;
         if (cudaMemcpy(&state, &rt->d_actors[a].state, sizeof(state), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -257,6 +262,12 @@ int pm_pump(caf_gpu_runtime *rt) {
 
 // Put one message on its way (caller holds rt->mu).
 int submit_locked(caf_gpu_runtime *rt, uint32_t a, const caf_gpu_msg *m, uint64_t reply_addr, uint32_t token) {
+    if (rt->backend == CAF_GPU_BACKEND_PER_MESSAGE_LAUNCH && (m->kind == kGemmBf16 || m->kind == kGemmSplit)) {
+        CK(launch_gemm_one(m->A, m->B, m->C, m->n, m->kind == kGemmSplit, reply_addr, token, rt->d_scratch + 2,
+                           rt->cfg.wait_limit_ns, rt->d_ctl, rt->stream));
+        rt->launches += 1;
+        return 0;
+    }
     IngressEntry e{};
     e.actor = a;
     e.kind = m->kind | (m->flags << 16);
@@ -403,6 +414,7 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
         CK(cudaMemset(rt->d_log, 0, sizeof(LogRow) * (size_t)c.log_capacity));
     }
     CK(cudaMalloc(&rt->d_scratch, 64));
+    CK(cudaMemset(rt->d_scratch, 0, 64));
     const uint32_t scratch_init[2] = {kNoFactor, 0};
     CK(cudaMemcpy(rt->d_scratch, scratch_init, sizeof(scratch_init), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&rt->d_zero, 64));
