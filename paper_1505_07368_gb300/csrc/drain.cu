@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "factor.cuh"
+#include "gemm_tc.cuh"
 #include "layout.h"
 
 namespace cafgpu {
@@ -257,7 +258,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(const DrainParams &P, uint64_t
 // consumer holds a message, then ends the stream with a tile that carries no
 // data (its full barrier is completed by a plain arrive; final_tile marks it).
 // `t` counts ring tiles over the whole kernel; stage = t % kStages, use = t / kStages.
-__device__ void group_produce(const DrainParams &P, GroupShared &G, uint32_t &t) {
+__device__ void group_produce(const DrainParams &P, GroupShared &G, TableTile *ring, uint32_t &t) {
     const uint32_t limit = G.limit_tiles;
     bool ok = true;
     for (uint32_t i = 0;; ++i, ++t) {
@@ -273,9 +274,9 @@ __device__ void group_produce(const DrainParams &P, GroupShared &G, uint32_t &t)
         const uint32_t i0 = i * kTile;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&G.full[st], 3 * kTile * 4);
-        bulk_g2s(G.tile[st].p, P.primes + i0, kTile * 4, &G.full[st]);
-        bulk_g2s(G.tile[st].pinv, P.pinv + i0, kTile * 4, &G.full[st]);
-        bulk_g2s(G.tile[st].plim, P.plim + i0, kTile * 4, &G.full[st]);
+        bulk_g2s(ring[st].p, P.primes + i0, kTile * 4, &G.full[st]);
+        bulk_g2s(ring[st].pinv, P.pinv + i0, kTile * 4, &G.full[st]);
+        bulk_g2s(ring[st].plim, P.plim + i0, kTile * 4, &G.full[st]);
     }
 }
 
@@ -283,8 +284,8 @@ __device__ void group_produce(const DrainParams &P, GroupShared &G, uint32_t &t)
 // streamed tiles.  A team of `wpb` warps shares one batch; member `r` tests
 // the chunks u of each tile with u % wpb == r, and members drop messages that
 // another member has already decided below their position.
-__device__ void group_consume(const DrainParams &P, GroupShared &G, uint32_t &t, uint32_t b, uint32_t r,
-                              uint32_t wpb) {
+__device__ void group_consume(const DrainParams &P, GroupShared &G, const TableTile *ring, uint32_t &t,
+                              uint32_t b, uint32_t r, uint32_t wpb) {
     const uint32_t lane = lane_id();
     FactorBatch *B = (b != kNone) ? &P.batches[b] : nullptr;
     SweepRegs s;
@@ -332,15 +333,16 @@ __device__ void group_consume(const DrainParams &P, GroupShared &G, uint32_t &t,
                 sweep_remove_mask(s, __ballot_sync(FULL, rm));
                 if (s.k > 0) next_drop = sweep_min_bound(s, B);
             }
-            const TableTile &T = G.tile[st];
+            const uint32_t tbase = smem_u32(&ring[st]);
             // one copy of the chunk body: the test switch is large, and an
             // unrolled tile loop overflows the instruction cache
 #pragma unroll 1
             for (uint32_t u = r; u < kTile / 32 && s.k > 0; u += wpb) {
                 const uint32_t c = start + u * 32;
-                const uint32_t p = T.p[u * 32 + lane];
-                const uint32_t pinv = T.pinv[u * 32 + lane];
-                const uint32_t plim = T.plim[u * 32 + lane];
+                const uint32_t off = (u * 32 + lane) * 4;
+                const uint32_t p = lds_u32(tbase + off);
+                const uint32_t pinv = lds_u32(tbase + kTile * 4 + off);
+                const uint32_t plim = lds_u32(tbase + 2 * kTile * 4 + off);
                 tests += (uint64_t)s.k * 32u;
                 if (__any_sync(FULL, sweep_chunk(s, p, pinv, plim))) {
                     const uint32_t hits = sweep_which(s, p, pinv, plim);
@@ -622,9 +624,139 @@ __device__ __forceinline__ bool quiescent(const DrainParams &P) {
     return c == i;
 }
 
+// ---------------------------------------------------------------------------
+// GEMM actors in the drain
+// ---------------------------------------------------------------------------
+// Warp-collective push of `count` items base | i (i < count) into an MPMC
+// queue, positions reserved with one atomic add.
+__device__ bool q_push_block(const DrainParams &P, QueueHdr *q, QCell *cells, uint32_t base, uint32_t count) {
+    const uint32_t lane = lane_id();
+    uint64_t pos0 = 0;
+    if (lane == 0) pos0 = add_u64(&q->enq, count);
+    pos0 = __shfl_sync(FULL, pos0, 0);
+    bool ok = true;
+    for (uint32_t i = lane; i < count && ok; i += 32) {
+        const uint64_t pos = pos0 + i;
+        QCell *c = &cells[pos & q->mask];
+        if (ld_acquire_gpu(&c->seq) != pos) {
+            WaitClock w(P.wait_limit_ns);
+            while (ld_acquire_gpu(&c->seq) != pos) {
+                if (!w.again()) { ok = false; break; }
+            }
+        }
+        if (ok) {
+            c->val = base | i;
+            st_release_gpu(&c->seq, pos + 1);
+        }
+    }
+    if (!__all_sync(FULL, ok)) {
+        if (lane == 0) fail(P, kErrWaitQueue, 15, count, base);
+        return false;
+    }
+    return true;
+}
+
+// Claim a GEMM actor: take up to 32 messages (as many as there are free job
+// records), turn each into a job and queue its output tiles in job order.
+__device__ __noinline__ void claim_gemm(const DrainParams &P, uint32_t a) {
+    const uint32_t lane = lane_id();
+    DevCtl *ctl = P.ctl;
+    ActorDesc *A = &P.actors[a];
+    const uint32_t split = A->kind == kGemmSplit ? 1u : 0u;
+    if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
+    __syncwarp();
+    const uint64_t head = *((volatile uint64_t *)&A->head);
+    const uint64_t tail = ld_acquire_gpu(&A->tail);
+    uint64_t avail = tail - head;
+    uint32_t want = avail < 32 ? (uint32_t)avail : 32u;
+    if (P.max_claim && P.max_claim < want) want = P.max_claim;
+    if (lane == 0) add_u64(&ctl->claims, 1);
+    // reserve job records first, so a claim never waits for one
+    uint32_t j = kNone;
+    bool got = lane < want && q_try_pop(&ctl->jobq, P.jobq, &j);
+    const uint32_t gm = __ballot_sync(FULL, got);
+    const uint32_t nj = (gm == FULL) ? 32u : (uint32_t)(__ffs(~gm) - 1);
+    MsgData m{};
+    const uint32_t take = nj ? warp_dequeue(P, a, head, nj, m) : 0u;
+    if (got && lane >= take) {
+        q_push(&ctl->jobq, P.jobq, j, P.wait_limit_ns);
+        got = false;
+    }
+    release_actor(P, a, head + take);
+    bool valid = false;
+    uint32_t tiles = 0;
+    if (lane < take) {
+        const GemmDesc *d = reinterpret_cast<const GemmDesc *>(m.payload);
+        const uint32_t n = d ? d->n : 0u;
+        if (d && n > 0 && n <= kMaxDrainGemmN && d->A && d->B && d->C) {
+            const uint32_t t = (n + kGemmBN - 1) / kGemmBN;
+            GemmJob *J = &P.jobs[j];
+            J->A = d->A;
+            J->B = d->B;
+            J->C = d->C;
+            J->n = n;
+            J->split = split;
+            J->tiles = t * t;
+            J->done = 0;
+            J->reply_addr = m.reply_addr;
+            J->reply_token = m.reply_token;
+            tiles = t * t;
+            valid = true;
+        } else {
+            write_reply(m.reply_addr, 3, 0, n, m.tag, m.reply_token);
+            q_push(&ctl->jobq, P.jobq, j, P.wait_limit_ns);
+        }
+    }
+    const uint32_t bad = __popc(__ballot_sync(FULL, lane < take && !valid));
+    if (lane == 0 && bad) {
+        __threadfence();
+        add_u64(&ctl->completed, bad);
+    }
+    __threadfence();
+    for (uint32_t i = 0; i < take; ++i) {
+        const bool v = __shfl_sync(FULL, valid, i);
+        const uint32_t ji = __shfl_sync(FULL, j, i);
+        const uint32_t ti = __shfl_sync(FULL, tiles, i);
+        if (v && !q_push_block(P, &ctl->workq, P.workq, ji << 16, ti)) return;
+    }
+}
+
+struct NamedBarSync {
+    uint32_t nthreads;
+    __device__ __forceinline__ void operator()() const { named_bar_sync(1, nthreads); }
+};
+
+// Run GEMM tile `item` with the whole CTA; the CTA that finishes a job's last
+// tile writes its reply and frees the job record.
+__device__ __noinline__ void drain_gemm_tile(const DrainParams &P, GroupShared &G, GemmOps &ops, uint32_t item,
+                                uint32_t &stage_uses, uint32_t &tiles, uint32_t bar_threads) {
+    const uint32_t j = item >> 16, tile = item & 0xFFFFu;
+    GemmJob *J = &P.jobs[j];
+    const uint32_t n = J->n;
+    const uint32_t tn_count = (n + kGemmBN - 1) / kGemmBN;
+    const bool ok = gemm_tile(reinterpret_cast<const float *>(J->A), reinterpret_cast<const float *>(J->B),
+                              reinterpret_cast<float *>(J->C), n, tile / tn_count, tile % tn_count, J->split != 0,
+                              ops, G.gb, stage_uses, tiles, P.wait_limit_ns, NamedBarSync{bar_threads});
+    if (threadIdx.x == 0) {
+        if (!ok) fail(P, kErrGemm, 16, item, n);
+        heartbeat(P);
+        __threadfence();
+        add_u64(&P.ctl->gemm_tiles, 1);
+        if (atomicAdd(reinterpret_cast<unsigned int *>(&J->done), 1u) == J->tiles - 1) {
+            __threadfence();
+            write_reply(J->reply_addr, ok ? 0 : 3, 0, n, 0, J->reply_token);
+            __threadfence();
+            add_u64(&P.ctl->messages, 1);
+            add_u64(&P.ctl->completed, 1);
+            if (!q_push(&P.ctl->jobq, P.jobq, j, P.wait_limit_ns)) fail(P, kErrWaitQueue, 17);
+        }
+    }
+}
+
 // A team leader looks for a factor batch to sweep: pop ready actors, claim
 // factor actors into a fresh batch record, and run ring-token actors on the
 // way (a few at most, so the group forms quickly).
+template <bool kGemm>
 __device__ uint32_t find_batch(const DrainParams &P) {
     const uint32_t lane = lane_id();
     DevCtl *ctl = P.ctl;
@@ -651,6 +783,8 @@ __device__ uint32_t find_batch(const DrainParams &P) {
             if (r != kNone) return r;
         } else if (kind == kToken) {
             claim_ring(P, a);
+        } else if (kGemm && (kind == kGemmBf16 || kind == kGemmSplit)) {
+            claim_gemm(P, a);
         }
         if (exit_requested(ctl)) return kNone;
     }
@@ -695,9 +829,13 @@ __device__ void agent_loop(const DrainParams &P) {
 // sweeps its batch against it, so one pass over the table serves up to
 // kConsumerWarps * K messages.  With the live host ring, warp 0 of CTA 0 is
 // the ingress warp and takes no part in groups.
+template <bool kGemm>
 __global__ void __launch_bounds__(kThreads, 2) k_drain(DrainParams P) {
     extern __shared__ __align__(128) uint8_t drain_smem[];
-    GroupShared &G = *reinterpret_cast<GroupShared *>(drain_smem);
+    uint8_t *base = drain_smem + ((1024u - (smem_u32(drain_smem) & 1023u)) & 1023u);
+    GroupShared &G = *reinterpret_cast<GroupShared *>(base);
+    TableTile *ring = reinterpret_cast<TableTile *>(base + kDrainHeader);
+    GemmOps &gops = *reinterpret_cast<GemmOps *>(base + kDrainHeader);
     const uint32_t lane = lane_id();
     const uint32_t warp = threadIdx.x >> 5;
     const bool live0 = P.live && blockIdx.x == 0;
@@ -719,6 +857,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_drain(DrainParams P) {
         }
         fence_barrier_init();
     }
+    if constexpr (kGemm) {
+        if (producer) gemm_bars_init(G.gb);   // GEMM barriers + tensor memory (warp-wide)
+        tc_fence_before();
+    }
     const uint32_t gw = blockIdx.x * kConsumerWarps + ci;
     if (!producer && P.batch_count && gw < P.n_routers) {
         route_batch(P, gw);
@@ -729,6 +871,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_drain(DrainParams P) {
         }
     }
     named_bar_sync(1, bar_threads);
+    if constexpr (kGemm) tc_fence_after();
     // teams: consumer warps [j*wpb, (j+1)*wpb); an incomplete last team idles
     const uint32_t team = producer ? 0 : ci / wpb;
     const uint32_t rank = producer ? 0 : ci % wpb;
@@ -737,14 +880,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_drain(DrainParams P) {
     bool idle = false;
     uint64_t idle_start = 0;
     uint32_t idle_ns = 256;
+    uint32_t held = kNone;                 // a team leader's claimed batch, kept across GEMM tiles
+    uint32_t g_stage_uses = 0, g_tiles = 0;
+    const bool gemm_cta = kGemm && !live0;
     for (;;) {
         // ---- form a group
-        uint32_t mine = kNone;
-        if (!producer && team_ok && rank == 0) mine = find_batch(P);
-        if (!producer && lane == 0) G.batch[ci] = mine;
-        if (producer && lane == 0) G.exit = exit_requested(ctl) ? 1u : 0u;
+        if (!producer && team_ok && rank == 0 && held == kNone) held = find_batch<kGemm>(P);
+        if (!producer && lane == 0) G.batch[ci] = (team_ok && rank == 0) ? held : kNone;
+        if (producer && lane == 0) {
+            G.exit = exit_requested(ctl) ? 1u : 0u;
+            uint32_t item = kNone;
+            if (gemm_cta && !G.exit && !q_try_pop(&ctl->workq, P.workq, &item)) item = kNone;
+            G.gemm_item = item;
+        }
         named_bar_sync(1, bar_threads);
         if (G.exit) break;
+        if constexpr (kGemm) {
+            if (G.gemm_item != kNone) {
+                // GEMM tiles first: short, and other CTAs may wait on the same job
+                drain_gemm_tile(P, G, gops, G.gemm_item, g_stage_uses, g_tiles, bar_threads);
+                idle = false;
+                idle_ns = 256;
+                continue;
+            }
+        }
+        uint32_t mine = kNone;
         if (!producer) mine = team_ok ? G.batch[team * wpb] : kNone;
         if (producer && lane == 0) {
             uint32_t active = 0, limit = 0;
@@ -790,12 +950,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_drain(DrainParams P) {
         // ---- sweep
         if (producer) {
             uint32_t tt = t;
-            if (lane == 0) group_produce(P, G, tt);
+            if (lane == 0) group_produce(P, G, ring, tt);
             t = __shfl_sync(FULL, tt, 0);
         } else {
-            group_consume(P, G, t, mine, rank, wpb);
+            group_consume(P, G, ring, t, mine, rank, wpb);
         }
+        held = kNone;
         named_bar_sync(1, bar_threads);
+    }
+    if constexpr (kGemm) {
+        // release tensor memory (after every tcgen05 operation of this CTA)
+        tc_fence_before();
+        named_bar_sync(1, bar_threads);
+        if (producer) {
+            tc_fence_after();
+            tmem_dealloc(G.gb.tmem, kGemmTmemCols);
+        }
     }
 }
 
@@ -1057,21 +1227,27 @@ namespace cafgpu {
 static cudaError_t drain_attr() {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_drain, cudaFuncAttributeMaxDynamicSharedMemorySize, kDrainSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_drain<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDrainSmemFactor);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_drain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDrainSmemMixed);
     if (e == cudaSuccess) done = true;
     return e;
 }
 
-cudaError_t drain_occupancy(int *ctas_per_sm) {
+cudaError_t drain_occupancy(bool gemm, int *ctas_per_sm) {
     cudaError_t e = drain_attr();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain, kThreads, kDrainSmem);
+    if (gemm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain<true>, kThreads, kDrainSmemMixed);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain<false>, kThreads, kDrainSmemFactor);
 }
 
 cudaError_t launch_drain(const DrainParams &p, unsigned grid, cudaStream_t stream) {
     cudaError_t e = drain_attr();
     if (e != cudaSuccess) return e;
-    k_drain<<<grid, kThreads, kDrainSmem, stream>>>(p);
+    if (p.gemm)
+        k_drain<true><<<grid, kThreads, kDrainSmemMixed, stream>>>(p);
+    else
+        k_drain<false><<<grid, kThreads, kDrainSmemFactor, stream>>>(p);
     return cudaGetLastError();
 }
 

@@ -36,16 +36,19 @@ constexpr uint32_t kGemmConvWarps = 8;
 constexpr uint32_t kGemmOperandBytes = kGemmBM * kGemmBK * 2;   // 16 KB per operand tile
 constexpr uint32_t kGemmTmemCols = 128;
 
-// Shared memory of one GEMM CTA (operand tiles first: 1024-byte aligned).
-struct GemmSmem {
+// Operand tiles of one GEMM CTA (1024-byte aligned: the swizzle pattern
+// repeats every 1024 bytes).
+struct GemmOps {
     uint8_t a_hi[kGemmStages][kGemmOperandBytes];
     uint8_t b_hi[kGemmStages][kGemmOperandBytes];
     uint8_t a_lo[kGemmStages][kGemmOperandBytes];
     uint8_t b_lo[kGemmStages][kGemmOperandBytes];
-    uint64_t full[kGemmStages];     // converters -> MMA thread
-    uint64_t empty[kGemmStages];    // MMA completion -> converters
-    uint64_t done;                  // last MMA completed -> epilogue
-    uint32_t tmem;                  // accumulator address from tcgen05.alloc
+};
+static_assert(sizeof(GemmOps) == kGemmOpsBytes, "operand area size");
+static_assert(kGemmStages == 2, "GemmBars holds two stages");
+struct GemmSmem {
+    GemmOps ops;
+    GemmBars bars;
 };
 
 // ---- tcgen05 wrappers -------------------------------------------------------
@@ -192,18 +195,23 @@ __device__ __forceinline__ GemmSmem &gemm_smem(uint8_t *raw) {
     return *reinterpret_cast<GemmSmem *>(raw + pad);
 }
 
-// Barrier set-up and tensor-memory allocation (whole CTA; warp kGemmConvWarps allocates).
-__device__ __forceinline__ void gemm_cta_init(GemmSmem &S) {
-    const uint32_t warp = threadIdx.x >> 5;
-    if (threadIdx.x == kGemmConvWarps * 32) {
+// Barrier set-up and tensor-memory allocation, run by warp kGemmConvWarps
+// (the caller synchronises the CTA afterwards, with tcgen05 fences).
+__device__ __forceinline__ void gemm_bars_init(GemmBars &Bb) {
+    if (lane_id() == 0) {
         for (uint32_t s = 0; s < kGemmStages; ++s) {
-            mbar_init(&S.full[s], kGemmConvWarps);
-            mbar_init(&S.empty[s], 1);
+            mbar_init(&Bb.full[s], kGemmConvWarps);
+            mbar_init(&Bb.empty[s], 1);
         }
-        mbar_init(&S.done, 1);
+        mbar_init(&Bb.done, 1);
         fence_barrier_init();
     }
-    if (warp == kGemmConvWarps) tmem_alloc(&S.tmem, kGemmTmemCols);
+    __syncwarp();
+    tmem_alloc(&Bb.tmem, kGemmTmemCols);
+}
+
+__device__ __forceinline__ void gemm_cta_init(GemmSmem &S) {
+    if ((threadIdx.x >> 5) == kGemmConvWarps) gemm_bars_init(S.bars);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -214,7 +222,7 @@ __device__ __forceinline__ void gemm_cta_exit(GemmSmem &S) {
     __syncthreads();
     if ((threadIdx.x >> 5) == kGemmConvWarps) {
         tc_fence_after();
-        tmem_dealloc(S.tmem, kGemmTmemCols);
+        tmem_dealloc(S.bars.tmem, kGemmTmemCols);
     }
 }
 
@@ -232,9 +240,16 @@ __device__ __forceinline__ bool gemm_wait(uint64_t *bar, uint32_t parity, uint64
 // `stage_uses` counts operand-stage uses over the CTA's life and `tiles`
 // the tiles it has computed (barrier phases follow from both).  Returns false
 // if a bounded wait expired.
+// Whole-CTA synchronisation for gemm_tile.
+struct CtaSyncAll {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// `cta_sync` synchronises the warps taking part (all kGemmConvWarps + 1).
+template <class CtaSync>
 __device__ bool gemm_tile(const float *__restrict__ A, const float *__restrict__ B, float *__restrict__ C,
-                          uint32_t n, uint32_t tm, uint32_t tn, bool split, GemmSmem &S, uint32_t &stage_uses,
-                          uint32_t &tiles, uint64_t limit_ns) {
+                          uint32_t n, uint32_t tm, uint32_t tn, bool split, GemmOps &S, GemmBars &Bb,
+                          uint32_t &stage_uses, uint32_t &tiles, uint64_t limit_ns, CtaSync cta_sync) {
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t nk = (n + kGemmBK - 1) / kGemmBK;
     bool ok = true;
@@ -242,20 +257,20 @@ __device__ bool gemm_tile(const float *__restrict__ A, const float *__restrict__
         for (uint32_t kb = 0; kb < nk && ok; ++kb) {
             const uint32_t it = stage_uses + kb;
             const uint32_t st = it % kGemmStages, use = it / kGemmStages;
-            if (use >= 1) ok = gemm_wait(&S.empty[st], (use - 1) & 1u, limit_ns);
+            if (use >= 1) ok = gemm_wait(&Bb.empty[st], (use - 1) & 1u, limit_ns);
             if (!__all_sync(0xFFFFFFFFu, ok)) { ok = false; break; }
             gemm_convert_block(A, B, n, tm, tn, kb, S.a_hi[st], S.b_hi[st], S.a_lo[st], S.b_lo[st], split,
                                threadIdx.x);
             fence_proxy_async_smem();   // generic-proxy writes -> tensor-core (async proxy) reads
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S.full[st])) : "memory");
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&Bb.full[st])) : "memory");
         }
     } else if (lane == 0) {
         const uint32_t idesc = gemm_idesc(kGemmBM, kGemmBN);
         for (uint32_t kb = 0; kb < nk && ok; ++kb) {
             const uint32_t it = stage_uses + kb;
             const uint32_t st = it % kGemmStages, use = it / kGemmStages;
-            ok = gemm_wait(&S.full[st], use & 1u, limit_ns);
+            ok = gemm_wait(&Bb.full[st], use & 1u, limit_ns);
             if (!ok) break;
             tc_fence_after();
             const uint64_t ah = smem_desc_sw128(S.a_hi[st]), bh = smem_desc_sw128(S.b_hi[st]);
@@ -263,21 +278,21 @@ __device__ bool gemm_tile(const float *__restrict__ A, const float *__restrict__
 #pragma unroll
             for (uint32_t k16 = 0; k16 < kGemmBK / 16; ++k16) {
                 const uint64_t ko = (k16 * 32u) >> 4;   // 16 BF16 = 32 bytes along k inside the swizzle atom
-                tc_mma_f16(S.tmem, ah + ko, bh + ko, idesc, (kb | k16) != 0);
+                tc_mma_f16(Bb.tmem, ah + ko, bh + ko, idesc, (kb | k16) != 0);
                 if (split) {
-                    tc_mma_f16(S.tmem, ah + ko, bl + ko, idesc, 1u);
-                    tc_mma_f16(S.tmem, al + ko, bh + ko, idesc, 1u);
+                    tc_mma_f16(Bb.tmem, ah + ko, bl + ko, idesc, 1u);
+                    tc_mma_f16(Bb.tmem, al + ko, bh + ko, idesc, 1u);
                 }
             }
-            tc_commit(&S.empty[st]);
+            tc_commit(&Bb.empty[st]);
         }
-        tc_commit(&S.done);
+        tc_commit(&Bb.done);
     }
     stage_uses += nk;
     // epilogue: converter warps read the accumulator (warp w: TMEM lanes
     // 32*(w%4).., columns 64*(w/4)..) and store the tile
     if (warp < kGemmConvWarps) {
-        bool dok = ok && gemm_wait(&S.done, tiles & 1u, limit_ns);
+        bool dok = ok && gemm_wait(&Bb.done, tiles & 1u, limit_ns);
         dok = __all_sync(0xFFFFFFFFu, dok);
         if (dok) {
             tc_fence_after();
@@ -286,7 +301,7 @@ __device__ bool gemm_tile(const float *__restrict__ A, const float *__restrict__
 #pragma unroll
             for (uint32_t cc = 0; cc < 64; cc += 32) {
                 uint32_t r[32];
-                tmem_ld_32x32(S.tmem + (row0 << 16) + col0 + cc, r);
+                tmem_ld_32x32(Bb.tmem + (row0 << 16) + col0 + cc, r);
                 if (gr < n) {
                     float *crow = C + (size_t)gr * n;
                     const uint32_t gc0 = tn * kGemmBN + col0 + cc;
@@ -302,7 +317,7 @@ __device__ bool gemm_tile(const float *__restrict__ A, const float *__restrict__
     // the next tile's MMAs overwrite the accumulator: every epilogue read
     // must be complete first
     tc_fence_before();
-    __syncthreads();
+    cta_sync();
     tc_fence_after();
     return ok;
 }

@@ -39,19 +39,60 @@ struct TableTile {
     uint32_t plim[kTile];
 };
 
-// Per-CTA shared state of the cooperative sweep: the table ring and the
-// group (one factor batch per team of consumer warps) it serves.
+// Barriers and tensor-memory address of the GEMM tile engine.
+struct GemmBars {
+    uint64_t full[2];              // converters -> MMA thread
+    uint64_t empty[2];             // MMA completion -> converters
+    uint64_t done;                 // last MMA completed -> epilogue
+    uint32_t tmem;                 // accumulator address from tcgen05.alloc
+    uint32_t pad;
+};
+
+// Per-CTA shared state of the drain: the table ring's barriers, the GEMM
+// barriers, and the group (one factor batch per team of consumer warps).
+// The operand area -- table tiles, or GEMM operand tiles -- follows at
+// kDrainHeader (1024-byte aligned).
 struct GroupShared {
-    TableTile tile[kStages];
     uint64_t full[kStages];        // producer -> consumers (bulk copies landed)
     uint64_t empty[kStages];       // consumers -> producer (stage free again)
+    GemmBars gb;
     uint32_t batch[kConsumerWarps];
     uint32_t limit_tiles;          // tiles needed by the group's largest bound
     uint32_t final_tile;           // tile index at which the group's stream ends
     uint32_t active;               // consumer warps still holding messages
     uint32_t exit;
+    uint32_t gemm_item;            // GEMM tile this CTA runs next (kNone: none)
 };
-constexpr uint32_t kDrainSmem = (uint32_t)sizeof(GroupShared);
+constexpr uint32_t kDrainHeader = 1024;
+static_assert(sizeof(GroupShared) <= kDrainHeader, "drain header fits");
+constexpr uint32_t kTableRingBytes = kStages * (uint32_t)sizeof(TableTile);
+constexpr uint32_t kGemmOpsBytes = 4u * 2u * 128u * 64u * 2u;   // hi/lo x A/B x 2 stages x 16 KB
+// dynamic shared memory of the drain (+1024 for aligning the base)
+constexpr uint32_t kDrainSmemFactor = 1024 + kDrainHeader + kTableRingBytes;
+constexpr uint32_t kDrainSmemMixed = 1024 + kDrainHeader + (kGemmOpsBytes > kTableRingBytes ? kGemmOpsBytes : kTableRingBytes);
+
+// A GEMM message being computed by the drain: its 128 x 128 output tiles are
+// items (job << 16 | tile) in the tile queue.
+struct GemmJob {
+    uint64_t A, B, C;
+    uint32_t n;
+    uint32_t split;
+    uint32_t tiles;                // tiles of the output
+    uint32_t done;                 // tiles finished (atomic)
+    uint64_t reply_addr;
+    uint32_t reply_token;
+    uint32_t pad[3];
+};
+static_assert(sizeof(GemmJob) == 64, "GemmJob is 64 bytes");
+constexpr uint32_t kMaxDrainGemmN = 4096;   // <= 1024 tiles per job
+constexpr uint32_t kGemmJobs = 1024;         // GEMM messages in flight in the drain
+
+// Operand descriptor referenced by a GEMM message (same layout as caf_gpu_gemm_desc).
+struct GemmDesc {
+    uint64_t A, B, C;
+    uint32_t n;
+    uint32_t pad;
+};
 
 // actor lifecycle (Sec. 6: ready / waiting / running / done)
 enum : uint32_t { kWaiting = 0, kReady = 1, kRunning = 2, kDone = 3 };
@@ -200,7 +241,8 @@ struct DevCtl {
     uint64_t pad3[5];
     QueueHdr readyq;
     QueueHdr freeq;
-    QueueHdr workq;
+    QueueHdr workq;                // GEMM tile items
+    QueueHdr jobq;                 // free GemmJob records
 };
 
 // Host-visible control block (pinned, mapped).
@@ -245,6 +287,11 @@ struct DrainParams {
     HostCtl *hctl;
     uint32_t ring_mask;
     uint32_t live;
+    // GEMM actors (gemm != 0: tensor memory and the GEMM shared-memory layout)
+    GemmJob *jobs;
+    QCell *jobq;
+    uint32_t gemm;
+    uint32_t pad1;
 };
 
 }  // namespace cafgpu

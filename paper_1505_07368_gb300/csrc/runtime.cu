@@ -64,6 +64,11 @@ struct caf_gpu_runtime {
     uint32_t readyq_cap = 0, freeq_cap = 0, workq_cap = 0;
     FactorBatch *d_batches = nullptr;
     uint32_t n_batches = 0;
+    GemmJob *d_jobs = nullptr;
+    QCell *d_jobq = nullptr;
+    uint32_t jobq_cap = 0;
+    bool gemm_enabled = false;             // a GEMM actor exists: drains use the GEMM layout
+    unsigned grid_factor = 0, grid_mixed = 0;
     uint32_t *d_primes = nullptr, *d_pinv = nullptr, *d_plim = nullptr;
     uint32_t nprimes = 0;
     uint64_t prime_limit = 0;
@@ -79,6 +84,7 @@ struct caf_gpu_runtime {
     IngressEntry *ring = nullptr;
     HostCtl *hctl = nullptr;
     Reply *replies = nullptr;
+    GemmDesc *gemm_descs = nullptr;        // one per reply slot (host GEMM requests)
     IngressEntry *outbox = nullptr;
     uint32_t outbox_per_msg = 4;
     uint32_t outbox_msgs = 256;
@@ -134,8 +140,13 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.ring = rt->ring;
     p.hctl = rt->hctl;
     p.ring_mask = rt->cfg.ingress_capacity - 1;
+    p.jobs = rt->d_jobs;
+    p.jobq = rt->d_jobq;
+    p.gemm = rt->gemm_enabled ? 1u : 0u;
     return p;
 }
+
+unsigned drain_grid(caf_gpu_runtime *rt) { return rt->gemm_enabled ? rt->grid_mixed : rt->grid_factor; }
 
 int init_queue(caf_gpu_runtime *rt, QCell **cells, uint32_t cap, QueueHdr *hdr_dev,
                const std::vector<uint32_t> &initial) {
@@ -163,7 +174,7 @@ int launch_live(caf_gpu_runtime *rt) {
     DrainParams p = make_params(rt);
     p.live = 1;
     CK(launch_reset_ctl(rt->d_ctl, rt->stream));
-    CK(launch_drain(p, rt->grid, rt->stream));
+    CK(launch_drain(p, drain_grid(rt), rt->stream));
     CK(cudaEventRecord(rt->live_done, rt->stream));
     rt->live_launched = true;
     rt->launches += 2;
@@ -197,7 +208,7 @@ int check_msg(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *m, uint3
     if (m->kind == kFactor && m->u64 > rt->cfg.max_factor_n) return CAF_GPU_EINVAL;
     if (m->kind == kGemmBf16 || m->kind == kGemmSplit) {
         if (!m->A || !m->B || !m->C || m->n == 0 || m->n > kMaxGemmN) return CAF_GPU_EINVAL;
-        if (rt->backend == CAF_GPU_BACKEND_PERSISTENT) return CAF_GPU_EINVAL;  // drain path: see gemm jobs
+        if (rt->backend == CAF_GPU_BACKEND_PERSISTENT && m->n > kMaxDrainGemmN) return CAF_GPU_EINVAL;
     }
     if (m->kind == kToken) {
         uint32_t state = 0;
@@ -269,11 +280,23 @@ int submit_locked(caf_gpu_runtime *rt, uint32_t a, const caf_gpu_msg *m, uint64_
         return 0;
     }
     IngressEntry e{};
+    uint64_t payload = m->u64;
+    if (m->kind == kGemmBf16 || m->kind == kGemmSplit) {
+        // the drain reads the operands through a descriptor kept with the reply slot
+        if (!reply_addr) return CAF_GPU_EINVAL;
+        const size_t slot = (size_t)((reinterpret_cast<Reply *>(reply_addr)) - rt->replies);
+        GemmDesc *d = &rt->gemm_descs[slot];
+        d->A = (uint64_t)m->A;
+        d->B = (uint64_t)m->B;
+        d->C = (uint64_t)m->C;
+        d->n = m->n;
+        payload = (uint64_t)d;
+    }
     e.actor = a;
     e.kind = m->kind | (m->flags << 16);
     e.sender = m->sender;
     e.sender_seq = rt->sender_seq[m->sender]++;
-    e.payload = m->u64;
+    e.payload = payload;
     e.reply_addr = reply_addr;
     e.reply_token = token;
     e.tag = m->tag;
@@ -333,6 +356,9 @@ void free_runtime(caf_gpu_runtime *rt) {
     cudaFree(rt->d_freeq);
     cudaFree(rt->d_workq);
     cudaFree(rt->d_batches);
+    cudaFree(rt->d_jobs);
+    cudaFree(rt->d_jobq);
+    if (rt->gemm_descs) cudaFreeHost(rt->gemm_descs);
     cudaFree(rt->d_primes);
     cudaFree(rt->d_pinv);
     cudaFree(rt->d_plim);
@@ -376,10 +402,13 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     CK(cudaDeviceGetAttribute(&rt->n_sms, cudaDevAttrMultiProcessorCount, rt->device));
     // every drain CTA must be resident at once (router and ingress warps are
     // waited on by the others), so the grid never exceeds the occupancy limit
-    int fit = 0;
-    CK(drain_occupancy(&fit));
-    if (fit < 1) return CAF_GPU_ECUDA;
-    rt->grid = (unsigned)rt->n_sms * std::min<uint32_t>(c.ctas_per_sm, (uint32_t)fit);
+    int fit = 0, fit_mixed = 0;
+    CK(drain_occupancy(false, &fit));
+    CK(drain_occupancy(true, &fit_mixed));
+    if (fit < 1 || fit_mixed < 1) return CAF_GPU_ECUDA;
+    rt->grid_factor = (unsigned)rt->n_sms * std::min<uint32_t>(c.ctas_per_sm, (uint32_t)fit);
+    rt->grid_mixed = (unsigned)rt->n_sms * std::min<uint32_t>(c.ctas_per_sm, (uint32_t)fit_mixed);
+    rt->grid = rt->grid_factor;
     if (c.cuda_stream) {
         rt->stream = (cudaStream_t)c.cuda_stream;
     } else {
@@ -397,18 +426,24 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     rt->n_slots = (uint64_t)c.max_actors * c.mailbox_capacity;
     CK(cudaMalloc(&rt->d_slots, sizeof(Slot) * rt->n_slots));
     CK(cudaMemset(rt->d_slots, 0, sizeof(Slot) * rt->n_slots));
-    rt->n_batches = std::max<uint32_t>(4096, 2u * rt->grid * kConsumerWarps);
+    rt->n_batches = std::max<uint32_t>(4096, 2u * rt->grid_factor * kConsumerWarps);
     CK(cudaMalloc(&rt->d_batches, sizeof(FactorBatch) * rt->n_batches));
     CK(cudaMemset(rt->d_batches, 0, sizeof(FactorBatch) * rt->n_batches));
     rt->readyq_cap = next_pow2((uint64_t)c.max_actors + 1);
     rt->freeq_cap = next_pow2((uint64_t)rt->n_batches + 1);
-    rt->workq_cap = next_pow2((uint64_t)rt->n_batches * c.factor_warps + 1);
+    rt->workq_cap = next_pow2((uint64_t)kGemmJobs * (kMaxDrainGemmN / 128) * (kMaxDrainGemmN / 128) + 1);
+    rt->jobq_cap = next_pow2((uint64_t)kGemmJobs + 1);
     std::vector<uint32_t> none, all(rt->n_batches);
     for (uint32_t i = 0; i < rt->n_batches; ++i) all[i] = i;
     int r;
     if ((r = init_queue(rt, &rt->d_readyq, rt->readyq_cap, &rt->d_ctl->readyq, none))) return r;
     if ((r = init_queue(rt, &rt->d_freeq, rt->freeq_cap, &rt->d_ctl->freeq, all))) return r;
     if ((r = init_queue(rt, &rt->d_workq, rt->workq_cap, &rt->d_ctl->workq, none))) return r;
+    std::vector<uint32_t> jobs(kGemmJobs);
+    for (uint32_t i = 0; i < kGemmJobs; ++i) jobs[i] = i;
+    if ((r = init_queue(rt, &rt->d_jobq, rt->jobq_cap, &rt->d_ctl->jobq, jobs))) return r;
+    CK(cudaMalloc(&rt->d_jobs, sizeof(GemmJob) * kGemmJobs));
+    CK(cudaMemset(rt->d_jobs, 0, sizeof(GemmJob) * kGemmJobs));
     if (c.validation_mode) {
         CK(cudaMalloc(&rt->d_log, sizeof(LogRow) * (size_t)c.log_capacity));
         CK(cudaMemset(rt->d_log, 0, sizeof(LogRow) * (size_t)c.log_capacity));
@@ -436,6 +471,8 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     memset(rt->hctl, 0, sizeof(HostCtl));
     CK(cudaHostAlloc(&rt->replies, sizeof(Reply) * (size_t)c.max_inflight_requests, cudaHostAllocMapped));
     memset(rt->replies, 0, sizeof(Reply) * (size_t)c.max_inflight_requests);
+    CK(cudaHostAlloc(&rt->gemm_descs, sizeof(GemmDesc) * (size_t)c.max_inflight_requests, cudaHostAllocMapped));
+    memset(rt->gemm_descs, 0, sizeof(GemmDesc) * (size_t)c.max_inflight_requests);
     CK(cudaHostAlloc(&rt->outbox, sizeof(IngressEntry) * rt->outbox_per_msg * rt->outbox_msgs,
                      cudaHostAllocMapped));
     memset(rt->outbox, 0, sizeof(IngressEntry) * rt->outbox_per_msg * rt->outbox_msgs);
@@ -508,6 +545,13 @@ int caf_gpu_runtime_destroy(caf_gpu_runtime *rt) {
 int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_cfg *cfg, caf_gpu_actor *out) {
     if (!rt || !out) return CAF_GPU_EINVAL;
     if (kernel_id < kFactor || kernel_id > kToken) return CAF_GPU_EINVAL;
+    if ((kernel_id == kGemmBf16 || kernel_id == kGemmSplit) && !rt->gemm_enabled) {
+        // drains launched from now on carry tensor memory and the GEMM layout
+        int r = caf_gpu_sync(rt);
+        if (r) return r;
+        std::lock_guard<std::mutex> g(rt->mu);
+        rt->gemm_enabled = true;
+    }
     caf_gpu_actor_cfg c{};
     if (cfg) c = *cfg;
     const uint32_t cap = c.mailbox_capacity ? c.mailbox_capacity : rt->cfg.mailbox_capacity;
@@ -550,6 +594,7 @@ int caf_gpu_send(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *msg) 
     uint32_t a;
     int r = check_msg(rt, to, msg, &a);
     if (r) return r;
+    if (msg->kind == kGemmBf16 || msg->kind == kGemmSplit) return CAF_GPU_EINVAL;  // a GEMM needs a reply
     {
         std::lock_guard<std::mutex> g(rt->mu);
         r = submit_locked(rt, a, msg, 0, 0);
@@ -664,9 +709,9 @@ int caf_gpu_request_batch_device(caf_gpu_runtime *rt, const caf_gpu_dmsg *d_msgs
     p.batch_msgs = d_msgs;
     p.batch_replies = reinterpret_cast<Reply *>(d_replies);
     p.batch_count = count;
-    p.n_routers = std::min<uint32_t>(rt->grid * kConsumerWarps, 128);
+    p.n_routers = std::min<uint32_t>(drain_grid(rt) * kConsumerWarps, 128);
     CK(launch_reset_ctl(rt->d_ctl, rt->stream));
-    CK(launch_drain(p, rt->grid, rt->stream));
+    CK(launch_drain(p, drain_grid(rt), rt->stream));
     rt->launches += 2;
     return 0;
 }

@@ -9,7 +9,7 @@ from paper_1505_07368_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _run(rt, actor, kind, A, B, backend=C.BACKEND_PER_MESSAGE_LAUNCH):
+def _run(rt, actor, kind, A, B, backend=None):
     import torch
     n = A.shape[0]
     dA = torch.from_numpy(np.ascontiguousarray(A)).cuda()
@@ -68,3 +68,89 @@ def test_normal_matrices_error_bounds(rt_pm, n):
     assert e_bf16 <= 1e-2, e_bf16
     assert e_split <= 1e-5, e_split
     assert e_split < e_bf16 / 50
+
+
+# ---- GEMM actors in the persistent drain -----------------------------------
+
+def test_persistent_host_requests():
+    with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=8) as rt:
+        a_bf16 = rt.spawn(C.GEMM_BF16)
+        a_split = rt.spawn(C.GEMM_SPLIT_BF16X3)
+        for n in (64, 100, 256):
+            A = W.integer_matrix(W.stream_key(31, n), n)
+            B = W.integer_matrix(W.stream_key(32, n), n)
+            want = oracle.gemm_f64(A, B)
+            for actor, kind in ((a_bf16, C.GEMM_BF16), (a_split, C.GEMM_SPLIT_BF16X3)):
+                got = _run(rt, actor, kind, A, B, backend=C.BACKEND_PERSISTENT)
+                assert np.array_equal(got.astype(np.float64), want), (n, kind)
+
+
+def _gemm_device_batch(rt, actor_idx, kinds, sizes, pool, seed):
+    """Device batch of GEMM messages with operands at seeded offsets in `pool` (device)."""
+    import torch
+    from helpers import to_device
+    count = len(sizes)
+    offs_a = W._offsets(W.stream_key(seed, 1), np.asarray(sizes), pool.numel())
+    offs_b = W._offsets(W.stream_key(seed, 2), np.asarray(sizes), pool.numel())
+    outs = [torch.full((int(n), int(n)), float("nan"), dtype=torch.float32, device="cuda") for n in sizes]
+    desc = np.zeros(count, C.GEMM_DESC_DTYPE)
+    base = pool.data_ptr()
+    for i, n in enumerate(sizes):
+        desc[i] = (base + 4 * int(offs_a[i]), base + 4 * int(offs_b[i]), outs[i].data_ptr(), int(n), 0)
+    d_desc = to_device(desc)
+    m = np.zeros(count, C.DMSG_DTYPE)
+    m["actor"] = actor_idx
+    m["kind"] = kinds
+    m["u64"] = d_desc.data_ptr() + np.arange(count, dtype=np.uint64) * C.GEMM_DESC_DTYPE.itemsize
+    m["tag"] = np.arange(count)
+    d_m = to_device(m)
+    d_r = torch.zeros(count * C.DREPLY_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    rt.request_batch_device(d_m.data_ptr(), count, d_r.data_ptr())
+    rt.stream_sync()
+    rep = d_r.cpu().numpy().view(C.DREPLY_DTYPE).copy()
+    return rep, offs_a, offs_b, [o.cpu().numpy() for o in outs]
+
+
+def test_persistent_device_batch_mixed_sizes_and_kinds():
+    import torch
+    pool_np = W.gemm_pool(33, 1 << 21)
+    pool = torch.from_numpy(pool_np).cuda()
+    sizes = [64, 128, 200, 256, 33, 512, 96, 384, 448, 64, 160, 320]
+    with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=8) as rt:
+        acts = [rt.spawn(C.GEMM_BF16), rt.spawn(C.GEMM_SPLIT_BF16X3), rt.spawn(C.GEMM_SPLIT_BF16X3)]
+        idx = np.array([acts[i % 3] - 1 for i in range(len(sizes))], np.uint32)
+        kinds = np.array([C.GEMM_BF16 if i % 3 == 0 else C.GEMM_SPLIT_BF16X3 for i in range(len(sizes))], np.uint32)
+        rep, oa, ob, outs = _gemm_device_batch(rt, idx, kinds, sizes, pool, 34)
+        st = rt.stats()
+    assert np.all(rep["done"] == 1) and np.all(rep["status"] == 0)
+    assert np.array_equal(rep["r1"], np.array(sizes, np.uint64))
+    expected_tiles = sum(((n + 127) // 128) ** 2 for n in sizes)
+    assert st["gemm_tiles"] == expected_tiles
+    for i, n in enumerate(sizes):
+        A = pool_np[oa[i]:oa[i] + n * n].reshape(n, n)
+        B = pool_np[ob[i]:ob[i] + n * n].reshape(n, n)
+        err = oracle.rel_frobenius(outs[i], oracle.gemm_f64(A, B))
+        assert err <= (1e-2 if kinds[i] == C.GEMM_BF16 else 1e-5), (n, kinds[i], err)
+
+
+def test_persistent_factor_and_gemm_in_one_drain():
+    import torch
+    pool_np = W.gemm_pool(35, 1 << 20)
+    pool = torch.from_numpy(pool_np).cuda()
+    wl = W.config1()
+    with C.Runtime(max_factor_n=(1 << 40) - 1, max_actors=8) as rt:
+        f = rt.spawn(C.FACTOR_U64)
+        g = rt.spawn(C.GEMM_SPLIT_BF16X3)
+        # GEMM batch and factor batch back to back on the runtime stream
+        from helpers import device_batch
+        sizes = [256, 128, 64, 300]
+        rep_g, oa, ob, outs = _gemm_device_batch(rt, np.full(len(sizes), g - 1, np.uint32),
+                                                 np.full(len(sizes), C.GEMM_SPLIT_BF16X3, np.uint32), sizes, pool, 36)
+        rep_f = device_batch(rt, np.full(wl.count, f - 1, np.uint32), C.FACTOR_U64, wl.n)
+    st, p, q = oracle.factor_batch(wl.n)
+    assert np.array_equal(rep_f["r0"], p) and np.array_equal(rep_f["r1"], q)
+    for i, n in enumerate(sizes):
+        A = pool_np[oa[i]:oa[i] + n * n].reshape(n, n)
+        B = pool_np[ob[i]:ob[i] + n * n].reshape(n, n)
+        assert oracle.rel_frobenius(outs[i], oracle.gemm_f64(A, B)) <= 1e-5
