@@ -263,6 +263,23 @@ int caf_gpu_read_log(caf_gpu_runtime *rt, caf_gpu_log_row *out, uint32_t cap, ui
  * clock in t_done, so t_done - t_mark is a message's latency from the mark. */
 int caf_gpu_mark(caf_gpu_runtime *rt);
 
+/* ---- CUDA graphs -----------------------------------------------------------
+ * The stream-ordered calls -- caf_gpu_reset_actors, caf_gpu_request_batch_device,
+ * caf_gpu_mark -- can be recorded once into a CUDA graph and replayed with one
+ * launch, so a whole actor workload (for example: reset the rings, send each
+ * master its start message, drain to completion) costs one host call.  The
+ * paper has no counterpart; it is how this library batches whole workloads.
+ * Between begin and end those calls are recorded, not run; every call that
+ * waits for the device (send, request, await, sync, stream_sync, read_log,
+ * actor_state) returns CAF_GPU_ESTATE.  The device buffers a recorded call
+ * names must stay valid while the graph exists. */
+typedef struct caf_gpu_graph caf_gpu_graph;   /* opaque */
+int caf_gpu_graph_begin(caf_gpu_runtime *rt);
+int caf_gpu_graph_end(caf_gpu_runtime *rt, caf_gpu_graph **out);
+/* Launch the graph on the runtime stream (returns at once; caf_gpu_stream_sync waits). */
+int caf_gpu_graph_launch(caf_gpu_runtime *rt, caf_gpu_graph *g);
+int caf_gpu_graph_destroy(caf_gpu_graph *g);
+
 /* The runtime's CUDA stream (cudaStream_t). */
 void *caf_gpu_stream(caf_gpu_runtime *rt);
 

@@ -83,6 +83,7 @@ EXPORTS = [
     "caf_gpu_request_batch_device", "caf_gpu_sync", "caf_gpu_stream_sync", "caf_gpu_set_backend",
     "caf_gpu_reset_actors", "caf_gpu_actor_state", "caf_gpu_stats_read", "caf_gpu_read_log",
     "caf_gpu_stream", "caf_gpu_mark", "caf_gpu_prime_table", "caf_gpu_debug_wait_expiry", "caf_gpu_clear_error",
+    "caf_gpu_graph_begin", "caf_gpu_graph_end", "caf_gpu_graph_launch", "caf_gpu_graph_destroy",
     "caf_gpu_factor_static", "caf_gpu_strerror",
 ]
 FACTOR_STATIC_MAX = 4096
@@ -124,6 +125,10 @@ def load(build: bool = True):
         "caf_gpu_clear_error": [vp],
         "caf_gpu_mark": [vp],
         "caf_gpu_factor_static": [vp, u32, vp, vp],
+        "caf_gpu_graph_begin": [vp],
+        "caf_gpu_graph_end": [vp, P(vp)],
+        "caf_gpu_graph_launch": [vp, vp],
+        "caf_gpu_graph_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -278,6 +283,21 @@ class Runtime:
         cnt = ctypes.c_uint32()
         _check(self.L.caf_gpu_read_log(self.h, out.ctypes.data, cap, ctypes.byref(cnt)), "caf_gpu_read_log")
         return out[:cnt.value].copy()
+
+    # -- CUDA graphs ----------------------------------------------------------
+    def graph_begin(self):
+        _check(self.L.caf_gpu_graph_begin(self.h), "caf_gpu_graph_begin")
+
+    def graph_end(self) -> int:
+        g = ctypes.c_void_p()
+        _check(self.L.caf_gpu_graph_end(self.h, ctypes.byref(g)), "caf_gpu_graph_end")
+        return g.value
+
+    def graph_launch(self, g: int):
+        _check(self.L.caf_gpu_graph_launch(self.h, g), "caf_gpu_graph_launch")
+
+    def graph_destroy(self, g: int):
+        _check(self.L.caf_gpu_graph_destroy(g), "caf_gpu_graph_destroy")
 
     def mark(self):
         _check(self.L.caf_gpu_mark(self.h), "caf_gpu_mark")

@@ -104,6 +104,13 @@ struct caf_gpu_runtime {
 
     // per-message backend: messages produced by token kernels, waiting for a launch
     std::deque<IngressEntry> pm_pending;
+
+    bool capturing = false;                // between caf_gpu_graph_begin and _end
+};
+
+struct caf_gpu_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -591,6 +598,7 @@ int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_c
 }
 
 int caf_gpu_send(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *msg) {
+    if (rt && rt->capturing) return CAF_GPU_ESTATE;
     uint32_t a;
     int r = check_msg(rt, to, msg, &a);
     if (r) return r;
@@ -604,6 +612,7 @@ int caf_gpu_send(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *msg) 
 }
 
 int caf_gpu_request(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *msg, caf_gpu_handle *out) {
+    if (rt && rt->capturing) return CAF_GPU_ESTATE;
     if (!out) return CAF_GPU_EINVAL;
     uint32_t a;
     int r = check_msg(rt, to, msg, &a);
@@ -624,6 +633,7 @@ int caf_gpu_request(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *ms
 int caf_gpu_request_batch(caf_gpu_runtime *rt, const caf_gpu_actor *to, const caf_gpu_msg *msgs, uint32_t count,
                           caf_gpu_handle *out) {
     if (!rt || (count && (!to || !msgs || !out))) return CAF_GPU_EINVAL;
+    if (rt->capturing) return CAF_GPU_ESTATE;
     for (uint32_t i = 0; i < count; ++i) {
         uint32_t a;
         int r = check_msg(rt, to[i], &msgs[i], &a);
@@ -649,6 +659,7 @@ int caf_gpu_request_batch(caf_gpu_runtime *rt, const caf_gpu_actor *to, const ca
 
 int caf_gpu_await(caf_gpu_runtime *rt, caf_gpu_handle h, uint64_t timeout_ns, caf_gpu_reply *out) {
     if (!rt || !out) return CAF_GPU_EINVAL;
+    if (rt->capturing) return CAF_GPU_ESTATE;
     const uint32_t slot = (uint32_t)(h & 0xFFFFFFFFu) - 1;
     const uint32_t gen = (uint32_t)(h >> 32);
     {
@@ -718,6 +729,7 @@ int caf_gpu_request_batch_device(caf_gpu_runtime *rt, const caf_gpu_dmsg *d_msgs
 
 int caf_gpu_sync(caf_gpu_runtime *rt) {
     if (!rt) return CAF_GPU_EINVAL;
+    if (rt->capturing) return CAF_GPU_ESTATE;
     if (rt->backend == CAF_GPU_BACKEND_PER_MESSAGE_LAUNCH) {
         std::lock_guard<std::mutex> g(rt->mu);
         int r = pm_pump(rt);
@@ -730,6 +742,7 @@ int caf_gpu_sync(caf_gpu_runtime *rt) {
 
 int caf_gpu_stream_sync(caf_gpu_runtime *rt) {
     if (!rt) return CAF_GPU_EINVAL;
+    if (rt->capturing) return CAF_GPU_ESTATE;
     CK(cudaStreamSynchronize(rt->stream));
     if (rt->hctl->error_word) return CAF_GPU_EWAITLIMIT;
     uint32_t err = 0;
@@ -739,6 +752,7 @@ int caf_gpu_stream_sync(caf_gpu_runtime *rt) {
 
 int caf_gpu_set_backend(caf_gpu_runtime *rt, int backend) {
     if (!rt) return CAF_GPU_EINVAL;
+    if (rt->capturing) return CAF_GPU_ESTATE;
     if (backend != CAF_GPU_BACKEND_PERSISTENT && backend != CAF_GPU_BACKEND_PER_MESSAGE_LAUNCH)
         return CAF_GPU_EINVAL;
     int r = caf_gpu_sync(rt);
@@ -758,6 +772,7 @@ int caf_gpu_reset_actors(caf_gpu_runtime *rt) {
 
 int caf_gpu_actor_state(caf_gpu_runtime *rt, caf_gpu_actor a, uint32_t *lifecycle, int32_t *user_state) {
     if (!rt || a == 0 || a > rt->n_actors) return CAF_GPU_EINVAL;
+    if (rt->capturing) return CAF_GPU_ESTATE;
     ActorDesc d;
     CK(cudaMemcpy(&d, &rt->d_actors[a - 1], sizeof(d), cudaMemcpyDeviceToHost));
     if (lifecycle) *lifecycle = d.state;
@@ -789,6 +804,7 @@ int caf_gpu_stats_read(caf_gpu_runtime *rt, caf_gpu_stats *out) {
 
 int caf_gpu_read_log(caf_gpu_runtime *rt, caf_gpu_log_row *out, uint32_t cap, uint32_t *count) {
     if (!rt || !count) return CAF_GPU_EINVAL;
+    if (rt->capturing) return CAF_GPU_ESTATE;
     if (!rt->d_log) return CAF_GPU_ESTATE;
     CK(cudaStreamSynchronize(rt->stream));
     uint64_t n = 0;
@@ -807,6 +823,50 @@ int caf_gpu_mark(caf_gpu_runtime *rt) {
     std::lock_guard<std::mutex> g(rt->mu);
     CK(launch_mark(rt->d_ctl, rt->stream));
     rt->launches += 1;
+    return 0;
+}
+
+int caf_gpu_graph_begin(caf_gpu_runtime *rt) {
+    if (!rt) return CAF_GPU_EINVAL;
+    if (rt->capturing || rt->backend != CAF_GPU_BACKEND_PERSISTENT) return CAF_GPU_ESTATE;
+    int r = caf_gpu_sync(rt);   // no live drain may be running on the stream being captured
+    if (r) return r;
+    std::lock_guard<std::mutex> g(rt->mu);
+    CK(cudaStreamBeginCapture(rt->stream, cudaStreamCaptureModeThreadLocal));
+    rt->capturing = true;
+    return 0;
+}
+
+int caf_gpu_graph_end(caf_gpu_runtime *rt, caf_gpu_graph **out) {
+    if (!rt || !out) return CAF_GPU_EINVAL;
+    std::lock_guard<std::mutex> g(rt->mu);
+    if (!rt->capturing) return CAF_GPU_ESTATE;
+    rt->capturing = false;
+    caf_gpu_graph *gr = new caf_gpu_graph();
+    if (cudaStreamEndCapture(rt->stream, &gr->graph) != cudaSuccess ||
+        cudaGraphInstantiate(&gr->exec, gr->graph, 0) != cudaSuccess) {
+        if (gr->graph) cudaGraphDestroy(gr->graph);
+        delete gr;
+        return CAF_GPU_ECUDA;
+    }
+    *out = gr;
+    return 0;
+}
+
+int caf_gpu_graph_launch(caf_gpu_runtime *rt, caf_gpu_graph *gr) {
+    if (!rt || !gr) return CAF_GPU_EINVAL;
+    std::lock_guard<std::mutex> g(rt->mu);
+    if (rt->capturing) return CAF_GPU_ESTATE;
+    if (live_running(rt)) return CAF_GPU_ESTATE;   // a live drain owns the stream; sync first
+    CK(cudaGraphLaunch(gr->exec, rt->stream));
+    return 0;
+}
+
+int caf_gpu_graph_destroy(caf_gpu_graph *gr) {
+    if (!gr) return CAF_GPU_EINVAL;
+    if (gr->exec) cudaGraphExecDestroy(gr->exec);
+    if (gr->graph) cudaGraphDestroy(gr->graph);
+    delete gr;
     return 0;
 }
 

@@ -113,3 +113,38 @@ def test_rings_per_message_launch():
             for h in ring:
                 assert rt.actor_state(h)[0] == 3
     _check_factors(d_rep, wl)
+
+
+def test_config4_captured_graph_replays():
+    """The whole ring workload (reset the rings, start every master, drain) is
+    recorded once as a CUDA graph and replayed; each replay must reproduce the
+    exact per-ring traces and the factor replies."""
+    import torch
+    wl = W.config4()
+    with C.Runtime(max_actors=wl.n_rings * (wl.ring_len + 1), validation_mode=1) as rt:
+        masters, members, d_n, d_rep = build_rings(rt, wl)
+        m = np.zeros(len(masters), C.DMSG_DTYPE)
+        m["actor"] = np.array([h - 1 for h in masters], np.uint32)
+        m["kind"] = C.RING_TOKEN | (C.MSG_START << 16)
+        m["u64"] = wl.token
+        d_m = to_device(m)
+        d_r = torch.zeros(len(masters) * C.DREPLY_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        rt.graph_begin()
+        rt.reset_actors()
+        rt.request_batch_device(d_m.data_ptr(), len(masters), d_r.data_ptr())
+        with pytest.raises(C.CafGpuError) as e:
+            rt.sync()                         # waiting calls are refused while recording
+        assert e.value.code == C.ESTATE
+        g = rt.graph_end()
+        try:
+            for _ in range(3):
+                d_rep.zero_()
+                torch.cuda.synchronize()
+                rt.graph_launch(g)
+                rt.stream_sync()
+                log = rt.read_log()
+                _check_traces(log, members, wl)
+                _check_factors(d_rep, wl)
+        finally:
+            rt.graph_destroy(g)
