@@ -297,6 +297,60 @@ int caf_gpu_debug_wait_expiry(caf_gpu_runtime *rt, uint64_t limit_ns);
 /* Clear the device error word after a reported bounded-wait expiry. */
 int caf_gpu_clear_error(caf_gpu_runtime *rt);
 
+/* ---- serving loop ---------------------------------------------------------
+ * Open-loop serving with continuous batching.  Requests arrive at their
+ * t_arrival (seconds from the start of the run, non-decreasing); a request
+ * is admitted, in arrival order, once the bytes of the requests in flight
+ * plus its own fit the memory budget (GEMM: 12 n^2 bytes for A, B and C;
+ * factorization: 0) and its result buffer can be placed in the caller's
+ * result arena.  Admitted requests go to the running drain at once, so new
+ * work overlaps work already on the GPU; memory and reply slots are released
+ * as replies arrive.  The paper has no serving experiment; this is the
+ * measurement harness of the library, in the library so its timestamps are
+ * taken next to the calls they time.
+ *
+ * Ownership: reqs, results and stats are host arrays owned by the caller.
+ * GEMM operands A and B are the caller's device matrices, borrowed for the
+ * run; each GEMM result is written into c_arena (caller's device memory) at
+ * results[i].c_offset (bytes) and stays there until the next run. */
+typedef struct {
+    caf_gpu_actor actor;            /* receiver (its kind is the request kind)                */
+    double   t_arrival;             /* seconds from the start of the run                      */
+    uint64_t u64;                   /* FACTOR_U64: n                                          */
+    uint32_t n;                     /* GEMM: matrix size                                      */
+    uint32_t pad;
+    const float *A;                 /* GEMM operands (device), n x n row-major                */
+    const float *B;
+} caf_gpu_serve_req;
+
+typedef struct {
+    int32_t  status;                /* reply status                                            */
+    uint32_t pad;
+    uint64_t r0, r1;                /* reply values                                            */
+    uint64_t c_offset;              /* GEMM: byte offset of C in c_arena                       */
+    double   t_admit;               /* seconds from the start: admitted and sent               */
+    double   t_done;                /* seconds from the start: reply seen by the host          */
+} caf_gpu_serve_result;
+
+typedef struct {
+    uint64_t mem_budget_bytes;      /* 0: the runtime's mem_budget_bytes                      */
+    void    *c_arena;               /* device memory for GEMM results                         */
+    uint64_t c_arena_bytes;
+    uint64_t timeout_ns;            /* give up (ETIMEDOUT) after this long; 0 = no limit      */
+} caf_gpu_serve_cfg;
+
+typedef struct {
+    double   wall_s;                /* first arrival to last reply                             */
+    uint64_t peak_inflight_bytes;   /* never above the budget                                  */
+    uint32_t peak_inflight;         /* requests in flight at most                              */
+    uint32_t pad;
+    uint64_t launches;              /* kernels launched by the runtime during the run          */
+} caf_gpu_serve_stats;
+
+int caf_gpu_serve_run(caf_gpu_runtime *rt, const caf_gpu_serve_req *reqs, uint32_t count,
+                      const caf_gpu_serve_cfg *cfg, caf_gpu_serve_result *results,
+                      caf_gpu_serve_stats *stats);
+
 /* ---- factorization without device allocation ----------------------------
  *
  * The paper has no counterpart to this call: it exists for callers of this

@@ -76,6 +76,22 @@ class Stats(ctypes.Structure):
                 ("diag0", ctypes.c_uint64), ("diag1", ctypes.c_uint64), ("t_mark", ctypes.c_uint64)]
 
 
+SERVE_REQ_DTYPE = np.dtype([("actor", "<u8"), ("t_arrival", "<f8"), ("u64", "<u8"), ("n", "<u4"), ("pad", "<u4"),
+                            ("A", "<u8"), ("B", "<u8")])
+SERVE_RESULT_DTYPE = np.dtype([("status", "<i4"), ("pad", "<u4"), ("r0", "<u8"), ("r1", "<u8"),
+                               ("c_offset", "<u8"), ("t_admit", "<f8"), ("t_done", "<f8")])
+
+
+class ServeCfg(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("c_arena", ctypes.c_void_p),
+                ("c_arena_bytes", ctypes.c_uint64), ("timeout_ns", ctypes.c_uint64)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("wall_s", ctypes.c_double), ("peak_inflight_bytes", ctypes.c_uint64),
+                ("peak_inflight", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("launches", ctypes.c_uint64)]
+
+
 # Every symbol include/caf_gpu.h declares (checked by the CPU tests).
 EXPORTS = [
     "caf_gpu_runtime_create", "caf_gpu_runtime_destroy", "caf_gpu_spawn", "caf_gpu_send",
@@ -84,7 +100,7 @@ EXPORTS = [
     "caf_gpu_reset_actors", "caf_gpu_actor_state", "caf_gpu_stats_read", "caf_gpu_read_log",
     "caf_gpu_stream", "caf_gpu_mark", "caf_gpu_prime_table", "caf_gpu_debug_wait_expiry", "caf_gpu_clear_error",
     "caf_gpu_graph_begin", "caf_gpu_graph_end", "caf_gpu_graph_launch", "caf_gpu_graph_destroy",
-    "caf_gpu_factor_static", "caf_gpu_strerror",
+    "caf_gpu_serve_run", "caf_gpu_factor_static", "caf_gpu_strerror",
 ]
 FACTOR_STATIC_MAX = 4096
 
@@ -129,6 +145,7 @@ def load(build: bool = True):
         "caf_gpu_graph_end": [vp, P(vp)],
         "caf_gpu_graph_launch": [vp, vp],
         "caf_gpu_graph_destroy": [vp],
+        "caf_gpu_serve_run": [vp, vp, u32, P(ServeCfg), vp, P(ServeStats)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -283,6 +300,19 @@ class Runtime:
         cnt = ctypes.c_uint32()
         _check(self.L.caf_gpu_read_log(self.h, out.ctypes.data, cap, ctypes.byref(cnt)), "caf_gpu_read_log")
         return out[:cnt.value].copy()
+
+    # -- serving -----------------------------------------------------------------
+    def serve_run(self, reqs: np.ndarray, c_arena: int = 0, c_arena_bytes: int = 0, mem_budget_bytes: int = 0,
+                  timeout_ns: int = 0):
+        """Run the open-loop serving loop over `reqs` (SERVE_REQ_DTYPE, sorted by
+        t_arrival).  Returns (results as SERVE_RESULT_DTYPE, stats dict)."""
+        reqs = np.ascontiguousarray(reqs, dtype=SERVE_REQ_DTYPE)
+        res = np.zeros(reqs.size, dtype=SERVE_RESULT_DTYPE)
+        cfg = ServeCfg(mem_budget_bytes, c_arena or None, c_arena_bytes, timeout_ns)
+        st = ServeStats()
+        self._diag(self.L.caf_gpu_serve_run(self.h, reqs.ctypes.data, reqs.size, ctypes.byref(cfg),
+                                            res.ctypes.data, ctypes.byref(st)), "caf_gpu_serve_run")
+        return res, {k: getattr(st, k) for k, _ in ServeStats._fields_ if k != "pad"}
 
     # -- CUDA graphs ----------------------------------------------------------
     def graph_begin(self):

@@ -826,6 +826,186 @@ int caf_gpu_mark(caf_gpu_runtime *rt) {
     return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Serving loop
+// ---------------------------------------------------------------------------
+namespace {
+
+// Ring allocator over the caller's result arena: allocations in admission
+// order, space reclaimed from the oldest block once it is freed.
+struct ArenaRing {
+    uint64_t size = 0, head = 0, tail = 0;     // byte positions modulo size; head - tail in use
+    struct Block { uint64_t start, len; bool freed; };
+    std::deque<Block> blocks;
+    // *off: byte offset in the arena; *id: the block's position (for free_block)
+    bool alloc(uint64_t len, uint64_t *off, uint64_t *id) {
+        len = (len + 255) & ~255ull;
+        if (len > size) return false;
+        uint64_t pos = head % size;
+        uint64_t skip = 0;
+        if (pos + len > size) skip = size - pos;       // do not wrap inside a block
+        if (head + skip + len - tail > size) return false;
+        if (skip) blocks.push_back({head, skip, true});
+        head += skip;
+        *off = head % size;
+        *id = head;
+        blocks.push_back({head, len, false});
+        head += len;
+        return true;
+    }
+    // undo the most recent alloc (and its wrap filler)
+    void undo_last() {
+        if (blocks.empty()) return;
+        head = blocks.back().start;
+        blocks.pop_back();
+        if (!blocks.empty() && blocks.back().freed && blocks.back().start + blocks.back().len == head &&
+            head % size == 0) {
+            head = blocks.back().start;
+            blocks.pop_back();
+        }
+    }
+    void free_block(uint64_t start) {
+        for (auto &b : blocks)
+            if (b.start == start && !b.freed) {
+                b.freed = true;
+                break;
+            }
+        while (!blocks.empty() && blocks.front().freed) {
+            tail = blocks.front().start + blocks.front().len;
+            blocks.pop_front();
+        }
+    }
+};
+
+struct Inflight {
+    uint32_t req, slot, gen;
+    uint64_t bytes, arena_start;
+    bool gemm;
+};
+
+}  // namespace
+
+int caf_gpu_serve_run(caf_gpu_runtime *rt, const caf_gpu_serve_req *reqs, uint32_t count,
+                      const caf_gpu_serve_cfg *cfg, caf_gpu_serve_result *results, caf_gpu_serve_stats *stats) {
+    if (!rt || (count && (!reqs || !results))) return CAF_GPU_EINVAL;
+    if (rt->capturing) return CAF_GPU_ESTATE;
+    caf_gpu_serve_cfg c{};
+    if (cfg) c = *cfg;
+    const uint64_t budget = c.mem_budget_bytes ? c.mem_budget_bytes : rt->cfg.mem_budget_bytes;
+    // validate everything before the clock starts
+    for (uint32_t i = 0; i < count; ++i) {
+        const caf_gpu_serve_req &q = reqs[i];
+        if (q.actor == 0 || q.actor > rt->n_actors) return CAF_GPU_EINVAL;
+        if (i && q.t_arrival < reqs[i - 1].t_arrival) return CAF_GPU_EINVAL;
+        const uint32_t kind = rt->actors[q.actor - 1].kind;
+        if (kind == kGemmBf16 || kind == kGemmSplit) {
+            if (!q.A || !q.B || q.n == 0 || q.n > kMaxDrainGemmN || !c.c_arena) return CAF_GPU_EINVAL;
+            if (12ull * q.n * q.n > budget || 4ull * q.n * q.n > c.c_arena_bytes) return CAF_GPU_EINVAL;
+        } else if (kind == kFactor) {
+            if (q.u64 > rt->cfg.max_factor_n) return CAF_GPU_EINVAL;
+        } else {
+            return CAF_GPU_EINVAL;
+        }
+    }
+    int r = caf_gpu_sync(rt);
+    if (r) return r;
+    ArenaRing arena;
+    arena.size = c.c_arena_bytes;
+    std::deque<uint32_t> pending;
+    std::vector<Inflight> inflight;
+    uint64_t inflight_bytes = 0, peak_bytes = 0;
+    uint32_t peak_n = 0, next = 0, done = 0;
+    const uint64_t launches0 = rt->launches;
+    const uint64_t t0 = now_ns();
+    auto secs = [&](uint64_t t) { return (double)(t - t0) * 1e-9; };
+    while (done < count) {
+        const uint64_t now = now_ns();
+        if (c.timeout_ns && now - t0 > c.timeout_ns) return CAF_GPU_ETIMEDOUT;
+        if (load_acquire(&rt->hctl->error_word)) return CAF_GPU_EWAITLIMIT;
+        const double tnow = secs(now);
+        while (next < count && reqs[next].t_arrival <= tnow) pending.push_back(next++);
+        bool progress = false;
+        {
+            std::lock_guard<std::mutex> g(rt->mu);
+            while (!pending.empty()) {
+                const uint32_t i = pending.front();
+                const caf_gpu_serve_req &q = reqs[i];
+                const uint32_t kind = rt->actors[q.actor - 1].kind;
+                const bool gemm = kind != kFactor;
+                const uint64_t bytes = gemm ? 12ull * q.n * q.n : 0;
+                if (inflight_bytes + bytes > budget) break;
+                uint64_t off = 0, id = 0;
+                if (gemm && !arena.alloc(4ull * q.n * q.n, &off, &id)) break;
+                uint32_t slot, gen;
+                if (reserve_reply(rt, &slot, &gen)) {
+                    if (gemm) arena.undo_last();
+                    break;
+                }
+                caf_gpu_msg m{};
+                m.kind = kind;
+                m.sender = 0;
+                m.u64 = q.u64;
+                m.n = q.n;
+                m.A = q.A;
+                m.B = q.B;
+                m.C = gemm ? reinterpret_cast<float *>(static_cast<uint8_t *>(c.c_arena) + off) : nullptr;
+                m.tag = i;
+                r = submit_locked(rt, q.actor - 1, &m, (uint64_t)&rt->replies[slot], gen);
+                if (r) return r;
+                results[i].c_offset = off;
+                results[i].t_admit = secs(now_ns());
+                inflight.push_back({i, slot, gen, bytes, id, gemm});
+                inflight_bytes += bytes;
+                peak_bytes = std::max(peak_bytes, inflight_bytes);
+                peak_n = std::max<uint32_t>(peak_n, (uint32_t)inflight.size());
+                pending.pop_front();
+                progress = true;
+            }
+            if (progress) {
+                r = kick_locked(rt);
+                if (r) return r;
+            }
+        }
+        // completions
+        for (size_t k = 0; k < inflight.size();) {
+            Inflight &f = inflight[k];
+            if (load_acquire(&rt->replies[f.slot].done) == f.gen) {
+                const Reply &rep = rt->replies[f.slot];
+                caf_gpu_serve_result &res = results[f.req];
+                res.status = rep.status;
+                res.r0 = rep.r0;
+                res.r1 = rep.r1;
+                res.t_done = secs(now_ns());
+                {
+                    std::lock_guard<std::mutex> g(rt->mu);
+                    rt->in_use[f.slot] = 0;
+                    rt->free_slots.push_back(f.slot);
+                }
+                inflight_bytes -= f.bytes;
+                if (f.gemm) arena.free_block(f.arena_start);
+                ++done;
+                progress = true;
+                f = inflight.back();
+                inflight.pop_back();
+            } else {
+                ++k;
+            }
+        }
+        if (!progress) {
+            kick(rt);
+            std::this_thread::yield();
+        }
+    }
+    if (stats) {
+        stats->wall_s = secs(now_ns());
+        stats->peak_inflight_bytes = peak_bytes;
+        stats->peak_inflight = peak_n;
+        stats->pad = 0;
+        stats->launches = rt->launches - launches0;
+    }
+    return 0;
+}
+
 int caf_gpu_graph_begin(caf_gpu_runtime *rt) {
     if (!rt) return CAF_GPU_EINVAL;
     if (rt->capturing || rt->backend != CAF_GPU_BACKEND_PERSISTENT) return CAF_GPU_ESTATE;

@@ -391,13 +391,17 @@ class ServingWorkload:
 
 def config5(seed: int = SEED_BASE + 5, n_requests: int = 1_000_000, rate: float = 1e5,
             frac_factor: float = 0.7, n_factor_actors: int = 2048, n_gemm_actors: int = 1024,
-            pool_elems: int = 1 << 24, max_gemm: int = 2048) -> ServingWorkload:
+            pool_elems: int = 1 << 24, max_gemm: int = 2048, factor_lo: int = 1 << 16,
+            factor_hi: int = 1 << 31) -> ServingWorkload:
+    """Open-loop serving mix: Poisson arrivals at `rate`/s, `frac_factor` factorization
+    requests (log-uniform prime factors in [factor_lo, factor_hi)), the rest split-BF16x3
+    GEMMs with n log-uniform in [32, max_gemm].  Smaller ranges give the parity cases."""
     gaps = -np.log(uniform_open(stream_key(seed, 11), 0, n_requests)) / rate
     t = np.cumsum(gaps)
     is_factor = uniform01(stream_key(seed, 12), 0, n_requests) < frac_factor
     nf = int(is_factor.sum())
     ng = n_requests - nf
-    nn, pp, qq = semiprimes(primes_loguniform(stream_key(seed, 13), 2 * nf, 1 << 16, 1 << 31))
+    nn, pp, qq = semiprimes(primes_loguniform(stream_key(seed, 13), 2 * nf, factor_lo, factor_hi))
     a, b = math.log(32), math.log(max_gemm)
     sizes = np.rint(np.exp(a + uniform01(stream_key(seed, 14), 0, ng) * (b - a))).astype(np.int64)
     sizes = np.clip(sizes, 32, max_gemm)

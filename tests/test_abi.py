@@ -36,6 +36,10 @@ def test_struct_sizes():
     assert cafgpu.DREPLY_DTYPE.itemsize == 32
     assert cafgpu.GEMM_DESC_DTYPE.itemsize == 32
     assert cafgpu.LOG_DTYPE.itemsize == 40
+    assert cafgpu.SERVE_REQ_DTYPE.itemsize == 48
+    assert cafgpu.SERVE_RESULT_DTYPE.itemsize == 48
+    assert ctypes.sizeof(cafgpu.ServeCfg) == 32
+    assert ctypes.sizeof(cafgpu.ServeStats) == 32
     assert ctypes.sizeof(cafgpu.RuntimeCfg) == 80
 
 
