@@ -62,6 +62,11 @@ def parse_args(argv=None):
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--max-messages", type=int, default=None, help="truncate the workload (profiling)")
+    ap.add_argument("--workload", choices=["factor", "gemm", "ring", "serve"], default="factor",
+                    help="factor: the batched-factorization line (default); the others measure the "
+                         "GEMM, token-ring and serving configurations")
+    ap.add_argument("--no-autotune", action="store_true", help="use --factor-batch/--factor-warps as given")
+    ap.add_argument("--requests", type=int, default=100_000, help="serve: requests in the trace")
     return ap.parse_args(argv)
 
 
@@ -249,6 +254,15 @@ def run_ours(args):
 
     wl = W.config2(max_messages=args.max_messages)
     count = wl.count
+    tuned = None
+    if not args.no_autotune:
+        from paper_1505_07368_gb300 import autotune
+        best, table = autotune.tune_factor(wl.actor, wl.n, wl.n_actors, (1 << 56) - 1,
+                                           runtime_kwargs={"mailbox_capacity": 512},
+                                           log=lambda m: print(m, file=sys.stderr))
+        args.factor_batch, args.factor_warps, args.ctas_per_sm = (best["factor_batch"], best["factor_warps"],
+                                                                  best["ctas_per_sm"])
+        tuned = {"best": best, "measured": [[c, round(t * 1e3, 2)] for c, t in table] or "cached"}
     rt = C.Runtime(max_factor_n=(1 << 56) - 1, max_actors=wl.n_actors, mailbox_capacity=512,
                    ingress_capacity=1 << 17, max_inflight_requests=1 << 17, factor_batch=args.factor_batch,
                    factor_warps=args.factor_warps, ctas_per_sm=args.ctas_per_sm)
@@ -333,7 +347,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "messages": count, "actors": wl.n_actors,
                    "factor_batch": args.factor_batch, "factor_warps": args.factor_warps,
                    "ctas_per_sm": args.ctas_per_sm, "l2": "flushed between steps (256 MiB write)",
-                   "timing": "CUDA events on the runtime stream, per step"},
+                   "timing": "CUDA events on the runtime stream, per step",
+                   "autotune": tuned if tuned else "off"},
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
                        "max": float(lat_ms.max()), "from": "step start (device clock) to reply written"},
         "gpu_launches": st["launches"],
@@ -407,10 +422,234 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# other configurations (measurement lines for the record; the default line is
+# the default batched-factorization workload)
+# ---------------------------------------------------------------------------
+def _events(stream):
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_gemm(args):
+    """GEMM actors: 256 actors, 4096 messages, n uniform in {64, ..., 1024}, N(0,1)
+    operands (views into a 256 MiB pool), BF16 and split-BF16x3, one drain per step."""
+    import torch
+
+    from paper_1505_07368_gb300 import cafgpu as C
+    torch.cuda.set_device(0)
+    wl = W.config3(pool_elems=1 << 26)
+    pool = torch.from_numpy(W.gemm_pool(wl.pool_seed, wl.pool_elems)).cuda()
+    sizes = wl.size.astype(np.int64)
+    outs = torch.empty(int((4 * sizes * sizes).sum() // 4), dtype=torch.float32, device="cuda")
+    c_off = np.concatenate([[0], np.cumsum(sizes * sizes)[:-1]])
+    desc = np.zeros(wl.count, C.GEMM_DESC_DTYPE)
+    desc["A"] = pool.data_ptr() + 4 * wl.a_off.astype(np.uint64)
+    desc["B"] = pool.data_ptr() + 4 * wl.b_off.astype(np.uint64)
+    desc["C"] = outs.data_ptr() + 4 * c_off.astype(np.uint64)
+    desc["n"] = sizes
+    d_desc = torch.from_numpy(desc.view(np.uint8).copy()).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    useful_flops = float((2 * sizes.astype(np.float64) ** 3).sum())
+    alg_bytes = float((12 * sizes.astype(np.float64) ** 2).sum())
+    peaks = measured_peaks()
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "bf16 operands, f32 accumulate", "data": "synthetic",
+            "config": {"workload": "GEMM actors: 256 actors, 4096 messages, n uniform in {64,...,1024}, N(0,1)",
+                       "messages": wl.count, "l2": "flushed between steps (256 MiB write)"}, "variants": {}}
+    for kind, name in ((C.GEMM_BF16, "bf16"), (C.GEMM_SPLIT_BF16X3, "split_bf16x3")):
+        with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=wl.n_actors, mailbox_capacity=64) as rt:
+            for _ in range(wl.n_actors):
+                rt.spawn(kind)
+            m = np.zeros(wl.count, C.DMSG_DTYPE)
+            m["actor"] = wl.actor
+            m["kind"] = kind
+            m["u64"] = d_desc.data_ptr() + np.arange(wl.count, dtype=np.uint64) * 32
+            m["tag"] = np.arange(wl.count)
+            d_m = torch.from_numpy(m.view(np.uint8).copy()).cuda()
+            d_r = torch.zeros(wl.count * 32, dtype=torch.uint8, device="cuda")
+            stream = torch.cuda.ExternalStream(rt.stream())
+            torch.cuda.synchronize()
+            for _ in range(args.warmup):
+                rt.request_batch_device(d_m.data_ptr(), wl.count, d_r.data_ptr())
+            rt.stream_sync()
+            times = []
+            for _ in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.add_(1.0)
+                e0, e1 = _events(stream)
+                e0.record(stream)
+                rt.mark()
+                rt.request_batch_device(d_m.data_ptr(), wl.count, d_r.data_ptr())
+                e1.record(stream)
+                rt.stream_sync()
+                times.append(e0.elapsed_time(e1) / 1e3)
+            st = rt.stats()
+            rep = d_r.cpu().numpy().view(C.DREPLY_DTYPE)
+            if not (np.all(rep["status"] == 0) and np.array_equal(rep["r1"], sizes.astype(np.uint64))):
+                raise SystemExit("bench: GEMM replies incomplete")
+            lat = (rep["t_done"].astype(np.int64) - np.int64(st["t_mark"])) / 1e6
+            t = float(np.mean(times))
+            mult = 3.0 if kind == C.GEMM_SPLIT_BF16X3 else 1.0
+            v = {"value": wl.count / t, "ms_per_step": 1e3 * t,
+                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                 "roofline": {
+                     "hbm": {"achieved": alg_bytes / t / 1e9, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                             "frac": alg_bytes / t / 1e9 / peaks.get("hbm_gbs", 6800.0)},
+                     "tensor": {"achieved": mult * useful_flops / t / 1e12,
+                                "peak": peaks.get("bf16_tflops", 1900.0), "unit": "TFLOP/s",
+                                "frac": mult * useful_flops / t / 1e12 / peaks.get("bf16_tflops", 1900.0),
+                                "note": "executed flops (split: 3 products per useful one)"}},
+                 "useful_tflops": useful_flops / t / 1e12, "gpu_launches": st["launches"]}
+            if not args.skip_per_message:
+                rt.set_backend(C.BACKEND_PER_MESSAGE_LAUNCH)
+                msgs = (C.Msg * wl.count)()
+                for i in range(wl.count):
+                    msgs[i] = C.Runtime.msg(kind, n=int(sizes[i]), A=int(desc["A"][i]), B=int(desc["B"][i]),
+                                            C=int(desc["C"][i]), tag=i)
+                e0, e1 = _events(stream)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                h = rt.request_batch(wl.actor.astype(np.uint64) + 1, msgs)
+                e1.record(stream)
+                rt.await_batch(h)
+                torch.cuda.synchronize()
+                pm = e0.elapsed_time(e1) / 1e3
+                v["per_message_launch"] = {"value": wl.count / pm, "ms": 1e3 * pm,
+                                           "speedup_persistent": (wl.count / t) / (wl.count / pm)}
+            line["variants"][name] = v
+    line["value"] = line["variants"]["split_bf16x3"]["value"]
+    print(json.dumps(line))
+    return 0
+
+
+def run_ring(args):
+    """Mixed workload: 64 rings of 128 actors, token 1000 decremented per hop,
+    each master sending 8 factorization requests (factors in [2^30, 2^31)) to its
+    ring's worker; the whole workload is one captured CUDA graph per step."""
+    import torch
+
+    from paper_1505_07368_gb300 import cafgpu as C
+    torch.cuda.set_device(0)
+    wl = W.config4()
+    R, L, rounds = wl.n_rings, wl.ring_len, wl.n.shape[1]
+    out = {}
+    for label, with_factor in (("tokens_only", False), ("mixed", True)):
+        with C.Runtime(max_actors=R * (L + 1)) as rt:
+            d_n = torch.from_numpy(wl.n.astype(np.uint64).reshape(-1).copy()).cuda()
+            d_rep = torch.zeros(R * rounds * 32, dtype=torch.uint8, device="cuda")
+            masters = []
+            for r in range(R):
+                worker = rt.spawn(C.FACTOR_U64, mailbox_capacity=16)
+                base = worker + 1
+                for i in range(L):
+                    nxt = base + (i + 1) % L
+                    if i == 0:
+                        h = rt.spawn(C.RING_TOKEN, mailbox_capacity=4, next=nxt, flags=C.ACTOR_MASTER, worker=worker,
+                                     factor_n=d_n.data_ptr() + r * rounds * 8, factor_count=rounds if with_factor else 0,
+                                     factor_replies=d_rep.data_ptr() + r * rounds * 32)
+                        masters.append(h)
+                    else:
+                        rt.spawn(C.RING_TOKEN, mailbox_capacity=4, next=nxt)
+            m = np.zeros(R, C.DMSG_DTYPE)
+            m["actor"] = np.array(masters, np.uint32) - 1
+            m["kind"] = C.RING_TOKEN | (C.MSG_START << 16)
+            m["u64"] = wl.token
+            d_m = torch.from_numpy(m.view(np.uint8).copy()).cuda()
+            d_r = torch.zeros(R * 32, dtype=torch.uint8, device="cuda")
+            torch.cuda.synchronize()
+            rt.graph_begin()
+            rt.reset_actors()
+            rt.request_batch_device(d_m.data_ptr(), R, d_r.data_ptr())
+            g = rt.graph_end()
+            stream = torch.cuda.ExternalStream(rt.stream())
+            for _ in range(args.warmup):
+                rt.graph_launch(g)
+            rt.stream_sync()
+            times = []
+            for _ in range(args.steps):
+                e0, e1 = _events(stream)
+                e0.record(stream)
+                rt.graph_launch(g)
+                e1.record(stream)
+                rt.stream_sync()
+                times.append(e0.elapsed_time(e1) / 1e3)
+            rt.graph_destroy(g)
+            t = float(np.mean(times))
+            hops = L + wl.token            # deliveries per ring (the 0 travels once around)
+            msgs = R * (hops + 1) + (R * rounds if with_factor else 0)
+            out[label] = {"ms_per_step": 1e3 * t, "msgs_per_s": msgs / t, "ns_per_hop": 1e9 * t / hops,
+                          "messages": msgs}
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "token rings (64 x 128, token 1000) + "
+                      "8 factorization requests per ring, captured CUDA graph", "steps": args.steps,
+                      "results": out, "value": out["mixed"]["msgs_per_s"]}))
+    return 0
+
+
+def run_serve(args):
+    """Serving: open-loop Poisson arrivals, 70 % factorization (log-uniform factors in
+    [2^16, 2^31)), 30 % split-BF16x3 GEMM (n log-uniform in [32, 2048]), 8 GB budget.
+    Closed-loop capacity first, then open loop at 0.8 of it, persistent vs per-message."""
+    import torch
+
+    from paper_1505_07368_gb300 import cafgpu as C
+    torch.cuda.set_device(0)
+    count = args.requests
+    n_f, n_g = 2048, 1024
+    base_wl = W.config5(n_requests=count, rate=1e6, pool_elems=1 << 24)
+    pool = torch.from_numpy(W.gemm_pool(base_wl.pool_seed, base_wl.pool_elems)).cuda()
+    arena_bytes = 4 << 30
+    arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
+    result = {"metric": METRIC, "unit": UNIT, "requests": count,
+              "workload": "serving: Poisson arrivals, 70% factor / 30% split GEMM, 8 GB budget"}
+
+    def trace(wl, actors_f, actors_g):
+        reqs = np.zeros(wl.count, C.SERVE_REQ_DTYPE)
+        isf = wl.kind == C.FACTOR_U64
+        reqs["actor"] = np.where(isf, np.array(actors_f, np.uint64)[wl.actor % n_f],
+                                 np.array(actors_g, np.uint64)[(wl.actor - n_f) % n_g])
+        reqs["t_arrival"] = wl.t
+        reqs["u64"] = wl.n
+        reqs["n"] = wl.size
+        reqs["A"] = np.where(isf, 0, pool.data_ptr() + 4 * wl.a_off.astype(np.uint64))
+        reqs["B"] = np.where(isf, 0, pool.data_ptr() + 4 * wl.b_off.astype(np.uint64))
+        return reqs
+
+    with C.Runtime(max_actors=n_f + n_g, mailbox_capacity=256, max_inflight_requests=1 << 17,
+                   ingress_capacity=1 << 17) as rt:
+        af = [rt.spawn(C.FACTOR_U64) for _ in range(n_f)]
+        ag = [rt.spawn(C.GEMM_SPLIT_BF16X3) for _ in range(n_g)]
+        closed = trace(base_wl, af, ag)
+        closed["t_arrival"] = 0.0
+        torch.cuda.synchronize()
+        res, st = rt.serve_run(closed, arena.data_ptr(), arena_bytes, mem_budget_bytes=8 << 30)
+        capacity = count / st["wall_s"]
+        result["closed_loop"] = {"msgs_per_s": capacity, "wall_s": st["wall_s"]}
+        lam = 0.8 * capacity
+        wl = W.config5(n_requests=count, rate=lam, pool_elems=1 << 24)
+        reqs = trace(wl, af, ag)
+        for backend, label in ((C.BACKEND_PERSISTENT, "persistent"), (C.BACKEND_PER_MESSAGE_LAUNCH, "per_message_launch")):
+            rt.set_backend(backend)
+            res, st = rt.serve_run(reqs, arena.data_ptr(), arena_bytes, mem_budget_bytes=8 << 30)
+            lat = (res["t_done"] - wl.t) * 1e3
+            result[label] = {"rate_offered": lam, "msgs_per_s": count / st["wall_s"],
+                             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                             "peak_inflight_bytes": st["peak_inflight_bytes"], "launches": st["launches"]}
+    result["value"] = result["persistent"]["msgs_per_s"]
+    print(json.dumps(result))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "gemm":
+        return run_gemm(args)
+    if args.workload == "ring":
+        return run_ring(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -1,0 +1,121 @@
+"""Autotuner for the drain's scheduling knobs.
+
+The persistent drain has three knobs that trade per-message latency against
+throughput, the GPU counterpart of the scheduler settings of the paper's
+Sec. 6.1 (number of workers, messages per actor run):
+
+* ``factor_batch`` (K): messages a team sweeps together against one pass of
+  the prime table;
+* ``factor_warps`` (W): warps per team, i.e. warps working on one batch;
+* ``ctas_per_sm``: resident drain CTAs per SM (the worker count).
+
+``tune_factor`` runs one device batch of the caller's workload for every
+candidate setting on the current GPU, keeps the fastest, and caches the
+choice in a JSON file keyed by GPU name and workload signature.  The timing
+is CUDA events on the runtime's stream; every candidate must reproduce the
+same replies as the first one, so a setting that breaks results is never
+chosen.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+
+import numpy as np
+
+from . import cafgpu as C
+
+DEFAULT_CANDIDATES = [
+    {"factor_batch": k, "factor_warps": w, "ctas_per_sm": c}
+    for k in (8, 16) for w in (2, 4, 8) for c in (2,)
+]
+
+
+def cache_path() -> str:
+    base = os.environ.get("CAFGPU_CACHE_DIR") or os.path.join(
+        os.environ.get("XDG_CACHE_HOME", os.path.expanduser("~/.cache")), "cafgpu")
+    return os.path.join(base, "autotune.json")
+
+
+def _load_cache() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_cache(c: dict) -> None:
+    p = cache_path()
+    try:
+        os.makedirs(os.path.dirname(p), exist_ok=True)
+        tmp = p + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(c, f, indent=1, sort_keys=True)
+        os.replace(tmp, p)
+    except OSError:
+        pass
+
+
+def workload_key(gpu: str, n_actors: int, n: np.ndarray, max_factor_n: int) -> str:
+    h = hashlib.sha1(np.ascontiguousarray(n, dtype=np.uint64).tobytes()).hexdigest()[:16]
+    return f"{gpu}|factor|actors={n_actors}|msgs={n.size}|max_n={max_factor_n}|{h}"
+
+
+def tune_factor(actor_idx: np.ndarray, n: np.ndarray, n_actors: int, max_factor_n: int,
+                candidates=None, runtime_kwargs=None, use_cache: bool = True, log=None):
+    """Pick the fastest (factor_batch, factor_warps, ctas_per_sm) for this workload.
+
+    Returns (best_cfg, table) where table lists (cfg, seconds) for every candidate
+    measured (empty when the cached choice was used)."""
+    import torch
+    candidates = candidates or DEFAULT_CANDIDATES
+    runtime_kwargs = dict(runtime_kwargs or {})
+    gpu = torch.cuda.get_device_name()
+    key = workload_key(gpu, n_actors, n, max_factor_n)
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        return cache[key]["best"], []
+    count = n.size
+    m = np.zeros(count, C.DMSG_DTYPE)
+    m["actor"] = actor_idx
+    m["kind"] = C.FACTOR_U64
+    m["u64"] = n
+    m["tag"] = np.arange(count)
+    d_msgs = torch.from_numpy(m.view(np.uint8).copy()).cuda()
+    d_rep = torch.zeros(count * C.DREPLY_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    table = []
+    ref = None
+    for cand in candidates:
+        kw = dict(runtime_kwargs)
+        kw.update(cand)
+        with C.Runtime(max_factor_n=max_factor_n, max_actors=n_actors, **kw) as rt:
+            for _ in range(n_actors):
+                rt.spawn(C.FACTOR_U64)
+            stream = torch.cuda.ExternalStream(rt.stream())
+            torch.cuda.synchronize()
+            rt.request_batch_device(d_msgs.data_ptr(), count, d_rep.data_ptr())   # warm-up
+            rt.stream_sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rt.request_batch_device(d_msgs.data_ptr(), count, d_rep.data_ptr())
+            e1.record(stream)
+            rt.stream_sync()
+            secs = e0.elapsed_time(e1) / 1e3
+            rep = d_rep.cpu().numpy().view(C.DREPLY_DTYPE)
+            res = (rep["status"].copy(), rep["r0"].copy(), rep["r1"].copy())
+        if ref is None:
+            ref = res
+        ok = all(np.array_equal(a, b) for a, b in zip(res, ref))
+        table.append((cand, secs if ok else float("inf")))
+        if log:
+            log(f"autotune {cand}: {secs * 1e3:.1f} ms{'' if ok else ' (results differ: rejected)'}")
+    best = min(table, key=lambda x: x[1])[0]
+    if use_cache:
+        cache = _load_cache()
+        cache[key] = {"best": best, "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+                      "table": [[c, s] for c, s in table]}
+        _store_cache(cache)
+    return best, table
