@@ -64,7 +64,12 @@ __device__ __forceinline__ void heartbeat(const DrainParams &P) {
 // for the receiver to make room (waking first keeps a full mailbox from
 // waiting on a consumer that was never scheduled).  Returns false (all
 // lanes) on a wait that expired.
-__device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const MsgData &m) {
+// With `handoff` set, a receiver this call wakes is not queued: its id is
+// returned through *handoff (kNone if none was woken) and the caller runs it
+// next -- the paper's internal enqueue, which puts an actor readied by a
+// worker at the front of that worker's own queue.  Only for single-lane sends.
+__device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const MsgData &m,
+                             uint32_t *handoff = nullptr) {
     const uint32_t lane = lane_id();
     const uint32_t vmask = __ballot_sync(FULL, valid);
     if (!vmask) return true;
@@ -99,9 +104,16 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
         // wake the receiver (fence: Dekker pattern with release_actor)
         asm volatile("fence.sc.gpu;" ::: "memory");
         bool qok = true;
+        bool woke = false;
         if (valid && (int)lane == leader) {
-            if (cas_u32(&A->state, kWaiting, kReady) == kWaiting)
-                qok = q_push(&P.ctl->readyq, P.readyq, a, P.wait_limit_ns);
+            if (cas_u32(&A->state, kWaiting, kReady) == kWaiting) {
+                if (handoff) woke = true;
+                else qok = q_push(&P.ctl->readyq, P.readyq, a, P.wait_limit_ns);
+            }
+        }
+        if (handoff) {
+            const uint32_t wm = __ballot_sync(FULL, woke);
+            if (wm) *handoff = __shfl_sync(FULL, a, __ffs(wm) - 1);
         }
         if (!__all_sync(FULL, qok)) {
             if (!qok) fail(P, kErrWaitQueue, 2, P.ctl->readyq.enq, a);
@@ -471,7 +483,7 @@ __device__ bool ring_emit_factor(const DrainParams &P, uint32_t a) {
     return warp_enqueue(P, valid, worker, m);
 }
 
-__device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v) {
+__device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v, uint32_t *handoff) {
     ActorDesc *A = &P.actors[a];
     const uint32_t next = A->next;
     MsgData m{};
@@ -481,11 +493,14 @@ __device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v) {
     m.sender_seq = (uint32_t)v;
     const bool send = lane_id() == 0;
     if (lane_id() == 0) add_u64(&P.ctl->device_sends, 1);
-    return warp_enqueue(P, send, next, m);
+    return warp_enqueue(P, send, next, m, handoff);
 }
 
-__device__ void claim_ring(const DrainParams &P, uint32_t a) {
+// Run the claimed ring actor `a`; returns the successor this warp woke (to be
+// run next by the same warp) or kNone.
+__device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a) {
     const uint32_t lane = lane_id();
+    uint32_t handoff = kNone;
     ActorDesc *A = &P.actors[a];
     if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
     __syncwarp();
@@ -496,7 +511,7 @@ __device__ void claim_ring(const DrainParams &P, uint32_t a) {
     if (lane == 0) add_u64(&P.ctl->claims, 1);
     for (uint64_t i = 0; i < take; ++i) {
         MsgData m{};
-        if (warp_dequeue(P, a, head, 1, m) == 0) return;
+        if (warp_dequeue(P, a, head, 1, m) == 0) return kNone;
         m.payload = __shfl_sync(FULL, m.payload, 0);
         m.kind = __shfl_sync(FULL, m.kind, 0);
         m.reply_addr = __shfl_sync(FULL, m.reply_addr, 0);
@@ -509,17 +524,17 @@ __device__ void claim_ring(const DrainParams &P, uint32_t a) {
         if (dead) {
             if (lane == 0) write_reply(m.reply_addr, 2, 0, 0, m.tag, m.reply_token);
         } else if ((m.kind >> 16) & kMsgStart) {
-            ok = ring_emit_factor(P, a) && ring_forward(P, a, v);
+            ok = ring_emit_factor(P, a) && ring_forward(P, a, v, &handoff);
         } else if (v > 0) {
-            ok = ring_emit_factor(P, a) && ring_forward(P, a, v - 1);
+            ok = ring_emit_factor(P, a) && ring_forward(P, a, v - 1, &handoff);
         } else {
             if (lane == 0) *((volatile uint32_t *)&A->state) = kDone;
             uint32_t succ_state = 0;
             if (lane == 0) succ_state = *((volatile uint32_t *)&P.actors[A->next].state);
             succ_state = __shfl_sync(FULL, succ_state, 0);
-            if (succ_state != kDone) ok = ring_forward(P, a, 0);
+            if (succ_state != kDone) ok = ring_forward(P, a, 0, &handoff);
         }
-        if (!ok) return;
+        if (!ok) return kNone;
         if (!dead && lane == 0) {
             A->user_state = v;
             write_reply(m.reply_addr, 0, (uint64_t)(uint32_t)v, 0, m.tag, m.reply_token);
@@ -532,6 +547,21 @@ __device__ void claim_ring(const DrainParams &P, uint32_t a) {
         }
     }
     release_actor(P, a, head);
+    return handoff;
+}
+
+// Claim a ring actor and keep running the actors its messages wake, up to a
+// bound, after which the next one goes back to the ready queue.
+__device__ void claim_ring(const DrainParams &P, uint32_t a) {
+    constexpr int kMaxChain = 1 << 14;
+    uint32_t cur = a;
+    for (int i = 0; cur != kNone && i < kMaxChain && !exit_requested(P.ctl); ++i) {
+        cur = run_ring_actor(P, cur);
+        if ((i & 255) == 0 && lane_id() == 0) heartbeat(P);
+    }
+    if (cur != kNone && lane_id() == 0 && !q_push(&P.ctl->readyq, P.readyq, cur, P.wait_limit_ns))
+        fail(P, kErrWaitQueue, 18);
+    __syncwarp();
 }
 
 // Answer a message that cannot be handled (unknown actor, kind mismatch,
