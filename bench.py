@@ -371,7 +371,7 @@ def run_ours(args):
         rt.mark()
         h = rt.request_batch(actors, msgs)
         e1.record(stream)
-        rrep = rt.await_batch(h)
+        rrep = rt.await_batch(h, timeout_ns=AWAIT_NS)
         torch.cuda.synchronize()
         pm_s = e0.elapsed_time(e1) / 1e3
         pst = rt.stats()
@@ -391,14 +391,14 @@ def run_ours(args):
             msgs[i] = C.Runtime.msg(C.FACTOR_U64, int(wl.n[i]), sender=int(wl.sender[i]), tag=i)
         actors = (wl.actor.astype(np.uint64) + 1)
         h = rt.request_batch(actors, msgs)      # warm-up pass
-        rt.await_batch(h)
+        rt.await_batch(h, timeout_ns=AWAIT_NS)
         rt.sync()
         times = []
         for _ in range(max(1, min(args.steps, 3))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = rt.request_batch(actors, msgs)
-            erep = rt.await_batch(h)
+            erep = rt.await_batch(h, timeout_ns=AWAIT_NS)
             times.append(time.perf_counter() - t0)
             rt.sync()
         if not (np.array_equal(erep["r0"], wl.p) and np.array_equal(erep["r1"], wl.q)):
@@ -426,6 +426,13 @@ def run_ours(args):
 # other configurations (measurement lines for the record; the default line is
 # the default batched-factorization workload)
 # ---------------------------------------------------------------------------
+def _note(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
+AWAIT_NS = 300_000_000_000     # host waits in the bench give up after 5 minutes
+
+
 def _events(stream):
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -458,6 +465,7 @@ def run_gemm(args):
             "config": {"workload": "GEMM actors: 256 actors, 4096 messages, n uniform in {64,...,1024}, N(0,1)",
                        "messages": wl.count, "l2": "flushed between steps (256 MiB write)"}, "variants": {}}
     for kind, name in ((C.GEMM_BF16, "bf16"), (C.GEMM_SPLIT_BF16X3, "split_bf16x3")):
+        _note(f"gemm {name}: persistent")
         with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=wl.n_actors, mailbox_capacity=64) as rt:
             for _ in range(wl.n_actors):
                 rt.spawn(kind)
@@ -502,6 +510,7 @@ def run_gemm(args):
                                 "note": "executed flops (split: 3 products per useful one)"}},
                  "useful_tflops": useful_flops / t / 1e12, "gpu_launches": st["launches"]}
             if not args.skip_per_message:
+                _note(f"gemm {name}: per-message launch")
                 rt.set_backend(C.BACKEND_PER_MESSAGE_LAUNCH)
                 msgs = (C.Msg * wl.count)()
                 for i in range(wl.count):
@@ -512,7 +521,7 @@ def run_gemm(args):
                 e0.record(stream)
                 h = rt.request_batch(wl.actor.astype(np.uint64) + 1, msgs)
                 e1.record(stream)
-                rt.await_batch(h)
+                rt.await_batch(h, timeout_ns=AWAIT_NS)
                 torch.cuda.synchronize()
                 pm = e0.elapsed_time(e1) / 1e3
                 v["per_message_launch"] = {"value": wl.count / pm, "ms": 1e3 * pm,

@@ -243,8 +243,13 @@ __device__ __forceinline__ uint32_t sweep_min_bound(const SweepRegs &s, const Fa
     return __reduce_min_sync(FULL, pb);
 }
 
+// CTA barrier over the first `nthreads` threads' warps.  Callers reach it
+// right after lane-0-only blocks, so the warp is reconverged first and the
+// non-aligned barrier form is used (bar.sync is barrier.sync.aligned, which
+// requires the whole warp to execute it together).
 __device__ __forceinline__ void named_bar_sync(uint32_t id, uint32_t nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+    __syncwarp();
+    asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -759,14 +764,14 @@ struct NamedBarSync {
 // Run GEMM tile `item` with the whole CTA; the CTA that finishes a job's last
 // tile writes its reply and frees the job record.
 __device__ __noinline__ void drain_gemm_tile(const DrainParams &P, GroupShared &G, GemmOps &ops, uint32_t item,
-                                uint32_t &stage_uses, uint32_t &tiles, uint32_t bar_threads) {
+                                GemmCounters &K, uint32_t bar_threads) {
     const uint32_t j = item >> 16, tile = item & 0xFFFFu;
     GemmJob *J = &P.jobs[j];
     const uint32_t n = J->n;
     const uint32_t tn_count = (n + kGemmBN - 1) / kGemmBN;
     const bool ok = gemm_tile(reinterpret_cast<const float *>(J->A), reinterpret_cast<const float *>(J->B),
                               reinterpret_cast<float *>(J->C), n, tile / tn_count, tile % tn_count, J->split != 0,
-                              ops, G.gb, stage_uses, tiles, P.wait_limit_ns, NamedBarSync{bar_threads});
+                              ops, G.gb, K, P.wait_limit_ns, NamedBarSync{bar_threads});
     if (threadIdx.x == 0) {
         if (!ok) fail(P, kErrGemm, 16, item, n);
         heartbeat(P);
@@ -911,24 +916,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_drain(DrainParams P) {
     uint64_t idle_start = 0;
     uint32_t idle_ns = 256;
     uint32_t held = kNone;                 // a team leader's claimed batch, kept across GEMM tiles
-    uint32_t g_stage_uses = 0, g_tiles = 0;
+    GemmCounters gk{0, 0, 0};
+    uint64_t seen_completed = 0, seen_at = 0;   // completion watchdog (producer lane)
     const bool gemm_cta = kGemm && !live0;
     for (;;) {
-        // ---- form a group
-        if (!producer && team_ok && rank == 0 && held == kNone) held = find_batch<kGemm>(P);
+        // ---- form a group: team leaders claim actors (skipped while the GEMM
+        // tile queue already holds plenty of work for every CTA)
+        if (!producer && team_ok && rank == 0 && held == kNone) {
+            bool skip = false;
+            if (kGemm && lane == 0) skip = q_len(&ctl->workq) > 2 * (int64_t)gridDim.x;
+            if (!__shfl_sync(FULL, skip, 0)) held = find_batch<kGemm>(P);
+        }
         if (!producer && lane == 0) G.batch[ci] = (team_ok && rank == 0) ? held : kNone;
         if (producer && lane == 0) {
             G.exit = exit_requested(ctl) ? 1u : 0u;
             uint32_t item = kNone;
             if (gemm_cta && !G.exit && !q_try_pop(&ctl->workq, P.workq, &item)) item = kNone;
             G.gemm_item = item;
+            // watchdog: busy warps can keep the heartbeat fresh without any
+            // message completing; give up if nothing completes for a long time
+            const uint64_t done_now = ld_relaxed_gpu(&ctl->completed);
+            const uint64_t tnow = globaltimer();
+            if (done_now != seen_completed || seen_at == 0 || quiescent(P)) {
+                seen_completed = done_now;
+                seen_at = tnow;
+            } else if (tnow > seen_at && tnow - seen_at > kCompletionLimitNs) {
+                fail(P, kErrNoCompletion, 20, done_now, ld_acquire_gpu(&ctl->ingested));
+            }
         }
         named_bar_sync(1, bar_threads);
         if (G.exit) break;
         if constexpr (kGemm) {
             if (G.gemm_item != kNone) {
                 // GEMM tiles first: short, and other CTAs may wait on the same job
-                drain_gemm_tile(P, G, gops, G.gemm_item, g_stage_uses, g_tiles, bar_threads);
+                drain_gemm_tile(P, G, gops, G.gemm_item, gk, bar_threads);
                 idle = false;
                 idle_ns = 256;
                 continue;

@@ -20,9 +20,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const uint32_t tiles_n = (n + kGemmBN - 1) / kGemmBN;
     const uint32_t tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
     gemm_cta_init(S);
-    uint32_t stage_uses = 0, tiles = 0;
-    const bool ok = gemm_tile(A, B, C, n, tm, tn, split != 0, S.ops, S.bars, stage_uses, tiles, limit_ns,
-                              CtaSyncAll{});
+    GemmCounters K{0, 0, 0};
+    const bool ok = gemm_tile(A, B, C, n, tm, tn, split != 0, S.ops, S.bars, K, limit_ns, CtaSyncAll{});
     gemm_cta_exit(S);
     __shared__ uint32_t last;
     if (threadIdx.x == 0) {

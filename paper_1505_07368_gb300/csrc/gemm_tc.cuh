@@ -7,19 +7,22 @@
 //   split-BF16x3:    C = hi(A)*hi(B) + hi(A)*lo(B) + lo(A)*hi(B)
 //                    with hi(x) = bf16_rn(x), lo(x) = bf16_rn(x - hi(x))
 //
-// One CTA computes one 128 x 128 output tile:
-//   * 8 converter warps load FP32 operand blocks (128 rows x 64 k) from
-//     global memory, round them to BF16 (hi, and lo for the split form) and
-//     store them into shared memory in the canonical K-major 128-byte-swizzle
-//     layout the tensor core reads (B is transposed on the way, so both
-//     operands are K-major);
+// One CTA computes one 128 x 128 output tile, k in blocks of 64:
+//   * each of the 8 converter warps owns a slice of every k block -- 16 rows
+//     of the A block and 8 rows (k) of the B block -- and stages it into
+//     shared memory with bulk asynchronous copies (one per row, completing on
+//     the warp's own mbarrier), two blocks ahead;
+//   * the warp then rounds its FP32 slice to BF16 (hi, and lo for the split
+//     form) and writes it in the canonical K-major 128-byte-swizzle layout
+//     the tensor core reads (B transposed on the way, so both operands are
+//     K-major), and refills the staging stage with the block two ahead;
 //   * one thread issues tcgen05.mma (M=128, N=128, K=16, kind::f16, BF16 in,
-//     FP32 accumulator in tensor memory) and commits each stage back to the
-//     converters through an mbarrier;
-//   * the same 8 warps then read the accumulator with tcgen05.ld and store
-//     the tile (masked at the matrix edge).
-// Two operand stages let the conversion of block k+1 overlap the MMAs of
-// block k.
+//     FP32 accumulator in tensor memory) and commits the operand buffer back
+//     to the converters through an mbarrier;
+//   * the converter warps read the accumulator with tcgen05.ld and store the
+//     tile (masked at the matrix edge).
+// Bulk copies need 16-byte aligned rows; when n is not a multiple of 4 (or an
+// operand is unaligned) the converters read global memory directly instead.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -31,24 +34,31 @@ namespace cafgpu {
 constexpr uint32_t kGemmBM = 128;          // tile rows (MMA M)
 constexpr uint32_t kGemmBN = 128;          // tile columns (MMA N)
 constexpr uint32_t kGemmBK = 64;           // k per stage: one 128-byte swizzle atom of BF16
-constexpr uint32_t kGemmStages = 2;
 constexpr uint32_t kGemmConvWarps = 8;
-constexpr uint32_t kGemmOperandBytes = kGemmBM * kGemmBK * 2;   // 16 KB per operand tile
+constexpr uint32_t kGemmOperandBytes = kGemmBM * kGemmBK * 2;   // 16 KB per BF16 operand tile
 constexpr uint32_t kGemmTmemCols = 128;
 
 // Operand tiles of one GEMM CTA (1024-byte aligned: the swizzle pattern
-// repeats every 1024 bytes).
+// repeats every 1024 bytes), then the FP32 staging.
 struct GemmOps {
-    uint8_t a_hi[kGemmStages][kGemmOperandBytes];
-    uint8_t b_hi[kGemmStages][kGemmOperandBytes];
-    uint8_t a_lo[kGemmStages][kGemmOperandBytes];
-    uint8_t b_lo[kGemmStages][kGemmOperandBytes];
+    uint8_t a_hi[kGemmOperandBytes];
+    uint8_t b_hi[kGemmOperandBytes];
+    uint8_t a_lo[kGemmOperandBytes];
+    uint8_t b_lo[kGemmOperandBytes];
+    float a32[2][kGemmBM * kGemmBK];   // A block: 128 rows x 64 k
+    float b32[2][kGemmBK * kGemmBN];   // B block: 64 rows (k) x 128 columns
 };
 static_assert(sizeof(GemmOps) == kGemmOpsBytes, "operand area size");
-static_assert(kGemmStages == 2, "GemmBars holds two stages");
 struct GemmSmem {
     GemmOps ops;
     GemmBars bars;
+};
+
+// Barrier phases of one CTA across the tiles it computes.
+struct GemmCounters {
+    uint32_t f32_uses;   // k blocks staged so far (staging stage = use & 1)
+    uint32_t bf_uses;    // k blocks converted so far (one BF16 operand buffer)
+    uint32_t tiles;      // tiles finished (done barrier phase)
 };
 
 // ---- tcgen05 wrappers -------------------------------------------------------
@@ -146,38 +156,70 @@ __device__ __forceinline__ void convert8(const float (&x)[8], uint8_t *hi_dst, u
     }
 }
 
-// Converter thread work for one k block: this CTA's 256 converter threads
-// write A (rows tm*128.., k kb*64..) and B^T (rows = columns tn*128.. of B).
-// Each thread produces 4 chunks of A and 4 of B (one chunk = 8 consecutive k).
-__device__ __forceinline__ void gemm_convert_block(const float *__restrict__ A, const float *__restrict__ B,
+// Issue the bulk copies of this warp's slice of k block kb into staging
+// stage st (warp-collective): A rows 16w..16w+15 of the tile, B rows
+// k0+8w..k0+8w+7.  Rows past n are not copied (the converter zero-fills).
+__device__ __forceinline__ void gemm_stage_issue(const float *A, const float *B, uint32_t n, uint32_t tm,
+                                                 uint32_t tn, uint32_t kb, float *a32, float *b32, uint64_t *bar,
+                                                 uint32_t w) {
+    const uint32_t lane = lane_id();
+    const uint32_t k0 = kb * kGemmBK, col0 = tn * kGemmBN, row0 = tm * kGemmBM + 16 * w;
+    const uint32_t a_bytes = min(kGemmBK, n - k0) * 4u;
+    const uint32_t b_bytes = min(kGemmBN, n - col0) * 4u;
+    const uint32_t na = row0 < n ? min(16u, n - row0) : 0u;
+    const uint32_t nb = (k0 + 8 * w) < n ? min(8u, n - (k0 + 8 * w)) : 0u;
+    fence_proxy_async_smem();   // earlier generic reads of this stage before the async writes
+    __syncwarp();
+    if (lane == 0) mbar_arrive_expect_tx(bar, na * a_bytes + nb * b_bytes);
+    __syncwarp();
+    if (lane < na)
+        bulk_g2s(a32 + (16 * w + lane) * kGemmBK, A + (size_t)(row0 + lane) * n + k0, a_bytes, bar);
+    else if (lane >= 16 && lane - 16 < nb)
+        bulk_g2s(b32 + (8 * w + lane - 16) * kGemmBN, B + (size_t)(k0 + 8 * w + lane - 16) * n + col0, b_bytes,
+                 bar);
+}
+
+// Convert this warp's slice of k block kb to BF16 (hi, lo) into the operand
+// tiles.  Source: the staged FP32 slice, or global memory when `direct`.
+__device__ __forceinline__ void gemm_convert_slice(const float *__restrict__ A, const float *__restrict__ B,
                                                    uint32_t n, uint32_t tm, uint32_t tn, uint32_t kb,
-                                                   uint8_t *a_hi, uint8_t *b_hi, uint8_t *a_lo, uint8_t *b_lo,
-                                                   bool split, uint32_t tid) {
+                                                   const float *a32, const float *b32, bool direct,
+                                                   GemmOps &O, bool split, uint32_t w) {
+    const uint32_t lane = lane_id();
     const uint32_t k0 = kb * kGemmBK;
-    // A: chunk id c in [0, 1024): row = c / 8, kchunk = c % 8; thread handles c = tid + 256 i
+    // A: rows 16w + (c >> 3), k chunk c & 7, for c = lane + 32 i
 #pragma unroll
     for (uint32_t i = 0; i < 4; ++i) {
-        const uint32_t c = tid + 256u * i;
-        const uint32_t r = c >> 3, kc = c & 7u;
+        const uint32_t c = lane + 32u * i;
+        const uint32_t r = 16 * w + (c >> 3), kc = c & 7u;
         const uint32_t gr = tm * kGemmBM + r, gk = k0 + kc * 8;
         float x[8];
+        if (direct) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) x[j] = (gr < n && gk + j < n) ? __ldg(A + (size_t)gr * n + gk + j) : 0.0f;
+            for (int j = 0; j < 8; ++j) x[j] = (gr < n && gk + j < n) ? __ldg(A + (size_t)gr * n + gk + j) : 0.0f;
+        } else {
+            const float4 *src = reinterpret_cast<const float4 *>(a32 + r * kGemmBK + kc * 8);
+            const float4 lo = src[0], hi = src[1];
+            const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[j] = (gr < n && gk + j < n) ? v[j] : 0.0f;
+        }
         const uint32_t off = sw128_offset(r, kc);
-        convert8(x, a_hi + off, a_lo + off, split);
+        convert8(x, O.a_hi + off, O.a_lo + off, split);
     }
-    // B^T: row = column of B (col), k chunk; thread layout: lanes over columns
-    // so that each k row of B is read contiguously by a warp.
+    // B^T: columns lane + 32 i of the tile, k chunk w (B rows k0+8w .. k0+8w+7)
 #pragma unroll
     for (uint32_t i = 0; i < 4; ++i) {
-        const uint32_t c = tid + 256u * i;
-        const uint32_t col = c & 127u, kc = c >> 7;
-        const uint32_t gc = tn * kGemmBN + col, gk = k0 + kc * 8;
+        const uint32_t col = lane + 32u * i;
+        const uint32_t gc = tn * kGemmBN + col, gk = k0 + 8 * w;
         float x[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) x[j] = (gc < n && gk + j < n) ? __ldg(B + (size_t)(gk + j) * n + gc) : 0.0f;
-        const uint32_t off = sw128_offset(col, kc);
-        convert8(x, b_hi + off, b_lo + off, split);
+        for (int j = 0; j < 8; ++j) {
+            const bool in = gc < n && gk + j < n;
+            x[j] = !in ? 0.0f : (direct ? __ldg(B + (size_t)(gk + j) * n + gc) : b32[(8 * w + j) * kGemmBN + col]);
+        }
+        const uint32_t off = sw128_offset(col, w);
+        convert8(x, O.b_hi + off, O.b_lo + off, split);
     }
 }
 
@@ -199,10 +241,10 @@ __device__ __forceinline__ GemmSmem &gemm_smem(uint8_t *raw) {
 // (the caller synchronises the CTA afterwards, with tcgen05 fences).
 __device__ __forceinline__ void gemm_bars_init(GemmBars &Bb) {
     if (lane_id() == 0) {
-        for (uint32_t s = 0; s < kGemmStages; ++s) {
-            mbar_init(&Bb.full[s], kGemmConvWarps);
-            mbar_init(&Bb.empty[s], 1);
-        }
+        for (uint32_t s = 0; s < 2; ++s)
+            for (uint32_t w = 0; w < kGemmConvWarps; ++w) mbar_init(&Bb.f32_full[s][w], 1);
+        mbar_init(&Bb.full, kGemmConvWarps);
+        mbar_init(&Bb.empty, 1);
         mbar_init(&Bb.done, 1);
         fence_barrier_init();
     }
@@ -236,45 +278,58 @@ __device__ __forceinline__ bool gemm_wait(uint64_t *bar, uint32_t parity, uint64
     return true;
 }
 
-// Compute output tile (tm, tn) of C = A * B with the whole CTA.
-// `stage_uses` counts operand-stage uses over the CTA's life and `tiles`
-// the tiles it has computed (barrier phases follow from both).  Returns false
-// if a bounded wait expired.
 // Whole-CTA synchronisation for gemm_tile.
 struct CtaSyncAll {
-    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+    __device__ __forceinline__ void operator()() const {
+        __syncwarp();   // the MMA warp's lane 0 diverged while issuing
+        __syncthreads();
+    }
 };
 
-// `cta_sync` synchronises the warps taking part (all kGemmConvWarps + 1).
+// Compute output tile (tm, tn) of C = A * B with the whole CTA (converter
+// warps 0..7 and the MMA warp kGemmConvWarps).  `K` carries the barrier
+// phases across the tiles this CTA computes.  Returns false if a bounded wait
+// expired.
 template <class CtaSync>
 __device__ bool gemm_tile(const float *__restrict__ A, const float *__restrict__ B, float *__restrict__ C,
-                          uint32_t n, uint32_t tm, uint32_t tn, bool split, GemmOps &S, GemmBars &Bb,
-                          uint32_t &stage_uses, uint32_t &tiles, uint64_t limit_ns, CtaSync cta_sync) {
+                          uint32_t n, uint32_t tm, uint32_t tn, bool split, GemmOps &O, GemmBars &Bb,
+                          GemmCounters &K, uint64_t limit_ns, CtaSync cta_sync) {
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t nk = (n + kGemmBK - 1) / kGemmBK;
+    // bulk copies need 16-byte aligned rows
+    const bool direct = (n & 3u) != 0 || (reinterpret_cast<uintptr_t>(A) & 15u) != 0 ||
+                        (reinterpret_cast<uintptr_t>(B) & 15u) != 0;
     bool ok = true;
     if (warp < kGemmConvWarps) {
-        for (uint32_t kb = 0; kb < nk && ok; ++kb) {
-            const uint32_t it = stage_uses + kb;
-            const uint32_t st = it % kGemmStages, use = it / kGemmStages;
-            if (use >= 1) ok = gemm_wait(&Bb.empty[st], (use - 1) & 1u, limit_ns);
-            if (!__all_sync(0xFFFFFFFFu, ok)) { ok = false; break; }
-            gemm_convert_block(A, B, n, tm, tn, kb, S.a_hi[st], S.b_hi[st], S.a_lo[st], S.b_lo[st], split,
-                               threadIdx.x);
+        const uint32_t w = warp;
+        if (!direct) {
+            for (uint32_t kb = 0; kb < 2 && kb < nk; ++kb) {
+                const uint32_t st = (K.f32_uses + kb) & 1u;
+                gemm_stage_issue(A, B, n, tm, tn, kb, O.a32[st], O.b32[st], &Bb.f32_full[st][w], w);
+            }
+        }
+        for (uint32_t kb = 0; kb < nk; ++kb) {
+            const uint32_t fu = K.f32_uses + kb, bu = K.bf_uses + kb;
+            const uint32_t st = fu & 1u;
+            bool okw = true;
+            if (!direct) okw = gemm_wait(&Bb.f32_full[st][w], (fu >> 1) & 1u, limit_ns);
+            if (okw && bu >= 1) okw = gemm_wait(&Bb.empty, (bu - 1) & 1u, limit_ns);
+            if (!__all_sync(0xFFFFFFFFu, okw)) { ok = false; break; }
+            gemm_convert_slice(A, B, n, tm, tn, kb, O.a32[st], O.b32[st], direct, O, split, w);
             fence_proxy_async_smem();   // generic-proxy writes -> tensor-core (async proxy) reads
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&Bb.full[st])) : "memory");
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&Bb.full)) : "memory");
+            if (!direct && kb + 2 < nk)
+                gemm_stage_issue(A, B, n, tm, tn, kb + 2, O.a32[st], O.b32[st], &Bb.f32_full[st][w], w);
         }
     } else if (lane == 0) {
         const uint32_t idesc = gemm_idesc(kGemmBM, kGemmBN);
+        const uint64_t ah = smem_desc_sw128(O.a_hi), bh = smem_desc_sw128(O.b_hi);
+        const uint64_t al = smem_desc_sw128(O.a_lo), bl = smem_desc_sw128(O.b_lo);
         for (uint32_t kb = 0; kb < nk && ok; ++kb) {
-            const uint32_t it = stage_uses + kb;
-            const uint32_t st = it % kGemmStages, use = it / kGemmStages;
-            ok = gemm_wait(&Bb.full[st], use & 1u, limit_ns);
+            ok = gemm_wait(&Bb.full, (K.bf_uses + kb) & 1u, limit_ns);
             if (!ok) break;
             tc_fence_after();
-            const uint64_t ah = smem_desc_sw128(S.a_hi[st]), bh = smem_desc_sw128(S.b_hi[st]);
-            const uint64_t al = smem_desc_sw128(S.a_lo[st]), bl = smem_desc_sw128(S.b_lo[st]);
 #pragma unroll
             for (uint32_t k16 = 0; k16 < kGemmBK / 16; ++k16) {
                 const uint64_t ko = (k16 * 32u) >> 4;   // 16 BF16 = 32 bytes along k inside the swizzle atom
@@ -284,15 +339,17 @@ __device__ bool gemm_tile(const float *__restrict__ A, const float *__restrict__
                     tc_mma_f16(Bb.tmem, al + ko, bh + ko, idesc, 1u);
                 }
             }
-            tc_commit(&Bb.empty[st]);
+            tc_commit(&Bb.empty);
         }
         tc_commit(&Bb.done);
     }
-    stage_uses += nk;
+    if (warp == kGemmConvWarps) __syncwarp();
+    K.f32_uses += direct ? 0 : nk;
+    K.bf_uses += nk;
     // epilogue: converter warps read the accumulator (warp w: TMEM lanes
     // 32*(w%4).., columns 64*(w/4)..) and store the tile
     if (warp < kGemmConvWarps) {
-        bool dok = ok && gemm_wait(&Bb.done, tiles & 1u, limit_ns);
+        bool dok = ok && gemm_wait(&Bb.done, K.tiles & 1u, limit_ns);
         dok = __all_sync(0xFFFFFFFFu, dok);
         if (dok) {
             tc_fence_after();
@@ -305,15 +362,23 @@ __device__ bool gemm_tile(const float *__restrict__ A, const float *__restrict__
                 if (gr < n) {
                     float *crow = C + (size_t)gr * n;
                     const uint32_t gc0 = tn * kGemmBN + col0 + cc;
+                    if (gc0 + 32 <= n && (reinterpret_cast<uintptr_t>(crow + gc0) & 15u) == 0) {
 #pragma unroll
-                    for (uint32_t j = 0; j < 32; ++j)
-                        if (gc0 + j < n) crow[gc0 + j] = __uint_as_float(r[j]);
+                        for (uint32_t j = 0; j < 32; j += 4)
+                            *reinterpret_cast<float4 *>(crow + gc0 + j) =
+                                make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                            __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                    } else {
+#pragma unroll
+                        for (uint32_t j = 0; j < 32; ++j)
+                            if (gc0 + j < n) crow[gc0 + j] = __uint_as_float(r[j]);
+                    }
                 }
             }
         }
         ok = ok && dok;
     }
-    ++tiles;
+    ++K.tiles;
     // the next tile's MMAs overwrite the accumulator: every epilogue read
     // must be complete first
     tc_fence_before();

@@ -41,8 +41,9 @@ struct TableTile {
 
 // Barriers and tensor-memory address of the GEMM tile engine.
 struct GemmBars {
-    uint64_t full[2];              // converters -> MMA thread
-    uint64_t empty[2];             // MMA completion -> converters
+    uint64_t f32_full[2][8];       // per staging stage and converter warp: its FP32 slice landed
+    uint64_t full;                 // converters -> MMA thread (BF16 operands ready)
+    uint64_t empty;                // MMA completion -> converters (BF16 operands free)
     uint64_t done;                 // last MMA completed -> epilogue
     uint32_t tmem;                 // accumulator address from tcgen05.alloc
     uint32_t pad;
@@ -66,7 +67,8 @@ struct GroupShared {
 constexpr uint32_t kDrainHeader = 1024;
 static_assert(sizeof(GroupShared) <= kDrainHeader, "drain header fits");
 constexpr uint32_t kTableRingBytes = kStages * (uint32_t)sizeof(TableTile);
-constexpr uint32_t kGemmOpsBytes = 4u * 2u * 128u * 64u * 2u;   // hi/lo x A/B x 2 stages x 16 KB
+// BF16 hi/lo x A/B (16 KB each) + FP32 A and B staging, 2 stages x 32 KB each
+constexpr uint32_t kGemmOpsBytes = 4u * 128u * 64u * 2u + 2u * 2u * 128u * 64u * 4u;
 // dynamic shared memory of the drain (+1024 for aligning the base)
 constexpr uint32_t kDrainSmemFactor = 1024 + kDrainHeader + kTableRingBytes;
 constexpr uint32_t kDrainSmemMixed = 1024 + kDrainHeader + (kGemmOpsBytes > kTableRingBytes ? kGemmOpsBytes : kTableRingBytes);
@@ -112,7 +114,9 @@ enum : uint32_t {
     kErrGemm = 6,          // GEMM pipeline wait expired
     kErrStall = 7,         // no progress anywhere while messages were in flight
     kErrWaitTable = 8,     // a prime-table bulk copy did not complete
+    kErrNoCompletion = 9,  // messages in flight but none completed for kCompletionLimitNs
 };
+constexpr uint64_t kCompletionLimitNs = 30ull * 1000 * 1000 * 1000;
 
 // Device-resident message (same layout as caf_gpu_dmsg).
 struct caf_dmsg_t {
