@@ -735,6 +735,12 @@ __device__ __noinline__ void claim_gemm(const DrainParams &P, uint32_t a) {
             J->done = 0;
             J->reply_addr = m.reply_addr;
             J->reply_token = m.reply_token;
+            // operands staged by tensor copies when the rows are 16-byte aligned
+            J->tma = 0;
+            if (P.gemm_tmpl && (n & 3u) == 0 && ((d->A | d->B) & 15u) == 0) {
+                gemm_build_tmaps(J->tmap_a, J->tmap_b, P.gemm_tmpl + 256u * (n / 4u - 1u), d->A, d->B);
+                J->tma = 1;
+            }
             tiles = t * t;
             valid = true;
         } else {
@@ -769,9 +775,11 @@ __device__ __noinline__ void drain_gemm_tile(const DrainParams &P, GroupShared &
     GemmJob *J = &P.jobs[j];
     const uint32_t n = J->n;
     const uint32_t tn_count = (n + kGemmBN - 1) / kGemmBN;
-    const bool ok = gemm_tile(reinterpret_cast<const float *>(J->A), reinterpret_cast<const float *>(J->B),
-                              reinterpret_cast<float *>(J->C), n, tile / tn_count, tile % tn_count, J->split != 0,
-                              ops, G.gb, K, P.wait_limit_ns, NamedBarSync{bar_threads});
+    const bool tma = J->tma != 0;
+    const GemmArgs g{reinterpret_cast<const float *>(J->A), reinterpret_cast<const float *>(J->B),
+                     reinterpret_cast<float *>(J->C), tma ? J->tmap_a : nullptr, tma ? J->tmap_b : nullptr,
+                     n, tile / tn_count, tile % tn_count, J->split != 0, true};
+    const bool ok = gemm_tile(g, ops, G.gb, K, P.wait_limit_ns, NamedBarSync{bar_threads});
     if (threadIdx.x == 0) {
         if (!ok) fail(P, kErrGemm, 16, item, n);
         heartbeat(P);
@@ -865,7 +873,7 @@ __device__ void agent_loop(const DrainParams &P) {
 // kConsumerWarps * K messages.  With the live host ring, warp 0 of CTA 0 is
 // the ingress warp and takes no part in groups.
 template <bool kGemm>
-__global__ void __launch_bounds__(kThreads, 2) k_drain(DrainParams P) {
+__global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P) {
     extern __shared__ __align__(128) uint8_t drain_smem[];
     uint8_t *base = drain_smem + ((1024u - (smem_u32(drain_smem) & 1023u)) & 1023u);
     GroupShared &G = *reinterpret_cast<GroupShared *>(base);

@@ -1,6 +1,12 @@
 // GEMM kernels outside the persistent drain: one launch per GEMM message
-// (the per-message-launch form), each CTA one 128 x 128 output tile.
+// (the per-message-launch form), each CTA one 128 x 128 output tile; and the
+// host side of the tensor maps the tile engine stages its operands with.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "factor.cuh"
@@ -11,17 +17,20 @@
 namespace cafgpu {
 
 // scratch[0] counts the CTAs of this launch that have finished; the last one
-// writes the reply and puts the counter back to 0.
+// writes the reply and puts the counter back to 0.  use_tma: tma_a / tma_b
+// describe A and B (else the converters read them directly).
 __global__ void __launch_bounds__(kGemmThreads, 1)
-    k_gemm_one(const float *A, const float *B, float *C, uint32_t n, uint32_t split, uint64_t reply_addr,
-               uint32_t reply_token, uint32_t *scratch, uint64_t limit_ns, DevCtl *ctl) {
+    k_gemm_one(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b,
+               uint32_t use_tma, const float *A, const float *B, float *C, uint32_t n, uint32_t split,
+               uint64_t reply_addr, uint32_t reply_token, uint32_t *scratch, uint64_t limit_ns, DevCtl *ctl) {
     extern __shared__ uint8_t gemm_raw[];
     GemmSmem &S = gemm_smem(gemm_raw);
     const uint32_t tiles_n = (n + kGemmBN - 1) / kGemmBN;
-    const uint32_t tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
     gemm_cta_init(S);
     GemmCounters K{0, 0, 0};
-    const bool ok = gemm_tile(A, B, C, n, tm, tn, split != 0, S.ops, S.bars, K, limit_ns, CtaSyncAll{});
+    const GemmArgs g{A, B, C, use_tma ? &tma_a : nullptr, use_tma ? &tma_b : nullptr,
+                     n, blockIdx.x / tiles_n, blockIdx.x % tiles_n, split != 0, false};
+    const bool ok = gemm_tile(g, S.ops, S.bars, K, limit_ns, CtaSyncAll{});
     gemm_cta_exit(S);
     __shared__ uint32_t last;
     if (threadIdx.x == 0) {
@@ -39,6 +48,44 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
 }
 
+// Device-side construction of the two tensor maps from the templates (the
+// drain's path), written to out[0..255] for comparison with the host encoder.
+__global__ void k_gemm_tmap_build(const uint8_t *tmpl, uint64_t A, uint64_t B, uint32_t n, uint8_t *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) gemm_build_tmaps(out, out + 128, tmpl + 256u * (n / 4u - 1u), A, B);
+}
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+}  // namespace
+
+int gemm_encode_tmap(void *out128, const void *base, uint32_t n, bool is_a) {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    std::memset(out128, 0, 128);
+    if (!g_encode || n == 0) return -1;
+    const cuuint64_t dims[2] = {n, n};
+    const cuuint64_t strides[1] = {(cuuint64_t)n * 4u};
+    const cuuint32_t box_a[2] = {32, kGemmBM}, box_b[2] = {kGemmBN, kGemmBK};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult r =
+        g_encode(static_cast<CUtensorMap *>(out128), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base),
+                 dims, strides, is_a ? box_a : box_b, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                 is_a ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+bool gemm_tma_ok(const void *A, const void *B, uint32_t n) {
+    return (n & 3u) == 0 && ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15u) == 0;
+}
+
 cudaError_t launch_gemm_one(const float *A, const float *B, float *C, uint32_t n, bool split, uint64_t reply_addr,
                             uint32_t reply_token, uint32_t *scratch, uint64_t limit_ns, DevCtl *ctl,
                             cudaStream_t stream) {
@@ -48,9 +95,23 @@ cudaError_t launch_gemm_one(const float *A, const float *B, float *C, uint32_t n
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    CUtensorMap ta, tb;
+    const bool tma = gemm_tma_ok(A, B, n) && gemm_encode_tmap(&ta, A, n, true) == 0 &&
+                     gemm_encode_tmap(&tb, B, n, false) == 0;
+    if (!tma) {
+        std::memset(&ta, 0, sizeof ta);
+        std::memset(&tb, 0, sizeof tb);
+    }
     const uint32_t t = (n + kGemmBN - 1) / kGemmBN;
-    k_gemm_one<<<t * t, kGemmThreads, kGemmSmemBytes, stream>>>(A, B, C, n, split ? 1u : 0u, reply_addr,
-                                                                reply_token, scratch, limit_ns, ctl);
+    k_gemm_one<<<t * t, kGemmThreads, kGemmSmemBytes, stream>>>(ta, tb, tma ? 1u : 0u, A, B, C, n, split ? 1u : 0u,
+                                                                reply_addr, reply_token, scratch, limit_ns, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tmap_build(const uint8_t *tmpl, const void *A, const void *B, uint32_t n, uint8_t *out,
+                                   cudaStream_t stream) {
+    k_gemm_tmap_build<<<1, 32, 0, stream>>>(tmpl, reinterpret_cast<uint64_t>(A), reinterpret_cast<uint64_t>(B), n,
+                                            out);
     return cudaGetLastError();
 }
 

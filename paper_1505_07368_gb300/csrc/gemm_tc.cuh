@@ -4,25 +4,34 @@
 // matrices and producing their product), computed as
 //
 //   BF16:            C = bf16(A) * bf16(B)                     (FP32 accumulate)
-//   split-BF16x3:    C = hi(A)*hi(B) + hi(A)*lo(B) + lo(A)*hi(B)
+//   split-BF16x3:    C = hi(A)*hi(B) + [hi(A)*lo(B) + lo(A)*hi(B)]
 //                    with hi(x) = bf16_rn(x), lo(x) = bf16_rn(x - hi(x))
 //
-// One CTA computes one 128 x 128 output tile, k in blocks of 64:
-//   * each of the 8 converter warps owns a slice of every k block -- 16 rows
-//     of the A block and 8 rows (k) of the B block -- and stages it into
-//     shared memory with bulk asynchronous copies (one per row, completing on
-//     the warp's own mbarrier), two blocks ahead;
-//   * the warp then rounds its FP32 slice to BF16 (hi, and lo for the split
-//     form) and writes it in the canonical K-major 128-byte-swizzle layout
-//     the tensor core reads (B transposed on the way, so both operands are
-//     K-major), and refills the staging stage with the block two ahead;
-//   * one thread issues tcgen05.mma (M=128, N=128, K=16, kind::f16, BF16 in,
-//     FP32 accumulator in tensor memory) and commits the operand buffer back
-//     to the converters through an mbarrier;
-//   * the converter warps read the accumulator with tcgen05.ld and store the
+// One CTA computes one 128 x 128 output tile.  k runs in slices of 64 (the
+// FP32 staging unit) and blocks of 16 (one MMA step, the BF16 unit):
+//   * one thread stages each slice with three tensor copies (TMA) described
+//     by per-matrix tensor maps: A as two 32-wide k halves with the 128-byte
+//     swizzle, B as one 128-column x 64-k box.  The copies zero-fill whatever
+//     lies outside the n x n matrices, so the edge tiles need no masking.  Two
+//     slices are in flight; the last converter warp done with a stage issues
+//     its refill;
+//   * each of the 8 converter warps rounds its share of the slice to BF16 (hi,
+//     and lo for the split form) into a ring of operand slots, one 16-wide k
+//     block per slot, laid out K-major with the 32-byte swizzle the tensor
+//     core reads.  Warp w converts 16 rows of A for every block and 8 k rows of
+//     B (one half of one block's B^T, transposed on the way);
+//   * one thread issues tcgen05.mma per block (M=128, kind::f16, BF16 in, FP32
+//     accumulators in tensor memory) and frees the slot with tcgen05.commit.
+//     The split form is two MMAs: hi(A) against [hi(B); lo(B)] as one N=256
+//     operand (accumulator columns 0..255), then lo(A) against hi(B) into
+//     columns 128..255, so the tile is D[0..127] + D[128..255];
+//   * the converter warps read the accumulators with tcgen05.ld and store the
 //     tile (masked at the matrix edge).
-// Bulk copies need 16-byte aligned rows; when n is not a multiple of 4 (or an
-// operand is unaligned) the converters read global memory directly instead.
+// The slot ring lets conversion of block u overlap the MMAs of earlier
+// blocks; the staging ring lets the copies of slice s+2 overlap both.
+// Tensor maps need 16-byte aligned rows; when n is not a multiple of 4 (or an
+// operand is unaligned, or no maps were built) the converters read global
+// memory directly instead.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -32,21 +41,35 @@
 namespace cafgpu {
 
 constexpr uint32_t kGemmBM = 128;          // tile rows (MMA M)
-constexpr uint32_t kGemmBN = 128;          // tile columns (MMA N)
-constexpr uint32_t kGemmBK = 64;           // k per stage: one 128-byte swizzle atom of BF16
+constexpr uint32_t kGemmBN = 128;          // tile columns (MMA N of one product)
+constexpr uint32_t kGemmBK = 64;           // k per FP32 staging slice
+constexpr uint32_t kGemmKB = 16;           // k per BF16 block (one MMA)
+constexpr uint32_t kGemmBlocks = kGemmBK / kGemmKB;   // blocks per slice
 constexpr uint32_t kGemmConvWarps = 8;
-constexpr uint32_t kGemmOperandBytes = kGemmBM * kGemmBK * 2;   // 16 KB per BF16 operand tile
-constexpr uint32_t kGemmTmemCols = 128;
+constexpr uint32_t kGemmPlaneBytes = kGemmBM * kGemmKB * 2;   // 4 KB: 128 rows x 16 k BF16
+constexpr uint32_t kGemmTmemCols = 256;
 
-// Operand tiles of one GEMM CTA (1024-byte aligned: the swizzle pattern
-// repeats every 1024 bytes), then the FP32 staging.
+// One BF16 operand slot: 128 rows x 16 k per plane, K-major, 32-byte swizzle.
+// b_hi and b_lo are adjacent so the split form reads them as one 256-row B.
+struct GemmBfSlot {
+    uint8_t a_hi[kGemmPlaneBytes];
+    uint8_t a_lo[kGemmPlaneBytes];
+    uint8_t b_hi[kGemmPlaneBytes];
+    uint8_t b_lo[kGemmPlaneBytes];
+};
+static_assert(sizeof(GemmBfSlot) == kGemmSlotBytes, "slot size");
+// One FP32 staging stage: the A slice as two 32-wide k halves (128 rows of
+// 128 bytes, 128-byte swizzle: 16-byte chunk q of row r at chunk q ^ (r & 7)),
+// and the B slice (64 rows of k, 128 columns, dense).
+struct GemmF32Stage {
+    float a[2][kGemmBM * 32];
+    float b[kGemmBK * kGemmBN];
+};
+static_assert(sizeof(GemmF32Stage) == kGemmStageBytes, "stage size");
+// Operand area of one GEMM CTA (1024-byte aligned).
 struct GemmOps {
-    uint8_t a_hi[kGemmOperandBytes];
-    uint8_t b_hi[kGemmOperandBytes];
-    uint8_t a_lo[kGemmOperandBytes];
-    uint8_t b_lo[kGemmOperandBytes];
-    float a32[2][kGemmBM * kGemmBK];   // A block: 128 rows x 64 k
-    float b32[2][kGemmBK * kGemmBN];   // B block: 64 rows (k) x 128 columns
+    GemmBfSlot bf[kGemmBfSlots];
+    GemmF32Stage f32[kGemmF32Stages];
 };
 static_assert(sizeof(GemmOps) == kGemmOpsBytes, "operand area size");
 struct GemmSmem {
@@ -54,12 +77,64 @@ struct GemmSmem {
     GemmBars bars;
 };
 
+// One output tile's operands.  tmap_a / tmap_b: tensor maps of A and B (in
+// global or kernel-parameter memory), or null for the direct path.
+// tmap_fence: the maps were written by device code and need a tensormap-proxy
+// acquire before use.
+struct GemmArgs {
+    const float *A, *B;
+    float *C;
+    const void *tmap_a, *tmap_b;
+    uint32_t n, tm, tn;
+    bool split, tmap_fence;
+};
+
 // Barrier phases of one CTA across the tiles it computes.
 struct GemmCounters {
-    uint32_t f32_uses;   // k blocks staged so far (staging stage = use & 1)
-    uint32_t bf_uses;    // k blocks converted so far (one BF16 operand buffer)
+    uint32_t f32_uses;   // slices staged so far (stage = use % kGemmF32Stages)
+    uint32_t bf_uses;    // BF16 blocks converted so far (slot = use % kGemmBfSlots)
     uint32_t tiles;      // tiles finished (done barrier phase)
 };
+
+// ---- tensor copies ------------------------------------------------------
+// 2-D tiled tensor copy global -> shared (box at element coordinates x
+// (innermost) and y), completing on an mbarrier.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int32_t x, int32_t y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// Make a tensor map written through the generic proxy visible to this
+// thread's tensor copies.
+__device__ __forceinline__ void tmap_acquire(const void *tmap) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
+}
+
+// Tensor maps of A and B, built on the device by copying the host-encoded
+// pair for this n (the encoder's output depends on n in ways tensormap.replace
+// does not reproduce -- it marks maps of tensors above 128 KiB -- so there is
+// one template pair per n) and pointing it at the operands.  One thread;
+// ma, mb: global memory, 128-byte aligned.
+__device__ __forceinline__ void tmap_set_address(uint8_t *map, uint64_t base) {
+    const uint64_t m = reinterpret_cast<uint64_t>(map);
+    asm volatile("tensormap.replace.tile.global_address.global.b1024.b64 [%0], %1;" ::"l"(m), "l"(base) : "memory");
+}
+__device__ __forceinline__ void gemm_build_tmaps(uint8_t *ma, uint8_t *mb, const uint8_t *pair, uint64_t A,
+                                                 uint64_t B) {
+    const uint4 *t = reinterpret_cast<const uint4 *>(pair);
+    uint4 *da = reinterpret_cast<uint4 *>(ma);
+    uint4 *db = reinterpret_cast<uint4 *>(mb);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        da[i] = t[i];
+        db[i] = t[8 + i];
+    }
+    tmap_set_address(ma, A);
+    tmap_set_address(mb, B);
+    asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
+}
 
 // ---- tcgen05 wrappers -------------------------------------------------------
 __device__ __forceinline__ void tmem_alloc(uint32_t *smem_result, uint32_t ncols) {
@@ -106,12 +181,14 @@ __device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, uint32_t (&r)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), version 1.
-__device__ __forceinline__ uint64_t smem_desc_sw128(const void *p) {
+// Shared-memory matrix descriptor: K-major operand, 32-byte swizzle (rows of
+// 32 bytes = one 16-wide k block, so one swizzle atom spans the MMA's K and
+// the leading byte offset is unused), 8-row groups 256 bytes apart (stride
+// byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw32(const void *p) {
     const uint64_t addr = smem_u32(p);
-    return ((addr >> 4) & 0x3FFFull) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
-           (2ull << 61);
+    return ((addr >> 4) & 0x3FFFull) | (1ull << 16) | ((uint64_t)(256 >> 4) << 32) | (1ull << 46) |
+           (6ull << 61);
 }
 
 // Instruction descriptor, kind::f16: D F32, A and B BF16, both K-major, M x N.
@@ -119,9 +196,10 @@ __host__ __device__ constexpr uint32_t gemm_idesc(uint32_t m, uint32_t n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
 }
 
-// Byte offset of element (row r, k) in a 128-row x 64-k K-major SW128 tile.
-__device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t chunk /* k / 8 */) {
-    return (r >> 3) * 1024u + (r & 7u) * 128u + (((chunk ^ r) & 7u) << 4);
+// Byte offset of the 8-element chunk c (k 8c..8c+7) of row r in a 128-row x
+// 16-k K-major plane with the 32-byte swizzle (address bit 4 ^= bit 7).
+__device__ __forceinline__ uint32_t sw32_offset(uint32_t r, uint32_t c) {
+    return r * 32u + ((c ^ ((r >> 2) & 1u)) << 4);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -156,71 +234,66 @@ __device__ __forceinline__ void convert8(const float (&x)[8], uint8_t *hi_dst, u
     }
 }
 
-// Issue the bulk copies of this warp's slice of k block kb into staging
-// stage st (warp-collective): A rows 16w..16w+15 of the tile, B rows
-// k0+8w..k0+8w+7.  Rows past n are not copied (the converter zero-fills).
-__device__ __forceinline__ void gemm_stage_issue(const float *A, const float *B, uint32_t n, uint32_t tm,
-                                                 uint32_t tn, uint32_t kb, float *a32, float *b32, uint64_t *bar,
-                                                 uint32_t w) {
-    const uint32_t lane = lane_id();
-    const uint32_t k0 = kb * kGemmBK, col0 = tn * kGemmBN, row0 = tm * kGemmBM + 16 * w;
-    const uint32_t a_bytes = min(kGemmBK, n - k0) * 4u;
-    const uint32_t b_bytes = min(kGemmBN, n - col0) * 4u;
-    const uint32_t na = row0 < n ? min(16u, n - row0) : 0u;
-    const uint32_t nb = (k0 + 8 * w) < n ? min(8u, n - (k0 + 8 * w)) : 0u;
+// Stage slice kb of tile (tm, tn) into S (one thread): A's two k halves and
+// B's 64 k rows.  The full box is always written (zero outside the matrix),
+// so the transaction count is the stage size.
+__device__ __forceinline__ void gemm_stage_issue(const GemmArgs &g, uint32_t kb, GemmF32Stage &S, uint64_t *bar) {
+    const int32_t k0 = (int32_t)(kb * kGemmBK), row0 = (int32_t)(g.tm * kGemmBM), col0 = (int32_t)(g.tn * kGemmBN);
     fence_proxy_async_smem();   // earlier generic reads of this stage before the async writes
-    __syncwarp();
-    if (lane == 0) mbar_arrive_expect_tx(bar, na * a_bytes + nb * b_bytes);
-    __syncwarp();
-    if (lane < na)
-        bulk_g2s(a32 + (16 * w + lane) * kGemmBK, A + (size_t)(row0 + lane) * n + k0, a_bytes, bar);
-    else if (lane >= 16 && lane - 16 < nb)
-        bulk_g2s(b32 + (8 * w + lane - 16) * kGemmBN, B + (size_t)(k0 + 8 * w + lane - 16) * n + col0, b_bytes,
-                 bar);
+    mbar_arrive_expect_tx(bar, kGemmStageBytes);
+    tma_load_2d(S.a[0], g.tmap_a, k0, row0, bar);
+    tma_load_2d(S.a[1], g.tmap_a, k0 + 32, row0, bar);
+    tma_load_2d(S.b, g.tmap_b, col0, k0, bar);
 }
 
-// Convert this warp's slice of k block kb to BF16 (hi, lo) into the operand
-// tiles.  Source: the staged FP32 slice, or global memory when `direct`.
-__device__ __forceinline__ void gemm_convert_slice(const float *__restrict__ A, const float *__restrict__ B,
-                                                   uint32_t n, uint32_t tm, uint32_t tn, uint32_t kb,
-                                                   const float *a32, const float *b32, bool direct,
-                                                   GemmOps &O, bool split, uint32_t w) {
+// B part of slice kb: warp w's 8 k rows (k0+8w..) for all 128 columns, as
+// chunk w&1 of block w>>1's B^T rows.  Lane: columns lane + 32i.  Source: the
+// staged slice, or global memory (kDirect, masked at the matrix edge).
+template <bool kDirect>
+__device__ __forceinline__ void gemm_convert_b(const GemmArgs &g, const GemmF32Stage &S, uint32_t k0,
+                                               GemmBfSlot &slot, uint32_t w) {
     const uint32_t lane = lane_id();
-    const uint32_t k0 = kb * kGemmBK;
-    // A: rows 16w + (c >> 3), k chunk c & 7, for c = lane + 32 i
+    const uint32_t c = w & 1u, gk = k0 + 8 * w;
 #pragma unroll
     for (uint32_t i = 0; i < 4; ++i) {
-        const uint32_t c = lane + 32u * i;
-        const uint32_t r = 16 * w + (c >> 3), kc = c & 7u;
-        const uint32_t gr = tm * kGemmBM + r, gk = k0 + kc * 8;
-        float x[8];
-        if (direct) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) x[j] = (gr < n && gk + j < n) ? __ldg(A + (size_t)gr * n + gk + j) : 0.0f;
-        } else {
-            const float4 *src = reinterpret_cast<const float4 *>(a32 + r * kGemmBK + kc * 8);
-            const float4 lo = src[0], hi = src[1];
-            const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-#pragma unroll
-            for (int j = 0; j < 8; ++j) x[j] = (gr < n && gk + j < n) ? v[j] : 0.0f;
-        }
-        const uint32_t off = sw128_offset(r, kc);
-        convert8(x, O.a_hi + off, O.a_lo + off, split);
-    }
-    // B^T: columns lane + 32 i of the tile, k chunk w (B rows k0+8w .. k0+8w+7)
-#pragma unroll
-    for (uint32_t i = 0; i < 4; ++i) {
-        const uint32_t col = lane + 32u * i;
-        const uint32_t gc = tn * kGemmBN + col, gk = k0 + 8 * w;
+        const uint32_t col = lane + 32u * i, gc = g.tn * kGemmBN + col;
         float x[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const bool in = gc < n && gk + j < n;
-            x[j] = !in ? 0.0f : (direct ? __ldg(B + (size_t)(gk + j) * n + gc) : b32[(8 * w + j) * kGemmBN + col]);
+        for (uint32_t j = 0; j < 8; ++j) {
+            if (kDirect)
+                x[j] = (gc < g.n && gk + j < g.n) ? __ldg(g.B + (size_t)(gk + j) * g.n + gc) : 0.0f;
+            else
+                x[j] = S.b[(8 * w + j) * kGemmBN + col];
         }
-        const uint32_t off = sw128_offset(col, w);
-        convert8(x, O.b_hi + off, O.b_lo + off, split);
+        const uint32_t off = sw32_offset(col, c);
+        convert8(x, slot.b_hi + off, slot.b_lo + off, g.split);
     }
+}
+
+// A part of block j of slice kb: warp w's rows 16w..16w+15, k 16j..16j+15.
+// Lane: row 16w + (lane & 15), chunk lane >> 4.
+template <bool kDirect>
+__device__ __forceinline__ void gemm_convert_a(const GemmArgs &g, const GemmF32Stage &S, uint32_t k0,
+                                               GemmBfSlot &slot, uint32_t w, uint32_t j) {
+    const uint32_t lane = lane_id();
+    const uint32_t r = 16 * w + (lane & 15u), c = lane >> 4;
+    float x[8];
+    if (kDirect) {
+        const uint32_t gr = g.tm * kGemmBM + r, gk = k0 + 16 * j + 8 * c;
+#pragma unroll
+        for (uint32_t e = 0; e < 8; ++e)
+            x[e] = (gr < g.n && gk + e < g.n) ? __ldg(g.A + (size_t)gr * g.n + gk + e) : 0.0f;
+    } else {
+        // 16-byte chunks q, q+1 of row r in k half j>>1
+        const uint8_t *row = reinterpret_cast<const uint8_t *>(S.a[j >> 1]) + r * 128u;
+        const uint32_t q = 4 * (j & 1u) + 2 * c;
+        const float4 lo = *reinterpret_cast<const float4 *>(row + ((q ^ (r & 7u)) << 4));
+        const float4 hi = *reinterpret_cast<const float4 *>(row + (((q + 1) ^ (r & 7u)) << 4));
+        x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
+        x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
+    }
+    const uint32_t off = sw32_offset(r, c);
+    convert8(x, slot.a_hi + off, slot.a_lo + off, g.split);
 }
 
 }  // namespace cafgpu
@@ -241,10 +314,14 @@ __device__ __forceinline__ GemmSmem &gemm_smem(uint8_t *raw) {
 // (the caller synchronises the CTA afterwards, with tcgen05 fences).
 __device__ __forceinline__ void gemm_bars_init(GemmBars &Bb) {
     if (lane_id() == 0) {
-        for (uint32_t s = 0; s < 2; ++s)
-            for (uint32_t w = 0; w < kGemmConvWarps; ++w) mbar_init(&Bb.f32_full[s][w], 1);
-        mbar_init(&Bb.full, kGemmConvWarps);
-        mbar_init(&Bb.empty, 1);
+        for (uint32_t s = 0; s < kGemmF32Stages; ++s) {
+            mbar_init(&Bb.f32_full[s], 1);
+            Bb.f32_read[s] = 0;
+        }
+        for (uint32_t s = 0; s < kGemmBfSlots; ++s) {
+            mbar_init(&Bb.bf_full[s], kGemmConvWarps);
+            mbar_init(&Bb.bf_empty[s], 1);
+        }
         mbar_init(&Bb.done, 1);
         fence_barrier_init();
     }
@@ -286,67 +363,120 @@ struct CtaSyncAll {
     }
 };
 
-// Compute output tile (tm, tn) of C = A * B with the whole CTA (converter
-// warps 0..7 and the MMA warp kGemmConvWarps).  `K` carries the barrier
-// phases across the tiles this CTA computes.  Returns false if a bounded wait
+// Wait (warp-wide) until slot use u may be overwritten: the MMAs of use
+// u - kGemmBfSlots have completed.
+__device__ __forceinline__ bool gemm_slot_free(GemmBars &Bb, uint32_t u, uint64_t limit_ns) {
+    if (u < kGemmBfSlots) return true;
+    return gemm_wait(&Bb.bf_empty[u % kGemmBfSlots], (u / kGemmBfSlots - 1u) & 1u, limit_ns);
+}
+
+// One slice of converter warp w: the B part first (so every block's last
+// contribution from this warp is its A part), then the A part of each block,
+// publishing each block to the MMA thread.  Returns false if a wait expired.
+template <bool kDirect>
+__device__ __forceinline__ bool gemm_convert_slice(const GemmArgs &g, const GemmF32Stage &S, uint32_t k0,
+                                                   GemmOps &O, GemmBars &Bb, uint32_t u0, uint32_t w,
+                                                   uint64_t limit_ns) {
+    const uint32_t lane = lane_id();
+    const uint32_t ub = u0 + (w >> 1);
+    bool ok = gemm_slot_free(Bb, ub, limit_ns);
+    if (!__all_sync(0xFFFFFFFFu, ok)) return false;
+    gemm_convert_b<kDirect>(g, S, k0, O.bf[ub % kGemmBfSlots], w);
+#pragma unroll 1
+    for (uint32_t j = 0; j < kGemmBlocks; ++j) {
+        const uint32_t u = u0 + j;
+        if (j != (w >> 1)) {
+            ok = gemm_slot_free(Bb, u, limit_ns);
+            if (!__all_sync(0xFFFFFFFFu, ok)) return false;
+        }
+        gemm_convert_a<kDirect>(g, S, k0, O.bf[u % kGemmBfSlots], w, j);
+        fence_proxy_async_smem();   // generic-proxy writes -> tensor-core (async proxy) reads
+        __syncwarp();
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&Bb.bf_full[u % kGemmBfSlots]))
+                         : "memory");
+    }
+    return true;
+}
+
+// Compute one output tile of C = A * B with the whole CTA (converter warps
+// 0..7 and the MMA warp kGemmConvWarps).  `K` carries the barrier phases
+// across the tiles this CTA computes.  Returns false if a bounded wait
 // expired.
 template <class CtaSync>
-__device__ bool gemm_tile(const float *__restrict__ A, const float *__restrict__ B, float *__restrict__ C,
-                          uint32_t n, uint32_t tm, uint32_t tn, bool split, GemmOps &O, GemmBars &Bb,
-                          GemmCounters &K, uint64_t limit_ns, CtaSync cta_sync) {
+__device__ bool gemm_tile(const GemmArgs &g, GemmOps &O, GemmBars &Bb, GemmCounters &K, uint64_t limit_ns,
+                          CtaSync cta_sync) {
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-    const uint32_t nk = (n + kGemmBK - 1) / kGemmBK;
-    // bulk copies need 16-byte aligned rows
-    const bool direct = (n & 3u) != 0 || (reinterpret_cast<uintptr_t>(A) & 15u) != 0 ||
-                        (reinterpret_cast<uintptr_t>(B) & 15u) != 0;
+    const uint32_t n = g.n, nk = (n + kGemmBK - 1) / kGemmBK;
+    const bool staged = g.tmap_a != nullptr;
     bool ok = true;
     if (warp < kGemmConvWarps) {
         const uint32_t w = warp;
-        if (!direct) {
-            for (uint32_t kb = 0; kb < 2 && kb < nk; ++kb) {
-                const uint32_t st = (K.f32_uses + kb) & 1u;
-                gemm_stage_issue(A, B, n, tm, tn, kb, O.a32[st], O.b32[st], &Bb.f32_full[st][w], w);
+        if (staged && lane == 0) {
+            // any converter warp may issue a refill
+            if (g.tmap_fence) {
+                tmap_acquire(g.tmap_a);
+                tmap_acquire(g.tmap_b);
             }
+            if (w == 0)
+                for (uint32_t kb = 0; kb < kGemmF32Stages && kb < nk; ++kb) {
+                    const uint32_t st = (K.f32_uses + kb) % kGemmF32Stages;
+                    gemm_stage_issue(g, kb, O.f32[st], &Bb.f32_full[st]);
+                }
         }
-        for (uint32_t kb = 0; kb < nk; ++kb) {
-            const uint32_t fu = K.f32_uses + kb, bu = K.bf_uses + kb;
-            const uint32_t st = fu & 1u;
-            bool okw = true;
-            if (!direct) okw = gemm_wait(&Bb.f32_full[st][w], (fu >> 1) & 1u, limit_ns);
-            if (okw && bu >= 1) okw = gemm_wait(&Bb.empty, (bu - 1) & 1u, limit_ns);
-            if (!__all_sync(0xFFFFFFFFu, okw)) { ok = false; break; }
-            gemm_convert_slice(A, B, n, tm, tn, kb, O.a32[st], O.b32[st], direct, O, split, w);
-            fence_proxy_async_smem();   // generic-proxy writes -> tensor-core (async proxy) reads
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&Bb.full)) : "memory");
-            if (!direct && kb + 2 < nk)
-                gemm_stage_issue(A, B, n, tm, tn, kb + 2, O.a32[st], O.b32[st], &Bb.f32_full[st][w], w);
+        __syncwarp();
+        uint32_t kb = 0;
+#pragma unroll 1
+        for (; kb < nk; ++kb) {
+            const uint32_t u0 = K.bf_uses + kb * kGemmBlocks;
+            if (!staged) {
+                ok = gemm_convert_slice<true>(g, O.f32[0], kb * kGemmBK, O, Bb, u0, w, limit_ns);
+            } else {
+                const uint32_t fu = K.f32_uses + kb, st = fu % kGemmF32Stages;
+                bool okw = gemm_wait(&Bb.f32_full[st], (fu / kGemmF32Stages) & 1u, limit_ns);
+                if (!__all_sync(0xFFFFFFFFu, okw)) { ok = false; break; }
+                ok = gemm_convert_slice<false>(g, O.f32[st], kb * kGemmBK, O, Bb, u0, w, limit_ns);
+                // release the stage; the last warp out issues its refill
+                if (ok && lane == 0) {
+                    __threadfence_block();
+                    const uint32_t prev = atomicAdd(&Bb.f32_read[st], 1u);
+                    if ((prev + 1) % kGemmConvWarps == 0 && kb + kGemmF32Stages < nk)
+                        gemm_stage_issue(g, kb + kGemmF32Stages, O.f32[st], &Bb.f32_full[st]);
+                }
+                __syncwarp();
+            }
+            if (!ok) break;
+        }
+        // after an expired wait, let copies possibly still in flight land
+        // (bounded) before the shared memory can be reused
+        for (uint32_t q = kb; staged && !ok && q < nk && q < kb + kGemmF32Stages; ++q) {
+            const uint32_t fu = K.f32_uses + q;
+            gemm_wait(&Bb.f32_full[fu % kGemmF32Stages], (fu / kGemmF32Stages) & 1u, limit_ns);
         }
     } else if (lane == 0) {
-        const uint32_t idesc = gemm_idesc(kGemmBM, kGemmBN);
-        const uint64_t ah = smem_desc_sw128(O.a_hi), bh = smem_desc_sw128(O.b_hi);
-        const uint64_t al = smem_desc_sw128(O.a_lo), bl = smem_desc_sw128(O.b_lo);
-        for (uint32_t kb = 0; kb < nk && ok; ++kb) {
-            ok = gemm_wait(&Bb.full, (K.bf_uses + kb) & 1u, limit_ns);
+        const uint32_t id128 = gemm_idesc(kGemmBM, kGemmBN), id256 = gemm_idesc(kGemmBM, 2 * kGemmBN);
+        const uint32_t nb = nk * kGemmBlocks;
+        for (uint32_t i = 0; i < nb && ok; ++i) {
+            const uint32_t u = K.bf_uses + i, s = u % kGemmBfSlots;
+            ok = gemm_wait(&Bb.bf_full[s], (u / kGemmBfSlots) & 1u, limit_ns);
             if (!ok) break;
             tc_fence_after();
-#pragma unroll
-            for (uint32_t k16 = 0; k16 < kGemmBK / 16; ++k16) {
-                const uint64_t ko = (k16 * 32u) >> 4;   // 16 BF16 = 32 bytes along k inside the swizzle atom
-                tc_mma_f16(Bb.tmem, ah + ko, bh + ko, idesc, (kb | k16) != 0);
-                if (split) {
-                    tc_mma_f16(Bb.tmem, ah + ko, bl + ko, idesc, 1u);
-                    tc_mma_f16(Bb.tmem, al + ko, bh + ko, idesc, 1u);
-                }
+            GemmBfSlot &sl = O.bf[s];
+            const uint64_t ah = smem_desc_sw32(sl.a_hi), bh = smem_desc_sw32(sl.b_hi);
+            if (g.split) {
+                tc_mma_f16(Bb.tmem, ah, bh, id256, i != 0);   // hi*hi -> cols 0..127, hi*lo -> 128..255
+                tc_mma_f16(Bb.tmem + kGemmBN, smem_desc_sw32(sl.a_lo), bh, id128, 1u);   // lo*hi -> 128..255
+            } else {
+                tc_mma_f16(Bb.tmem, ah, bh, id128, i != 0);
             }
-            tc_commit(&Bb.empty);
+            tc_commit(&Bb.bf_empty[s]);
         }
         tc_commit(&Bb.done);
     }
     if (warp == kGemmConvWarps) __syncwarp();
-    K.f32_uses += direct ? 0 : nk;
-    K.bf_uses += nk;
-    // epilogue: converter warps read the accumulator (warp w: TMEM lanes
+    K.f32_uses += staged ? nk : 0;
+    K.bf_uses += nk * kGemmBlocks;
+    // epilogue: converter warps read the accumulators (warp w: TMEM lanes
     // 32*(w%4).., columns 64*(w/4)..) and store the tile
     if (warp < kGemmConvWarps) {
         bool dok = ok && gemm_wait(&Bb.done, K.tiles & 1u, limit_ns);
@@ -354,14 +484,21 @@ __device__ bool gemm_tile(const float *__restrict__ A, const float *__restrict__
         if (dok) {
             tc_fence_after();
             const uint32_t row0 = (warp & 3u) * 32u, col0 = (warp >> 2) * 64u;
-            const uint32_t gr = tm * kGemmBM + row0 + lane;
+            const uint32_t gr = g.tm * kGemmBM + row0 + lane;
 #pragma unroll
             for (uint32_t cc = 0; cc < 64; cc += 32) {
                 uint32_t r[32];
                 tmem_ld_32x32(Bb.tmem + (row0 << 16) + col0 + cc, r);
+                if (g.split) {
+                    uint32_t r2[32];
+                    tmem_ld_32x32(Bb.tmem + (row0 << 16) + kGemmBN + col0 + cc, r2);
+#pragma unroll
+                    for (uint32_t j = 0; j < 32; ++j)
+                        r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(r2[j]));
+                }
                 if (gr < n) {
-                    float *crow = C + (size_t)gr * n;
-                    const uint32_t gc0 = tn * kGemmBN + col0 + cc;
+                    float *crow = g.C + (size_t)gr * n;
+                    const uint32_t gc0 = g.tn * kGemmBN + col0 + cc;
                     if (gc0 + 32 <= n && (reinterpret_cast<uintptr_t>(crow + gc0) & 15u) == 0) {
 #pragma unroll
                         for (uint32_t j = 0; j < 32; j += 4)
@@ -379,7 +516,7 @@ __device__ bool gemm_tile(const float *__restrict__ A, const float *__restrict__
         ok = ok && dok;
     }
     ++K.tiles;
-    // the next tile's MMAs overwrite the accumulator: every epilogue read
+    // the next tile's MMAs overwrite the accumulators: every epilogue read
     // must be complete first
     tc_fence_before();
     cta_sync();

@@ -17,6 +17,7 @@
 // the reply slots that caf_gpu_await polls, and a small control block.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 
 namespace cafgpu {
@@ -39,13 +40,22 @@ struct TableTile {
     uint32_t plim[kTile];
 };
 
+// GEMM tile engine geometry (see gemm_tc.cuh): FP32 staging stages of one
+// 64-wide k slice each, and a ring of BF16 operand slots of one 16-wide k
+// block each.
+constexpr uint32_t kGemmF32Stages = 2;
+constexpr uint32_t kGemmBfSlots = 6;
+constexpr uint32_t kGemmStageBytes = 2u * 128u * 32u * 4u + 64u * 128u * 4u;   // A halves + B: 64 KB
+constexpr uint32_t kGemmSlotBytes = 4u * 128u * 16u * 2u;                      // 4 BF16 planes: 16 KB
+
 // Barriers and tensor-memory address of the GEMM tile engine.
 struct GemmBars {
-    uint64_t f32_full[2][8];       // per staging stage and converter warp: its FP32 slice landed
-    uint64_t full;                 // converters -> MMA thread (BF16 operands ready)
-    uint64_t empty;                // MMA completion -> converters (BF16 operands free)
-    uint64_t done;                 // last MMA completed -> epilogue
-    uint32_t tmem;                 // accumulator address from tcgen05.alloc
+    uint64_t f32_full[kGemmF32Stages];     // tensor copies of a staged slice landed
+    uint64_t bf_full[kGemmBfSlots];        // converters -> MMA thread (BF16 block ready)
+    uint64_t bf_empty[kGemmBfSlots];       // MMA completion -> converters (slot free again)
+    uint64_t done;                         // last MMA of a tile completed -> epilogue
+    uint32_t f32_read[kGemmF32Stages];     // converter warps done with a stage (monotonic count)
+    uint32_t tmem;                         // accumulator address from tcgen05.alloc
     uint32_t pad;
 };
 
@@ -67,15 +77,15 @@ struct GroupShared {
 constexpr uint32_t kDrainHeader = 1024;
 static_assert(sizeof(GroupShared) <= kDrainHeader, "drain header fits");
 constexpr uint32_t kTableRingBytes = kStages * (uint32_t)sizeof(TableTile);
-// BF16 hi/lo x A/B (16 KB each) + FP32 A and B staging, 2 stages x 32 KB each
-constexpr uint32_t kGemmOpsBytes = 4u * 128u * 64u * 2u + 2u * 2u * 128u * 64u * 4u;
+// BF16 operand slots + FP32 staging stages
+constexpr uint32_t kGemmOpsBytes = kGemmBfSlots * kGemmSlotBytes + kGemmF32Stages * kGemmStageBytes;
 // dynamic shared memory of the drain (+1024 for aligning the base)
 constexpr uint32_t kDrainSmemFactor = 1024 + kDrainHeader + kTableRingBytes;
 constexpr uint32_t kDrainSmemMixed = 1024 + kDrainHeader + (kGemmOpsBytes > kTableRingBytes ? kGemmOpsBytes : kTableRingBytes);
 
 // A GEMM message being computed by the drain: its 128 x 128 output tiles are
 // items (job << 16 | tile) in the tile queue.
-struct GemmJob {
+struct alignas(128) GemmJob {
     uint64_t A, B, C;
     uint32_t n;
     uint32_t split;
@@ -83,9 +93,13 @@ struct GemmJob {
     uint32_t done;                 // tiles finished (atomic)
     uint64_t reply_addr;
     uint32_t reply_token;
-    uint32_t pad[3];
+    uint32_t tma;                  // 1: the tensor maps below describe A and B
+    uint32_t pad[18];
+    alignas(128) uint8_t tmap_a[128];   // CUtensorMap of A (n x n FP32, box 32 k x 128 rows, 128-byte swizzle)
+    alignas(128) uint8_t tmap_b[128];   // CUtensorMap of B (n x n FP32, box 128 columns x 64 k, no swizzle)
 };
-static_assert(sizeof(GemmJob) == 64, "GemmJob is 64 bytes");
+static_assert(sizeof(GemmJob) == 384 && offsetof(GemmJob, tmap_a) == 128 && offsetof(GemmJob, tmap_b) == 256,
+              "GemmJob layout");
 constexpr uint32_t kMaxDrainGemmN = 4096;   // <= 1024 tiles per job
 constexpr uint32_t kGemmJobs = 1024;         // GEMM messages in flight in the drain
 
@@ -294,6 +308,7 @@ struct DrainParams {
     // GEMM actors (gemm != 0: tensor memory and the GEMM shared-memory layout)
     GemmJob *jobs;
     QCell *jobq;
+    const uint8_t *gemm_tmpl;      // tensor-map templates: pair (A, B) for n = 4(i+1) at 256 i
     uint32_t gemm;
     uint32_t pad1;
 };

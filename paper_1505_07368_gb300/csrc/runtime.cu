@@ -67,6 +67,7 @@ struct caf_gpu_runtime {
     GemmJob *d_jobs = nullptr;
     QCell *d_jobq = nullptr;
     uint32_t jobq_cap = 0;
+    uint8_t *d_gemm_tmpl = nullptr;        // tensor-map templates of A and B (null: no tensor copies)
     bool gemm_enabled = false;             // a GEMM actor exists: drains use the GEMM layout
     unsigned grid_factor = 0, grid_mixed = 0;
     uint32_t *d_primes = nullptr, *d_pinv = nullptr, *d_plim = nullptr;
@@ -149,6 +150,7 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.ring_mask = rt->cfg.ingress_capacity - 1;
     p.jobs = rt->d_jobs;
     p.jobq = rt->d_jobq;
+    p.gemm_tmpl = rt->d_gemm_tmpl;
     p.gemm = rt->gemm_enabled ? 1u : 0u;
     return p;
 }
@@ -365,6 +367,7 @@ void free_runtime(caf_gpu_runtime *rt) {
     cudaFree(rt->d_batches);
     cudaFree(rt->d_jobs);
     cudaFree(rt->d_jobq);
+    cudaFree(rt->d_gemm_tmpl);
     if (rt->gemm_descs) cudaFreeHost(rt->gemm_descs);
     cudaFree(rt->d_primes);
     cudaFree(rt->d_pinv);
@@ -451,6 +454,27 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     if ((r = init_queue(rt, &rt->d_jobq, rt->jobq_cap, &rt->d_ctl->jobq, jobs))) return r;
     CK(cudaMalloc(&rt->d_jobs, sizeof(GemmJob) * kGemmJobs));
     CK(cudaMemset(rt->d_jobs, 0, sizeof(GemmJob) * kGemmJobs));
+    {
+        // tensor-map templates the drain copies and points at each GEMM's A and
+        // B: one host-encoded pair per n (a multiple of 4, up to the drain's
+        // limit); without the driver's encoder the converters read the
+        // operands directly
+        const uint32_t pairs = kMaxDrainGemmN / 4;
+        std::vector<uint8_t> tmpl((size_t)pairs * 256);
+        CK(cudaMalloc(&rt->d_gemm_tmpl, tmpl.size()));
+        bool ok = true;
+        for (uint32_t i = 0; i < pairs && ok; ++i) {
+            const uint32_t n = 4 * (i + 1);
+            ok = gemm_encode_tmap(&tmpl[256 * (size_t)i], rt->d_gemm_tmpl, n, true) == 0 &&
+                 gemm_encode_tmap(&tmpl[256 * (size_t)i + 128], rt->d_gemm_tmpl, n, false) == 0;
+        }
+        if (ok) {
+            CK(cudaMemcpy(rt->d_gemm_tmpl, tmpl.data(), tmpl.size(), cudaMemcpyHostToDevice));
+        } else {
+            cudaFree(rt->d_gemm_tmpl);
+            rt->d_gemm_tmpl = nullptr;
+        }
+    }
     if (c.validation_mode) {
         CK(cudaMalloc(&rt->d_log, sizeof(LogRow) * (size_t)c.log_capacity));
         CK(cudaMemset(rt->d_log, 0, sizeof(LogRow) * (size_t)c.log_capacity));
@@ -1068,6 +1092,22 @@ int caf_gpu_debug_wait_expiry(caf_gpu_runtime *rt, uint64_t limit_ns) {
     rt->launches += 1;
     CK(cudaStreamSynchronize(rt->stream));
     return rt->hctl->error_word ? CAF_GPU_EWAITLIMIT : 0;
+}
+
+int caf_gpu_debug_gemm_tmaps(caf_gpu_runtime *rt, const void *A, const void *B, uint32_t n, uint8_t *device_built,
+                             uint8_t *host_encoded) {
+    if (!rt || !device_built || !host_encoded || n == 0) return CAF_GPU_EINVAL;
+    if (!rt->d_gemm_tmpl || !gemm_tma_ok(A, B, n) || n > kMaxDrainGemmN) return CAF_GPU_EINVAL;
+    if (gemm_encode_tmap(host_encoded, A, n, true) || gemm_encode_tmap(host_encoded + 128, B, n, false))
+        return CAF_GPU_EINVAL;
+    uint8_t *d_out = nullptr;
+    CK(cudaMalloc(&d_out, 256));
+    cudaError_t e = launch_gemm_tmap_build(rt->d_gemm_tmpl, A, B, n, d_out, rt->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(device_built, d_out, 256, cudaMemcpyDeviceToHost, rt->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(rt->stream);
+    cudaFree(d_out);
+    rt->launches += 1;
+    return e == cudaSuccess ? 0 : CAF_GPU_ECUDA;
 }
 
 int caf_gpu_clear_error(caf_gpu_runtime *rt) {
