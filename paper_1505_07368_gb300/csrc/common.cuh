@@ -156,13 +156,28 @@ __device__ __forceinline__ void raise_error(DevCtl *ctl, uint32_t code, uint32_t
 }
 
 // ---------------------------------------------------------------------------
-// Bounded MPMC queue (array of cells with sequence numbers; a push reserves a
-// position with one atomic add, a pop claims the head with one CAS).  Each
+// Bounded MPMC queue: an array of cells with sequence numbers, positions
+// handed out by atomic adds on the tail (push) and head (pop) -- no CAS retry
+// loop, so many CTAs can pop at once without the pops serialising on one
+// word, and each pop is served in the order it arrived.
+//
+// A pop first reserves an item on `avail` (published items not yet reserved;
+// an add of -1 that finds it <= 0 is undone and the pop reports empty), then
+// takes the next head position.  Reservations never exceed the items
+// published, so every position a pop takes is (or is about to be) filled by a
+// push that already holds it; the pop waits, bounded, for that cell.  A push
+// takes a tail position, waits (bounded) until the cell's previous occupant
+// has been popped, publishes the value and then counts it in `avail`.  Each
 // value is in the queue at most once per push; capacity is a power of two and
-// is sized by the host so that a push never needs to wait for space except
-// for the short window in which a popper has claimed the cell but not yet
-// released it.
+// is sized by the host so that a push never needs to wait for space.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t q_avail(QueueHdr *q) {
+    return (int64_t)ld_relaxed_gpu(reinterpret_cast<const uint64_t *>(&q->avail));
+}
+__device__ __forceinline__ int64_t q_avail_add(QueueHdr *q, int64_t v) {
+    return (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(&q->avail), (unsigned long long)v);
+}
+
 __device__ __forceinline__ bool q_push(QueueHdr *q, QCell *cells, uint32_t v, uint64_t limit_ns) {
     uint64_t pos = add_u64(&q->enq, 1);
     QCell *c = &cells[pos & q->mask];
@@ -174,37 +189,33 @@ __device__ __forceinline__ bool q_push(QueueHdr *q, QCell *cells, uint32_t v, ui
     }
     c->val = v;
     st_release_gpu(&c->seq, pos + 1);
+    q_avail_add(q, 1);
     return true;
 }
 
-// Non-blocking pop: false when the queue is empty.
-__device__ __forceinline__ bool q_try_pop(QueueHdr *q, QCell *cells, uint32_t *out) {
-    uint64_t pos = ld_relaxed_gpu(&q->deq);
-    for (int tries = 0; tries < 64; ++tries) {
-        QCell *c = &cells[pos & q->mask];
-        uint64_t seq = ld_acquire_gpu(&c->seq);
-        int64_t diff = (int64_t)(seq - (pos + 1));
-        if (diff == 0) {
-            uint64_t prev = cas_u64(&q->deq, pos, pos + 1);
-            if (prev == pos) {
-                uint32_t v = *((volatile uint32_t *)&c->val);
-                st_release_gpu(&c->seq, pos + (uint64_t)q->mask + 1);
-                *out = v;
-                return true;
-            }
-            pos = prev;
-        } else if (diff < 0) {
-            return false;
-        } else {
-            pos = ld_relaxed_gpu(&q->deq);
+// Non-blocking pop: 1 with *out set, 0 when the queue is empty, -1 when the
+// cell of a reserved position was not published within `limit_ns` (an error:
+// the caller reports it).
+__device__ __forceinline__ int q_try_pop(QueueHdr *q, QCell *cells, uint32_t *out, uint64_t limit_ns) {
+    if (q_avail(q) <= 0) return 0;
+    if (q_avail_add(q, -1) <= 0) {
+        q_avail_add(q, 1);
+        return 0;
+    }
+    const uint64_t pos = add_u64(&q->deq, 1);
+    QCell *c = &cells[pos & q->mask];
+    if (ld_acquire_gpu(&c->seq) != pos + 1) {
+        WaitClock w(limit_ns);
+        while (ld_acquire_gpu(&c->seq) != pos + 1) {
+            if (!w.again()) return -1;
         }
     }
-    return false;
+    *out = *((volatile uint32_t *)&c->val);
+    st_release_gpu(&c->seq, pos + (uint64_t)q->mask + 1);
+    return 1;
 }
 
-// Approximate length (for scheduling decisions only).
-__device__ __forceinline__ int64_t q_len(QueueHdr *q) {
-    return (int64_t)(ld_relaxed_gpu(&q->enq) - ld_relaxed_gpu(&q->deq));
-}
+// Items published and not yet reserved (for scheduling decisions only).
+__device__ __forceinline__ int64_t q_len(QueueHdr *q) { return q_avail(q); }
 
 }  // namespace cafgpu

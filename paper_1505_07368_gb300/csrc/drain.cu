@@ -688,6 +688,7 @@ __device__ bool q_push_block(const DrainParams &P, QueueHdr *q, QCell *cells, ui
         if (lane == 0) fail(P, kErrWaitQueue, 15, count, base);
         return false;
     }
+    if (lane == 0) q_avail_add(q, count);
     return true;
 }
 
@@ -708,7 +709,9 @@ __device__ __noinline__ void claim_gemm(const DrainParams &P, uint32_t a) {
     if (lane == 0) add_u64(&ctl->claims, 1);
     // reserve job records first, so a claim never waits for one
     uint32_t j = kNone;
-    bool got = lane < want && q_try_pop(&ctl->jobq, P.jobq, &j);
+    const int pr = lane < want ? q_try_pop(&ctl->jobq, P.jobq, &j, P.wait_limit_ns) : 0;
+    if (pr < 0) fail(P, kErrWaitQueue, 21);
+    bool got = pr > 0;
     const uint32_t gm = __ballot_sync(FULL, got);
     const uint32_t nj = (gm == FULL) ? 32u : (uint32_t)(__ffs(~gm) - 1);
     MsgData m{};
@@ -806,7 +809,11 @@ __device__ uint32_t find_batch(const DrainParams &P) {
     for (int attempt = 0; attempt < 4; ++attempt) {
         uint32_t a = 0;
         bool got = false;
-        if (lane == 0) got = q_try_pop(&ctl->readyq, P.readyq, &a);
+        if (lane == 0) {
+            const int pr = q_try_pop(&ctl->readyq, P.readyq, &a, P.wait_limit_ns);
+            if (pr < 0) fail(P, kErrWaitQueue, 22);
+            got = pr > 0;
+        }
         got = __shfl_sync(FULL, got, 0);
         if (!got) return kNone;
         a = __shfl_sync(FULL, a, 0);
@@ -814,7 +821,11 @@ __device__ uint32_t find_batch(const DrainParams &P) {
         if (kind == kFactor) {
             uint32_t b = 0;
             bool gb = false;
-            if (lane == 0) gb = q_try_pop(&ctl->freeq, P.freeq, &b);
+            if (lane == 0) {
+                const int pr = q_try_pop(&ctl->freeq, P.freeq, &b, P.wait_limit_ns);
+                if (pr < 0) fail(P, kErrWaitQueue, 23);
+                gb = pr > 0;
+            }
             gb = __shfl_sync(FULL, gb, 0);
             if (!gb) {
                 // no batch record free: leave the actor READY for later
@@ -939,7 +950,11 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
         if (producer && lane == 0) {
             G.exit = exit_requested(ctl) ? 1u : 0u;
             uint32_t item = kNone;
-            if (gemm_cta && !G.exit && !q_try_pop(&ctl->workq, P.workq, &item)) item = kNone;
+            if (gemm_cta && !G.exit) {
+                const int pr = q_try_pop(&ctl->workq, P.workq, &item, P.wait_limit_ns);
+                if (pr < 0) fail(P, kErrWaitQueue, 24);
+                if (pr <= 0) item = kNone;
+            }
             G.gemm_item = item;
             // watchdog: busy warps can keep the heartbeat fresh without any
             // message completing; give up if nothing completes for a long time

@@ -144,10 +144,12 @@ struct caf_dmsg_t {
 static_assert(sizeof(caf_dmsg_t) == 32, "caf_dmsg_t is 32 bytes");
 
 struct QueueHdr {
-    uint64_t enq;
+    uint64_t enq;                  // tail: next push position
     uint64_t pad0[15];
-    uint64_t deq;
+    uint64_t deq;                  // head: next pop position
     uint64_t pad1[15];
+    int64_t avail;                 // published items not yet reserved by a pop
+    uint64_t pad3[15];
     uint32_t mask;
     uint32_t pad2[31];
 };

@@ -174,6 +174,7 @@ int init_queue(caf_gpu_runtime *rt, QCell **cells, uint32_t cap, QueueHdr *hdr_d
     QueueHdr q{};
     q.enq = initial.size();
     q.deq = 0;
+    q.avail = (int64_t)initial.size();
     q.mask = cap - 1;
     CK(cudaMemcpy(hdr_dev, &q, sizeof(q), cudaMemcpyHostToDevice));
     return 0;
