@@ -370,30 +370,30 @@ __device__ __forceinline__ bool gemm_slot_free(GemmBars &Bb, uint32_t u, uint64_
     return gemm_wait(&Bb.bf_empty[u % kGemmBfSlots], (u / kGemmBfSlots - 1u) & 1u, limit_ns);
 }
 
-// One slice of converter warp w: the B part first (so every block's last
-// contribution from this warp is its A part), then the A part of each block,
-// publishing each block to the MMA thread.  Returns false if a wait expired.
+// One slice of converter warp w: its B part, then the A parts of all the
+// slice's blocks (independent work the warp can overlap), then one publish of
+// every block to the MMA thread.  Returns false if a wait expired.
 template <bool kDirect>
 __device__ __forceinline__ bool gemm_convert_slice(const GemmArgs &g, const GemmF32Stage &S, uint32_t k0,
                                                    GemmOps &O, GemmBars &Bb, uint32_t u0, uint32_t w,
                                                    uint64_t limit_ns) {
     const uint32_t lane = lane_id();
-    const uint32_t ub = u0 + (w >> 1);
-    bool ok = gemm_slot_free(Bb, ub, limit_ns);
+    const uint32_t jb = w >> 1, ub = u0 + jb;
+    bool ok = true;
+#pragma unroll
+    for (uint32_t j = 0; j < kGemmBlocks; ++j) ok = ok && gemm_slot_free(Bb, u0 + j, limit_ns);
     if (!__all_sync(0xFFFFFFFFu, ok)) return false;
     gemm_convert_b<kDirect>(g, S, k0, O.bf[ub % kGemmBfSlots], w);
-#pragma unroll 1
-    for (uint32_t j = 0; j < kGemmBlocks; ++j) {
-        const uint32_t u = u0 + j;
-        if (j != (w >> 1)) {
-            ok = gemm_slot_free(Bb, u, limit_ns);
-            if (!__all_sync(0xFFFFFFFFu, ok)) return false;
-        }
-        gemm_convert_a<kDirect>(g, S, k0, O.bf[u % kGemmBfSlots], w, j);
-        fence_proxy_async_smem();   // generic-proxy writes -> tensor-core (async proxy) reads
-        __syncwarp();
-        if (lane == 0)
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&Bb.bf_full[u % kGemmBfSlots]))
+#pragma unroll
+    for (uint32_t j = 0; j < kGemmBlocks; ++j)
+        gemm_convert_a<kDirect>(g, S, k0, O.bf[(u0 + j) % kGemmBfSlots], w, j);
+    fence_proxy_async_smem();   // generic-proxy writes -> tensor-core (async proxy) reads
+    __syncwarp();
+    if (lane == 0) {
+#pragma unroll
+        for (uint32_t j = 0; j < kGemmBlocks; ++j)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                             smem_u32(&Bb.bf_full[(u0 + j) % kGemmBfSlots]))
                          : "memory");
     }
     return true;
