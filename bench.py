@@ -445,7 +445,7 @@ def run_gemm(args):
 
     from paper_1505_07368_gb300 import cafgpu as C
     torch.cuda.set_device(0)
-    wl = W.config3(pool_elems=1 << 26)
+    wl = W.config3(pool_elems=1 << 26, n_messages=args.max_messages or 4096)
     pool = torch.from_numpy(W.gemm_pool(wl.pool_seed, wl.pool_elems)).cuda()
     sizes = wl.size.astype(np.int64)
     outs = torch.empty(int((4 * sizes * sizes).sum() // 4), dtype=torch.float32, device="cuda")
@@ -462,7 +462,7 @@ def run_gemm(args):
     peaks = measured_peaks()
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "bf16 operands, f32 accumulate", "data": "synthetic",
-            "config": {"workload": "GEMM actors: 256 actors, 4096 messages, n uniform in {64,...,1024}, N(0,1)",
+            "config": {"workload": f"GEMM actors: 256 actors, {wl.count} messages, n uniform in {{64,...,1024}}, N(0,1)",
                        "messages": wl.count, "l2": "flushed between steps (256 MiB write)"}, "variants": {}}
     for kind, name in ((C.GEMM_BF16, "bf16"), (C.GEMM_SPLIT_BF16X3, "split_bf16x3")):
         _note(f"gemm {name}: persistent")
