@@ -168,3 +168,49 @@ def test_persistent_factor_and_gemm_in_one_drain():
         A = pool_np[oa[i]:oa[i] + n * n].reshape(n, n)
         B = pool_np[ob[i]:ob[i] + n * n].reshape(n, n)
         assert oracle.rel_frobenius(outs[i], oracle.gemm_f64(A, B)) <= 1e-5
+
+
+def test_error_table_every_workload_size():
+    """Relative Frobenius error against the float64 oracle for every n of the
+    GEMM-actor workload (64, 128, ..., 1024), N(0,1) operands, BF16 and split
+    forms of the same product, through the persistent drain.  Prints the table."""
+    import torch
+    from helpers import to_device
+    sizes = list(range(64, 1025, 64))
+    pool_np = W.gemm_pool(37, 1 << 21)
+    pool = torch.from_numpy(pool_np).cuda()
+    offs_a = W._offsets(W.stream_key(37, 1), np.asarray(sizes), pool.numel())
+    offs_b = W._offsets(W.stream_key(37, 2), np.asarray(sizes), pool.numel())
+    with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=4) as rt:
+        a_bf, a_sp = rt.spawn(C.GEMM_BF16), rt.spawn(C.GEMM_SPLIT_BF16X3)
+        outs = [torch.full((n, n), float("nan"), dtype=torch.float32, device="cuda") for n in sizes for _ in (0, 1)]
+        count = len(outs)
+        desc = np.zeros(count, C.GEMM_DESC_DTYPE)
+        m = np.zeros(count, C.DMSG_DTYPE)
+        for i, n in enumerate(sizes):
+            for k, (actor, kind) in enumerate(((a_bf, C.GEMM_BF16), (a_sp, C.GEMM_SPLIT_BF16X3))):
+                j = 2 * i + k
+                desc[j] = (pool.data_ptr() + 4 * int(offs_a[i]), pool.data_ptr() + 4 * int(offs_b[i]),
+                           outs[j].data_ptr(), n, 0)
+                m[j]["actor"] = actor - 1
+                m[j]["kind"] = kind
+                m[j]["tag"] = j
+        d_desc = to_device(desc)
+        m["u64"] = d_desc.data_ptr() + np.arange(count, dtype=np.uint64) * C.GEMM_DESC_DTYPE.itemsize
+        d_m = to_device(m)
+        d_r = torch.zeros(count * C.DREPLY_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        rt.request_batch_device(d_m.data_ptr(), count, d_r.data_ptr())
+        rt.stream_sync()
+        rep = d_r.cpu().numpy().view(C.DREPLY_DTYPE)
+        got = [o.cpu().numpy() for o in outs]
+    assert np.all(rep["done"] == 1) and np.all(rep["status"] == 0)
+    print("\nGEMM-ERROR-TABLE n bf16 split")
+    for i, n in enumerate(sizes):
+        A = pool_np[offs_a[i]:offs_a[i] + n * n].reshape(n, n)
+        B = pool_np[offs_b[i]:offs_b[i] + n * n].reshape(n, n)
+        C64 = oracle.gemm_f64(A, B)
+        e_bf, e_sp = oracle.rel_frobenius(got[2 * i], C64), oracle.rel_frobenius(got[2 * i + 1], C64)
+        print(f"GEMM-ERROR-TABLE {n} {e_bf:.3e} {e_sp:.3e}")
+        assert e_bf <= 1e-2, (n, e_bf)
+        assert e_sp <= 1e-5, (n, e_sp)
