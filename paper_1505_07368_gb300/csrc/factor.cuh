@@ -190,6 +190,43 @@ __device__ __forceinline__ bool sweep_chunk(const SweepRegs &s, uint32_t p, uint
 #undef CAFGPU_TEST_BLOCK
 static_assert(kFactorKMax == 16, "sweep_chunk unrolls 16 slots in blocks of four");
 
+// Two primes per lane (p0 from one chunk, p1 from another): eight independent
+// multiply chains per block of four slots.
+#define CAFGPU_TEST_BLOCK2(B)                                                             \
+    case (B) / 4 + 1: {                                                                   \
+        const uint32_t a0 = s.nl[(B) + 0] * i0, a1 = s.nl[(B) + 1] * i0;                  \
+        const uint32_t a2 = s.nl[(B) + 2] * i0, a3 = s.nl[(B) + 3] * i0;                  \
+        const uint32_t c0 = s.nl[(B) + 0] * i1, c1 = s.nl[(B) + 1] * i1;                  \
+        const uint32_t c2 = s.nl[(B) + 2] * i1, c3 = s.nl[(B) + 3] * i1;                  \
+        const uint32_t b0 = __umulhi(a0, p0) + s.ch[(B) + 0];                             \
+        const uint32_t b1 = __umulhi(a1, p0) + s.ch[(B) + 1];                             \
+        const uint32_t b2 = __umulhi(a2, p0) + s.ch[(B) + 2];                             \
+        const uint32_t b3 = __umulhi(a3, p0) + s.ch[(B) + 3];                             \
+        const uint32_t d0 = __umulhi(c0, p1) + s.ch[(B) + 0];                             \
+        const uint32_t d1 = __umulhi(c1, p1) + s.ch[(B) + 1];                             \
+        const uint32_t d2 = __umulhi(c2, p1) + s.ch[(B) + 2];                             \
+        const uint32_t d3 = __umulhi(c3, p1) + s.ch[(B) + 3];                             \
+        const uint32_t m0 = min(min(b0 * i0, b1 * i0), min(b2 * i0, b3 * i0));            \
+        const uint32_t m1 = min(min(d0 * i1, d1 * i1), min(d2 * i1, d3 * i1));            \
+        hit |= (m0 <= l0) | (m1 <= l1);                                                   \
+    }
+
+// True if any held message is divisible by either of this lane's primes.
+__device__ __forceinline__ bool sweep_chunk2(const SweepRegs &s, uint32_t p0, uint32_t i0, uint32_t l0,
+                                             uint32_t p1, uint32_t i1, uint32_t l1) {
+    bool hit = false;
+    switch ((s.k + 3) >> 2) {
+        CAFGPU_TEST_BLOCK2(12)
+        CAFGPU_TEST_BLOCK2(8)
+        CAFGPU_TEST_BLOCK2(4)
+        CAFGPU_TEST_BLOCK2(0)
+        default:
+            break;
+    }
+    return hit;
+}
+#undef CAFGPU_TEST_BLOCK2
+
 // Bit j set if this lane's prime divides the message in slot j (slow path,
 // run only for chunks where some lane hit).
 __device__ __forceinline__ uint32_t sweep_which(const SweepRegs &s, uint32_t p, uint32_t pinv, uint32_t plim) {

@@ -29,8 +29,8 @@ constexpr uint32_t kOneThreads = 256;                      // per-message factor
 constexpr uint32_t kFactorKMax = 16;     // messages per factor batch, upper bound
 constexpr uint32_t kRangePrimes = 4096;  // table padding granule
 constexpr uint32_t kNoFactor = 0xFFFFFFFFu;
-constexpr uint32_t kTile = 512;          // primes per staged table tile (16 chunks of 32)
-constexpr uint32_t kStages = 8;          // tiles in flight per CTA
+constexpr uint32_t kTile = 2048;         // primes per staged table tile (64 chunks of 32)
+constexpr uint32_t kStages = 4;          // tiles in flight per CTA
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 // One staged tile of the prime table (shared memory, 16-byte aligned).
