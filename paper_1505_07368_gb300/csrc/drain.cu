@@ -301,7 +301,8 @@ __device__ void group_produce(const DrainParams &P, GroupShared &G, TableTile *r
 // streamed tiles.  A team of `wpb` warps shares one batch; member `r` tests
 // the chunks u of each tile with u % wpb == r, and members drop messages that
 // another member has already decided below their position.
-static_assert((kTile / 32) % (2 * kConsumerWarps) == 0, "a tile splits into chunk pairs for any team size");
+constexpr uint32_t kSweepPrimes = 4;   // chunks (primes per lane) tested per step
+static_assert((kTile / 32) % (kSweepPrimes * kConsumerWarps) == 0, "a tile splits into steps for any team size");
 __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableTile *ring, uint32_t &t,
                               uint32_t b, uint32_t r, uint32_t wpb) {
     const uint32_t lane = lane_id();
@@ -354,33 +355,41 @@ __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableT
             }
             const uint32_t tbase = smem_u32(&ring[st]);
             uint32_t tile_tests = 0;
-            // two chunks per step, u and u + wpb (kTile / 32 is a multiple of
-            // 2 * wpb); one copy of the body: the test switch is large, and an
-            // unrolled tile loop overflows the instruction cache
+            // kSweepPrimes chunks per step, u + q wpb (kTile / 32 is a multiple
+            // of kSweepPrimes * wpb); one copy of the body: the test switch is
+            // large, and an unrolled tile loop overflows the instruction cache
 #pragma unroll 1
-            for (uint32_t u = r; u < kTile / 32 && s.k > 0; u += 2 * wpb) {
-                const uint32_t c0 = start + u * 32, c1 = c0 + 32 * wpb;
-                const uint32_t off0 = (u * 32 + lane) * 4, off1 = off0 + 32 * wpb * 4;
-                const uint32_t p0 = lds_u32(tbase + off0);
-                const uint32_t i0 = lds_u32(tbase + kTile * 4 + off0);
-                const uint32_t l0 = lds_u32(tbase + 2 * kTile * 4 + off0);
-                const uint32_t p1 = lds_u32(tbase + off1);
-                const uint32_t i1 = lds_u32(tbase + kTile * 4 + off1);
-                const uint32_t l1 = lds_u32(tbase + 2 * kTile * 4 + off1);
-                tile_tests += (uint32_t)s.k * 64u;
-                if (__any_sync(FULL, sweep_chunk2(s, p0, i0, l0, p1, i1, l1))) {
-                    const uint32_t h0 = sweep_which(s, p0, i0, l0);
-                    const uint32_t h1 = sweep_which(s, p1, i1, l1);
-                    const uint32_t any = __reduce_or_sync(FULL, h0 | h1);
+            for (uint32_t u = r; u < kTile / 32 && s.k > 0; u += kSweepPrimes * wpb) {
+                const uint32_t c0 = start + u * 32;
+                uint32_t pp[kSweepPrimes], pi[kSweepPrimes], pl[kSweepPrimes];
+#pragma unroll
+                for (uint32_t q = 0; q < kSweepPrimes; ++q) {
+                    const uint32_t off = ((u + q * wpb) * 32 + lane) * 4;
+                    pp[q] = lds_u32(tbase + off);
+                    pi[q] = lds_u32(tbase + kTile * 4 + off);
+                    pl[q] = lds_u32(tbase + 2 * kTile * 4 + off);
+                }
+                tile_tests += (uint32_t)s.k * 32u * kSweepPrimes;
+                if (__any_sync(FULL, sweep_chunks<kSweepPrimes>(s, pp, pi, pl))) {
+                    uint32_t h[kSweepPrimes], hh = 0;
+#pragma unroll
+                    for (uint32_t q = 0; q < kSweepPrimes; ++q) {
+                        h[q] = sweep_which(s, pp[q], pi[q], pl[q]);
+                        hh |= h[q];
+                    }
+                    const uint32_t any = __reduce_or_sync(FULL, hh);
                     for (uint32_t m = any; m; m &= m - 1) {
                         const int j = __ffs(m) - 1;
-                        const uint32_t x0 = ((h0 >> j) & 1u) ? c0 + lane : 0xFFFFFFFFu;
-                        const uint32_t x1 = ((h1 >> j) & 1u) ? c1 + lane : 0xFFFFFFFFu;
-                        const uint32_t mn = __reduce_min_sync(FULL, min(x0, x1));
+                        uint32_t x = 0xFFFFFFFFu;
+#pragma unroll
+                        for (uint32_t q = 0; q < kSweepPrimes; ++q)
+                            if ((h[q] >> j) & 1u) x = min(x, c0 + q * 32 * wpb + lane);
+                        const uint32_t mn = __reduce_min_sync(FULL, x);
                         if (lane == 0) atomicMin(reinterpret_cast<unsigned int *>(&B->found[slot_id(s, j)]), mn);
                     }
                     sweep_remove_mask(s, any);
                 }
+                const uint32_t c1 = c0 + (kSweepPrimes - 1) * 32 * wpb;
                 // the next step starts at c1 + 32 * wpb
                 if (s.k > 0 && c1 + 32 * wpb >= next_drop) {
                     bool rm = false;

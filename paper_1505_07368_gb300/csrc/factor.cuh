@@ -159,73 +159,45 @@ __device__ __forceinline__ bool sweep_test(const SweepRegs &s, int j, uint32_t p
     return n1 * pinv <= plim;
 }
 
-// Four independent tests (slots B..B+3), written so the multiplies of the
-// four chains interleave.
-#define CAFGPU_TEST_BLOCK(B)                                                              \
-    case (B) / 4 + 1: {                                                                   \
-        const uint32_t a0 = s.nl[(B) + 0] * pinv, a1 = s.nl[(B) + 1] * pinv;              \
-        const uint32_t a2 = s.nl[(B) + 2] * pinv, a3 = s.nl[(B) + 3] * pinv;              \
-        const uint32_t b0 = __umulhi(a0, p) + s.ch[(B) + 0];                              \
-        const uint32_t b1 = __umulhi(a1, p) + s.ch[(B) + 1];                              \
-        const uint32_t b2 = __umulhi(a2, p) + s.ch[(B) + 2];                              \
-        const uint32_t b3 = __umulhi(a3, p) + s.ch[(B) + 3];                              \
-        const bool h = (b0 * pinv <= plim) | (b1 * pinv <= plim) | (b2 * pinv <= plim) |   \
-                       (b3 * pinv <= plim);                                               \
-        hit |= h;                                                                         \
-    }
-
-// True if any held message is divisible by this lane's prime.
-__device__ __forceinline__ bool sweep_chunk(const SweepRegs &s, uint32_t p, uint32_t pinv, uint32_t plim) {
+// Slots B..B+3 against NP primes per lane (one per chunk): 4 NP independent
+// multiply chains; a hit is the minimum of the four m1 at or below the limit.
+template <int B, int NP>
+__device__ __forceinline__ bool sweep_block(const SweepRegs &s, const uint32_t (&p)[NP], const uint32_t (&pi)[NP],
+                                            const uint32_t (&pl)[NP]) {
+    uint32_t a[NP][4];
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[q][i] = s.nl[B + i] * pi[q];
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[q][i] = __umulhi(a[q][i], p[q]) + s.ch[B + i];
     bool hit = false;
-    switch ((s.k + 3) >> 2) {
-        CAFGPU_TEST_BLOCK(12)
-        CAFGPU_TEST_BLOCK(8)
-        CAFGPU_TEST_BLOCK(4)
-        CAFGPU_TEST_BLOCK(0)
-        default:
-            break;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const uint32_t m = min(min(a[q][0] * pi[q], a[q][1] * pi[q]), min(a[q][2] * pi[q], a[q][3] * pi[q]));
+        hit |= m <= pl[q];
     }
     return hit;
 }
-#undef CAFGPU_TEST_BLOCK
-static_assert(kFactorKMax == 16, "sweep_chunk unrolls 16 slots in blocks of four");
 
-// Two primes per lane (p0 from one chunk, p1 from another): eight independent
-// multiply chains per block of four slots.
-#define CAFGPU_TEST_BLOCK2(B)                                                             \
-    case (B) / 4 + 1: {                                                                   \
-        const uint32_t a0 = s.nl[(B) + 0] * i0, a1 = s.nl[(B) + 1] * i0;                  \
-        const uint32_t a2 = s.nl[(B) + 2] * i0, a3 = s.nl[(B) + 3] * i0;                  \
-        const uint32_t c0 = s.nl[(B) + 0] * i1, c1 = s.nl[(B) + 1] * i1;                  \
-        const uint32_t c2 = s.nl[(B) + 2] * i1, c3 = s.nl[(B) + 3] * i1;                  \
-        const uint32_t b0 = __umulhi(a0, p0) + s.ch[(B) + 0];                             \
-        const uint32_t b1 = __umulhi(a1, p0) + s.ch[(B) + 1];                             \
-        const uint32_t b2 = __umulhi(a2, p0) + s.ch[(B) + 2];                             \
-        const uint32_t b3 = __umulhi(a3, p0) + s.ch[(B) + 3];                             \
-        const uint32_t d0 = __umulhi(c0, p1) + s.ch[(B) + 0];                             \
-        const uint32_t d1 = __umulhi(c1, p1) + s.ch[(B) + 1];                             \
-        const uint32_t d2 = __umulhi(c2, p1) + s.ch[(B) + 2];                             \
-        const uint32_t d3 = __umulhi(c3, p1) + s.ch[(B) + 3];                             \
-        const uint32_t m0 = min(min(b0 * i0, b1 * i0), min(b2 * i0, b3 * i0));            \
-        const uint32_t m1 = min(min(d0 * i1, d1 * i1), min(d2 * i1, d3 * i1));            \
-        hit |= (m0 <= l0) | (m1 <= l1);                                                   \
-    }
+// True if any held message is divisible by any of this lane's NP primes.
+static_assert(kFactorKMax == 16, "sweep_chunks unrolls 16 slots in blocks of four");
 
-// True if any held message is divisible by either of this lane's primes.
-__device__ __forceinline__ bool sweep_chunk2(const SweepRegs &s, uint32_t p0, uint32_t i0, uint32_t l0,
-                                             uint32_t p1, uint32_t i1, uint32_t l1) {
+template <int NP>
+__device__ __forceinline__ bool sweep_chunks(const SweepRegs &s, const uint32_t (&p)[NP], const uint32_t (&pi)[NP],
+                                             const uint32_t (&pl)[NP]) {
     bool hit = false;
     switch ((s.k + 3) >> 2) {
-        CAFGPU_TEST_BLOCK2(12)
-        CAFGPU_TEST_BLOCK2(8)
-        CAFGPU_TEST_BLOCK2(4)
-        CAFGPU_TEST_BLOCK2(0)
-        default:
-            break;
+        case 4: hit |= sweep_block<12, NP>(s, p, pi, pl); [[fallthrough]];
+        case 3: hit |= sweep_block<8, NP>(s, p, pi, pl); [[fallthrough]];
+        case 2: hit |= sweep_block<4, NP>(s, p, pi, pl); [[fallthrough]];
+        case 1: hit |= sweep_block<0, NP>(s, p, pi, pl); break;
+        default: break;
     }
     return hit;
 }
-#undef CAFGPU_TEST_BLOCK2
 
 // Bit j set if this lane's prime divides the message in slot j (slow path,
 // run only for chunks where some lane hit).
