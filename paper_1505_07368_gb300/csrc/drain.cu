@@ -236,11 +236,17 @@ __device__ __forceinline__ void sweep_remove_mask(SweepRegs &s, uint32_t mask) {
     }
 }
 
-// Smallest bound among the held slots.
-__device__ __forceinline__ uint32_t sweep_min_bound(const SweepRegs &s, const FactorBatch *B) {
+// Per-slot value v of the held slot at position `lane` (lane j of `v` holds
+// the value of batch message j); 0xFFFFFFFF for lanes past the held slots.
+__device__ __forceinline__ uint32_t held_value(const SweepRegs &s, uint32_t v) {
     const uint32_t lane = lane_id();
-    const uint32_t pb = (int)lane < s.k ? B->pbound[slot_id(s, lane)] : 0xFFFFFFFFu;
-    return __reduce_min_sync(FULL, pb);
+    const uint32_t x = __shfl_sync(FULL, v, slot_id(s, lane & 15u));
+    return (int)lane < s.k ? x : 0xFFFFFFFFu;
+}
+
+// Smallest bound among the held slots (pb: lane j holds message j's bound).
+__device__ __forceinline__ uint32_t sweep_min_bound(const SweepRegs &s, uint32_t pb) {
+    return __reduce_min_sync(FULL, held_value(s, pb));
 }
 
 // CTA barrier over the first `nthreads` threads' warps.  Callers reach it
@@ -331,7 +337,9 @@ __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableT
         if (lane == 0) atomicSub(&G.active, 1u);
         counted = false;
     }
-    uint32_t next_drop = s.k > 0 ? sweep_min_bound(s, B) : 0xFFFFFFFFu;
+    // bounds of the batch's messages, lane j holding message j's
+    const uint32_t pbv = (B && lane < B->count) ? B->pbound[lane] : 0xFFFFFFFFu;
+    uint32_t next_drop = s.k > 0 ? sweep_min_bound(s, pbv) : 0xFFFFFFFFu;
     uint64_t tests = 0;
     for (uint32_t i = 0;; ++i, ++t) {
         const uint32_t st = t % kStages;
@@ -346,13 +354,11 @@ __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableT
         }
         if (s.k > 0) {
             const uint32_t start = i * kTile;
-            if (wpb > 1) {
-                // drop messages a teammate has already factored below this tile
-                bool rm = false;
-                if ((int)lane < s.k) rm = *((volatile uint32_t *)&B->found[slot_id(s, lane)]) < start;
-                sweep_remove_mask(s, __ballot_sync(FULL, rm));
-                if (s.k > 0) next_drop = sweep_min_bound(s, B);
-            }
+            // teammates' hits (lane j: message j), read now and applied after
+            // this tile so the load's latency overlaps the tests; a stale
+            // value only costs tests
+            uint32_t fv = 0xFFFFFFFFu;
+            if (wpb > 1 && lane < kFactorKMax) fv = ld_relaxed_gpu(&B->found[lane]);
             const uint32_t tbase = smem_u32(&ring[st]);
             uint32_t tile_tests = 0;
             // kSweepPrimes chunks per step, u + q wpb (kTile / 32 is a multiple
@@ -392,13 +398,21 @@ __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableT
                 const uint32_t c1 = c0 + (kSweepPrimes - 1) * 32 * wpb;
                 // the next step starts at c1 + 32 * wpb
                 if (s.k > 0 && c1 + 32 * wpb >= next_drop) {
-                    bool rm = false;
-                    if ((int)lane < s.k) rm = B->pbound[slot_id(s, lane)] <= c1 + 32 * wpb;
-                    sweep_remove_mask(s, __ballot_sync(FULL, rm));
-                    if (s.k > 0) next_drop = sweep_min_bound(s, B);
+                    const uint32_t rm = __ballot_sync(FULL, held_value(s, pbv) <= c1 + 32 * wpb);
+                    sweep_remove_mask(s, rm);
+                    next_drop = s.k > 0 ? sweep_min_bound(s, pbv) : 0xFFFFFFFFu;
                 }
             }
             tests += tile_tests;
+            // drop messages a teammate has factored below the next tile: this
+            // warp's remaining primes cannot give a smaller divisor
+            if (wpb > 1 && s.k > 0) {
+                const uint32_t rm = __ballot_sync(FULL, held_value(s, fv) < start + kTile);
+                if (rm) {
+                    sweep_remove_mask(s, rm);
+                    next_drop = s.k > 0 ? sweep_min_bound(s, pbv) : 0xFFFFFFFFu;
+                }
+            }
             if (s.k == 0 && counted) {
                 if (lane == 0) atomicSub(&G.active, 1u);
                 counted = false;
