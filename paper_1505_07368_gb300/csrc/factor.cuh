@@ -111,7 +111,7 @@ struct SweepRegs {
 };
 
 // Slots at index >= k hold n = 1, which no prime divides, so the test can
-// run over whole blocks of four slots without checking k per slot.
+// run over whole blocks of slots without checking k per slot.
 constexpr uint32_t kDummyNl = 0xFFFFFFFFu;   // -1 mod 2^32
 constexpr uint32_t kDummyCh = 1u;            // 0 + [1 != 0]
 
@@ -159,40 +159,42 @@ __device__ __forceinline__ bool sweep_test(const SweepRegs &s, int j, uint32_t p
     return n1 * pinv <= plim;
 }
 
-// Slots B..B+3 against NP primes per lane (one per chunk): 4 NP independent
-// multiply chains; a hit is the minimum of the four m1 at or below the limit.
+// Slots B, B+1 against NP primes per lane (one per chunk): 2 NP independent
+// multiply chains; a hit is the smaller m1 at or below the limit.
 template <int B, int NP>
 __device__ __forceinline__ bool sweep_block(const SweepRegs &s, const uint32_t (&p)[NP], const uint32_t (&pi)[NP],
                                             const uint32_t (&pl)[NP]) {
-    uint32_t a[NP][4];
+    uint32_t a[NP][2];
 #pragma unroll
     for (int q = 0; q < NP; ++q)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[q][i] = s.nl[B + i] * pi[q];
+        for (int i = 0; i < 2; ++i) a[q][i] = s.nl[B + i] * pi[q];
 #pragma unroll
     for (int q = 0; q < NP; ++q)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[q][i] = __umulhi(a[q][i], p[q]) + s.ch[B + i];
+        for (int i = 0; i < 2; ++i) a[q][i] = __umulhi(a[q][i], p[q]) + s.ch[B + i];
     bool hit = false;
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        const uint32_t m = min(min(a[q][0] * pi[q], a[q][1] * pi[q]), min(a[q][2] * pi[q], a[q][3] * pi[q]));
-        hit |= m <= pl[q];
-    }
+    for (int q = 0; q < NP; ++q) hit |= min(a[q][0] * pi[q], a[q][1] * pi[q]) <= pl[q];
     return hit;
 }
 
-// True if any held message is divisible by any of this lane's NP primes.
-static_assert(kFactorKMax == 16, "sweep_chunks unrolls 16 slots in blocks of four");
+static_assert(kFactorKMax == 16, "sweep_chunks unrolls 16 slots in blocks of two");
 
+// True if any held message is divisible by any of this lane's NP primes.
+// Slots at index >= k hold n = 1, so only whole blocks of two are tested.
 template <int NP>
 __device__ __forceinline__ bool sweep_chunks(const SweepRegs &s, const uint32_t (&p)[NP], const uint32_t (&pi)[NP],
                                              const uint32_t (&pl)[NP]) {
     bool hit = false;
-    switch ((s.k + 3) >> 2) {
-        case 4: hit |= sweep_block<12, NP>(s, p, pi, pl); [[fallthrough]];
-        case 3: hit |= sweep_block<8, NP>(s, p, pi, pl); [[fallthrough]];
-        case 2: hit |= sweep_block<4, NP>(s, p, pi, pl); [[fallthrough]];
+    switch ((s.k + 1) >> 1) {
+        case 8: hit |= sweep_block<14, NP>(s, p, pi, pl); [[fallthrough]];
+        case 7: hit |= sweep_block<12, NP>(s, p, pi, pl); [[fallthrough]];
+        case 6: hit |= sweep_block<10, NP>(s, p, pi, pl); [[fallthrough]];
+        case 5: hit |= sweep_block<8, NP>(s, p, pi, pl); [[fallthrough]];
+        case 4: hit |= sweep_block<6, NP>(s, p, pi, pl); [[fallthrough]];
+        case 3: hit |= sweep_block<4, NP>(s, p, pi, pl); [[fallthrough]];
+        case 2: hit |= sweep_block<2, NP>(s, p, pi, pl); [[fallthrough]];
         case 1: hit |= sweep_block<0, NP>(s, p, pi, pl); break;
         default: break;
     }
