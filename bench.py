@@ -339,6 +339,14 @@ def run_ours(args):
                 "kernel": "k_drain", "algorithmic_tests_per_step": tests_alg,
                 "executed_tests_per_step": st["prime_tests"] / args.steps,
                 "peak_basis": f"{SM_COUNT} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz (sm_max_mhz of measured)"}
+    # what the test's own instruction mix can reach on this GPU (measured after
+    # the timed steps): its high multiply runs at a lower rate than the low one
+    rates = C.measure_mul_rates()
+    chain = rates["test_chain_mul_per_s"] / 1e12
+    roofline["measured_ceiling"] = {
+        "unit": "Tmul/s", "test_chain": chain, "mul_lo": rates["mul_lo_per_s"] / 1e12,
+        "mul_hi": rates["mul_hi_per_s"] / 1e12, "frac_of_test_chain": achieved_tops / chain,
+        "basis": "caf_gpu_measure_mul_rates: 8 independent chains per thread, 8 CTAs x 256 threads per SM"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -306,6 +306,16 @@ int caf_gpu_debug_wait_expiry(caf_gpu_runtime *rt, uint64_t limit_ns);
 int caf_gpu_debug_gemm_tmaps(caf_gpu_runtime *rt, const void *A, const void *B, uint32_t n, uint8_t *device_built,
                              uint8_t *host_encoded);
 
+/* Measured throughput, on the current device, of the 32-bit multiplies the
+ * factorization test is built from (the test is two low multiplies and one
+ * high multiply per (n, p) pair; Sec. 5's prime factorization, see
+ * caf_gpu_spawn): rates[0] = low multiply-adds/s, rates[1] = high multiplies/s,
+ * rates[2] = multiplies/s of the test's own three-multiply chain.  rates:
+ * host array of 3 doubles.  Runs three short kernels (a few ms) on the
+ * current device and allocates, then frees, a small buffer; needs no runtime.
+ * Returns CAF_GPU_EINVAL for a null pointer, CAF_GPU_ECUDA on a CUDA error. */
+int caf_gpu_measure_mul_rates(double *rates);
+
 /* Clear the device error word after a reported bounded-wait expiry. */
 int caf_gpu_clear_error(caf_gpu_runtime *rt);
 

@@ -99,7 +99,7 @@ EXPORTS = [
     "caf_gpu_request_batch_device", "caf_gpu_sync", "caf_gpu_stream_sync", "caf_gpu_set_backend",
     "caf_gpu_reset_actors", "caf_gpu_actor_state", "caf_gpu_stats_read", "caf_gpu_read_log",
     "caf_gpu_stream", "caf_gpu_mark", "caf_gpu_prime_table", "caf_gpu_debug_wait_expiry", "caf_gpu_clear_error",
-    "caf_gpu_debug_gemm_tmaps",
+    "caf_gpu_debug_gemm_tmaps", "caf_gpu_measure_mul_rates",
     "caf_gpu_graph_begin", "caf_gpu_graph_end", "caf_gpu_graph_launch", "caf_gpu_graph_destroy",
     "caf_gpu_serve_run", "caf_gpu_factor_static", "caf_gpu_strerror",
 ]
@@ -140,6 +140,7 @@ def load(build: bool = True):
         "caf_gpu_prime_table": [vp, P(vp), P(u32)],
         "caf_gpu_debug_wait_expiry": [vp, u64],
         "caf_gpu_debug_gemm_tmaps": [vp, vp, vp, u32, vp, vp],
+        "caf_gpu_measure_mul_rates": [vp],
         "caf_gpu_clear_error": [vp],
         "caf_gpu_mark": [vp],
         "caf_gpu_factor_static": [vp, u32, vp, vp],
@@ -159,6 +160,13 @@ def load(build: bool = True):
     L.caf_gpu_strerror.restype = ctypes.c_char_p
     _lib = L
     return L
+
+
+def measure_mul_rates() -> dict:
+    """Measured low-multiply, high-multiply and divisibility-test-chain rates (multiplies/s)."""
+    out = (ctypes.c_double * 3)()
+    _check(load().caf_gpu_measure_mul_rates(out), "caf_gpu_measure_mul_rates")
+    return {"mul_lo_per_s": out[0], "mul_hi_per_s": out[1], "test_chain_mul_per_s": out[2]}
 
 
 def factor_static(d_n: int, count: int, d_replies: int, stream: int = 0) -> int:
