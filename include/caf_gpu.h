@@ -294,18 +294,6 @@ int caf_gpu_prime_table(caf_gpu_runtime *rt, const uint32_t **d_primes, uint32_t
  * usable again. */
 int caf_gpu_debug_wait_expiry(caf_gpu_runtime *rt, uint64_t limit_ns);
 
-/* Validation hook for the GEMM payload's tensor copies: the drain builds the
- * tensor maps of each GEMM's A and B on the device, from host-encoded
- * templates (one pair per n) whose base address it replaces (tensormap.replace).  This writes the two 128-byte maps the device builds for
- * (A, B, n) to device_built[0..255] (host memory) and the driver encoder's maps
- * for the same operands to host_encoded[0..255]; equal bytes show the device
- * construction is the encoder's.  A, B: device pointers, 16-byte aligned, n a
- * multiple of 4 and at most 4096 (else CAF_GPU_EINVAL, as when the encoder is
- * unavailable).
- * Nothing is copied through the maps. */
-int caf_gpu_debug_gemm_tmaps(caf_gpu_runtime *rt, const void *A, const void *B, uint32_t n, uint8_t *device_built,
-                             uint8_t *host_encoded);
-
 /* Measured throughput, on the current device, of the 32-bit multiplies the
  * factorization test is built from (the test is two low multiplies and one
  * high multiply per (n, p) pair; Sec. 5's prime factorization, see

@@ -99,7 +99,7 @@ EXPORTS = [
     "caf_gpu_request_batch_device", "caf_gpu_sync", "caf_gpu_stream_sync", "caf_gpu_set_backend",
     "caf_gpu_reset_actors", "caf_gpu_actor_state", "caf_gpu_stats_read", "caf_gpu_read_log",
     "caf_gpu_stream", "caf_gpu_mark", "caf_gpu_prime_table", "caf_gpu_debug_wait_expiry", "caf_gpu_clear_error",
-    "caf_gpu_debug_gemm_tmaps", "caf_gpu_measure_mul_rates",
+    "caf_gpu_measure_mul_rates",
     "caf_gpu_graph_begin", "caf_gpu_graph_end", "caf_gpu_graph_launch", "caf_gpu_graph_destroy",
     "caf_gpu_serve_run", "caf_gpu_factor_static", "caf_gpu_strerror",
 ]
@@ -139,7 +139,6 @@ def load(build: bool = True):
         "caf_gpu_read_log": [vp, vp, u32, P(u32)],
         "caf_gpu_prime_table": [vp, P(vp), P(u32)],
         "caf_gpu_debug_wait_expiry": [vp, u64],
-        "caf_gpu_debug_gemm_tmaps": [vp, vp, vp, u32, vp, vp],
         "caf_gpu_measure_mul_rates": [vp],
         "caf_gpu_clear_error": [vp],
         "caf_gpu_mark": [vp],
@@ -353,13 +352,6 @@ class Runtime:
 
     def debug_wait_expiry(self, limit_ns: int) -> int:
         return self.L.caf_gpu_debug_wait_expiry(self.h, limit_ns)
-
-    def debug_gemm_tmaps(self, A: int, B: int, n: int):
-        """(device-built, host-encoded) tensor maps of A and B, 256 bytes each."""
-        dev = (ctypes.c_uint8 * 256)()
-        host = (ctypes.c_uint8 * 256)()
-        _check(self.L.caf_gpu_debug_gemm_tmaps(self.h, A, B, n, dev, host), "caf_gpu_debug_gemm_tmaps")
-        return bytes(dev), bytes(host)
 
     def clear_error(self):
         _check(self.L.caf_gpu_clear_error(self.h), "caf_gpu_clear_error")

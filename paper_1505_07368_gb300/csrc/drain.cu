@@ -25,7 +25,7 @@
 
 #include "common.cuh"
 #include "factor.cuh"
-#include "gemm_tc.cuh"
+#include "gemm_packed.cuh"
 #include "layout.h"
 
 namespace cafgpu {
@@ -307,6 +307,7 @@ __device__ void group_produce(const DrainParams &P, GroupShared &G, TableTile *r
 // streamed tiles.  A team of `wpb` warps shares one batch; member `r` tests
 // the chunks u of each tile with u % wpb == r, and members drop messages that
 // another member has already decided below their position.
+constexpr uint32_t kItemsPerRound = 4;   // GEMM work items a CTA takes per round
 constexpr uint32_t kSweepPrimes = 4;   // chunks (primes per lane) tested per step
 static_assert((kTile / 32) % (kSweepPrimes * kConsumerWarps) == 0, "a tile splits into steps for any team size");
 __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableTile *ring, uint32_t &t,
@@ -726,8 +727,20 @@ __device__ bool q_push_block(const DrainParams &P, QueueHdr *q, QCell *cells, ui
     return true;
 }
 
+// Job record j's queue and packed-operand scratch.
+__device__ __forceinline__ bool job_small(uint32_t j) { return j < kGemmJobsSmall; }
+__device__ __forceinline__ uint8_t *job_scratch(const DrainParams &P, uint32_t j) {
+    return job_small(j) ? P.pack_small + (size_t)j * kPackSmallBytes
+                        : P.pack_large + (size_t)(j - kGemmJobsSmall) * kPackLargeBytes;
+}
+__device__ __forceinline__ bool job_free(const DrainParams &P, uint32_t j) {
+    return job_small(j) ? q_push(&P.ctl->jobq, P.jobq, j, P.wait_limit_ns)
+                        : q_push(&P.ctl->jobq_large, P.jobq_large, j, P.wait_limit_ns);
+}
+
 // Claim a GEMM actor: take up to 32 messages (as many as there are free job
-// records), turn each into a job and queue its output tiles in job order.
+// records of the size class each needs), turn each into a job and queue its
+// pack items (two per 128-wide panel: one of A, one of B^T).
 __device__ __noinline__ void claim_gemm(const DrainParams &P, uint32_t a) {
     const uint32_t lane = lane_id();
     DevCtl *ctl = P.ctl;
@@ -741,48 +754,52 @@ __device__ __noinline__ void claim_gemm(const DrainParams &P, uint32_t a) {
     uint32_t want = avail < 32 ? (uint32_t)avail : 32u;
     if (P.max_claim && P.max_claim < want) want = P.max_claim;
     if (lane == 0) add_u64(&ctl->claims, 1);
-    // reserve job records first, so a claim never waits for one
+    // read each message's descriptor in place (published slots only), then
+    // reserve a job record of its class, so a claim never waits for one
+    const uint64_t t = head + lane;
+    const Slot *sl = &P.slots[A->slot_base + (t & A->cap_mask)];
+    const bool pub = lane < want && ld_acquire_gpu(&sl->seq) == t + 1;
+    const uint32_t pm = __ballot_sync(FULL, pub);
+    const uint32_t npub = (pm == FULL) ? 32u : (uint32_t)(__ffs(~pm) - 1);
+    const GemmDesc *d = lane < npub ? reinterpret_cast<const GemmDesc *>(sl->payload) : nullptr;
+    const uint32_t n = d ? d->n : 0u;
+    const bool valid = d && n > 0 && n <= kMaxDrainGemmN && d->A && d->B && d->C;
     uint32_t j = kNone;
-    const int pr = lane < want ? q_try_pop(&ctl->jobq, P.jobq, &j, P.wait_limit_ns) : 0;
-    if (pr < 0) fail(P, kErrWaitQueue, 21);
-    bool got = pr > 0;
-    const uint32_t gm = __ballot_sync(FULL, got);
-    const uint32_t nj = (gm == FULL) ? 32u : (uint32_t)(__ffs(~gm) - 1);
+    bool got = false;
+    if (valid) {
+        const int pr = n <= kPackSmallMaxN ? q_try_pop(&ctl->jobq, P.jobq, &j, P.wait_limit_ns)
+                                           : q_try_pop(&ctl->jobq_large, P.jobq_large, &j, P.wait_limit_ns);
+        if (pr < 0) fail(P, kErrWaitQueue, 21);
+        got = pr > 0;
+    }
+    const uint32_t okm = __ballot_sync(FULL, lane < npub && (!valid || got));
+    const uint32_t nj = (okm == FULL) ? 32u : (uint32_t)(__ffs(~okm) - 1);
     MsgData m{};
     const uint32_t take = nj ? warp_dequeue(P, a, head, nj, m) : 0u;
     if (got && lane >= take) {
-        q_push(&ctl->jobq, P.jobq, j, P.wait_limit_ns);
+        job_free(P, j);
         got = false;
     }
     release_actor(P, a, head + take);
-    bool valid = false;
-    uint32_t tiles = 0;
+    uint32_t panels = 0;
     if (lane < take) {
-        const GemmDesc *d = reinterpret_cast<const GemmDesc *>(m.payload);
-        const uint32_t n = d ? d->n : 0u;
-        if (d && n > 0 && n <= kMaxDrainGemmN && d->A && d->B && d->C) {
-            const uint32_t t = (n + kGemmBN - 1) / kGemmBN;
+        if (valid) {
+            const uint32_t tt = (n + kGemmBN - 1) / kGemmBN;
             GemmJob *J = &P.jobs[j];
             J->A = d->A;
             J->B = d->B;
             J->C = d->C;
             J->n = n;
             J->split = split;
-            J->tiles = t * t;
+            J->tiles = tt * tt;
             J->done = 0;
+            J->packs_left = 2 * tt;
             J->reply_addr = m.reply_addr;
             J->reply_token = m.reply_token;
-            // operands staged by tensor copies when the rows are 16-byte aligned
-            J->tma = 0;
-            if (P.gemm_tmpl && (n & 3u) == 0 && ((d->A | d->B) & 15u) == 0) {
-                gemm_build_tmaps(J->tmap_a, J->tmap_b, P.gemm_tmpl + 256u * (n / 4u - 1u), d->A, d->B);
-                J->tma = 1;
-            }
-            tiles = t * t;
-            valid = true;
+            J->pack = reinterpret_cast<uint64_t>(job_scratch(P, j));
+            panels = tt;
         } else {
             write_reply(m.reply_addr, 3, 0, n, m.tag, m.reply_token);
-            q_push(&ctl->jobq, P.jobq, j, P.wait_limit_ns);
         }
     }
     const uint32_t bad = __popc(__ballot_sync(FULL, lane < take && !valid));
@@ -792,10 +809,11 @@ __device__ __noinline__ void claim_gemm(const DrainParams &P, uint32_t a) {
     }
     __threadfence();
     for (uint32_t i = 0; i < take; ++i) {
-        const bool v = __shfl_sync(FULL, valid, i);
+        const uint32_t pi = __shfl_sync(FULL, panels, i);
         const uint32_t ji = __shfl_sync(FULL, j, i);
-        const uint32_t ti = __shfl_sync(FULL, tiles, i);
-        if (v && !q_push_block(P, &ctl->workq, P.workq, ji << 16, ti)) return;
+        if (!pi) continue;
+        if (!q_push_block(P, &ctl->packq, P.packq, (ji << 16) | kPackItemFlag, pi)) return;
+        if (!q_push_block(P, &ctl->packq, P.packq, (ji << 16) | kPackItemFlag | 64u, pi)) return;
     }
 }
 
@@ -804,19 +822,52 @@ struct NamedBarSync {
     __device__ __forceinline__ void operator()() const { named_bar_sync(1, nthreads); }
 };
 
-// Run GEMM tile `item` with the whole CTA; the CTA that finishes a job's last
-// tile writes its reply and frees the job record.
-__device__ __noinline__ void drain_gemm_tile(const DrainParams &P, GroupShared &G, GemmOps &ops, uint32_t item,
-                                GemmCounters &K, uint32_t bar_threads) {
-    const uint32_t j = item >> 16, tile = item & 0xFFFFu;
+// Run GEMM work item `item` with the whole CTA.  A pack item (flag
+// kPackItemFlag; bit 6: B instead of A; bits 0..5: panel) converts one panel;
+// the CTA that finishes a job's last pack item queues its tiles.  A tile item
+// computes one output tile; the CTA that finishes a job's last tile writes
+// its reply and frees the job record.
+__device__ __noinline__ void drain_gemm_item(const DrainParams &P, GroupShared &G, PackedSlots &slots, uint32_t item,
+                                             GemmCounters &K, uint32_t bar_threads) {
+    const uint32_t j = item >> 16, x = item & 0xFFFFu;
     GemmJob *J = &P.jobs[j];
     const uint32_t n = J->n;
-    const uint32_t tn_count = (n + kGemmBN - 1) / kGemmBN;
-    const bool tma = J->tma != 0;
-    const GemmArgs g{reinterpret_cast<const float *>(J->A), reinterpret_cast<const float *>(J->B),
-                     reinterpret_cast<float *>(J->C), tma ? J->tmap_a : nullptr, tma ? J->tmap_b : nullptr,
-                     n, tile / tn_count, tile % tn_count, J->split != 0, true};
-    const bool ok = gemm_tile(g, ops, G.gb, K, P.wait_limit_ns, NamedBarSync{bar_threads});
+    const bool split = J->split != 0;
+    const PackGeom g = pack_geom(reinterpret_cast<uint8_t *>(J->pack), n, split);
+    if (x & kPackItemFlag) {
+        const uint32_t panel = x & 63u;
+        if ((threadIdx.x >> 5) < kGemmConvWarps) {
+            const float *src = reinterpret_cast<const float *>((x & 64u) ? J->B : J->A);
+            // staged copies need 16-byte aligned rows
+            const bool staged = (n & 3u) == 0 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+            uint8_t *stage = reinterpret_cast<uint8_t *>(&slots);
+            if (x & 64u) {
+                if (staged) gemm_pack_b_staged(src, g, panel, split, stage);
+                else gemm_pack_b(src, g, panel, split);
+            } else {
+                if (staged) gemm_pack_a_staged(src, g, panel, split, stage);
+                else gemm_pack_a(src, g, panel, split);
+            }
+        }
+        named_bar_sync(1, bar_threads);
+        if (threadIdx.x < 32) {
+            uint32_t last = 0;
+            if (threadIdx.x == 0) {
+                heartbeat(P);
+                __threadfence();   // this CTA's packed stores before the count
+                last = atomicSub(reinterpret_cast<unsigned int *>(&J->packs_left), 1u) == 1u;
+            }
+            if (__shfl_sync(FULL, last, 0)) {
+                __threadfence();
+                if (!q_push_block(P, &P.ctl->workq, P.workq, j << 16, J->tiles) && threadIdx.x == 0)
+                    fail(P, kErrWaitQueue, 18);
+            }
+        }
+        return;
+    }
+    const uint32_t tn_count = g.t;
+    const bool ok = gemm_tile_packed(g, reinterpret_cast<float *>(J->C), x / tn_count, x % tn_count, split, slots,
+                                     G.gb, K, P.wait_limit_ns, NamedBarSync{bar_threads});
     if (threadIdx.x == 0) {
         if (!ok) fail(P, kErrGemm, 16, item, n);
         heartbeat(P);
@@ -828,7 +879,7 @@ __device__ __noinline__ void drain_gemm_tile(const DrainParams &P, GroupShared &
             __threadfence();
             add_u64(&P.ctl->messages, 1);
             add_u64(&P.ctl->completed, 1);
-            if (!q_push(&P.ctl->jobq, P.jobq, j, P.wait_limit_ns)) fail(P, kErrWaitQueue, 17);
+            if (!job_free(P, j)) fail(P, kErrWaitQueue, 17);
         }
     }
 }
@@ -923,7 +974,7 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
     uint8_t *base = drain_smem + ((1024u - (smem_u32(drain_smem) & 1023u)) & 1023u);
     GroupShared &G = *reinterpret_cast<GroupShared *>(base);
     TableTile *ring = reinterpret_cast<TableTile *>(base + kDrainHeader);
-    GemmOps &gops = *reinterpret_cast<GemmOps *>(base + kDrainHeader);
+    PackedSlots &gslots = *reinterpret_cast<PackedSlots *>(base + kDrainHeader);
     const uint32_t lane = lane_id();
     const uint32_t warp = threadIdx.x >> 5;
     const bool live0 = P.live && blockIdx.x == 0;
@@ -969,44 +1020,60 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
     uint64_t idle_start = 0;
     uint32_t idle_ns = 256;
     uint32_t held = kNone;                 // a team leader's claimed batch, kept across GEMM tiles
-    GemmCounters gk{0, 0, 0};
+    GemmCounters gk{0, 0, 0, 0};
     uint64_t seen_completed = 0, seen_at = 0;   // completion watchdog (producer lane)
+    uint32_t rounds = 0;
     const bool gemm_cta = kGemm && !live0;
     for (;;) {
         // ---- form a group: team leaders claim actors (skipped while the GEMM
         // tile queue already holds plenty of work for every CTA)
         if (!producer && team_ok && rank == 0 && held == kNone) {
             bool skip = false;
-            if (kGemm && lane == 0) skip = q_len(&ctl->workq) > 2 * (int64_t)gridDim.x;
+            if (kGemm && lane == 0) skip = q_len(&ctl->workq) + q_len(&ctl->packq) > 2 * (int64_t)gridDim.x;
             if (!__shfl_sync(FULL, skip, 0)) held = find_batch<kGemm>(P);
         }
         if (!producer && lane == 0) G.batch[ci] = (team_ok && rank == 0) ? held : kNone;
-        if (producer && lane == 0) {
-            G.exit = exit_requested(ctl) ? 1u : 0u;
+        if (producer) {
+            uint32_t ex = 0;
+            if (lane == 0) ex = exit_requested(ctl) ? 1u : 0u;
+            ex = __shfl_sync(FULL, ex, 0);
+            // up to kItemsPerRound GEMM items, popped in parallel by as many
+            // lanes (one pop's latency); tiles first, so a job's tiles run
+            // while its packed operands are still in L2
             uint32_t item = kNone;
-            if (gemm_cta && !G.exit) {
-                const int pr = q_try_pop(&ctl->workq, P.workq, &item, P.wait_limit_ns);
+            if (gemm_cta && !ex && lane < kItemsPerRound) {
+                int pr = q_try_pop(&ctl->workq, P.workq, &item, P.wait_limit_ns);
+                if (pr == 0) pr = q_try_pop(&ctl->packq, P.packq, &item, P.wait_limit_ns);
                 if (pr < 0) fail(P, kErrWaitQueue, 24);
                 if (pr <= 0) item = kNone;
             }
-            G.gemm_item = item;
-            // watchdog: busy warps can keep the heartbeat fresh without any
-            // message completing; give up if nothing completes for a long time
-            const uint64_t done_now = ld_relaxed_gpu(&ctl->completed);
-            const uint64_t tnow = globaltimer();
-            if (done_now != seen_completed || seen_at == 0 || quiescent(P)) {
-                seen_completed = done_now;
-                seen_at = tnow;
-            } else if (tnow > seen_at && tnow - seen_at > kCompletionLimitNs) {
-                fail(P, kErrNoCompletion, 20, done_now, ld_acquire_gpu(&ctl->ingested));
+            const uint32_t got = __ballot_sync(FULL, item != kNone);
+            if (item != kNone) G.items[__popc(got & ((1u << lane) - 1u))] = item;
+            if (lane == 0) {
+                G.exit = ex;
+                G.nitems = __popc(got);
+                // watchdog: busy warps can keep the heartbeat fresh without any
+                // message completing; give up if nothing completes for a long
+                // time (checked when idle, and every 64th round)
+                if (got == 0 || (++rounds & 63u) == 0) {
+                    const uint64_t done_now = ld_relaxed_gpu(&ctl->completed);
+                    const uint64_t tnow = globaltimer();
+                    if (done_now != seen_completed || seen_at == 0 || quiescent(P)) {
+                        seen_completed = done_now;
+                        seen_at = tnow;
+                    } else if (tnow > seen_at && tnow - seen_at > kCompletionLimitNs) {
+                        fail(P, kErrNoCompletion, 20, done_now, ld_acquire_gpu(&ctl->ingested));
+                    }
+                }
             }
         }
         named_bar_sync(1, bar_threads);
         if (G.exit) break;
         if constexpr (kGemm) {
-            if (G.gemm_item != kNone) {
-                // GEMM tiles first: short, and other CTAs may wait on the same job
-                drain_gemm_tile(P, G, gops, G.gemm_item, gk, bar_threads);
+            const uint32_t ni = G.nitems;
+            if (ni) {
+                // GEMM items first: short, and other CTAs may wait on the same job
+                for (uint32_t i = 0; i < ni; ++i) drain_gemm_item(P, G, gslots, G.items[i], gk, bar_threads);
                 idle = false;
                 idle_ns = 256;
                 continue;

@@ -27,9 +27,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     GemmSmem &S = gemm_smem(gemm_raw);
     const uint32_t tiles_n = (n + kGemmBN - 1) / kGemmBN;
     gemm_cta_init(S);
-    GemmCounters K{0, 0, 0};
+    GemmCounters K{0, 0, 0, 0};
     const GemmArgs g{A, B, C, use_tma ? &tma_a : nullptr, use_tma ? &tma_b : nullptr,
-                     n, blockIdx.x / tiles_n, blockIdx.x % tiles_n, split != 0, false};
+                     n, blockIdx.x / tiles_n, blockIdx.x % tiles_n, split != 0};
     const bool ok = gemm_tile(g, S.ops, S.bars, K, limit_ns, CtaSyncAll{});
     gemm_cta_exit(S);
     __shared__ uint32_t last;
@@ -46,12 +46,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         add_u64(&ctl->messages, 1);
         add_u64(&ctl->gemm_tiles, gridDim.x);
     }
-}
-
-// Device-side construction of the two tensor maps from the templates (the
-// drain's path), written to out[0..255] for comparison with the host encoder.
-__global__ void k_gemm_tmap_build(const uint8_t *tmpl, uint64_t A, uint64_t B, uint32_t n, uint8_t *out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) gemm_build_tmaps(out, out + 128, tmpl + 256u * (n / 4u - 1u), A, B);
 }
 
 namespace {
@@ -105,13 +99,6 @@ cudaError_t launch_gemm_one(const float *A, const float *B, float *C, uint32_t n
     const uint32_t t = (n + kGemmBN - 1) / kGemmBN;
     k_gemm_one<<<t * t, kGemmThreads, kGemmSmemBytes, stream>>>(ta, tb, tma ? 1u : 0u, A, B, C, n, split ? 1u : 0u,
                                                                 reply_addr, reply_token, scratch, limit_ns, ctl);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_gemm_tmap_build(const uint8_t *tmpl, const void *A, const void *B, uint32_t n, uint8_t *out,
-                                   cudaStream_t stream) {
-    k_gemm_tmap_build<<<1, 32, 0, stream>>>(tmpl, reinterpret_cast<uint64_t>(A), reinterpret_cast<uint64_t>(B), n,
-                                            out);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,318 @@
+// GEMM payload, packed form (the persistent drain's engine).
+//
+// The per-message engine (gemm_tc.cuh) rounds FP32 operands to BF16 inside
+// every output tile, so a 128-row panel of A is converted once per tile of
+// its row, t times for an n x n product with t = ceil(n / 128).  Here each
+// GEMM message first has its operands packed, once, by "pack" work items:
+//
+//   * a pack item converts one 128-row panel of A, or one 128-column panel
+//     of B (as rows of B^T), over all k, to BF16 hi (and lo = bf16(x - hi)
+//     for the split form), written in exactly the shared-memory image the
+//     tensor core reads: per 16-wide k block, a 128-row x 32-byte K-major
+//     plane with the 32-byte swizzle (4 KB), hi then lo.  Rows, columns and k
+//     past n are written as zeros, so any n works and tiles need no masks;
+//   * the CTA that finishes a message's last pack item queues its output
+//     tiles (no CTA ever waits for another);
+//   * a tile is then a TMA -> tensor-core loop: one thread streams the
+//     (panel, block) images of A and B^T into a ring of operand slots with
+//     bulk copies (cp.async.bulk), four k blocks per slot and two copies per
+//     slot (the blocks of a panel are contiguous), one thread issues
+//     tcgen05.mma per block (the same instructions as gemm_tc.cuh), and the
+//     converter warps only run the epilogue.  Waits and commits are per
+//     slot: an mbarrier wait costs hundreds of cycles even when the phase has
+//     completed, more than the MMAs of one block.
+//
+// Packed size per message: 2 t ceil(n/16) blocks of 4 KB (BF16) or 8 KB
+// (split), e.g. 8 MB for a split n = 1024 product.
+#pragma once
+
+#include "gemm_tc.cuh"
+
+namespace cafgpu {
+
+constexpr uint32_t kPackPlane = kGemmPlaneBytes;       // 4 KB: 128 rows x 16 k BF16
+constexpr uint32_t kPackItemFlag = 0x8000u;            // work item: pack (else tile)
+
+// Operand slots of a packed tile (the drain's GEMM shared-memory area): each
+// holds kPackSlotBlocks consecutive k blocks, the A panel's images first
+// (block b at b * blk), then B^T's (at kPackSlotBlocks * blk + b * blk).  A
+// block image is its hi plane and, for the split form, its lo plane.
+constexpr uint32_t kPackSlotBytes = 2 * kPackSlotBlocks * 2 * kGemmPlaneBytes;   // 64 KB
+struct PackedSlots {
+    uint8_t s[kPackSlots][kPackSlotBytes];
+};
+static_assert(sizeof(PackedSlots) <= kGemmOpsBytes, "packed slots fit the GEMM area");
+
+// Where a message's packed operands live.
+struct PackGeom {
+    uint8_t *a;      // A panels: block (panel p, k block kb) at a + (p * nkb + kb) * blk
+    uint8_t *b;      // B^T panels, same indexing
+    uint32_t n, t, nkb, blk;
+};
+
+__device__ __forceinline__ PackGeom pack_geom(uint8_t *base, uint32_t n, bool split) {
+    PackGeom g;
+    g.n = n;
+    g.t = (n + kGemmBM - 1) / kGemmBM;
+    g.nkb = (n + kGemmKB - 1) / kGemmKB;
+    g.blk = split ? 2 * kPackPlane : kPackPlane;
+    g.a = base;
+    g.b = base + (size_t)g.t * g.nkb * g.blk;
+    return g;
+}
+
+// Bytes a message of size n needs (host and device).
+__host__ __device__ constexpr uint64_t pack_bytes(uint32_t n, bool split) {
+    return 2ull * ((n + kGemmBM - 1) / kGemmBM) * ((n + kGemmKB - 1) / kGemmKB) * (split ? 2u : 1u) * kPackPlane;
+}
+
+// Pack panel p of A (rows 128p..128p+127), converter warps 0..7.  Warp w
+// owns rows 16w..16w+15; lane: row 16w + (lane & 15), 8-wide k chunk
+// lane >> 4 of each block.  Eight blocks per step keep eight 32-byte loads
+// per lane in flight.
+__device__ __forceinline__ void gemm_pack_a(const float *__restrict__ A, const PackGeom &g, uint32_t p,
+                                            bool split) {
+    const uint32_t w = threadIdx.x >> 5, lane = lane_id();
+    const uint32_t r = 16 * w + (lane & 15u), c = lane >> 4, gr = p * kGemmBM + r, n = g.n;
+    const bool vec = (n & 3u) == 0 && (reinterpret_cast<uintptr_t>(A) & 15u) == 0;
+    const float *row = A + (size_t)min(gr, n - 1) * n;
+    const uint32_t off = sw32_offset(r, c);
+    uint8_t *dst0 = g.a + (size_t)p * g.nkb * g.blk;
+    for (uint32_t kb0 = 0; kb0 < g.nkb; kb0 += 8) {
+        float x[8][8];
+#pragma unroll
+        for (uint32_t q = 0; q < 8; ++q) {
+            const uint32_t gk = (kb0 + q) * kGemmKB + 8 * c;
+            if (vec && gr < n && gk + 8 <= n) {
+                const float4 lo = __ldg(reinterpret_cast<const float4 *>(row + gk));
+                const float4 hi = __ldg(reinterpret_cast<const float4 *>(row + gk + 4));
+                x[q][0] = lo.x; x[q][1] = lo.y; x[q][2] = lo.z; x[q][3] = lo.w;
+                x[q][4] = hi.x; x[q][5] = hi.y; x[q][6] = hi.z; x[q][7] = hi.w;
+            } else {
+#pragma unroll
+                for (uint32_t e = 0; e < 8; ++e) x[q][e] = (gr < n && gk + e < n) ? __ldg(row + gk + e) : 0.0f;
+            }
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < 8; ++q) {
+            if (kb0 + q < g.nkb) {
+                uint8_t *d = dst0 + (size_t)(kb0 + q) * g.blk + off;
+                convert8(x[q], d, d + kPackPlane, split);
+            }
+        }
+    }
+}
+
+// Pack panel p of B^T (columns 128p..128p+127 of B), converter warps 0..7.
+// Warp w: 8-wide k chunk w & 1 of every block, columns 32(w >> 1) + lane; the
+// eight k rows of a chunk are eight coalesced 128-byte row reads per warp.
+__device__ __forceinline__ void gemm_pack_b(const float *__restrict__ B, const PackGeom &g, uint32_t p,
+                                            bool split) {
+    const uint32_t w = threadIdx.x >> 5, lane = lane_id();
+    const uint32_t c = w & 1u, cl = 32 * (w >> 1) + lane, gc = p * kGemmBN + cl, n = g.n;
+    const uint32_t off = sw32_offset(cl, c);
+    const float *col = B + min(gc, n - 1);
+    uint8_t *dst0 = g.b + (size_t)p * g.nkb * g.blk;
+    for (uint32_t kb0 = 0; kb0 < g.nkb; kb0 += 4) {
+        float x[4][8];
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q) {
+            const uint32_t gk = (kb0 + q) * kGemmKB + 8 * c;
+#pragma unroll
+            for (uint32_t j = 0; j < 8; ++j)
+                x[q][j] = (gc < n && gk + j < n) ? __ldg(col + (size_t)(gk + j) * n) : 0.0f;
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q) {
+            if (kb0 + q < g.nkb) {
+                uint8_t *d = dst0 + (size_t)(kb0 + q) * g.blk + off;
+                convert8(x[q], d, d + kPackPlane, split);
+            }
+        }
+    }
+}
+
+// ---- staged packing (16-byte aligned rows) ---------------------------------
+// cp.async copies (16 bytes per thread, zero-filled past `valid` bytes) into
+// a per-warp ring of kPackStages shared-memory stages, so a warp keeps
+// kPackStages - 1 slices of 64 k in flight while it converts one.  Each warp
+// loads only what it converts, so a __syncwarp orders the stage's reuse.
+constexpr uint32_t kPackStages = 5;
+constexpr uint32_t kPackApitch = 68;                 // floats per staged A row (conflict-free reads)
+constexpr uint32_t kPackWarpStage = 16 * kPackApitch * 4;   // >= 8 k rows x 128 floats of B
+static_assert(8 * 128 * 4 <= kPackWarpStage, "a B stage fits a warp's stage");
+static_assert(kGemmConvWarps * kPackStages * kPackWarpStage <= kGemmOpsBytes, "pack stages fit the GEMM area");
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gsrc, uint32_t valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gsrc), "r"(valid)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_stages() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(kPackStages - 1) : "memory");
+}
+
+// A panel p, 16-byte aligned rows: warp w stages its rows 16w..16w+15 in
+// slices of 64 k (lane: row 2q + (lane >> 4), 16-byte chunk lane & 15).
+__device__ __forceinline__ void gemm_pack_a_staged(const float *__restrict__ A, const PackGeom &g, uint32_t p,
+                                                   bool split, uint8_t *stage_area) {
+    const uint32_t w = threadIdx.x >> 5, lane = lane_id(), n = g.n;
+    float *st = reinterpret_cast<float *>(stage_area + (size_t)w * kPackStages * kPackWarpStage);
+    const uint32_t nsl = (n + 63) / 64;
+    auto issue = [&](uint32_t sl) {
+        if (sl < nsl) {
+            float *buf = st + (sl % kPackStages) * (kPackWarpStage / 4);
+#pragma unroll
+            for (uint32_t q = 0; q < 8; ++q) {
+                const uint32_t rr = 2 * q + (lane >> 4), ch = lane & 15u;
+                const uint32_t gr = p * kGemmBM + 16 * w + rr, gk = sl * 64 + 4 * ch;
+                const uint32_t valid = (gr < n && gk < n) ? min(16u, (n - gk) * 4) : 0u;
+                const float *src = valid ? A + (size_t)gr * n + gk : A;
+                cp_async16(buf + rr * kPackApitch + 4 * ch, src, valid);
+            }
+        }
+        cp_async_commit();
+    };
+    for (uint32_t sl = 0; sl + 1 < kPackStages; ++sl) issue(sl);
+    const uint32_t r = 16 * w + (lane & 15u), c = lane >> 4, rl = lane & 15u;
+    const uint32_t off = sw32_offset(r, c);
+    uint8_t *dst0 = g.a + (size_t)p * g.nkb * g.blk;
+    for (uint32_t sl = 0; sl < nsl; ++sl) {
+        issue(sl + kPackStages - 1);
+        cp_async_wait_stages();
+        __syncwarp();
+        const float *buf = st + (sl % kPackStages) * (kPackWarpStage / 4) + rl * kPackApitch;
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) {
+            const uint32_t kb = 4 * sl + j;
+            if (kb < g.nkb) {
+                const float4 lo = *reinterpret_cast<const float4 *>(buf + 16 * j + 8 * c);
+                const float4 hi = *reinterpret_cast<const float4 *>(buf + 16 * j + 8 * c + 4);
+                const float x[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+                uint8_t *d = dst0 + (size_t)kb * g.blk + off;
+                convert8(x, d, d + kPackPlane, split);
+            }
+        }
+        __syncwarp();
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// B^T panel p, 16-byte aligned rows: warp w stages k rows 8w..8w+7 of each
+// 64-k slice (128 columns, lane: row q, 16-byte chunk lane) and converts them
+// as chunk w & 1 of block w >> 1 of the slice for columns lane + 32i.
+__device__ __forceinline__ void gemm_pack_b_staged(const float *__restrict__ B, const PackGeom &g, uint32_t p,
+                                                   bool split, uint8_t *stage_area) {
+    const uint32_t w = threadIdx.x >> 5, lane = lane_id(), n = g.n;
+    float *st = reinterpret_cast<float *>(stage_area + (size_t)w * kPackStages * kPackWarpStage);
+    const uint32_t nsl = (n + 63) / 64;
+    auto issue = [&](uint32_t sl) {
+        if (sl < nsl) {
+            float *buf = st + (sl % kPackStages) * (kPackWarpStage / 4);
+#pragma unroll
+            for (uint32_t q = 0; q < 8; ++q) {
+                const uint32_t gk = sl * 64 + 8 * w + q, gc = p * kGemmBN + 4 * lane;
+                const uint32_t valid = (gk < n && gc < n) ? min(16u, (n - gc) * 4) : 0u;
+                const float *src = valid ? B + (size_t)gk * n + gc : B;
+                cp_async16(buf + q * 128 + 4 * lane, src, valid);
+            }
+        }
+        cp_async_commit();
+    };
+    for (uint32_t sl = 0; sl + 1 < kPackStages; ++sl) issue(sl);
+    const uint32_t c = w & 1u, jb = w >> 1;
+    uint8_t *dst0 = g.b + (size_t)p * g.nkb * g.blk;
+    for (uint32_t sl = 0; sl < nsl; ++sl) {
+        issue(sl + kPackStages - 1);
+        cp_async_wait_stages();
+        __syncwarp();
+        const float *buf = st + (sl % kPackStages) * (kPackWarpStage / 4);
+        const uint32_t kb = 4 * sl + jb;
+        if (kb < g.nkb) {
+#pragma unroll
+            for (uint32_t i = 0; i < 4; ++i) {
+                const uint32_t col = lane + 32 * i;
+                float x[8];
+#pragma unroll
+                for (uint32_t q = 0; q < 8; ++q) x[q] = buf[q * 128 + col];
+                uint8_t *d = dst0 + (size_t)kb * g.blk + sw32_offset(col, c);
+                convert8(x, d, d + kPackPlane, split);
+            }
+        }
+        __syncwarp();
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Compute output tile (tm, tn) of a packed message with the whole CTA:
+// converter warp 0's lane 0 streams the k blocks' images of A panel tm and
+// B^T panel tn into the slot ring (two bulk copies per block), warp
+// kGemmConvWarps's lane 0 issues the MMAs, and warps 0..7 run the epilogue.
+// `K.pk_uses` carries the slot phases across tiles.  Returns false if a
+// bounded wait expired.
+template <class CtaSync>
+__device__ bool gemm_tile_packed(const PackGeom &g, float *__restrict__ C, uint32_t tm, uint32_t tn, bool split,
+                                 PackedSlots &S, GemmBars &Bb, GemmCounters &K, uint64_t limit_ns,
+                                 CtaSync cta_sync) {
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    const uint32_t nb = g.nkb, ns = (nb + kPackSlotBlocks - 1) / kPackSlotBlocks;
+    bool ok = true;
+    if (warp == 0 && lane == 0) {
+        // the images were written with ordinary stores by the CTAs that ran
+        // the pack items (ordered before this tile by the work queue); make
+        // them visible to the bulk copies
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        // a pack item may have used the slot area through ordinary accesses
+        // (ordered before this point by the CTA barrier between items)
+        fence_proxy_async_smem();
+        const uint8_t *ab = g.a + (size_t)tm * nb * g.blk, *bb = g.b + (size_t)tn * nb * g.blk;
+        uint32_t i = 0;
+        for (; i < ns; ++i) {
+            const uint32_t u = K.pk_uses + i, s = u % kPackSlots;
+            if (u >= kPackSlots) {
+                ok = gemm_wait(&Bb.pk_empty[s], (u / kPackSlots - 1u) & 1u, limit_ns);
+                if (!ok) break;
+            }
+            const uint32_t k0 = i * kPackSlotBlocks, kn = min(kPackSlotBlocks, nb - k0);
+            mbar_arrive_expect_tx(&Bb.pk_full[s], 2 * kn * g.blk);
+            bulk_g2s(S.s[s], ab + (size_t)k0 * g.blk, kn * g.blk, &Bb.pk_full[s]);
+            bulk_g2s(S.s[s] + kPackSlotBlocks * g.blk, bb + (size_t)k0 * g.blk, kn * g.blk, &Bb.pk_full[s]);
+        }
+        // after an expired wait, let the copies in flight land (bounded)
+        for (uint32_t q = (i > kPackSlots ? i - kPackSlots : 0); !ok && q < i; ++q) {
+            const uint32_t u = K.pk_uses + q;
+            gemm_wait(&Bb.pk_full[u % kPackSlots], (u / kPackSlots) & 1u, limit_ns);
+        }
+    } else if (warp == kGemmConvWarps && lane == 0) {
+        for (uint32_t i = 0; i < ns && ok; ++i) {
+            const uint32_t u = K.pk_uses + i, s = u % kPackSlots;
+            ok = gemm_wait(&Bb.pk_full[s], (u / kPackSlots) & 1u, limit_ns);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t kn = min(kPackSlotBlocks, nb - i * kPackSlotBlocks);
+            const uint8_t *sa = S.s[s], *sb = S.s[s] + kPackSlotBlocks * g.blk;
+            for (uint32_t b = 0; b < kn; ++b)
+                gemm_mma_planes(sa + b * g.blk, sa + b * g.blk + kPackPlane, sb + b * g.blk, Bb.tmem, split,
+                                i == 0 && b == 0);
+            tc_commit(&Bb.pk_empty[s]);
+        }
+        tc_commit(&Bb.done);
+    }
+    if (warp == 0 || warp == kGemmConvWarps) __syncwarp();
+    K.pk_uses += ns;
+    if (warp < kGemmConvWarps) ok = gemm_epilogue(C, g.n, tm, tn, split, Bb, K.tiles, ok, limit_ns);
+    ++K.tiles;
+    // the next tile's MMAs overwrite the accumulators: every epilogue read
+    // must be complete first
+    tc_fence_before();
+    cta_sync();
+    tc_fence_after();
+    return ok;
+}
+
+}  // namespace cafgpu
+
+namespace cafgpu {
+static_assert(pack_bytes(kPackSmallMaxN, true) == kPackSmallBytes, "small scratch class holds n <= kPackSmallMaxN");
+static_assert(pack_bytes(kMaxDrainGemmN, true) == kPackLargeBytes, "large scratch class holds n <= kMaxDrainGemmN");
+}  // namespace cafgpu

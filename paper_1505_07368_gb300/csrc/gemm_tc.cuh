@@ -77,16 +77,14 @@ struct GemmSmem {
     GemmBars bars;
 };
 
-// One output tile's operands.  tmap_a / tmap_b: tensor maps of A and B (in
-// global or kernel-parameter memory), or null for the direct path.
-// tmap_fence: the maps were written by device code and need a tensormap-proxy
-// acquire before use.
+// One output tile's operands.  tmap_a / tmap_b: tensor maps of A and B
+// (kernel-parameter memory), or null for the direct path.
 struct GemmArgs {
     const float *A, *B;
     float *C;
     const void *tmap_a, *tmap_b;
     uint32_t n, tm, tn;
-    bool split, tmap_fence;
+    bool split;
 };
 
 // Barrier phases of one CTA across the tiles it computes.
@@ -94,6 +92,7 @@ struct GemmCounters {
     uint32_t f32_uses;   // slices staged so far (stage = use % kGemmF32Stages)
     uint32_t bf_uses;    // BF16 blocks converted so far (slot = use % kGemmBfSlots)
     uint32_t tiles;      // tiles finished (done barrier phase)
+    uint32_t pk_uses;    // packed k blocks streamed so far (slot = use % kPackSlots)
 };
 
 // ---- tensor copies ------------------------------------------------------
@@ -105,35 +104,6 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int32_t
         "[%4];" ::"r"(smem_u32(dst)),
         "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
-}
-// Make a tensor map written through the generic proxy visible to this
-// thread's tensor copies.
-__device__ __forceinline__ void tmap_acquire(const void *tmap) {
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
-}
-
-// Tensor maps of A and B, built on the device by copying the host-encoded
-// pair for this n (the encoder's output depends on n in ways tensormap.replace
-// does not reproduce -- it marks maps of tensors above 128 KiB -- so there is
-// one template pair per n) and pointing it at the operands.  One thread;
-// ma, mb: global memory, 128-byte aligned.
-__device__ __forceinline__ void tmap_set_address(uint8_t *map, uint64_t base) {
-    const uint64_t m = reinterpret_cast<uint64_t>(map);
-    asm volatile("tensormap.replace.tile.global_address.global.b1024.b64 [%0], %1;" ::"l"(m), "l"(base) : "memory");
-}
-__device__ __forceinline__ void gemm_build_tmaps(uint8_t *ma, uint8_t *mb, const uint8_t *pair, uint64_t A,
-                                                 uint64_t B) {
-    const uint4 *t = reinterpret_cast<const uint4 *>(pair);
-    uint4 *da = reinterpret_cast<uint4 *>(ma);
-    uint4 *db = reinterpret_cast<uint4 *>(mb);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        da[i] = t[i];
-        db[i] = t[8 + i];
-    }
-    tmap_set_address(ma, A);
-    tmap_set_address(mb, B);
-    asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
 }
 
 // ---- tcgen05 wrappers -------------------------------------------------------
@@ -322,6 +292,10 @@ __device__ __forceinline__ void gemm_bars_init(GemmBars &Bb) {
             mbar_init(&Bb.bf_full[s], kGemmConvWarps);
             mbar_init(&Bb.bf_empty[s], 1);
         }
+        for (uint32_t s = 0; s < kPackSlots; ++s) {
+            mbar_init(&Bb.pk_full[s], 1);
+            mbar_init(&Bb.pk_empty[s], 1);
+        }
         mbar_init(&Bb.done, 1);
         fence_barrier_init();
     }
@@ -399,6 +373,70 @@ __device__ __forceinline__ bool gemm_convert_slice(const GemmArgs &g, const Gemm
     return true;
 }
 
+// Epilogue of a tile, converter warps 0..7: wait for the last MMA (done
+// barrier, phase `tiles`), read the accumulators (warp w: TMEM lanes
+// 32*(w%4).., columns 64*(w/4)..; the split form adds columns 128.. to them)
+// and store the tile of C, masked at the matrix edge.  Returns false if the
+// wait expired or `ok` was already false.
+__device__ __forceinline__ bool gemm_epilogue(float *__restrict__ C, uint32_t n, uint32_t tm, uint32_t tn,
+                                              bool split, GemmBars &Bb, uint32_t tiles, bool ok,
+                                              uint64_t limit_ns) {
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    bool dok = ok && gemm_wait(&Bb.done, tiles & 1u, limit_ns);
+    dok = __all_sync(0xFFFFFFFFu, dok);
+    if (!dok) return false;
+    tc_fence_after();
+    const uint32_t row0 = (warp & 3u) * 32u, col0 = (warp >> 2) * 64u;
+    const uint32_t gr = tm * kGemmBM + row0 + lane;
+#pragma unroll
+    for (uint32_t cc = 0; cc < 64; cc += 32) {
+        uint32_t r[32];
+        tmem_ld_32x32(Bb.tmem + (row0 << 16) + col0 + cc, r);
+        if (split) {
+            uint32_t r2[32];
+            tmem_ld_32x32(Bb.tmem + (row0 << 16) + kGemmBN + col0 + cc, r2);
+#pragma unroll
+            for (uint32_t j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(r2[j]));
+        }
+        if (gr < n) {
+            float *crow = C + (size_t)gr * n;
+            const uint32_t gc0 = tn * kGemmBN + col0 + cc;
+            if (gc0 + 32 <= n && (reinterpret_cast<uintptr_t>(crow + gc0) & 15u) == 0) {
+#pragma unroll
+                for (uint32_t j = 0; j < 32; j += 4)
+                    *reinterpret_cast<float4 *>(crow + gc0 + j) =
+                        make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                    __uint_as_float(r[j + 3]));
+            } else {
+#pragma unroll
+                for (uint32_t j = 0; j < 32; ++j)
+                    if (gc0 + j < n) crow[gc0 + j] = __uint_as_float(r[j]);
+            }
+        }
+    }
+    return true;
+}
+
+// Issue the MMAs of one 16-wide k block held in `sl` (one thread).  BF16:
+// hi(A) hi(B)^T, N = 128.  Split: hi(A) [hi(B); lo(B)]^T as one N = 256
+// product (columns 0..255), then lo(A) hi(B)^T into columns 128..255.
+// `first`: the tile's first block (overwrite instead of accumulate).
+// a_hi, a_lo, b_hi: the block's planes; b_lo must follow b_hi directly.
+__device__ __forceinline__ void gemm_mma_planes(const void *a_hi, const void *a_lo, const void *b_hi, uint32_t tmem,
+                                                bool split, bool first) {
+    const uint32_t id128 = gemm_idesc(kGemmBM, kGemmBN), id256 = gemm_idesc(kGemmBM, 2 * kGemmBN);
+    const uint64_t ah = smem_desc_sw32(a_hi), bh = smem_desc_sw32(b_hi);
+    if (split) {
+        tc_mma_f16(tmem, ah, bh, id256, first ? 0u : 1u);
+        tc_mma_f16(tmem + kGemmBN, smem_desc_sw32(a_lo), bh, id128, 1u);
+    } else {
+        tc_mma_f16(tmem, ah, bh, id128, first ? 0u : 1u);
+    }
+}
+__device__ __forceinline__ void gemm_mma_block(GemmBfSlot &sl, uint32_t tmem, bool split, bool first) {
+    gemm_mma_planes(sl.a_hi, sl.a_lo, sl.b_hi, tmem, split, first);
+}
+
 // Compute one output tile of C = A * B with the whole CTA (converter warps
 // 0..7 and the MMA warp kGemmConvWarps).  `K` carries the barrier phases
 // across the tiles this CTA computes.  Returns false if a bounded wait
@@ -413,11 +451,6 @@ __device__ bool gemm_tile(const GemmArgs &g, GemmOps &O, GemmBars &Bb, GemmCount
     if (warp < kGemmConvWarps) {
         const uint32_t w = warp;
         if (staged && lane == 0) {
-            // any converter warp may issue a refill
-            if (g.tmap_fence) {
-                tmap_acquire(g.tmap_a);
-                tmap_acquire(g.tmap_b);
-            }
             if (w == 0)
                 for (uint32_t kb = 0; kb < kGemmF32Stages && kb < nk; ++kb) {
                     const uint32_t st = (K.f32_uses + kb) % kGemmF32Stages;
@@ -454,21 +487,13 @@ __device__ bool gemm_tile(const GemmArgs &g, GemmOps &O, GemmBars &Bb, GemmCount
             gemm_wait(&Bb.f32_full[fu % kGemmF32Stages], (fu / kGemmF32Stages) & 1u, limit_ns);
         }
     } else if (lane == 0) {
-        const uint32_t id128 = gemm_idesc(kGemmBM, kGemmBN), id256 = gemm_idesc(kGemmBM, 2 * kGemmBN);
         const uint32_t nb = nk * kGemmBlocks;
         for (uint32_t i = 0; i < nb && ok; ++i) {
             const uint32_t u = K.bf_uses + i, s = u % kGemmBfSlots;
             ok = gemm_wait(&Bb.bf_full[s], (u / kGemmBfSlots) & 1u, limit_ns);
             if (!ok) break;
             tc_fence_after();
-            GemmBfSlot &sl = O.bf[s];
-            const uint64_t ah = smem_desc_sw32(sl.a_hi), bh = smem_desc_sw32(sl.b_hi);
-            if (g.split) {
-                tc_mma_f16(Bb.tmem, ah, bh, id256, i != 0);   // hi*hi -> cols 0..127, hi*lo -> 128..255
-                tc_mma_f16(Bb.tmem + kGemmBN, smem_desc_sw32(sl.a_lo), bh, id128, 1u);   // lo*hi -> 128..255
-            } else {
-                tc_mma_f16(Bb.tmem, ah, bh, id128, i != 0);
-            }
+            gemm_mma_block(O.bf[s], Bb.tmem, g.split, i == 0);
             tc_commit(&Bb.bf_empty[s]);
         }
         tc_commit(&Bb.done);
@@ -476,45 +501,7 @@ __device__ bool gemm_tile(const GemmArgs &g, GemmOps &O, GemmBars &Bb, GemmCount
     if (warp == kGemmConvWarps) __syncwarp();
     K.f32_uses += staged ? nk : 0;
     K.bf_uses += nk * kGemmBlocks;
-    // epilogue: converter warps read the accumulators (warp w: TMEM lanes
-    // 32*(w%4).., columns 64*(w/4)..) and store the tile
-    if (warp < kGemmConvWarps) {
-        bool dok = ok && gemm_wait(&Bb.done, K.tiles & 1u, limit_ns);
-        dok = __all_sync(0xFFFFFFFFu, dok);
-        if (dok) {
-            tc_fence_after();
-            const uint32_t row0 = (warp & 3u) * 32u, col0 = (warp >> 2) * 64u;
-            const uint32_t gr = g.tm * kGemmBM + row0 + lane;
-#pragma unroll
-            for (uint32_t cc = 0; cc < 64; cc += 32) {
-                uint32_t r[32];
-                tmem_ld_32x32(Bb.tmem + (row0 << 16) + col0 + cc, r);
-                if (g.split) {
-                    uint32_t r2[32];
-                    tmem_ld_32x32(Bb.tmem + (row0 << 16) + kGemmBN + col0 + cc, r2);
-#pragma unroll
-                    for (uint32_t j = 0; j < 32; ++j)
-                        r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(r2[j]));
-                }
-                if (gr < n) {
-                    float *crow = g.C + (size_t)gr * n;
-                    const uint32_t gc0 = g.tn * kGemmBN + col0 + cc;
-                    if (gc0 + 32 <= n && (reinterpret_cast<uintptr_t>(crow + gc0) & 15u) == 0) {
-#pragma unroll
-                        for (uint32_t j = 0; j < 32; j += 4)
-                            *reinterpret_cast<float4 *>(crow + gc0 + j) =
-                                make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                            __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-                    } else {
-#pragma unroll
-                        for (uint32_t j = 0; j < 32; ++j)
-                            if (gc0 + j < n) crow[gc0 + j] = __uint_as_float(r[j]);
-                    }
-                }
-            }
-        }
-        ok = ok && dok;
-    }
+    if (warp < kGemmConvWarps) ok = gemm_epilogue(g.C, n, g.tm, g.tn, g.split, Bb, K.tiles, ok, limit_ns);
     ++K.tiles;
     // the next tile's MMAs overwrite the accumulators: every epilogue read
     // must be complete first

@@ -33,10 +33,6 @@ cudaError_t launch_gemm_one(const float *A, const float *B, float *C, uint32_t n
 int gemm_encode_tmap(void *out128, const void *base, uint32_t n, bool is_a);
 // A and B can be staged through tensor maps (n % 4 == 0, 16-byte aligned).
 bool gemm_tma_ok(const void *A, const void *B, uint32_t n);
-// Build both maps on the device from the template pairs at tmpl (the
-// drain's construction; pair for n at 256 * (n / 4 - 1)) into out[0..255].
-cudaError_t launch_gemm_tmap_build(const uint8_t *tmpl, const void *A, const void *B, uint32_t n, uint8_t *out,
-                                   cudaStream_t stream);
 cudaError_t launch_debug_wait(const uint32_t *flag, uint64_t limit_ns, DevCtl *ctl, HostCtl *hctl,
                               cudaStream_t stream);
 // Prime table of the odd primes <= limit.  Allocates *primes/*pinv/*plim

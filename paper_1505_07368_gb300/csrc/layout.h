@@ -47,12 +47,16 @@ constexpr uint32_t kGemmF32Stages = 2;
 constexpr uint32_t kGemmBfSlots = 6;
 constexpr uint32_t kGemmStageBytes = 2u * 128u * 32u * 4u + 64u * 128u * 4u;   // A halves + B: 64 KB
 constexpr uint32_t kGemmSlotBytes = 4u * 128u * 16u * 2u;                      // 4 BF16 planes: 16 KB
+constexpr uint32_t kPackSlots = 3;         // operand slots of the packed tile loop (drain)
+constexpr uint32_t kPackSlotBlocks = 4;    // 16-wide k blocks per packed slot
 
 // Barriers and tensor-memory address of the GEMM tile engine.
 struct GemmBars {
     uint64_t f32_full[kGemmF32Stages];     // tensor copies of a staged slice landed
     uint64_t bf_full[kGemmBfSlots];        // converters -> MMA thread (BF16 block ready)
     uint64_t bf_empty[kGemmBfSlots];       // MMA completion -> converters (slot free again)
+    uint64_t pk_full[kPackSlots];          // packed tiles: slot's bulk copies landed
+    uint64_t pk_empty[kPackSlots];         // packed tiles: slot's MMAs completed
     uint64_t done;                         // last MMA of a tile completed -> epilogue
     uint32_t f32_read[kGemmF32Stages];     // converter warps done with a stage (monotonic count)
     uint32_t tmem;                         // accumulator address from tcgen05.alloc
@@ -72,7 +76,8 @@ struct GroupShared {
     uint32_t final_tile;           // tile index at which the group's stream ends
     uint32_t active;               // consumer warps still holding messages
     uint32_t exit;
-    uint32_t gemm_item;            // GEMM tile this CTA runs next (kNone: none)
+    uint32_t items[4];             // GEMM work items this CTA runs next
+    uint32_t nitems;
 };
 constexpr uint32_t kDrainHeader = 1024;
 static_assert(sizeof(GroupShared) <= kDrainHeader, "drain header fits");
@@ -85,7 +90,7 @@ constexpr uint32_t kDrainSmemMixed = 1024 + kDrainHeader + (kGemmOpsBytes > kTab
 
 // A GEMM message being computed by the drain: its 128 x 128 output tiles are
 // items (job << 16 | tile) in the tile queue.
-struct alignas(128) GemmJob {
+struct alignas(64) GemmJob {
     uint64_t A, B, C;
     uint32_t n;
     uint32_t split;
@@ -93,15 +98,20 @@ struct alignas(128) GemmJob {
     uint32_t done;                 // tiles finished (atomic)
     uint64_t reply_addr;
     uint32_t reply_token;
-    uint32_t tma;                  // 1: the tensor maps below describe A and B
-    uint32_t pad[18];
-    alignas(128) uint8_t tmap_a[128];   // CUtensorMap of A (n x n FP32, box 32 k x 128 rows, 128-byte swizzle)
-    alignas(128) uint8_t tmap_b[128];   // CUtensorMap of B (n x n FP32, box 128 columns x 64 k, no swizzle)
+    uint32_t packs_left;           // pack items not finished (atomic); the last one queues the tiles
+    uint64_t pack;                 // the record's packed-operand scratch (device)
 };
-static_assert(sizeof(GemmJob) == 384 && offsetof(GemmJob, tmap_a) == 128 && offsetof(GemmJob, tmap_b) == 256,
-              "GemmJob layout");
+static_assert(sizeof(GemmJob) == 64, "GemmJob is 64 bytes");
 constexpr uint32_t kMaxDrainGemmN = 4096;   // <= 1024 tiles per job
-constexpr uint32_t kGemmJobs = 1024;         // GEMM messages in flight in the drain
+// Job records come in two scratch classes: packed operands of a split n x n
+// product take 2 ceil(n/128) ceil(n/16) x 8 KB (gemm_packed.cuh), 8 MB for
+// n <= 1024 and 128 MB for n <= 4096.
+constexpr uint32_t kPackSmallMaxN = 1024;
+constexpr uint32_t kGemmJobsSmall = 256;
+constexpr uint32_t kGemmJobsLarge = 16;
+constexpr uint32_t kGemmJobs = kGemmJobsSmall + kGemmJobsLarge;   // GEMM messages in flight in the drain
+constexpr uint64_t kPackSmallBytes = 2ull * 8 * 64 * 8192;       // 8 MB
+constexpr uint64_t kPackLargeBytes = 2ull * 32 * 256 * 8192;     // 128 MB
 
 // Operand descriptor referenced by a GEMM message (same layout as caf_gpu_gemm_desc).
 struct GemmDesc {
@@ -261,8 +271,10 @@ struct DevCtl {
     uint64_t pad3[5];
     QueueHdr readyq;
     QueueHdr freeq;
-    QueueHdr workq;                // GEMM tile items
-    QueueHdr jobq;                 // free GemmJob records
+    QueueHdr workq;                // GEMM tile items (taken before pack items)
+    QueueHdr packq;                // GEMM pack items
+    QueueHdr jobq;                 // free GemmJob records, small scratch class
+    QueueHdr jobq_large;           // free GemmJob records, large scratch class
 };
 
 // Host-visible control block (pinned, mapped).
@@ -283,6 +295,7 @@ struct DrainParams {
     QCell *readyq;
     QCell *freeq;
     QCell *workq;
+    QCell *packq;
     FactorBatch *batches;
     const uint32_t *primes;
     const uint32_t *pinv;
@@ -310,7 +323,9 @@ struct DrainParams {
     // GEMM actors (gemm != 0: tensor memory and the GEMM shared-memory layout)
     GemmJob *jobs;
     QCell *jobq;
-    const uint8_t *gemm_tmpl;      // tensor-map templates: pair (A, B) for n = 4(i+1) at 256 i
+    QCell *jobq_large;
+    uint8_t *pack_small;           // kGemmJobsSmall x kPackSmallBytes (record j: j-th block)
+    uint8_t *pack_large;           // kGemmJobsLarge x kPackLargeBytes (record kGemmJobsSmall + i: i-th)
     uint32_t gemm;
     uint32_t pad1;
 };

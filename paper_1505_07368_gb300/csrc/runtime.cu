@@ -60,14 +60,14 @@ struct caf_gpu_runtime {
     ActorDesc *d_actors = nullptr;
     Slot *d_slots = nullptr;
     uint64_t n_slots = 0, slots_used = 0;
-    QCell *d_readyq = nullptr, *d_freeq = nullptr, *d_workq = nullptr;
+    QCell *d_readyq = nullptr, *d_freeq = nullptr, *d_workq = nullptr, *d_packq = nullptr;
     uint32_t readyq_cap = 0, freeq_cap = 0, workq_cap = 0;
     FactorBatch *d_batches = nullptr;
     uint32_t n_batches = 0;
     GemmJob *d_jobs = nullptr;
-    QCell *d_jobq = nullptr;
+    QCell *d_jobq = nullptr, *d_jobq_large = nullptr;
     uint32_t jobq_cap = 0;
-    uint8_t *d_gemm_tmpl = nullptr;        // tensor-map templates of A and B (null: no tensor copies)
+    uint8_t *d_pack_small = nullptr, *d_pack_large = nullptr;   // packed-operand scratch of the job records
     bool gemm_enabled = false;             // a GEMM actor exists: drains use the GEMM layout
     unsigned grid_factor = 0, grid_mixed = 0;
     uint32_t *d_primes = nullptr, *d_pinv = nullptr, *d_plim = nullptr;
@@ -131,6 +131,7 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.readyq = rt->d_readyq;
     p.freeq = rt->d_freeq;
     p.workq = rt->d_workq;
+    p.packq = rt->d_packq;
     p.batches = rt->d_batches;
     p.primes = rt->d_primes;
     p.pinv = rt->d_pinv;
@@ -150,7 +151,9 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.ring_mask = rt->cfg.ingress_capacity - 1;
     p.jobs = rt->d_jobs;
     p.jobq = rt->d_jobq;
-    p.gemm_tmpl = rt->d_gemm_tmpl;
+    p.jobq_large = rt->d_jobq_large;
+    p.pack_small = rt->d_pack_small;
+    p.pack_large = rt->d_pack_large;
     p.gemm = rt->gemm_enabled ? 1u : 0u;
     return p;
 }
@@ -365,10 +368,13 @@ void free_runtime(caf_gpu_runtime *rt) {
     cudaFree(rt->d_readyq);
     cudaFree(rt->d_freeq);
     cudaFree(rt->d_workq);
+    cudaFree(rt->d_packq);
     cudaFree(rt->d_batches);
     cudaFree(rt->d_jobs);
     cudaFree(rt->d_jobq);
-    cudaFree(rt->d_gemm_tmpl);
+    cudaFree(rt->d_jobq_large);
+    cudaFree(rt->d_pack_small);
+    cudaFree(rt->d_pack_large);
     if (rt->gemm_descs) cudaFreeHost(rt->gemm_descs);
     cudaFree(rt->d_primes);
     cudaFree(rt->d_pinv);
@@ -442,7 +448,9 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     CK(cudaMemset(rt->d_batches, 0, sizeof(FactorBatch) * rt->n_batches));
     rt->readyq_cap = next_pow2((uint64_t)c.max_actors + 1);
     rt->freeq_cap = next_pow2((uint64_t)rt->n_batches + 1);
-    rt->workq_cap = next_pow2((uint64_t)kGemmJobs * (kMaxDrainGemmN / 128) * (kMaxDrainGemmN / 128) + 1);
+    // every job's tiles, or its pack items, can be queued at once
+    rt->workq_cap = next_pow2((uint64_t)kGemmJobsSmall * (kPackSmallMaxN / 128) * (kPackSmallMaxN / 128) +
+                              (uint64_t)kGemmJobsLarge * (kMaxDrainGemmN / 128) * (kMaxDrainGemmN / 128) + 1);
     rt->jobq_cap = next_pow2((uint64_t)kGemmJobs + 1);
     std::vector<uint32_t> none, all(rt->n_batches);
     for (uint32_t i = 0; i < rt->n_batches; ++i) all[i] = i;
@@ -450,32 +458,16 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     if ((r = init_queue(rt, &rt->d_readyq, rt->readyq_cap, &rt->d_ctl->readyq, none))) return r;
     if ((r = init_queue(rt, &rt->d_freeq, rt->freeq_cap, &rt->d_ctl->freeq, all))) return r;
     if ((r = init_queue(rt, &rt->d_workq, rt->workq_cap, &rt->d_ctl->workq, none))) return r;
-    std::vector<uint32_t> jobs(kGemmJobs);
-    for (uint32_t i = 0; i < kGemmJobs; ++i) jobs[i] = i;
-    if ((r = init_queue(rt, &rt->d_jobq, rt->jobq_cap, &rt->d_ctl->jobq, jobs))) return r;
+    if ((r = init_queue(rt, &rt->d_packq, next_pow2(2ull * kGemmJobs * (kMaxDrainGemmN / 128) + 1),
+                        &rt->d_ctl->packq, none)))
+        return r;
+    std::vector<uint32_t> jobs_small(kGemmJobsSmall), jobs_large(kGemmJobsLarge);
+    for (uint32_t i = 0; i < kGemmJobsSmall; ++i) jobs_small[i] = i;
+    for (uint32_t i = 0; i < kGemmJobsLarge; ++i) jobs_large[i] = kGemmJobsSmall + i;
+    if ((r = init_queue(rt, &rt->d_jobq, rt->jobq_cap, &rt->d_ctl->jobq, jobs_small))) return r;
+    if ((r = init_queue(rt, &rt->d_jobq_large, rt->jobq_cap, &rt->d_ctl->jobq_large, jobs_large))) return r;
     CK(cudaMalloc(&rt->d_jobs, sizeof(GemmJob) * kGemmJobs));
     CK(cudaMemset(rt->d_jobs, 0, sizeof(GemmJob) * kGemmJobs));
-    {
-        // tensor-map templates the drain copies and points at each GEMM's A and
-        // B: one host-encoded pair per n (a multiple of 4, up to the drain's
-        // limit); without the driver's encoder the converters read the
-        // operands directly
-        const uint32_t pairs = kMaxDrainGemmN / 4;
-        std::vector<uint8_t> tmpl((size_t)pairs * 256);
-        CK(cudaMalloc(&rt->d_gemm_tmpl, tmpl.size()));
-        bool ok = true;
-        for (uint32_t i = 0; i < pairs && ok; ++i) {
-            const uint32_t n = 4 * (i + 1);
-            ok = gemm_encode_tmap(&tmpl[256 * (size_t)i], rt->d_gemm_tmpl, n, true) == 0 &&
-                 gemm_encode_tmap(&tmpl[256 * (size_t)i + 128], rt->d_gemm_tmpl, n, false) == 0;
-        }
-        if (ok) {
-            CK(cudaMemcpy(rt->d_gemm_tmpl, tmpl.data(), tmpl.size(), cudaMemcpyHostToDevice));
-        } else {
-            cudaFree(rt->d_gemm_tmpl);
-            rt->d_gemm_tmpl = nullptr;
-        }
-    }
     if (c.validation_mode) {
         CK(cudaMalloc(&rt->d_log, sizeof(LogRow) * (size_t)c.log_capacity));
         CK(cudaMemset(rt->d_log, 0, sizeof(LogRow) * (size_t)c.log_capacity));
@@ -578,10 +570,24 @@ int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_c
     if (!rt || !out) return CAF_GPU_EINVAL;
     if (kernel_id < kFactor || kernel_id > kToken) return CAF_GPU_EINVAL;
     if ((kernel_id == kGemmBf16 || kernel_id == kGemmSplit) && !rt->gemm_enabled) {
-        // drains launched from now on carry tensor memory and the GEMM layout
+        // drains launched from now on carry tensor memory and the GEMM layout,
+        // and GEMM jobs need their packed-operand scratch
         int r = caf_gpu_sync(rt);
         if (r) return r;
         std::lock_guard<std::mutex> g(rt->mu);
+        if (!rt->d_pack_small) {
+            if (cudaMalloc(&rt->d_pack_small, kPackSmallBytes * kGemmJobsSmall) != cudaSuccess) {
+                cudaGetLastError();
+                rt->d_pack_small = nullptr;
+                return CAF_GPU_ENOMEM;
+            }
+            if (cudaMalloc(&rt->d_pack_large, kPackLargeBytes * kGemmJobsLarge) != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(rt->d_pack_small);
+                rt->d_pack_small = rt->d_pack_large = nullptr;
+                return CAF_GPU_ENOMEM;
+            }
+        }
         rt->gemm_enabled = true;
     }
     caf_gpu_actor_cfg c{};
@@ -1093,22 +1099,6 @@ int caf_gpu_debug_wait_expiry(caf_gpu_runtime *rt, uint64_t limit_ns) {
     rt->launches += 1;
     CK(cudaStreamSynchronize(rt->stream));
     return rt->hctl->error_word ? CAF_GPU_EWAITLIMIT : 0;
-}
-
-int caf_gpu_debug_gemm_tmaps(caf_gpu_runtime *rt, const void *A, const void *B, uint32_t n, uint8_t *device_built,
-                             uint8_t *host_encoded) {
-    if (!rt || !device_built || !host_encoded || n == 0) return CAF_GPU_EINVAL;
-    if (!rt->d_gemm_tmpl || !gemm_tma_ok(A, B, n) || n > kMaxDrainGemmN) return CAF_GPU_EINVAL;
-    if (gemm_encode_tmap(host_encoded, A, n, true) || gemm_encode_tmap(host_encoded + 128, B, n, false))
-        return CAF_GPU_EINVAL;
-    uint8_t *d_out = nullptr;
-    CK(cudaMalloc(&d_out, 256));
-    cudaError_t e = launch_gemm_tmap_build(rt->d_gemm_tmpl, A, B, n, d_out, rt->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(device_built, d_out, 256, cudaMemcpyDeviceToHost, rt->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(rt->stream);
-    cudaFree(d_out);
-    rt->launches += 1;
-    return e == cudaSuccess ? 0 : CAF_GPU_ECUDA;
 }
 
 int caf_gpu_clear_error(caf_gpu_runtime *rt) {
