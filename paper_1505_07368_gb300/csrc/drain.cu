@@ -822,64 +822,94 @@ struct NamedBarSync {
     __device__ __forceinline__ void operator()() const { named_bar_sync(1, nthreads); }
 };
 
-// Run GEMM work item `item` with the whole CTA.  A pack item (flag
-// kPackItemFlag; bit 6: B instead of A; bits 0..5: panel) converts one panel;
-// the CTA that finishes a job's last pack item queues its tiles.  A tile item
-// computes one output tile; the CTA that finishes a job's last tile writes
-// its reply and frees the job record.
-__device__ __noinline__ void drain_gemm_item(const DrainParams &P, GroupShared &G, PackedSlots &slots, uint32_t item,
-                                             GemmCounters &K, uint32_t bar_threads) {
+// Run GEMM pack item `item` (flag kPackItemFlag; bit 6: B instead of A; bits
+// 0..5: panel) with the whole CTA; the CTA that finishes a job's last pack
+// item queues its tiles.
+__device__ __noinline__ void drain_gemm_pack(const DrainParams &P, PackedSlots &slots, uint32_t item,
+                                             uint32_t bar_threads) {
     const uint32_t j = item >> 16, x = item & 0xFFFFu;
     GemmJob *J = &P.jobs[j];
     const uint32_t n = J->n;
     const bool split = J->split != 0;
     const PackGeom g = pack_geom(reinterpret_cast<uint8_t *>(J->pack), n, split);
-    if (x & kPackItemFlag) {
-        const uint32_t panel = x & 63u;
-        if ((threadIdx.x >> 5) < kGemmConvWarps) {
-            const float *src = reinterpret_cast<const float *>((x & 64u) ? J->B : J->A);
-            // staged copies need 16-byte aligned rows
-            const bool staged = (n & 3u) == 0 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
-            uint8_t *stage = reinterpret_cast<uint8_t *>(&slots);
-            if (x & 64u) {
-                if (staged) gemm_pack_b_staged(src, g, panel, split, stage);
-                else gemm_pack_b(src, g, panel, split);
-            } else {
-                if (staged) gemm_pack_a_staged(src, g, panel, split, stage);
-                else gemm_pack_a(src, g, panel, split);
-            }
+    const uint32_t panel = x & 63u;
+    if ((threadIdx.x >> 5) < kGemmConvWarps) {
+        const float *src = reinterpret_cast<const float *>((x & 64u) ? J->B : J->A);
+        // staged copies need 16-byte aligned rows
+        const bool staged = (n & 3u) == 0 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+        uint8_t *stage = reinterpret_cast<uint8_t *>(&slots);
+        if (x & 64u) {
+            if (staged) gemm_pack_b_staged(src, g, panel, split, stage);
+            else gemm_pack_b(src, g, panel, split);
+        } else {
+            if (staged) gemm_pack_a_staged(src, g, panel, split, stage);
+            else gemm_pack_a(src, g, panel, split);
         }
-        named_bar_sync(1, bar_threads);
-        if (threadIdx.x < 32) {
-            uint32_t last = 0;
-            if (threadIdx.x == 0) {
-                heartbeat(P);
-                __threadfence();   // this CTA's packed stores before the count
-                last = atomicSub(reinterpret_cast<unsigned int *>(&J->packs_left), 1u) == 1u;
-            }
-            if (__shfl_sync(FULL, last, 0)) {
-                __threadfence();
-                if (!q_push_block(P, &P.ctl->workq, P.workq, j << 16, J->tiles) && threadIdx.x == 0)
-                    fail(P, kErrWaitQueue, 18);
-            }
-        }
-        return;
     }
-    const uint32_t tn_count = g.t;
-    const bool ok = gemm_tile_packed(g, reinterpret_cast<float *>(J->C), x / tn_count, x % tn_count, split, slots,
-                                     G.gb, K, P.wait_limit_ns, NamedBarSync{bar_threads});
+    named_bar_sync(1, bar_threads);
+    if (threadIdx.x < 32) {
+        uint32_t last = 0;
+        if (threadIdx.x == 0) {
+            heartbeat(P);
+            __threadfence();   // this CTA's packed stores before the count
+            last = atomicSub(reinterpret_cast<unsigned int *>(&J->packs_left), 1u) == 1u;
+        }
+        if (__shfl_sync(FULL, last, 0)) {
+            __threadfence();
+            if (!q_push_block(P, &P.ctl->workq, P.workq, j << 16, J->tiles) && threadIdx.x == 0)
+                fail(P, kErrWaitQueue, 18);
+        }
+    }
+}
+
+// Tile i of a run of tile items (item: job << 16 | tile index).
+struct RunTile {
+    const DrainParams *P;
+    const uint32_t *items;
+    __device__ TileRef operator()(uint32_t i) const {
+        const uint32_t item = items[i];
+        const GemmJob *J = &P->jobs[item >> 16];
+        TileRef r;
+        r.split = J->split != 0;
+        r.g = pack_geom(reinterpret_cast<uint8_t *>(J->pack), J->n, r.split);
+        r.C = reinterpret_cast<float *>(J->C);
+        r.tm = (item & 0xFFFFu) / r.g.t;
+        r.tn = (item & 0xFFFFu) % r.g.t;
+        return r;
+    }
+};
+
+// Run `count` tile items as one pipeline with the whole CTA; for each, the
+// CTA that finishes a job's last tile writes its reply and frees the record.
+__device__ __noinline__ void drain_gemm_tiles(const DrainParams &P, GroupShared &G, PackedSlots &slots,
+                                              const uint32_t *items, uint32_t count, GemmCounters &K,
+                                              uint32_t bar_threads) {
+    // `items` is shared memory the producer warp refills for its next round
+    // once the sequence's last barrier has passed: keep this run's ids
+    uint32_t mine[kItemsPerRound];
+#pragma unroll
+    for (uint32_t i = 0; i < kItemsPerRound; ++i) mine[i] = i < count ? items[i] : 0u;
+    const bool ok = gemm_tiles_packed(RunTile{&P, items}, count, slots, G.gb, K, P.wait_limit_ns,
+                                      NamedBarSync{bar_threads});
+    items = nullptr;
     if (threadIdx.x == 0) {
-        if (!ok) fail(P, kErrGemm, 16, item, n);
+        if (!ok) fail(P, kErrGemm, 16, mine[0], count);
         heartbeat(P);
         __threadfence();
-        add_u64(&P.ctl->gemm_tiles, 1);
-        if (atomicAdd(reinterpret_cast<unsigned int *>(&J->done), 1u) == J->tiles - 1) {
-            __threadfence();
-            write_reply(J->reply_addr, ok ? 0 : 3, 0, n, 0, J->reply_token);
-            __threadfence();
-            add_u64(&P.ctl->messages, 1);
-            add_u64(&P.ctl->completed, 1);
-            if (!job_free(P, j)) fail(P, kErrWaitQueue, 17);
+        add_u64(&P.ctl->gemm_tiles, count);
+#pragma unroll
+        for (uint32_t i = 0; i < kItemsPerRound; ++i) {
+            if (i >= count) break;
+            const uint32_t j = mine[i] >> 16;
+            GemmJob *J = &P.jobs[j];
+            if (atomicAdd(reinterpret_cast<unsigned int *>(&J->done), 1u) == J->tiles - 1) {
+                __threadfence();
+                write_reply(J->reply_addr, ok ? 0 : 3, 0, J->n, 0, J->reply_token);
+                __threadfence();
+                add_u64(&P.ctl->messages, 1);
+                add_u64(&P.ctl->completed, 1);
+                if (!job_free(P, j)) fail(P, kErrWaitQueue, 17);
+            }
         }
     }
 }
@@ -997,7 +1027,7 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
         fence_barrier_init();
     }
     if constexpr (kGemm) {
-        if (producer) gemm_bars_init(G.gb);   // GEMM barriers + tensor memory (warp-wide)
+        if (producer) gemm_bars_init(G.gb, kPackTmemCols);   // GEMM barriers + tensor memory (warp-wide)
         tc_fence_before();
     }
     const uint32_t gw = blockIdx.x * kConsumerWarps + ci;
@@ -1073,7 +1103,18 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
             const uint32_t ni = G.nitems;
             if (ni) {
                 // GEMM items first: short, and other CTAs may wait on the same job
-                for (uint32_t i = 0; i < ni; ++i) drain_gemm_item(P, G, gslots, G.items[i], gk, bar_threads);
+                for (uint32_t i = 0; i < ni;) {
+                    if (G.items[i] & kPackItemFlag) {
+                        drain_gemm_pack(P, gslots, G.items[i], bar_threads);
+                        ++i;
+                    } else {
+                        // consecutive tiles run as one pipeline
+                        uint32_t e = i + 1;
+                        while (e < ni && !(G.items[e] & kPackItemFlag)) ++e;
+                        drain_gemm_tiles(P, G, gslots, &G.items[i], e - i, gk, bar_threads);
+                        i = e;
+                    }
+                }
                 idle = false;
                 idle_ns = 256;
                 continue;
@@ -1139,7 +1180,7 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
         named_bar_sync(1, bar_threads);
         if (producer) {
             tc_fence_after();
-            tmem_dealloc(G.gb.tmem, kGemmTmemCols);
+            tmem_dealloc(G.gb.tmem, kPackTmemCols);
         }
     }
 }

@@ -244,66 +244,154 @@ __device__ __forceinline__ void gemm_pack_b_staged(const float *__restrict__ B, 
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Compute output tile (tm, tn) of a packed message with the whole CTA:
-// converter warp 0's lane 0 streams the k blocks' images of A panel tm and
-// B^T panel tn into the slot ring (two bulk copies per block), warp
-// kGemmConvWarps's lane 0 issues the MMAs, and warps 0..7 run the epilogue.
-// `K.pk_uses` carries the slot phases across tiles.  Returns false if a
-// bounded wait expired.
-template <class CtaSync>
-__device__ bool gemm_tile_packed(const PackGeom &g, float *__restrict__ C, uint32_t tm, uint32_t tn, bool split,
-                                 PackedSlots &S, GemmBars &Bb, GemmCounters &K, uint64_t limit_ns,
-                                 CtaSync cta_sync) {
+// ---- tile sequences ---------------------------------------------------------
+constexpr uint32_t kPackTmemCols = 512;   // two accumulator buffers of 256 columns
+
+// One output tile of a packed message.
+struct TileRef {
+    PackGeom g;
+    float *C;
+    uint32_t tm, tn;
+    bool split;
+};
+
+// Epilogue of a tile from the accumulator buffer at TMEM column `acc`, one
+// of warps 4..7: TMEM lanes 32 (w % 4).. (rows), all 128 columns; the split
+// form adds columns acc + 128.. to them.  Stores are masked at the edge.
+__device__ __forceinline__ void packed_epilogue(const TileRef &t, uint32_t tmem, uint32_t acc) {
+    const uint32_t lane = lane_id(), q = (threadIdx.x >> 5) & 3u, n = t.g.n;
+    const uint32_t gr = t.tm * kGemmBM + 32 * q + lane;
+    float *crow = t.C + (size_t)min(gr, n - 1) * n;
+#pragma unroll 1
+    for (uint32_t cc = 0; cc < kGemmBN; cc += 32) {
+        uint32_t r[32];
+        tmem_ld_32x32(tmem + ((32 * q) << 16) + acc + cc, r);
+        if (t.split) {
+            uint32_t r2[32];
+            tmem_ld_32x32(tmem + ((32 * q) << 16) + acc + kGemmBN + cc, r2);
+#pragma unroll
+            for (uint32_t j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(r2[j]));
+        }
+        if (gr < n) {
+            const uint32_t gc0 = t.tn * kGemmBN + cc;
+            if (gc0 + 32 <= n && (reinterpret_cast<uintptr_t>(crow + gc0) & 15u) == 0) {
+#pragma unroll
+                for (uint32_t j = 0; j < 32; j += 4)
+                    *reinterpret_cast<float4 *>(crow + gc0 + j) =
+                        make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                    __uint_as_float(r[j + 3]));
+            } else {
+#pragma unroll
+                for (uint32_t j = 0; j < 32; ++j)
+                    if (gc0 + j < n) crow[gc0 + j] = __uint_as_float(r[j]);
+            }
+        }
+    }
+}
+
+// Slots a tile of `g` streams.
+__device__ __forceinline__ uint32_t packed_slots_of(const PackGeom &g) {
+    return (g.nkb + kPackSlotBlocks - 1) / kPackSlotBlocks;
+}
+
+// Compute `count` output tiles (tile(i): TileRef of the i-th) as one
+// pipeline over the whole CTA:
+//   * warp 0's lane 0 streams every tile's k blocks into the slot ring (two
+//     bulk copies per slot of kPackSlotBlocks blocks), running ahead into the
+//     next tile while the current one is multiplied;
+//   * warp kGemmConvWarps's lane 0 issues the MMAs, alternating between two
+//     accumulator buffers (TMEM columns 0.. and 256..) so a tile's MMAs can
+//     start while the previous tile's epilogue still reads its buffer;
+//   * warps 4..7 run the epilogues, then free the buffer.
+// `K` carries the slot and buffer phases across calls (K.pk_uses, K.tiles).
+// Waits and commits are per slot: an mbarrier wait costs hundreds of cycles
+// even when the phase has completed, more than the MMAs of one k block.
+// Returns false if a bounded wait expired.
+template <class TileAt, class CtaSync>
+__device__ bool gemm_tiles_packed(TileAt tile, uint32_t count, PackedSlots &S, GemmBars &Bb, GemmCounters &K,
+                                  uint64_t limit_ns, CtaSync cta_sync) {
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-    const uint32_t nb = g.nkb, ns = (nb + kPackSlotBlocks - 1) / kPackSlotBlocks;
     bool ok = true;
     if (warp == 0 && lane == 0) {
         // the images were written with ordinary stores by the CTAs that ran
-        // the pack items (ordered before this tile by the work queue); make
-        // them visible to the bulk copies
-        asm volatile("fence.proxy.async.global;" ::: "memory");
+        // the pack items (ordered before these tiles by the work queue), and
         // a pack item may have used the slot area through ordinary accesses
-        // (ordered before this point by the CTA barrier between items)
+        // (ordered by the CTA barrier between items): make both visible to
+        // the bulk copies
+        asm volatile("fence.proxy.async.global;" ::: "memory");
         fence_proxy_async_smem();
-        const uint8_t *ab = g.a + (size_t)tm * nb * g.blk, *bb = g.b + (size_t)tn * nb * g.blk;
-        uint32_t i = 0;
-        for (; i < ns; ++i) {
-            const uint32_t u = K.pk_uses + i, s = u % kPackSlots;
-            if (u >= kPackSlots) {
-                ok = gemm_wait(&Bb.pk_empty[s], (u / kPackSlots - 1u) & 1u, limit_ns);
-                if (!ok) break;
+        uint32_t u = K.pk_uses;
+        for (uint32_t t = 0; t < count && ok; ++t) {
+            const TileRef r = tile(t);
+            const uint32_t nb = r.g.nkb, ns = packed_slots_of(r.g);
+            const uint8_t *ab = r.g.a + (size_t)r.tm * nb * r.g.blk, *bb = r.g.b + (size_t)r.tn * nb * r.g.blk;
+            for (uint32_t i = 0; i < ns; ++i, ++u) {
+                const uint32_t s = u % kPackSlots;
+                if (u >= kPackSlots) {
+                    ok = gemm_wait(&Bb.pk_empty[s], (u / kPackSlots - 1u) & 1u, limit_ns);
+                    if (!ok) break;
+                }
+                const uint32_t k0 = i * kPackSlotBlocks, kn = min(kPackSlotBlocks, nb - k0);
+                mbar_arrive_expect_tx(&Bb.pk_full[s], 2 * kn * r.g.blk);
+                bulk_g2s(S.s[s], ab + (size_t)k0 * r.g.blk, kn * r.g.blk, &Bb.pk_full[s]);
+                bulk_g2s(S.s[s] + kPackSlotBlocks * r.g.blk, bb + (size_t)k0 * r.g.blk, kn * r.g.blk,
+                         &Bb.pk_full[s]);
             }
-            const uint32_t k0 = i * kPackSlotBlocks, kn = min(kPackSlotBlocks, nb - k0);
-            mbar_arrive_expect_tx(&Bb.pk_full[s], 2 * kn * g.blk);
-            bulk_g2s(S.s[s], ab + (size_t)k0 * g.blk, kn * g.blk, &Bb.pk_full[s]);
-            bulk_g2s(S.s[s] + kPackSlotBlocks * g.blk, bb + (size_t)k0 * g.blk, kn * g.blk, &Bb.pk_full[s]);
         }
         // after an expired wait, let the copies in flight land (bounded)
-        for (uint32_t q = (i > kPackSlots ? i - kPackSlots : 0); !ok && q < i; ++q) {
-            const uint32_t u = K.pk_uses + q;
-            gemm_wait(&Bb.pk_full[u % kPackSlots], (u / kPackSlots) & 1u, limit_ns);
-        }
+        for (uint32_t q = (u - K.pk_uses > kPackSlots ? u - kPackSlots : K.pk_uses); !ok && q < u; ++q)
+            gemm_wait(&Bb.pk_full[q % kPackSlots], (q / kPackSlots) & 1u, limit_ns);
     } else if (warp == kGemmConvWarps && lane == 0) {
-        for (uint32_t i = 0; i < ns && ok; ++i) {
-            const uint32_t u = K.pk_uses + i, s = u % kPackSlots;
-            ok = gemm_wait(&Bb.pk_full[s], (u / kPackSlots) & 1u, limit_ns);
-            if (!ok) break;
+        uint32_t u = K.pk_uses, tt = K.tiles;
+        for (uint32_t t = 0; t < count && ok; ++t, ++tt) {
+            const TileRef r = tile(t);
+            const uint32_t nb = r.g.nkb, ns = packed_slots_of(r.g), bsel = tt & 1u, acc = Bb.tmem + bsel * 256u;
+            if (tt >= 2) {
+                ok = gemm_wait(&Bb.acc_empty[bsel], ((tt >> 1) - 1u) & 1u, limit_ns);
+                if (!ok) break;
+            }
             tc_fence_after();
-            const uint32_t kn = min(kPackSlotBlocks, nb - i * kPackSlotBlocks);
-            const uint8_t *sa = S.s[s], *sb = S.s[s] + kPackSlotBlocks * g.blk;
-            for (uint32_t b = 0; b < kn; ++b)
-                gemm_mma_planes(sa + b * g.blk, sa + b * g.blk + kPackPlane, sb + b * g.blk, Bb.tmem, split,
-                                i == 0 && b == 0);
-            tc_commit(&Bb.pk_empty[s]);
+            for (uint32_t i = 0; i < ns; ++i, ++u) {
+                const uint32_t s = u % kPackSlots;
+                ok = gemm_wait(&Bb.pk_full[s], (u / kPackSlots) & 1u, limit_ns);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t kn = min(kPackSlotBlocks, nb - i * kPackSlotBlocks);
+                const uint8_t *sa = S.s[s], *sb = S.s[s] + kPackSlotBlocks * r.g.blk;
+                for (uint32_t b = 0; b < kn; ++b)
+                    gemm_mma_planes(sa + b * r.g.blk, sa + b * r.g.blk + kPackPlane, sb + b * r.g.blk, acc, r.split,
+                                    i == 0 && b == 0);
+                tc_commit(&Bb.pk_empty[s]);
+            }
+            tc_commit(&Bb.acc_full[bsel]);
         }
-        tc_commit(&Bb.done);
+    } else if (warp >= 4 && warp < kGemmConvWarps) {
+        uint32_t tt = K.tiles;
+        for (uint32_t t = 0; t < count && ok; ++t, ++tt) {
+            const TileRef r = tile(t);
+            const uint32_t bsel = tt & 1u;
+            ok = gemm_wait(&Bb.acc_full[bsel], (tt >> 1) & 1u, limit_ns);
+            if (!__all_sync(0xFFFFFFFFu, ok)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            packed_epilogue(r, Bb.tmem, bsel * 256u);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&Bb.acc_empty[bsel]))
+                             : "memory");
+        }
     }
     if (warp == 0 || warp == kGemmConvWarps) __syncwarp();
-    K.pk_uses += ns;
-    if (warp < kGemmConvWarps) ok = gemm_epilogue(C, g.n, tm, tn, split, Bb, K.tiles, ok, limit_ns);
-    ++K.tiles;
-    // the next tile's MMAs overwrite the accumulators: every epilogue read
-    // must be complete first
+    // every thread advances the phase counters the same way
+    uint32_t slots = 0;
+    for (uint32_t t = 0; t < count; ++t) slots += packed_slots_of(tile(t).g);
+    K.pk_uses += slots;
+    K.tiles += count;
+    // the next sequence's MMAs overwrite the buffers, and a pack item may
+    // reuse the slot area: every epilogue read and MMA must be complete
     tc_fence_before();
     cta_sync();
     tc_fence_after();

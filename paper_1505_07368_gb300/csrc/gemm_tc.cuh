@@ -282,7 +282,7 @@ __device__ __forceinline__ GemmSmem &gemm_smem(uint8_t *raw) {
 
 // Barrier set-up and tensor-memory allocation, run by warp kGemmConvWarps
 // (the caller synchronises the CTA afterwards, with tcgen05 fences).
-__device__ __forceinline__ void gemm_bars_init(GemmBars &Bb) {
+__device__ __forceinline__ void gemm_bars_init(GemmBars &Bb, uint32_t tmem_cols = kGemmTmemCols) {
     if (lane_id() == 0) {
         for (uint32_t s = 0; s < kGemmF32Stages; ++s) {
             mbar_init(&Bb.f32_full[s], 1);
@@ -296,11 +296,15 @@ __device__ __forceinline__ void gemm_bars_init(GemmBars &Bb) {
             mbar_init(&Bb.pk_full[s], 1);
             mbar_init(&Bb.pk_empty[s], 1);
         }
+        for (uint32_t b = 0; b < 2; ++b) {
+            mbar_init(&Bb.acc_full[b], 1);
+            mbar_init(&Bb.acc_empty[b], 4);
+        }
         mbar_init(&Bb.done, 1);
         fence_barrier_init();
     }
     __syncwarp();
-    tmem_alloc(&Bb.tmem, kGemmTmemCols);
+    tmem_alloc(&Bb.tmem, tmem_cols);
 }
 
 __device__ __forceinline__ void gemm_cta_init(GemmSmem &S) {

@@ -57,6 +57,8 @@ struct GemmBars {
     uint64_t bf_empty[kGemmBfSlots];       // MMA completion -> converters (slot free again)
     uint64_t pk_full[kPackSlots];          // packed tiles: slot's bulk copies landed
     uint64_t pk_empty[kPackSlots];         // packed tiles: slot's MMAs completed
+    uint64_t acc_full[2];                  // packed tile sequence: accumulator buffer's MMAs completed
+    uint64_t acc_empty[2];                 // packed tile sequence: buffer's epilogue read it (4 warps)
     uint64_t done;                         // last MMA of a tile completed -> epilogue
     uint32_t f32_read[kGemmF32Stages];     // converter warps done with a stage (monotonic count)
     uint32_t tmem;                         // accumulator address from tcgen05.alloc
