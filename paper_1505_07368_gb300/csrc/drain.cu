@@ -308,6 +308,7 @@ __device__ void group_produce(const DrainParams &P, GroupShared &G, TableTile *r
 // the chunks u of each tile with u % wpb == r, and members drop messages that
 // another member has already decided below their position.
 constexpr uint32_t kItemsPerRound = 4;   // GEMM work items a CTA takes per round
+static_assert(kItemsPerRound <= sizeof(GroupShared::items) / sizeof(uint32_t), "round items fit");
 constexpr uint32_t kSweepPrimes = 4;   // chunks (primes per lane) tested per step
 static_assert((kTile / 32) % (kSweepPrimes * kConsumerWarps) == 0, "a tile splits into steps for any team size");
 __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableTile *ring, uint32_t &t,

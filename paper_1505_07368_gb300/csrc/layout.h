@@ -78,7 +78,7 @@ struct GroupShared {
     uint32_t final_tile;           // tile index at which the group's stream ends
     uint32_t active;               // consumer warps still holding messages
     uint32_t exit;
-    uint32_t items[4];             // GEMM work items this CTA runs next
+    uint32_t items[8];             // GEMM work items this CTA runs next
     uint32_t nitems;
 };
 constexpr uint32_t kDrainHeader = 1024;
