@@ -473,8 +473,16 @@ def run_gemm(args):
             "config": {"workload": f"GEMM actors: 256 actors, {wl.count} messages, n uniform in {{64,...,1024}}, N(0,1)",
                        "messages": wl.count, "l2": "flushed between steps (256 MiB write)"}, "variants": {}}
     for kind, name in ((C.GEMM_BF16, "bf16"), (C.GEMM_SPLIT_BF16X3, "split_bf16x3")):
-        _note(f"gemm {name}: persistent")
-        with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=wl.n_actors, mailbox_capacity=64) as rt:
+        sched = {}
+        if not args.no_autotune:
+            _note(f"gemm {name}: autotune")
+            from paper_1505_07368_gb300 import autotune
+            sched, table = autotune.tune_gemm(kind, wl.actor.astype(np.uint32), desc, outs, wl.n_actors,
+                                              runtime_kwargs={"mailbox_capacity": 64}, log=_note)
+            line["config"].setdefault("autotune", {})[name] = {
+                "best": sched, "measured": [[c, round(1e3 * t, 3)] for c, t in table]}
+        _note(f"gemm {name}: persistent {sched}")
+        with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=wl.n_actors, mailbox_capacity=64, **sched) as rt:
             for _ in range(wl.n_actors):
                 rt.spawn(kind)
             m = np.zeros(wl.count, C.DMSG_DTYPE)

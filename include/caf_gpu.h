@@ -94,6 +94,8 @@ typedef struct {
     uint32_t validation_mode;       /* 1: record a handling log (caf_gpu_read_log)            */
     uint32_t log_capacity;          /* log rows (default 1 << 20)                             */
     void    *cuda_stream;           /* cudaStream_t for all work; NULL = runtime's own stream */
+    uint32_t gemm_items_per_round;  /* GEMM work items a drain CTA takes per round, 1..8 (4)   */
+    uint32_t pad;
 } caf_gpu_runtime_cfg;
 
 /* Per-actor configuration for caf_gpu_spawn (may be NULL for defaults). */

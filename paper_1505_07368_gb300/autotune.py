@@ -1,20 +1,24 @@
 """Autotuner for the drain's scheduling knobs.
 
-The persistent drain has three knobs that trade per-message latency against
+The persistent drain has knobs that trade per-message latency against
 throughput, the GPU counterpart of the scheduler settings of the paper's
 Sec. 6.1 (number of workers, messages per actor run):
 
 * ``factor_batch`` (K): messages a team sweeps together against one pass of
   the prime table;
 * ``factor_warps`` (W): warps per team, i.e. warps working on one batch;
-* ``ctas_per_sm``: resident drain CTAs per SM (the worker count).
+* ``ctas_per_sm``: resident drain CTAs per SM (the worker count);
+* ``gemm_items_per_round``: GEMM work items (pack items and output tiles) a
+  CTA takes per round -- consecutive tiles of a round run as one pipeline;
+* ``max_msgs_per_claim``: messages one claim of an actor may take.
 
-``tune_factor`` runs one device batch of the caller's workload for every
-candidate setting on the current GPU, keeps the fastest, and caches the
-choice in a JSON file keyed by GPU name and workload signature.  The timing
-is CUDA events on the runtime's stream; every candidate must reproduce the
-same replies as the first one, so a setting that breaks results is never
-chosen.
+``tune_factor`` and ``tune_gemm`` run one device batch of the caller's
+workload for every candidate setting on the current GPU, keep the fastest,
+and cache the choice in a JSON file keyed by GPU name and workload
+signature.  The timing is CUDA events on the runtime's stream; every
+candidate must reproduce the first one's results (factor replies; GEMM
+replies and a checksum of every C), so a setting that breaks results is
+never chosen.
 """
 from __future__ import annotations
 
@@ -30,6 +34,10 @@ from . import cafgpu as C
 DEFAULT_CANDIDATES = [
     {"factor_batch": k, "factor_warps": w, "ctas_per_sm": c}
     for k in (8, 16) for w in (2, 4, 8) for c in (2,)
+]
+GEMM_CANDIDATES = [
+    {"gemm_items_per_round": i, "max_msgs_per_claim": c}
+    for i in (2, 4, 8) for c in (0, 8)
 ]
 
 
@@ -119,3 +127,75 @@ def tune_factor(actor_idx: np.ndarray, n: np.ndarray, n_actors: int, max_factor_
                       "table": [[c, s] for c, s in table]}
         _store_cache(cache)
     return best, table
+
+
+def _tune(key: str, candidates, run, use_cache: bool, log):
+    """Time `run(candidate) -> (seconds, signature)` for every candidate; keep
+    the fastest whose signature equals the first candidate's."""
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        return cache[key]["best"], []
+    table, ref = [], None
+    for cand in candidates:
+        secs, sig = run(cand)
+        if ref is None:
+            ref = sig
+        ok = sig == ref
+        table.append((cand, secs if ok else float("inf")))
+        if log:
+            log(f"autotune {cand}: {secs * 1e3:.2f} ms{'' if ok else ' (results differ: rejected)'}")
+    best = min(table, key=lambda x: x[1])[0]
+    if use_cache:
+        cache = _load_cache()
+        cache[key] = {"best": best, "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+                      "table": [[c, s] for c, s in table]}
+        _store_cache(cache)
+    return best, table
+
+
+def tune_gemm(kind: int, actor_idx: np.ndarray, desc: np.ndarray, outs, n_actors: int, candidates=None,
+              runtime_kwargs=None, use_cache: bool = True, log=None):
+    """Pick the fastest GEMM drain schedule (items per round, messages per claim)
+    for one device batch of GEMM messages of `kind` (BF16 or split).
+
+    desc: caf_gpu_gemm_desc records (host numpy, GEMM_DESC_DTYPE) whose C
+    pointers lie in the device tensor `outs`; actor_idx: receiving actor index
+    per message.  Returns (best_cfg, table)."""
+    import torch
+    candidates = candidates or GEMM_CANDIDATES
+    runtime_kwargs = dict(runtime_kwargs or {})
+    count = desc.size
+    h = hashlib.sha1(np.ascontiguousarray(desc["n"]).tobytes() + np.ascontiguousarray(actor_idx).tobytes())
+    key = f"{torch.cuda.get_device_name()}|gemm{kind}|actors={n_actors}|msgs={count}|{h.hexdigest()[:16]}"
+    d_desc = torch.from_numpy(desc.view(np.uint8).copy()).cuda()
+    m = np.zeros(count, C.DMSG_DTYPE)
+    m["actor"] = actor_idx
+    m["kind"] = kind
+    m["u64"] = d_desc.data_ptr() + np.arange(count, dtype=np.uint64) * C.GEMM_DESC_DTYPE.itemsize
+    m["tag"] = np.arange(count)
+    d_msgs = torch.from_numpy(m.view(np.uint8).copy()).cuda()
+    d_rep = torch.zeros(count * C.DREPLY_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+
+    def run(cand):
+        kw = dict(runtime_kwargs)
+        kw.update(cand)
+        with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=n_actors, **kw) as rt:
+            for _ in range(n_actors):
+                rt.spawn(kind)
+            stream = torch.cuda.ExternalStream(rt.stream())
+            torch.cuda.synchronize()
+            rt.request_batch_device(d_msgs.data_ptr(), count, d_rep.data_ptr())   # warm-up
+            rt.stream_sync()
+            outs.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rt.request_batch_device(d_msgs.data_ptr(), count, d_rep.data_ptr())
+            e1.record(stream)
+            rt.stream_sync()
+            secs = e0.elapsed_time(e1) / 1e3
+            rep = d_rep.cpu().numpy().view(C.DREPLY_DTYPE)
+            sig = (rep["status"].tobytes(), rep["r1"].tobytes(), float(outs.sum(dtype=torch.float64).item()))
+        return secs, sig
+
+    return _tune(key, candidates, run, use_cache, log)

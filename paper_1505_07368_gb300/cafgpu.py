@@ -47,7 +47,8 @@ class RuntimeCfg(ctypes.Structure):
                 ("max_factor_n", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_uint64),
                 ("wait_limit_ns", ctypes.c_uint64), ("idle_exit_ns", ctypes.c_uint64),
                 ("validation_mode", ctypes.c_uint32), ("log_capacity", ctypes.c_uint32),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("gemm_items_per_round", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
 
 
 class ActorCfg(ctypes.Structure):

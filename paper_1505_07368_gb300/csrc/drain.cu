@@ -307,8 +307,6 @@ __device__ void group_produce(const DrainParams &P, GroupShared &G, TableTile *r
 // streamed tiles.  A team of `wpb` warps shares one batch; member `r` tests
 // the chunks u of each tile with u % wpb == r, and members drop messages that
 // another member has already decided below their position.
-constexpr uint32_t kItemsPerRound = 4;   // GEMM work items a CTA takes per round
-static_assert(kItemsPerRound <= sizeof(GroupShared::items) / sizeof(uint32_t), "round items fit");
 constexpr uint32_t kSweepPrimes = 4;   // chunks (primes per lane) tested per step
 static_assert((kTile / 32) % (kSweepPrimes * kConsumerWarps) == 0, "a tile splits into steps for any team size");
 __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableTile *ring, uint32_t &t,
@@ -887,9 +885,9 @@ __device__ __noinline__ void drain_gemm_tiles(const DrainParams &P, GroupShared 
                                               uint32_t bar_threads) {
     // `items` is shared memory the producer warp refills for its next round
     // once the sequence's last barrier has passed: keep this run's ids
-    uint32_t mine[kItemsPerRound];
+    uint32_t mine[kMaxItemsPerRound];
 #pragma unroll
-    for (uint32_t i = 0; i < kItemsPerRound; ++i) mine[i] = i < count ? items[i] : 0u;
+    for (uint32_t i = 0; i < kMaxItemsPerRound; ++i) mine[i] = i < count ? items[i] : 0u;
     const bool ok = gemm_tiles_packed(RunTile{&P, items}, count, slots, G.gb, K, P.wait_limit_ns,
                                       NamedBarSync{bar_threads});
     items = nullptr;
@@ -899,7 +897,7 @@ __device__ __noinline__ void drain_gemm_tiles(const DrainParams &P, GroupShared 
         __threadfence();
         add_u64(&P.ctl->gemm_tiles, count);
 #pragma unroll
-        for (uint32_t i = 0; i < kItemsPerRound; ++i) {
+        for (uint32_t i = 0; i < kMaxItemsPerRound; ++i) {
             if (i >= count) break;
             const uint32_t j = mine[i] >> 16;
             GemmJob *J = &P.jobs[j];
@@ -1068,11 +1066,11 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
             uint32_t ex = 0;
             if (lane == 0) ex = exit_requested(ctl) ? 1u : 0u;
             ex = __shfl_sync(FULL, ex, 0);
-            // up to kItemsPerRound GEMM items, popped in parallel by as many
+            // up to P.gemm_items GEMM items, popped in parallel by as many
             // lanes (one pop's latency); tiles first, so a job's tiles run
             // while its packed operands are still in L2
             uint32_t item = kNone;
-            if (gemm_cta && !ex && lane < kItemsPerRound) {
+            if (gemm_cta && !ex && lane < P.gemm_items) {
                 int pr = q_try_pop(&ctl->workq, P.workq, &item, P.wait_limit_ns);
                 if (pr == 0) pr = q_try_pop(&ctl->packq, P.packq, &item, P.wait_limit_ns);
                 if (pr < 0) fail(P, kErrWaitQueue, 24);

@@ -32,6 +32,7 @@ constexpr uint32_t kNoFactor = 0xFFFFFFFFu;
 constexpr uint32_t kTile = 2048;         // primes per staged table tile (64 chunks of 32)
 constexpr uint32_t kStages = 4;          // tiles in flight per CTA
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kMaxItemsPerRound = 8;   // GEMM work items a drain CTA may take per round
 
 // One staged tile of the prime table (shared memory, 16-byte aligned).
 struct TableTile {
@@ -78,7 +79,7 @@ struct GroupShared {
     uint32_t final_tile;           // tile index at which the group's stream ends
     uint32_t active;               // consumer warps still holding messages
     uint32_t exit;
-    uint32_t items[8];             // GEMM work items this CTA runs next
+    uint32_t items[kMaxItemsPerRound];   // GEMM work items this CTA runs next
     uint32_t nitems;
 };
 constexpr uint32_t kDrainHeader = 1024;
@@ -306,6 +307,8 @@ struct DrainParams {
     uint32_t factor_k;             // messages per batch (<= kFactorKMax)
     uint32_t factor_w;             // work items per batch
     uint32_t max_claim;            // messages per claim (0: unlimited)
+    uint32_t gemm_items;           // GEMM work items per round (1..kMaxItemsPerRound)
+    uint32_t pad_gi;
     uint64_t max_n;                // largest factor message accepted
     uint64_t wait_limit_ns;
     uint64_t idle_exit_ns;

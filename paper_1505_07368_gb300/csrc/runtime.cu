@@ -140,6 +140,7 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.factor_k = rt->cfg.factor_batch;
     p.factor_w = rt->cfg.factor_warps;
     p.max_claim = rt->cfg.max_msgs_per_claim;
+    p.gemm_items = rt->cfg.gemm_items_per_round;
     p.max_n = rt->cfg.max_factor_n;
     p.wait_limit_ns = rt->cfg.wait_limit_ns;
     p.idle_exit_ns = rt->cfg.idle_exit_ns;
@@ -407,6 +408,8 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     if (!c.wait_limit_ns) c.wait_limit_ns = 200000000ull;
     if (!c.idle_exit_ns) c.idle_exit_ns = 2000000ull;
     if (!c.log_capacity) c.log_capacity = 1u << 20;
+    if (!c.gemm_items_per_round) c.gemm_items_per_round = 4;
+    if (c.gemm_items_per_round > kMaxItemsPerRound) return CAF_GPU_EINVAL;
     if (!is_pow2(c.mailbox_capacity) || !is_pow2(c.ingress_capacity)) return CAF_GPU_EINVAL;
     if (c.factor_batch > kFactorKMax || c.ctas_per_sm > 4) return CAF_GPU_EINVAL;
     if (c.factor_warps != 1 && c.factor_warps != 2 && c.factor_warps != 4 && c.factor_warps != 8)

@@ -40,7 +40,7 @@ def test_struct_sizes():
     assert cafgpu.SERVE_RESULT_DTYPE.itemsize == 48
     assert ctypes.sizeof(cafgpu.ServeCfg) == 32
     assert ctypes.sizeof(cafgpu.ServeStats) == 32
-    assert ctypes.sizeof(cafgpu.RuntimeCfg) == 80
+    assert ctypes.sizeof(cafgpu.RuntimeCfg) == 88
 
 
 def test_strerror_without_gpu():
