@@ -62,9 +62,9 @@ def parse_args(argv=None):
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--max-messages", type=int, default=None, help="truncate the workload (profiling)")
-    ap.add_argument("--workload", choices=["factor", "gemm", "ring", "serve"], default="factor",
+    ap.add_argument("--workload", choices=["factor", "gemm", "ring", "serve", "mailbox"], default="factor",
                     help="factor: the batched-factorization line (default); the others measure the "
-                         "GEMM, token-ring and serving configurations")
+                         "GEMM, token-ring, serving and mailbox-traffic configurations")
     ap.add_argument("--no-autotune", action="store_true", help="use --factor-batch/--factor-warps as given")
     ap.add_argument("--requests", type=int, default=100_000, help="serve: requests in the trace")
     return ap.parse_args(argv)
@@ -665,6 +665,64 @@ def run_serve(args):
     return 0
 
 
+def run_mailbox(args):
+    """Mailbox traffic: SOURCE actors stream into SINK actors (trivial payload),
+    N:1 -- 100 sources into one sink, the paper's mailbox experiment -- and
+    1024 independent source -> sink pairs; one persistent launch per step."""
+    import torch
+
+    from paper_1505_07368_gb300 import cafgpu as C
+    torch.cuda.set_device(0)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    slot_bytes = 128        # one 64-byte mailbox slot written and read per message
+    out = {}
+    for label, n_src, n_sink, per in (("n_to_1", 100, 1, 20_000), ("pairs", 1024, 1024, 2_000)):
+        # the slot pool is max_actors x the default capacity: the sinks' size
+        sink_cap = 1 << 14 if n_sink == 1 else 4096
+        with C.Runtime(max_actors=n_src + n_sink, mailbox_capacity=sink_cap) as rt:
+            sinks = [rt.spawn(C.SINK) for _ in range(n_sink)]
+            srcs = [rt.spawn(C.SOURCE, next=sinks[i % n_sink], mailbox_capacity=4) for i in range(n_src)]
+            m = np.zeros(n_src, C.DMSG_DTYPE)
+            m["actor"] = np.array(srcs, np.uint32) - 1
+            m["kind"] = C.SOURCE
+            m["u64"] = per
+            m["tag"] = np.arange(n_src)
+            d_m = torch.from_numpy(m.view(np.uint8).copy()).cuda()
+            d_r = torch.zeros(n_src * 32, dtype=torch.uint8, device="cuda")
+            stream = torch.cuda.ExternalStream(rt.stream())
+            torch.cuda.synchronize()
+            for _ in range(args.warmup):
+                rt.reset_actors()
+                rt.request_batch_device(d_m.data_ptr(), n_src, d_r.data_ptr())
+            rt.stream_sync()
+            times = []
+            for _ in range(args.steps):
+                rt.reset_actors()
+                e0, e1 = _events(stream)
+                e0.record(stream)
+                rt.request_batch_device(d_m.data_ptr(), n_src, d_r.data_ptr())
+                e1.record(stream)
+                rt.stream_sync()
+                times.append(e0.elapsed_time(e1) / 1e3)
+            total = sum(rt.sink_totals(s)[0] for s in sinks)
+            if total != n_src * per:
+                raise SystemExit(f"bench: mailbox {label}: sinks counted {total} of {n_src * per}")
+            st = rt.stats()
+            t = float(np.mean(times))
+            msgs = n_src * per
+            out[label] = {"sources": n_src, "sinks": n_sink, "messages": msgs, "ms_per_step": 1e3 * t,
+                          "msgs_per_s": msgs / t,
+                          "roofline": {"bound": "hbm", "achieved": slot_bytes * msgs / t / 1e9, "peak": hbm,
+                                       "unit": "GB/s", "frac": slot_bytes * msgs / t / 1e9 / hbm,
+                                       "bytes_per_msg": slot_bytes},
+                          "gpu_launches": st["launches"]}
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "mailbox: SOURCE actors streaming into SINK "
+                      "actors (N:1 and pairs)", "steps": args.steps, "results": out,
+                      "value": out["n_to_1"]["msgs_per_s"]}))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -675,6 +733,8 @@ def main(argv=None):
         return run_ring(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "mailbox":
+        return run_mailbox(args)
     return run_ours(args)
 
 

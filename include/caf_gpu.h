@@ -52,6 +52,19 @@ extern "C" {
 #define CAF_GPU_GEMM_BF16           2u  /* C = A*B, BF16 operands, FP32 accumulate   */
 #define CAF_GPU_GEMM_SPLIT_BF16X3   3u  /* C = A*B, split-BF16x3 compensated         */
 #define CAF_GPU_RING_TOKEN          4u  /* token ring member (stateful)              */
+#define CAF_GPU_SINK                5u  /* counts what it receives (stateful)        */
+#define CAF_GPU_SOURCE              6u  /* sends a stream of messages to a sink      */
+/* SINK and SOURCE are the two ends of the paper's mailbox experiment (Sec. 5,
+ * "Mailbox Performance in N:1 Communication Scenario": many senders, one
+ * receiver).  A SINK handles each message (u64 value v) by adding 1 to its
+ * count and v to its sum (caf_gpu_sink_totals); a request's reply is
+ * (count after this message, v).  A SOURCE is spawned with cfg.next = its
+ * target SINK; a message u64 = c makes it send c messages to the target, with
+ * values (source actor << 32) | k for k = 0 .. c-1, sender = the source, in k
+ * order, and a request's reply is (c, 0) once all c are sent.  It sends at most
+ * 1024 per run and continues with a message to itself, so a long stream never
+ * holds a worker.  Both kinds run in the persistent backend only
+ * (CAF_GPU_EINVAL under CAF_GPU_BACKEND_PER_MESSAGE_LAUNCH). */
 
 /* ---- backends ----------------------------------------------------------- */
 #define CAF_GPU_BACKEND_PERSISTENT          0  /* one persistent kernel drains all mailboxes */
@@ -246,13 +259,18 @@ int caf_gpu_stream_sync(caf_gpu_runtime *rt);
 /* Select the backend for subsequent messages (only while nothing is in flight). */
 int caf_gpu_set_backend(caf_gpu_runtime *rt, int backend);
 
-/* Reset every RING_TOKEN actor to its spawn state (lifecycle and user state),
- * stream-ordered, so a ring workload can be replayed or captured in a CUDA graph. */
+/* Reset every RING_TOKEN actor to its spawn state (lifecycle and user state)
+ * and zero every SINK's totals, stream-ordered, so a workload can be replayed
+ * or captured in a CUDA graph. */
 int caf_gpu_reset_actors(caf_gpu_runtime *rt);
 
 /* Lifecycle (0 waiting, 1 ready, 2 running, 3 done) and user state of an actor. */
 int caf_gpu_actor_state(caf_gpu_runtime *rt, caf_gpu_actor a, uint32_t *lifecycle,
                         int32_t *user_state);
+
+/* A SINK's totals: messages handled and the sum of their values.  EINVAL if
+ * `a` is not a SINK. */
+int caf_gpu_sink_totals(caf_gpu_runtime *rt, caf_gpu_actor a, uint64_t *count, uint64_t *sum);
 
 /* Counters and the device error word since the last call (which resets them). */
 int caf_gpu_stats_read(caf_gpu_runtime *rt, caf_gpu_stats *out);

@@ -127,3 +127,28 @@ def simulate_rings(n_rings: int, ring_len: int, token: int):
         assert all(done)
         rings.append({"trace": trace, "requests": len(req_after), "request_after": req_after})
     return rings
+
+
+def source_streams(sources):
+    """The messages the SINK / SOURCE reading of the N:1 mailbox experiment
+    (Sec. 5, "Mailbox Performance in N:1 Communication Scenario") sends:
+    source s (actor index) asked for c messages to sink t sends values
+    (s << 32) | k for k = 0 .. c-1, in k order, with sender s and sender
+    sequence k.  ``sources``: [(s, c, t), ...].
+
+    Returns (receiver, sender, sender_seq, value) arrays, one row per message,
+    each source's messages contiguous and in k order, and {t: (count, sum)}
+    with the sum taken mod 2^64 (the sink's counter width)."""
+    rec, snd, seq, val = [], [], [], []
+    totals = {}
+    for s, c, t in sources:
+        for k in range(c):
+            v = (s << 32) | k
+            rec.append(t)
+            snd.append(s)
+            seq.append(k)
+            val.append(v)
+            cnt, tot = totals.get(t, (0, 0))
+            totals[t] = (cnt + 1, (tot + v) % (1 << 64))
+    return (np.asarray(rec, np.int64), np.asarray(snd, np.int64), np.asarray(seq, np.int64),
+            np.asarray(val, np.uint64), totals)

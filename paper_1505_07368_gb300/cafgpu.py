@@ -19,7 +19,7 @@ from . import _build
 
 # ---- constants (caf_gpu.h) ------------------------------------------------
 OK, EINVAL, ENOMEM, EAGAIN, ETIMEDOUT, EDEAD, EWAITLIMIT, ESTATE, ECUDA = 0, -1, -2, -3, -4, -5, -6, -7, -8
-FACTOR_U64, GEMM_BF16, GEMM_SPLIT_BF16X3, RING_TOKEN = 1, 2, 3, 4
+FACTOR_U64, GEMM_BF16, GEMM_SPLIT_BF16X3, RING_TOKEN, SINK, SOURCE = 1, 2, 3, 4, 5, 6
 BACKEND_PERSISTENT, BACKEND_PER_MESSAGE_LAUNCH = 0, 1
 REPLY_OK, REPLY_NOFACTOR, REPLY_DEAD, REPLY_REJECTED = 0, 1, 2, 3
 MSG_START = 1
@@ -100,7 +100,7 @@ EXPORTS = [
     "caf_gpu_request_batch_device", "caf_gpu_sync", "caf_gpu_stream_sync", "caf_gpu_set_backend",
     "caf_gpu_reset_actors", "caf_gpu_actor_state", "caf_gpu_stats_read", "caf_gpu_read_log",
     "caf_gpu_stream", "caf_gpu_mark", "caf_gpu_prime_table", "caf_gpu_debug_wait_expiry", "caf_gpu_clear_error",
-    "caf_gpu_measure_mul_rates",
+    "caf_gpu_measure_mul_rates", "caf_gpu_sink_totals",
     "caf_gpu_graph_begin", "caf_gpu_graph_end", "caf_gpu_graph_launch", "caf_gpu_graph_destroy",
     "caf_gpu_serve_run", "caf_gpu_factor_static", "caf_gpu_strerror",
 ]
@@ -141,6 +141,7 @@ def load(build: bool = True):
         "caf_gpu_prime_table": [vp, P(vp), P(u32)],
         "caf_gpu_debug_wait_expiry": [vp, u64],
         "caf_gpu_measure_mul_rates": [vp],
+        "caf_gpu_sink_totals": [vp, u64, P(u64), P(u64)],
         "caf_gpu_clear_error": [vp],
         "caf_gpu_mark": [vp],
         "caf_gpu_factor_static": [vp, u32, vp, vp],
@@ -231,6 +232,13 @@ class Runtime:
         us = ctypes.c_int32()
         _check(self.L.caf_gpu_actor_state(self.h, actor, ctypes.byref(lc), ctypes.byref(us)), "caf_gpu_actor_state")
         return lc.value, us.value
+
+    def sink_totals(self, actor: int):
+        """(messages handled, sum of their values) of a SINK."""
+        c = ctypes.c_uint64()
+        t = ctypes.c_uint64()
+        _check(self.L.caf_gpu_sink_totals(self.h, actor, ctypes.byref(c), ctypes.byref(t)), "caf_gpu_sink_totals")
+        return c.value, t.value
 
     # -- messages -----------------------------------------------------------
     @staticmethod

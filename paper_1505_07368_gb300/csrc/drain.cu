@@ -603,6 +603,109 @@ __device__ void claim_ring(const DrainParams &P, uint32_t a) {
     __syncwarp();
 }
 
+// ---------------------------------------------------------------------------
+// SINK and SOURCE actors: the two ends of the paper's N:1 mailbox experiment
+// (Sec. 5, "Mailbox Performance in N:1 Communication Scenario").
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSinkChunk = 4096;     // messages a SINK handles per claim
+constexpr uint32_t kSourceChunk = 1024;   // messages a SOURCE sends per run
+
+// Warp sum of a 64-bit value (all lanes).
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Claimed SINK `a`: take up to kSinkChunk messages, 32 per dequeue; each adds
+// 1 to the count and its value to the sum; a request's reply is (count after
+// it, value).
+__device__ void run_sink(const DrainParams &P, uint32_t a) {
+    const uint32_t lane = lane_id();
+    ActorDesc *A = &P.actors[a];
+    if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
+    __syncwarp();
+    uint64_t head = *((volatile uint64_t *)&A->head);
+    const uint64_t tail = ld_acquire_gpu(&A->tail);
+    uint64_t left = tail - head;
+    if (left > kSinkChunk) left = kSinkChunk;
+    if (P.max_claim && left > P.max_claim) left = P.max_claim;
+    if (lane == 0) add_u64(&P.ctl->claims, 1);
+    uint64_t count = A->sink_count, sum = A->sink_sum, handled = 0;
+    while (left > 0) {
+        MsgData m{};
+        const uint32_t got = warp_dequeue(P, a, head, left < 32 ? (uint32_t)left : 32u, m);
+        if (got == 0) break;
+        const uint64_t v = lane < got ? m.payload : 0;
+        if (lane < got) write_reply(m.reply_addr, 0, count + lane + 1, v, m.tag, m.reply_token);
+        sum += warp_sum_u64(v);
+        count += got;
+        handled += got;
+        head += got;
+        left -= got;
+    }
+    if (lane == 0) {
+        A->sink_count = count;
+        A->sink_sum = sum;
+        __threadfence();
+        add_u64(&P.ctl->messages, handled);
+        add_u64(&P.ctl->completed, handled);
+    }
+    __syncwarp();
+    release_actor(P, a, head);
+}
+
+// Claimed SOURCE `a`: handle one message, (c remaining, k0 first index) with
+// c in the low and k0 in the high 32 bits: send up to kSourceChunk messages
+// (k0 + i) to the target SINK, 32 per warp-wide enqueue, then either send the
+// continuation (c', k0') to itself or, when all are sent, reply (total, 0).
+__device__ void run_source(const DrainParams &P, uint32_t a) {
+    const uint32_t lane = lane_id();
+    ActorDesc *A = &P.actors[a];
+    if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
+    __syncwarp();
+    const uint64_t head = *((volatile uint64_t *)&A->head);
+    if (lane == 0) add_u64(&P.ctl->claims, 1);
+    MsgData m{};
+    if (warp_dequeue(P, a, head, 1, m) == 0) return;
+    m.payload = __shfl_sync(FULL, m.payload, 0);
+    m.reply_addr = __shfl_sync(FULL, m.reply_addr, 0);
+    m.reply_token = __shfl_sync(FULL, m.reply_token, 0);
+    m.tag = __shfl_sync(FULL, m.tag, 0);
+    const uint32_t c = (uint32_t)m.payload, k0 = (uint32_t)(m.payload >> 32);
+    const uint32_t now = c < kSourceChunk ? c : kSourceChunk;
+    const uint32_t target = A->next;
+    bool ok = true;
+    for (uint32_t i = 0; i < now && ok; i += 32) {
+        MsgData s{};
+        const uint32_t k = k0 + i + lane;
+        s.payload = ((uint64_t)a << 32) | k;
+        s.kind = kSink;
+        s.sender = 0x80000000u | a;
+        s.sender_seq = k;
+        s.tag = k;
+        ok = warp_enqueue(P, i + lane < now, target, s);
+    }
+    if (lane == 0) add_u64(&P.ctl->device_sends, now);
+    if (ok && now < c) {
+        MsgData s = m;   // continuation: same reply route
+        s.payload = ((uint64_t)(k0 + now) << 32) | (c - now);
+        s.kind = kSource;
+        s.sender = 0x80000000u | a;
+        s.sender_seq = k0 + now;
+        ok = warp_enqueue(P, lane == 0, a, s);
+    } else if (ok && lane == 0) {
+        write_reply(m.reply_addr, 0, k0 + now, 0, m.tag, m.reply_token);
+    }
+    if (lane == 0) {
+        __threadfence();
+        add_u64(&P.ctl->messages, 1);
+        add_u64(&P.ctl->completed, 1);
+    }
+    __syncwarp();
+    release_actor(P, a, head + 1);
+}
+
 // Answer a message that cannot be handled (unknown actor, kind mismatch,
 // terminated receiver, n out of range).
 __device__ __forceinline__ void reject(uint64_t reply_addr, uint32_t token, uint64_t tag, int32_t status) {
@@ -951,6 +1054,10 @@ __device__ uint32_t find_batch(const DrainParams &P) {
             if (r != kNone) return r;
         } else if (kind == kToken) {
             claim_ring(P, a);
+        } else if (kind == kSink) {
+            run_sink(P, a);
+        } else if (kind == kSource) {
+            run_source(P, a);
         } else if (kGemm && (kind == kGemmBf16 || kind == kGemmSplit)) {
             claim_gemm(P, a);
         }
@@ -1295,6 +1402,9 @@ __global__ void k_reset_actors(ActorDesc *actors, uint32_t n_actors) {
         A->user_state = A->init_state;
         A->round = 0;
         A->head = A->tail;
+    } else if (A->kind == kSink) {
+        A->sink_count = 0;
+        A->sink_sum = 0;
     }
 }
 

@@ -127,7 +127,7 @@ struct GemmDesc {
 enum : uint32_t { kWaiting = 0, kReady = 1, kRunning = 2, kDone = 3 };
 
 // kinds (mirror caf_gpu.h)
-enum : uint32_t { kFactor = 1, kGemmBf16 = 2, kGemmSplit = 3, kToken = 4 };
+enum : uint32_t { kFactor = 1, kGemmBf16 = 2, kGemmSplit = 3, kToken = 4, kSink = 5, kSource = 6 };
 enum : uint32_t { kMsgStart = 1 };
 enum : uint32_t { kActorMaster = 1 };
 
@@ -180,7 +180,9 @@ struct ActorDesc {                 // 128 bytes
     uint32_t flags;
     uint64_t slot_base;            // first Slot of this actor's ring
     uint64_t head;                 // consumer position (written by the claim holder only)
-    uint64_t pad_a[4];
+    uint64_t sink_count;           // SINK: messages handled (claim holder only)
+    uint64_t sink_sum;             // SINK: sum of their values
+    uint64_t pad_a[2];
     uint64_t tail;                 // producer ticket (atomic add)
     int32_t user_state;
     uint32_t next;                 // ring successor

@@ -224,6 +224,9 @@ int check_msg(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *m, uint3
         if (!m->A || !m->B || !m->C || m->n == 0 || m->n > kMaxGemmN) return CAF_GPU_EINVAL;
         if (rt->backend == CAF_GPU_BACKEND_PERSISTENT && m->n > kMaxDrainGemmN) return CAF_GPU_EINVAL;
     }
+    if ((m->kind == kSink || m->kind == kSource) && rt->backend != CAF_GPU_BACKEND_PERSISTENT)
+        return CAF_GPU_EINVAL;
+    if (m->kind == kSource && m->u64 > 0xFFFFFFFFull) return CAF_GPU_EINVAL;
     if (m->kind == kToken) {
         uint32_t state = 0;
         if (cudaMemcpy(&state, &rt->d_actors[a].state, sizeof(state), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -571,7 +574,7 @@ int caf_gpu_runtime_destroy(caf_gpu_runtime *rt) {
 
 int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_cfg *cfg, caf_gpu_actor *out) {
     if (!rt || !out) return CAF_GPU_EINVAL;
-    if (kernel_id < kFactor || kernel_id > kToken) return CAF_GPU_EINVAL;
+    if (kernel_id < kFactor || kernel_id > kSource) return CAF_GPU_EINVAL;
     if ((kernel_id == kGemmBf16 || kernel_id == kGemmSplit) && !rt->gemm_enabled) {
         // drains launched from now on carry tensor memory and the GEMM layout,
         // and GEMM jobs need their packed-operand scratch
@@ -620,6 +623,11 @@ int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_c
         }
         d.init_state = c.init_state;
         d.user_state = c.init_state;
+    }
+    if (kernel_id == kSource) {
+        // the target must be an existing SINK
+        if (c.next == 0 || c.next > rt->n_actors || rt->actors[c.next - 1].kind != kSink) return CAF_GPU_EINVAL;
+        d.next = (uint32_t)(c.next - 1);
     }
     const uint32_t idx = rt->n_actors;
     CK(cudaMemcpyAsync(&rt->d_actors[idx], &d, sizeof(d), cudaMemcpyHostToDevice, rt->setup));
@@ -811,6 +819,16 @@ int caf_gpu_actor_state(caf_gpu_runtime *rt, caf_gpu_actor a, uint32_t *lifecycl
     CK(cudaMemcpy(&d, &rt->d_actors[a - 1], sizeof(d), cudaMemcpyDeviceToHost));
     if (lifecycle) *lifecycle = d.state;
     if (user_state) *user_state = d.user_state;
+    return 0;
+}
+
+int caf_gpu_sink_totals(caf_gpu_runtime *rt, caf_gpu_actor a, uint64_t *count, uint64_t *sum) {
+    if (!rt || a == 0 || a > rt->n_actors || rt->actors[a - 1].kind != kSink) return CAF_GPU_EINVAL;
+    if (rt->capturing) return CAF_GPU_ESTATE;
+    ActorDesc d;
+    CK(cudaMemcpy(&d, &rt->d_actors[a - 1], sizeof(d), cudaMemcpyDeviceToHost));
+    if (count) *count = d.sink_count;
+    if (sum) *sum = d.sink_sum;
     return 0;
 }
 

@@ -130,3 +130,58 @@ def test_bounded_wait_expiry_reports_and_recovers():
         rt.clear_error()
         h = rt.request(a, C.Runtime.msg(C.FACTOR_U64, 1000003 * 999983))
         assert rt.await_(h) == (0, 999983, 1000003)
+
+
+def test_n_to_1_sources_into_one_sink():
+    """The N:1 mailbox experiment: 40 SOURCE actors stream into one SINK
+    concurrently (counts above 1024 exercise the continuation messages); every
+    message is handled exactly once, in k order per source, and the sink's
+    totals and the sources' replies match the oracle."""
+    counts = [700 + 97 * i for i in range(40)]
+    # the slot pool is max_actors x the default capacity (the sink's)
+    with C.Runtime(max_factor_n=MAX32, max_actors=64, mailbox_capacity=4096, validation_mode=1) as rt:
+        sink = rt.spawn(C.SINK)
+        srcs = [rt.spawn(C.SOURCE, next=sink, mailbox_capacity=4) for _ in counts]
+        msgs = (C.Msg * len(srcs))()
+        for i, c in enumerate(counts):
+            msgs[i] = C.Runtime.msg(C.SOURCE, u64=c, tag=i)
+        h = rt.request_batch(np.array(srcs, np.uint64), msgs)
+        rep = rt.await_batch(h, timeout_ns=60_000_000_000)
+        # a source replies once it has sent its last message; the sink may
+        # still be handling them: wait until everything sent is handled
+        rt.sync()
+        count, total = rt.sink_totals(sink)
+        log = rt.read_log()
+    assert np.all(rep["status"] == 0) and list(rep["r0"]) == counts
+    rec, snd, seq, val, totals = A.source_streams([(s - 1, c, sink - 1) for s, c in zip(srcs, counts)])
+    assert (count, total) == totals[sink - 1]
+    rows = log[log["actor"] == sink - 1]
+    assert rows.size == rec.size
+    # map each handled sink message to its index in the oracle's stream
+    index = {(int(s), int(k)): i for i, (s, k) in enumerate(zip(snd, seq))}
+    src = rows["sender"].astype(np.int64) & 0x7FFFFFFF
+    msg = np.array([index[(int(s), int(k))] for s, k in zip(src, rows["sender_seq"])])
+    assert np.array_equal(rows["value"], val[msg])
+    errs = A.check_mailbox_log(rec, snd, seq, rows["actor"], msg, rows["stamp"])
+    assert errs == []
+
+
+def test_sink_request_replies_count_in_handling_order():
+    """Host requests to a SINK: replies are (position in the sink's handling
+    order, value), positions 1..N in FIFO order of one sender."""
+    vals = [5, 1 << 40, 3, 7, 11] * 20
+    with C.Runtime(max_factor_n=MAX32, max_actors=4) as rt:
+        sink = rt.spawn(C.SINK)
+        msgs = (C.Msg * len(vals))()
+        for i, v in enumerate(vals):
+            msgs[i] = C.Runtime.msg(C.SINK, u64=v, tag=i)
+        h = rt.request_batch(np.full(len(vals), sink, np.uint64), msgs)
+        rep = rt.await_batch(h, timeout_ns=60_000_000_000)
+        rt.sync()
+        count, total = rt.sink_totals(sink)
+        rt.reset_actors()
+        rt.stream_sync()
+        assert rt.sink_totals(sink) == (0, 0)
+    assert list(rep["r0"]) == list(range(1, len(vals) + 1))
+    assert list(rep["r1"]) == vals
+    assert (count, total) == (len(vals), sum(vals))

@@ -68,3 +68,21 @@ def test_rings_small_by_hand():
     r = actors.simulate_rings(1, 3, 2)[0]
     assert r["trace"] == [(1, 2), (2, 1), (0, 0), (1, 0), (2, 0)]
     assert r["requests"] == 1
+
+
+def test_source_streams_closed_form():
+    """Sink totals of the N:1 reading against their closed form: source s
+    sending c messages contributes c and c (s << 32) + c (c - 1) / 2."""
+    from oracle import actors as A
+    srcs = [(3, 5, 0), (7, 1, 0), (9, 2000, 1), (1 << 20, 3, 1)]
+    rec, snd, seq, val, totals = A.source_streams(srcs)
+    assert rec.size == sum(c for _, c, _ in srcs)
+    for t in (0, 1):
+        want_c = sum(c for s, c, tt in srcs if tt == t)
+        want_s = sum(c * (s << 32) + c * (c - 1) // 2 for s, c, tt in srcs if tt == t) % (1 << 64)
+        assert totals[t] == (want_c, want_s)
+    # each source's messages in k order, values encode (s, k)
+    for s, c, _ in srcs:
+        rows = snd == s
+        assert list(seq[rows]) == list(range(c))
+        assert all(int(v) >> 32 == s and int(v) & 0xFFFFFFFF == k for v, k in zip(val[rows], seq[rows]))
