@@ -62,7 +62,7 @@ def parse_args(argv=None):
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--max-messages", type=int, default=None, help="truncate the workload (profiling)")
-    ap.add_argument("--workload", choices=["factor", "gemm", "ring", "serve", "mailbox"], default="factor",
+    ap.add_argument("--workload", choices=["factor", "gemm", "ring", "serve", "mailbox", "small"], default="factor",
                     help="factor: the batched-factorization line (default); the others measure the "
                          "GEMM, token-ring, serving and mailbox-traffic configurations")
     ap.add_argument("--no-autotune", action="store_true", help="use --factor-batch/--factor-warps as given")
@@ -665,6 +665,47 @@ def run_serve(args):
     return 0
 
 
+def run_small(args):
+    """The plain small case (config 1): 1 actor, 1 mailbox, 256 semiprimes with
+    prime factors in [2^16, 2^20); the per-message-launch form (the config's
+    own method) against the persistent drain, and the oracle on one core."""
+    import torch
+
+    from paper_1505_07368_gb300 import cafgpu as C
+    torch.cuda.set_device(0)
+    wl = W.config1()
+    out = {}
+    for backend, label in ((C.BACKEND_PER_MESSAGE_LAUNCH, "per_message_launch"), (C.BACKEND_PERSISTENT, "persistent")):
+        with C.Runtime(max_factor_n=(1 << 40) - 1, max_actors=1) as rt:
+            a = rt.spawn(C.FACTOR_U64)
+            rt.set_backend(backend)
+            msgs = (C.Msg * wl.count)()
+            for i in range(wl.count):
+                msgs[i] = C.Runtime.msg(C.FACTOR_U64, u64=int(wl.n[i]), tag=i)
+            actors = np.full(wl.count, a, np.uint64)
+            for _ in range(args.warmup):
+                rt.await_batch(rt.request_batch(actors, msgs), timeout_ns=AWAIT_NS)
+            times, lat = [], []
+            for _ in range(args.steps):
+                t0 = time.perf_counter()
+                h = rt.request_batch(actors, msgs)
+                rep = rt.await_batch(h, timeout_ns=AWAIT_NS)
+                times.append(time.perf_counter() - t0)
+            if not (np.array_equal(rep["r0"], np.minimum(wl.p, wl.q)) and np.array_equal(rep["r1"], np.maximum(wl.p, wl.q))):
+                raise SystemExit(f"bench: small {label}: wrong factors")
+            t = float(np.mean(times))
+            out[label] = {"msgs_per_s": wl.count / t, "ms_per_step": 1e3 * t,
+                          "launches_per_step": rt.stats()["launches"] / (args.warmup + args.steps)}
+    rate, done, secs = cpu_oracle_rate(wl, args.cpu_seconds)
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "plain small case: 1 actor, 1 mailbox, 256 "
+                      "semiprimes, prime factors in [2^16, 2^20)", "steps": args.steps,
+                      "timing": "host wall clock around request_batch + await_batch (host API, end to end)",
+                      "results": out, "value": out["persistent"]["msgs_per_s"],
+                      "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                       "sample": f"{done} messages in {secs:.1f} s, single-threaded trial division"}}))
+    return 0
+
+
 def run_mailbox(args):
     """Mailbox traffic: SOURCE actors stream into SINK actors (trivial payload),
     N:1 -- 100 sources into one sink, the paper's mailbox experiment -- and
@@ -735,6 +776,8 @@ def main(argv=None):
         return run_serve(args)
     if args.workload == "mailbox":
         return run_mailbox(args)
+    if args.workload == "small":
+        return run_small(args)
     return run_ours(args)
 
 
