@@ -14,6 +14,9 @@ Functions and the passages they follow:
 * ``gemm_f64`` / ``gemm_entry`` -- the matrix product of the OpenCL actor
   example (Sec. 3.6) in float64 from float32 inputs.
 * ``rel_frobenius`` -- relative Frobenius error in float64.
+* ``mandel_point`` / ``mandel_rows`` -- escape counts of the Mandelbrot
+  iteration in float32 for the OpenCL actor experiment (Sec. 5,
+  "Integrating OpenCL Actors").
 * ``actors.simulate_mailboxes`` / ``actors.check_mailbox_log`` -- the
   mailbox of Sec. 3.2 and Sec. 2 (FIFO, one reader, exactly-once handling).
 * ``actors.simulate_rings`` -- the token rings of Sec. 5.
@@ -33,9 +36,13 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` into ``liboracle.so`` (gcc, -O2, no -march flags)."""
+    """Compile ``oracle.c`` into ``liboracle.so`` (gcc, -O2, no -march flags).
+
+    ``-ffp-contract=off``: every float operation is rounded on its own (no
+    fused multiply-add), on x86 and on Arm alike."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB,
+                               _SRC, "-lm"])
     return _LIB
 
 
@@ -62,6 +69,12 @@ def lib():
         L.oracle_gemm_entry.restype = ctypes.c_double
         L.oracle_rel_frobenius.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
         L.oracle_rel_frobenius.restype = ctypes.c_double
+        L.oracle_mandel_point.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_uint32]
+        L.oracle_mandel_point.restype = ctypes.c_uint32
+        L.oracle_mandel_rows.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                         ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                         ctypes.c_void_p]
+        L.oracle_mandel_rows.restype = ctypes.c_uint64
         _lib = L
     return _lib
 
@@ -114,3 +127,19 @@ def rel_frobenius(C: np.ndarray, C64: np.ndarray) -> float:
     C64 = np.ascontiguousarray(C64, dtype=np.float64)
     assert C.size == C64.size
     return float(lib().oracle_rel_frobenius(C.ctypes.data, C64.ctypes.data, C.size))
+
+
+def mandel_point(cx: float, cy: float, max_iter: int) -> int:
+    """Escape count of c = cx + i cy (both rounded to float32 first)."""
+    return int(lib().oracle_mandel_point(float(np.float32(cx)), float(np.float32(cy)), int(max_iter)))
+
+
+def mandel_rows(x0: float, y0: float, dx: float, dy: float, width: int, row0: int, rows: int, max_iter: int):
+    """Escape counts of rows row0 .. row0+rows-1 (pixel (i, j): c = x0 + i dx + (y0 + j dy) i, float32).
+
+    Returns (counts uint32 of shape (rows, width), sum of the counts)."""
+    out = np.empty((rows, width), dtype=np.uint32)
+    f = [float(np.float32(v)) for v in (x0, y0, dx, dy)]
+    s = lib().oracle_mandel_rows(f[0], f[1], f[2], f[3], int(width), int(row0), int(rows), int(max_iter),
+                                 out.ctypes.data)
+    return out, int(s)

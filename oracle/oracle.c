@@ -23,6 +23,17 @@
  *  - The relative Frobenius error ||C - C64||_F / ||C64||_F in float64.
  *
  *  - A trial-division primality test, used to check factor certificates.
+ *
+ *  - Mandelbrot escape counts (the OpenCL actor experiment of Sec. 5,
+ *    "Integrating OpenCL Actors": an image of 1920 x 1080 pixels over a cut
+ *    of the complex plane, 120 or 1200 maximum iterations).  The iteration
+ *    z <- z^2 + c from z = 0 in float32, each operation rounded to nearest
+ *    (the library must be built with -ffp-contract=off so that no multiply
+ *    and add are fused).  The count is the number of completed iterations
+ *    before |z|^2 > 4 is first seen, at most max_iter.  The paper fixes
+ *    neither the precision nor the order of the operations; this order
+ *    (squares, escape test, cross term doubled, then the new z) is the one
+ *    the GPU path follows.
  */
 #include <math.h>
 #include <stddef.h>
@@ -116,4 +127,46 @@ double oracle_rel_frobenius(const float *C, const double *C64, int64_t count)
     if (den == 0.0)
         return sqrt(num);
     return sqrt(num) / sqrt(den);
+}
+
+/* Escape count of c = cx + i*cy: iterate z <- z^2 + c from z = 0, testing
+ * |z|^2 = zr*zr + zi*zi > 4 before each update, for at most max_iter updates.
+ * Every operation is one float32 operation rounded to nearest:
+ *   x2 = zr*zr; y2 = zi*zi; stop if x2 + y2 > 4;
+ *   xy = zr*zi; zi = (xy + xy) + cy; zr = (x2 - y2) + cx. */
+uint32_t oracle_mandel_point(float cx, float cy, uint32_t max_iter)
+{
+    float zr = 0.0f, zi = 0.0f;
+    uint32_t k = 0;
+    while (k < max_iter) {
+        float x2 = zr * zr;
+        float y2 = zi * zi;
+        if (x2 + y2 > 4.0f)
+            break;
+        float xy = zr * zi;
+        zi = (xy + xy) + cy;
+        zr = (x2 - y2) + cx;
+        ++k;
+    }
+    return k;
+}
+
+/* Rows row0 .. row0+rows-1 of an image `width` pixels wide: pixel (i, j) is
+ * c = (x0 + i*dx) + (y0 + j*dy) i, each coordinate one rounded product and
+ * one rounded sum in float32.  out[(j - row0) * width + i] = its escape
+ * count; the return value is the sum of the counts. */
+uint64_t oracle_mandel_rows(float x0, float y0, float dx, float dy, uint32_t width, uint32_t row0,
+                            uint32_t rows, uint32_t max_iter, uint32_t *out)
+{
+    uint64_t sum = 0;
+    for (uint32_t r = 0; r < rows; ++r) {
+        float cy = y0 + (float)(row0 + r) * dy;
+        for (uint32_t i = 0; i < width; ++i) {
+            float cx = x0 + (float)i * dx;
+            uint32_t k = oracle_mandel_point(cx, cy, max_iter);
+            out[(size_t)r * width + i] = k;
+            sum += k;
+        }
+    }
+    return sum;
 }
