@@ -62,7 +62,8 @@ def parse_args(argv=None):
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--max-messages", type=int, default=None, help="truncate the workload (profiling)")
-    ap.add_argument("--workload", choices=["factor", "gemm", "ring", "serve", "mailbox", "small"], default="factor",
+    ap.add_argument("--workload", choices=["factor", "gemm", "ring", "serve", "mailbox", "small", "mandel"],
+                    default="factor",
                     help="factor: the batched-factorization line (default); the others measure the "
                          "GEMM, token-ring, serving and mailbox-traffic configurations")
     ap.add_argument("--no-autotune", action="store_true", help="use --factor-batch/--factor-warps as given")
@@ -764,6 +765,155 @@ def run_mailbox(args):
     return 0
 
 
+FP32_OPS_PER_ITER = 8          # 3 multiplies + 5 adds per escape iteration
+FP32_LANES_PER_SM = 128
+
+
+def run_mandel(args):
+    """Mandelbrot actors (the OpenCL actor experiment, Sec. 5): the 1920 x 1080
+    image of [-0.5 - 0.7375i, 0.1 - 0.1375i] at 120 and at 1200 iterations, sent
+    to one MANDELBROT actor as whole-image messages (100 per step, the paper's
+    100 runs) and as one message per row (10 images, 10,800 messages per step);
+    persistent drain against one kernel launch per message."""
+    import torch
+
+    import oracle
+    from paper_1505_07368_gb300 import cafgpu as C
+    torch.cuda.set_device(0)
+    Wd, Hd = W.MANDEL_WIDTH, W.MANDEL_HEIGHT
+    x0, y0, dx, dy = W.mandel_image()
+    peaks = measured_peaks()
+    fp32_rate = C.measure_fp32_rate()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    results = {}
+    clocks = ClockSampler(physical_gpu(0))
+    clocks.start()
+    for max_iter in W.MANDEL_ITERS:
+        for shape, images, rows_per_msg in (("image", 100, Hd), ("row", 10, 1)):
+            per_image = Hd // rows_per_msg
+            count = images * per_image
+            out = torch.zeros((images, Hd, Wd), dtype=torch.int32, device="cuda")
+            desc = np.zeros(count, C.MANDEL_DESC_DTYPE)
+            img = np.repeat(np.arange(images), per_image)
+            row0 = np.tile(np.arange(per_image) * rows_per_msg, images)
+            desc["out"] = out.data_ptr() + 4 * (img.astype(np.uint64) * Hd * Wd + row0.astype(np.uint64) * Wd)
+            desc["width"], desc["rows"], desc["row0"], desc["max_iter"] = Wd, rows_per_msg, row0, max_iter
+            desc["x0"], desc["y0"], desc["dx"], desc["dy"] = x0, y0, dx, dy
+            d_desc = torch.from_numpy(desc.view(np.uint8).copy()).cuda()
+            label = f"iter{max_iter}_{shape}"
+            _note(f"mandel {label}: {count} messages")
+            with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=1, mailbox_capacity=1 << 14) as rt:
+                a = rt.spawn(C.MANDELBROT)
+                m = np.zeros(count, C.DMSG_DTYPE)
+                m["actor"] = a - 1
+                m["kind"] = C.MANDELBROT
+                m["u64"] = d_desc.data_ptr() + np.arange(count, dtype=np.uint64) * C.MANDEL_DESC_DTYPE.itemsize
+                m["sender_seq"] = np.arange(count)
+                m["tag"] = np.arange(count)
+                d_m = torch.from_numpy(m.view(np.uint8).copy()).cuda()
+                d_r = torch.zeros(count * 32, dtype=torch.uint8, device="cuda")
+                stream = torch.cuda.ExternalStream(rt.stream())
+                torch.cuda.synchronize()
+                for _ in range(args.warmup):
+                    rt.request_batch_device(d_m.data_ptr(), count, d_r.data_ptr())
+                rt.stream_sync()
+                rt.stats()
+                times = []
+                for _ in range(args.steps):
+                    with torch.cuda.stream(stream):
+                        flush.add_(1.0)
+                    e0, e1 = _events(stream)
+                    e0.record(stream)
+                    rt.mark()
+                    rt.request_batch_device(d_m.data_ptr(), count, d_r.data_ptr())
+                    e1.record(stream)
+                    rt.stream_sync()
+                    times.append(e0.elapsed_time(e1) / 1e3)
+                st = rt.stats()
+                rep_ = d_r.cpu().numpy().view(C.DREPLY_DTYPE)
+                if not (np.all(rep_["status"] == 0) and np.all(rep_["r0"] == rows_per_msg * Wd)):
+                    raise SystemExit(f"bench: mandel {label}: replies incomplete")
+                counts_sum = int(rep_["r1"][:per_image].astype(np.uint64).sum())    # one image
+                sums = rep_["r1"].reshape(images, per_image).sum(axis=1)
+                if not np.all(sums == counts_sum):
+                    raise SystemExit(f"bench: mandel {label}: images differ")
+                got = out[0].cpu().numpy().view(np.uint32)
+                for j in (0, 311, 540, 777, Hd - 1):                  # sampled rows against the oracle
+                    want, _ = oracle.mandel_rows(x0, y0, dx, dy, Wd, j, 1, max_iter)
+                    if not np.array_equal(got[j], want[0]):
+                        raise SystemExit(f"bench: mandel {label}: row {j} differs from the oracle")
+                lat = (rep_["t_done"].astype(np.int64) - np.int64(st["t_mark"])) / 1e6
+                t = float(np.mean(times))
+                ops = FP32_OPS_PER_ITER * float(counts_sum) * images
+                v = {"messages": count, "images": images, "ms_per_step": 1e3 * t, "msgs_per_s": count / t,
+                     "images_per_s": images / t, "mpix_per_s": images * Wd * Hd / t / 1e6,
+                     "mean_iterations": counts_sum / (Wd * Hd),
+                     "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                     "fp32_tops": ops / t / 1e12, "gpu_launches": st["launches"]}
+                if not args.skip_per_message:
+                    rt.set_backend(C.BACKEND_PER_MESSAGE_LAUNCH)
+                    ds = [C.MandelDesc(int(desc["out"][i]), Wd, rows_per_msg, int(row0[i]), max_iter,
+                                       float(x0), float(y0), float(dx), float(dy)) for i in range(count)]
+                    msgs = (C.Msg * count)()
+                    for i in range(count):
+                        msgs[i] = C.Runtime.mandel_msg(ds[i], tag=i)
+                    actors = np.full(count, a, np.uint64)
+                    rt.await_batch(rt.request_batch(actors[:per_image], msgs), timeout_ns=AWAIT_NS)   # warm-up
+                    pm = []
+                    for _ in range(max(1, min(args.steps, 3))):
+                        with torch.cuda.stream(stream):
+                            flush.add_(1.0)
+                        e0, e1 = _events(stream)
+                        torch.cuda.synchronize()
+                        e0.record(stream)
+                        h = rt.request_batch(actors, msgs)
+                        e1.record(stream)
+                        prep = rt.await_batch(h, timeout_ns=AWAIT_NS)
+                        torch.cuda.synchronize()
+                        pm.append(e0.elapsed_time(e1) / 1e3)
+                    if not np.array_equal(prep["r1"], rep_["r1"]):
+                        raise SystemExit(f"bench: mandel {label}: per-message sums differ")
+                    tp = float(np.mean(pm))
+                    v["per_message_launch"] = {"ms": 1e3 * tp, "msgs_per_s": count / tp,
+                                               "speedup_persistent": tp / t}
+                results[label] = v
+            del out, d_desc
+            torch.cuda.empty_cache()
+    clk = clocks.stop()
+    mhz = clk.get("sm_max_mhz") or 2070.0
+    nominal = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
+    for v in results.values():
+        v["roofline"] = {"bound": "alu", "achieved": v["fp32_tops"], "peak": nominal, "unit": "TFLOP/s",
+                         "frac": v["fp32_tops"] / nominal, "measured_fp32_tops": fp32_rate / 1e12,
+                         "frac_of_measured": v["fp32_tops"] / (fp32_rate / 1e12),
+                         "note": "float32 multiplies and adds of the escape iterations (8 per iteration); "
+                                 "peak = 152 SMs x 128 lanes x max SM clock"}
+    # CPU baseline: the oracle on a bounded sample of rows of the large problem
+    budget = min(args.cpu_seconds, 10.0)
+    t0 = time.perf_counter()
+    done_px = done_iter = 0
+    j = 0
+    while time.perf_counter() - t0 < budget and j < Hd:
+        _, s_ = oracle.mandel_rows(x0, y0, dx, dy, Wd, (j * 37) % Hd, 1, 1200)
+        done_px += Wd
+        done_iter += s_
+        j += 1
+    secs = time.perf_counter() - t0
+    head = results["iter1200_image"]
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Mandelbrot actor: 1920 x 1080 over [-0.5-0.7375i, 0.1-0.1375i], 120 and 1200 "
+                                   "iterations; whole-image and per-row messages",
+                       "l2": "flushed between steps (256 MiB write); outputs 830 MB per image step"},
+            "value": head["msgs_per_s"], "ms_per_step": head["ms_per_step"], "results": results,
+            "roofline": head["roofline"], "clocks": clk,
+            "cpu_baseline": {"value": (done_px / (Wd * Hd)) / secs, "unit": "images/s (1200 iterations)",
+                             "cores": 1, "kind": "oracle",
+                             "sample": f"{j} sampled rows of the 1200-iteration image in {secs:.1f} s, one core"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -778,6 +928,8 @@ def main(argv=None):
         return run_mailbox(args)
     if args.workload == "small":
         return run_small(args)
+    if args.workload == "mandel":
+        return run_mandel(args)
     return run_ours(args)
 
 

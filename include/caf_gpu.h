@@ -3,9 +3,9 @@
  *
  * Actors live in device memory.  Each has a bounded lock-free mailbox in
  * HBM; a persistent kernel drains the mailboxes, runs the message's
- * data-parallel payload (64-bit trial-division factorization, or a dense
- * matrix product on the tcgen05 tensor cores), and writes the reply to the
- * request that asked for it.  The calls follow the actor model of
+ * data-parallel payload (64-bit trial-division factorization, a dense
+ * matrix product on the tcgen05 tensor cores, or a Mandelbrot image), and
+ * writes the reply to the request that asked for it.  The calls follow the actor model of
  * "Revisiting Actor Programming in C++" (Charousset, Hiesgen, Schmidt):
  *
  *   caf_gpu_spawn    -- spawn an actor from a compiled-in GPU kernel
@@ -54,6 +54,7 @@ extern "C" {
 #define CAF_GPU_RING_TOKEN          4u  /* token ring member (stateful)              */
 #define CAF_GPU_SINK                5u  /* counts what it receives (stateful)        */
 #define CAF_GPU_SOURCE              6u  /* sends a stream of messages to a sink      */
+#define CAF_GPU_MANDELBROT          7u  /* escape counts of an image's rows          */
 /* SINK and SOURCE are the two ends of the paper's mailbox experiment (Sec. 5,
  * "Mailbox Performance in N:1 Communication Scenario": many senders, one
  * receiver).  A SINK handles each message (u64 value v) by adding 1 to its
@@ -65,6 +66,26 @@ extern "C" {
  * 1024 per run and continues with a message to itself, so a long stream never
  * holds a worker.  Both kinds run in the persistent backend only
  * (CAF_GPU_EINVAL under CAF_GPU_BACKEND_PER_MESSAGE_LAUNCH). */
+
+/* MANDELBROT is the GPU actor of the paper's OpenCL experiment (Sec. 5,
+ * "Integrating OpenCL Actors": a 1920 x 1080 Mandelbrot image with 120 or
+ * 1200 maximum iterations).  A message names a caf_gpu_mandel_desc: in
+ * caf_gpu_msg.u64, the address of one in host memory, copied at the call; in
+ * caf_gpu_dmsg.u64, the address of one in device memory, read when the
+ * message is handled.  The actor writes the escape count of every pixel of
+ * the described rows and replies (r0, r1) = (pixels, sum of the counts).
+ * The count of c is the number of updates z <- z^2 + c, from z = 0, made
+ * before |z|^2 > 4 is first seen, at most max_iter, with every step one
+ * float32 operation rounded to nearest in this order:
+ *   x2 = zr*zr; y2 = zi*zi; stop if x2 + y2 > 4;
+ *   xy = zr*zi; zi = (xy + xy) + cy; zr = (x2 - y2) + cx;
+ * so counts are exact, reproducible integers.  Pixel (i, j) -- column i,
+ * image row j -- is c = (x0 + i*dx) + (y0 + j*dy) i, each coordinate one
+ * rounded float32 product and sum.  Limits: width * rows <= 2^24,
+ * width <= 2^24, row0 + rows <= 2^24, max_iter <= 65536, out 4-byte
+ * aligned; other descriptors are EINVAL at the call (host messages) or get
+ * reply status CAF_GPU_REPLY_REJECTED (device batches).  A message needs a
+ * reply (caf_gpu_send returns EINVAL). */
 
 /* ---- backends ----------------------------------------------------------- */
 #define CAF_GPU_BACKEND_PERSISTENT          0  /* one persistent kernel drains all mailboxes */
@@ -131,7 +152,8 @@ typedef struct {
     uint32_t flags;                 /* CAF_GPU_MSG_*                                           */
     uint32_t sender;                /* sender id: order is kept per (sender, receiver)         */
     uint32_t n;                     /* GEMM: matrix size (n x n, row-major, leading dim n)     */
-    uint64_t u64;                   /* FACTOR_U64: the number; RING_TOKEN: the token value     */
+    uint64_t u64;                   /* FACTOR_U64: the number; RING_TOKEN: the token value;    */
+                                    /* MANDELBROT: address of a host caf_gpu_mandel_desc       */
     uint64_t tag;                   /* caller's tag, echoed in the handling log                */
     const float *A;                 /* GEMM operands (device)                                  */
     const float *B;
@@ -142,7 +164,8 @@ typedef struct {
 typedef struct {
     int32_t  status;                /* CAF_GPU_REPLY_*                                         */
     uint32_t kind;
-    uint64_t r0, r1;                /* FACTOR_U64: (p, q) with p <= q; GEMM: (0, n)            */
+    uint64_t r0, r1;                /* FACTOR_U64: (p, q) with p <= q; GEMM: (0, n);           */
+                                    /* MANDELBROT: (pixels, sum of the escape counts)          */
     uint64_t t_done;                /* device clock when the reply was written (ns)            */
 } caf_gpu_reply;
 
@@ -153,7 +176,8 @@ typedef struct {
     uint32_t sender;
     uint32_t sender_seq;            /* position in that sender's stream (for the log)          */
     uint64_t u64;                   /* FACTOR: n; TOKEN: value; GEMM: device address of a      */
-                                    /* caf_gpu_gemm_desc                                        */
+                                    /* caf_gpu_gemm_desc; MANDELBROT: device address of a      */
+                                    /* caf_gpu_mandel_desc                                      */
     uint64_t tag;
 } caf_gpu_dmsg;
 
@@ -165,6 +189,20 @@ typedef struct {
     uint32_t n;
     uint32_t pad;
 } caf_gpu_gemm_desc;
+
+/* Mandelbrot job referenced by a MANDELBROT message (40 bytes).  out is device
+ * memory of width * rows uint32 counts, row-major: out[(j - row0) * width + i]
+ * is pixel (i, j); the caller owns it, and it must stay valid until the reply
+ * has been awaited. */
+typedef struct {
+    uint32_t *out;
+    uint32_t width;                 /* pixels per row                                          */
+    uint32_t rows;                  /* rows in this job                                        */
+    uint32_t row0;                  /* image row index j of the first row                      */
+    uint32_t max_iter;              /* iteration limit (<= 65536)                              */
+    float x0, y0;                   /* c of pixel (0, 0) of the image                          */
+    float dx, dy;                   /* step of c per column and per row                        */
+} caf_gpu_mandel_desc;
 
 /* Device-resident reply written by the drain (32 bytes). */
 typedef struct {
@@ -323,6 +361,14 @@ int caf_gpu_debug_wait_expiry(caf_gpu_runtime *rt, uint64_t limit_ns);
  * current device and allocates, then frees, a small buffer; needs no runtime.
  * Returns CAF_GPU_EINVAL for a null pointer, CAF_GPU_ECUDA on a CUDA error. */
 int caf_gpu_measure_mul_rates(double *rates);
+
+/* Measured throughput, on the current device, of float32 multiplies and adds
+ * (each rounded on its own, no fused multiply-add): the operations of the
+ * MANDELBROT escape iteration.  *ops_per_s = operations per second over all
+ * SMs.  Runs two short kernels on the current device and allocates, then
+ * frees, a small buffer; needs no runtime.  CAF_GPU_EINVAL for a null
+ * pointer, CAF_GPU_ECUDA on a CUDA error. */
+int caf_gpu_measure_fp32_rate(double *ops_per_s);
 
 /* Clear the device error word after a reported bounded-wait expiry. */
 int caf_gpu_clear_error(caf_gpu_runtime *rt);

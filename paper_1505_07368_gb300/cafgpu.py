@@ -19,7 +19,7 @@ from . import _build
 
 # ---- constants (caf_gpu.h) ------------------------------------------------
 OK, EINVAL, ENOMEM, EAGAIN, ETIMEDOUT, EDEAD, EWAITLIMIT, ESTATE, ECUDA = 0, -1, -2, -3, -4, -5, -6, -7, -8
-FACTOR_U64, GEMM_BF16, GEMM_SPLIT_BF16X3, RING_TOKEN, SINK, SOURCE = 1, 2, 3, 4, 5, 6
+FACTOR_U64, GEMM_BF16, GEMM_SPLIT_BF16X3, RING_TOKEN, SINK, SOURCE, MANDELBROT = 1, 2, 3, 4, 5, 6, 7
 BACKEND_PERSISTENT, BACKEND_PER_MESSAGE_LAUNCH = 0, 1
 REPLY_OK, REPLY_NOFACTOR, REPLY_DEAD, REPLY_REJECTED = 0, 1, 2, 3
 MSG_START = 1
@@ -29,6 +29,10 @@ DMSG_DTYPE = np.dtype([("actor", "<u4"), ("kind", "<u4"), ("sender", "<u4"), ("s
                        ("u64", "<u8"), ("tag", "<u8")])
 DREPLY_DTYPE = np.dtype([("status", "<i4"), ("done", "<u4"), ("r0", "<u8"), ("r1", "<u8"), ("t_done", "<u8")])
 GEMM_DESC_DTYPE = np.dtype([("A", "<u8"), ("B", "<u8"), ("C", "<u8"), ("n", "<u4"), ("pad", "<u4")])
+MANDEL_DESC_DTYPE = np.dtype([("out", "<u8"), ("width", "<u4"), ("rows", "<u4"), ("row0", "<u4"),
+                              ("max_iter", "<u4"), ("x0", "<f4"), ("y0", "<f4"), ("dx", "<f4"), ("dy", "<f4")])
+MANDEL_MAX_PIXELS = 1 << 24
+MANDEL_MAX_ITER = 1 << 16
 LOG_DTYPE = np.dtype([("actor", "<u4"), ("sender", "<u4"), ("sender_seq", "<u4"), ("kind", "<u4"),
                       ("stamp", "<u8"), ("tag", "<u8"), ("value", "<u8")])
 
@@ -62,6 +66,14 @@ class Msg(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("sender", ctypes.c_uint32),
                 ("n", ctypes.c_uint32), ("u64", ctypes.c_uint64), ("tag", ctypes.c_uint64),
                 ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p)]
+
+
+class MandelDesc(ctypes.Structure):
+    """caf_gpu_mandel_desc: rows row0 .. row0+rows-1 of an image `width` wide;
+    pixel (i, j) is c = (x0 + i dx) + (y0 + j dy) i; out: device uint32 counts."""
+    _fields_ = [("out", ctypes.c_void_p), ("width", ctypes.c_uint32), ("rows", ctypes.c_uint32),
+                ("row0", ctypes.c_uint32), ("max_iter", ctypes.c_uint32), ("x0", ctypes.c_float),
+                ("y0", ctypes.c_float), ("dx", ctypes.c_float), ("dy", ctypes.c_float)]
 
 
 class Reply(ctypes.Structure):
@@ -100,7 +112,7 @@ EXPORTS = [
     "caf_gpu_request_batch_device", "caf_gpu_sync", "caf_gpu_stream_sync", "caf_gpu_set_backend",
     "caf_gpu_reset_actors", "caf_gpu_actor_state", "caf_gpu_stats_read", "caf_gpu_read_log",
     "caf_gpu_stream", "caf_gpu_mark", "caf_gpu_prime_table", "caf_gpu_debug_wait_expiry", "caf_gpu_clear_error",
-    "caf_gpu_measure_mul_rates", "caf_gpu_sink_totals",
+    "caf_gpu_measure_mul_rates", "caf_gpu_measure_fp32_rate", "caf_gpu_sink_totals",
     "caf_gpu_graph_begin", "caf_gpu_graph_end", "caf_gpu_graph_launch", "caf_gpu_graph_destroy",
     "caf_gpu_serve_run", "caf_gpu_factor_static", "caf_gpu_strerror",
 ]
@@ -141,6 +153,7 @@ def load(build: bool = True):
         "caf_gpu_prime_table": [vp, P(vp), P(u32)],
         "caf_gpu_debug_wait_expiry": [vp, u64],
         "caf_gpu_measure_mul_rates": [vp],
+        "caf_gpu_measure_fp32_rate": [vp],
         "caf_gpu_sink_totals": [vp, u64, P(u64), P(u64)],
         "caf_gpu_clear_error": [vp],
         "caf_gpu_mark": [vp],
@@ -168,6 +181,13 @@ def measure_mul_rates() -> dict:
     out = (ctypes.c_double * 3)()
     _check(load().caf_gpu_measure_mul_rates(out), "caf_gpu_measure_mul_rates")
     return {"mul_lo_per_s": out[0], "mul_hi_per_s": out[1], "test_chain_mul_per_s": out[2]}
+
+
+def measure_fp32_rate() -> float:
+    """Measured float32 multiply + add rate (operations/s, each rounded on its own)."""
+    out = ctypes.c_double()
+    _check(load().caf_gpu_measure_fp32_rate(ctypes.byref(out)), "caf_gpu_measure_fp32_rate")
+    return out.value
 
 
 def factor_static(d_n: int, count: int, d_replies: int, stream: int = 0) -> int:
@@ -245,6 +265,11 @@ class Runtime:
     def msg(kind: int, u64: int = 0, sender: int = 0, flags: int = 0, tag: int = 0, n: int = 0,
             A: int = 0, B: int = 0, C: int = 0) -> Msg:
         return Msg(kind, flags, sender, n, u64, tag, A or None, B or None, C or None)
+
+    @staticmethod
+    def mandel_msg(desc: MandelDesc, sender: int = 0, tag: int = 0) -> Msg:
+        """A MANDELBROT message naming `desc` (the runtime copies it at the call)."""
+        return Msg(MANDELBROT, 0, sender, 0, ctypes.addressof(desc), tag, None, None, None)
 
     def send(self, actor: int, m: Msg) -> None:
         _check(self.L.caf_gpu_send(self.h, actor, ctypes.byref(m)), "caf_gpu_send")

@@ -27,6 +27,7 @@
 #include "factor.cuh"
 #include "gemm_packed.cuh"
 #include "layout.h"
+#include "mandel.cuh"
 
 namespace cafgpu {
 
@@ -865,7 +866,8 @@ __device__ __noinline__ void claim_gemm(const DrainParams &P, uint32_t a) {
     const uint32_t npub = (pm == FULL) ? 32u : (uint32_t)(__ffs(~pm) - 1);
     const GemmDesc *d = lane < npub ? reinterpret_cast<const GemmDesc *>(sl->payload) : nullptr;
     const uint32_t n = d ? d->n : 0u;
-    const bool valid = d && n > 0 && n <= kMaxDrainGemmN && d->A && d->B && d->C;
+    // (a drain launched without packed-operand scratch rejects GEMM messages)
+    const bool valid = d && n > 0 && n <= kMaxDrainGemmN && d->A && d->B && d->C && P.pack_small && P.pack_large;
     uint32_t j = kNone;
     bool got = false;
     if (valid) {
@@ -1016,6 +1018,160 @@ __device__ __noinline__ void drain_gemm_tiles(const DrainParams &P, GroupShared 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Mandelbrot actors in the drain
+// ---------------------------------------------------------------------------
+// Claim a Mandelbrot actor: take up to 32 messages (as many as there are free
+// job records), copy each message's descriptor into its job and queue the
+// job's bands (kMandelBand pixels each) as work items.
+__device__ __noinline__ void claim_mandel(const DrainParams &P, uint32_t a) {
+    const uint32_t lane = lane_id();
+    DevCtl *ctl = P.ctl;
+    ActorDesc *A = &P.actors[a];
+    if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
+    __syncwarp();
+    const uint64_t head = *((volatile uint64_t *)&A->head);
+    const uint64_t tail = ld_acquire_gpu(&A->tail);
+    const uint64_t avail = tail - head;
+    uint32_t want = avail < 32 ? (uint32_t)avail : 32u;
+    if (P.max_claim && P.max_claim < want) want = P.max_claim;
+    if (lane == 0) add_u64(&ctl->claims, 1);
+    // a record per message, reserved before the dequeue so a claim never waits for one
+    uint32_t j = kNone;
+    bool got = false;
+    if (lane < want) {
+        const int pr = q_try_pop(&ctl->mjobq, P.mjobq, &j, P.wait_limit_ns);
+        if (pr < 0) fail(P, kErrWaitQueue, 25);
+        got = pr > 0;
+    }
+    const uint32_t okm = __ballot_sync(FULL, got);
+    const uint32_t nj = (okm == FULL) ? 32u : (uint32_t)(__ffs(~okm) - 1);
+    MsgData m{};
+    const uint32_t take = nj ? warp_dequeue(P, a, head, nj, m) : 0u;
+    if (got && lane >= take) {
+        if (!q_push(&ctl->mjobq, P.mjobq, j, P.wait_limit_ns)) fail(P, kErrWaitQueue, 26);
+        got = false;
+    }
+    release_actor(P, a, head + take);
+    uint32_t bands = 0;
+    bool valid = false;
+    if (lane < take) {
+        const MandelDesc *dp = reinterpret_cast<const MandelDesc *>(m.payload);
+        MandelDesc d{};
+        if (dp) d = *dp;
+        valid = dp && mandel_desc_ok(d);
+        if (valid) {
+            MandelJob *J = &P.mjobs[j];
+            J->d = d;
+            bands = (d.width * d.rows + kMandelBand - 1) / kMandelBand;
+            J->bands = bands;
+            J->done = 0;
+            J->sum = 0;
+            J->reply_addr = m.reply_addr;
+            J->reply_token = m.reply_token;
+        } else {
+            write_reply(m.reply_addr, 3, 0, 0, m.tag, m.reply_token);
+            if (!q_push(&ctl->mjobq, P.mjobq, j, P.wait_limit_ns)) fail(P, kErrWaitQueue, 26);
+        }
+    }
+    const uint32_t bad = __popc(__ballot_sync(FULL, lane < take && !valid));
+    if (lane == 0 && bad) {
+        __threadfence();
+        add_u64(&ctl->completed, bad);
+    }
+    __threadfence();
+    for (uint32_t i = 0; i < take; ++i) {
+        const uint32_t bi = __shfl_sync(FULL, bands, i);
+        const uint32_t ji = __shfl_sync(FULL, j, i);
+        if (!bi) continue;
+        if (!q_push_block(P, &ctl->workq, P.workq, (ji << 16) | kMandelItemFlag, bi)) return;
+    }
+}
+
+// Item i of a round's `mine` (registers; no dynamic indexing).
+__device__ __forceinline__ uint32_t pick_item(const uint32_t (&mine)[kMaxItemsPerRound], uint32_t i) {
+    uint32_t v = mine[0];
+#pragma unroll
+    for (uint32_t k = 1; k < kMaxItemsPerRound; ++k)
+        if (k == i) v = mine[k];
+    return v;
+}
+
+// Run `count` Mandelbrot band items with the whole CTA as one pool of 32-pixel
+// groups: each warp takes the next group from a shared counter (so slow and
+// fast regions even out), lane l computes pixel 32 g + l of its band.  Then,
+// per band, thread 0 adds the band's count sum to its job, and the CTA that
+// finishes a job's last band writes the reply (pixels, sum of the counts) and
+// frees the record.  G.mnext and G.msum are zero on entry; thread 0 zeroes them
+// again after the closing barrier, before it reaches the next round's.
+__device__ __noinline__ void drain_mandel_bands(const DrainParams &P, GroupShared &G, const uint32_t *items,
+                                                uint32_t count, uint32_t bar_threads) {
+    constexpr uint32_t kGroups = kMandelBand / 32;
+    const uint32_t lane = lane_id();
+    uint32_t mine[kMaxItemsPerRound];
+#pragma unroll
+    for (uint32_t i = 0; i < kMaxItemsPerRound; ++i) mine[i] = i < count ? items[i] : 0u;
+    const uint32_t total = count * kGroups;
+    uint32_t cur = kNone;                  // band whose descriptor is in registers
+    uint32_t base = 0;                     // its first pixel
+    MandelDesc d{};
+    uint32_t pixels = 0;
+    unsigned long long acc = 0;            // this lane's count sum for band `cur`
+    for (;;) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(&G.mnext, 1u);
+        g = __shfl_sync(FULL, g, 0);
+        const uint32_t b = g < total ? g / kGroups : kNone;
+        if (b != cur) {
+            if (cur != kNone) {
+                const unsigned long long s = warp_sum_u64(acc);
+                if (lane == 0 && s) atomicAdd(&G.msum[cur], s);
+            }
+            acc = 0;
+            cur = b;
+            if (b == kNone) break;
+            const uint32_t it = pick_item(mine, b);
+            d = P.mjobs[it >> 16].d;
+            pixels = d.width * d.rows;
+            base = (it & (kMandelItemFlag - 1u)) * kMandelBand;
+        }
+        // long bands (max_iter up to 65536) keep the stall detector fed
+        if (lane == 0 && (g & 15u) == 0) heartbeat(P);
+        const uint32_t p = base + (g % kGroups) * 32u + lane;
+        if (p < pixels) {
+            float cx, cy;
+            mandel_c(d, p, cx, cy);
+            const uint32_t k = mandel_count(cx, cy, d.max_iter);
+            reinterpret_cast<uint32_t *>(d.out)[p] = k;
+            acc += k;
+        }
+    }
+    named_bar_sync(1, bar_threads);
+    if (threadIdx.x == 0) {
+        heartbeat(P);
+        __threadfence();   // the CTA's pixel stores before the band counts
+#pragma unroll
+        for (uint32_t i = 0; i < kMaxItemsPerRound; ++i) {
+            if (i >= count) break;
+            const uint32_t j = mine[i] >> 16;
+            MandelJob *J = &P.mjobs[j];
+            atomicAdd(reinterpret_cast<unsigned long long *>(&J->sum), G.msum[i]);
+            G.msum[i] = 0;
+            __threadfence();
+            if (atomicAdd(reinterpret_cast<unsigned int *>(&J->done), 1u) == J->bands - 1) {
+                __threadfence();
+                const uint64_t sum = atomicAdd(reinterpret_cast<unsigned long long *>(&J->sum), 0ull);
+                write_reply(J->reply_addr, 0, (uint64_t)J->d.width * J->d.rows, sum, 0, J->reply_token);
+                __threadfence();
+                add_u64(&P.ctl->messages, 1);
+                add_u64(&P.ctl->completed, 1);
+                if (!q_push(&P.ctl->mjobq, P.mjobq, j, P.wait_limit_ns)) fail(P, kErrWaitQueue, 27);
+            }
+        }
+        G.mnext = 0;
+    }
+}
+
 // A team leader looks for a factor batch to sweep: pop ready actors, claim
 // factor actors into a fresh batch record, and run ring-token actors on the
 // way (a few at most, so the group forms quickly).
@@ -1060,6 +1216,8 @@ __device__ uint32_t find_batch(const DrainParams &P) {
             run_source(P, a);
         } else if (kGemm && (kind == kGemmBf16 || kind == kGemmSplit)) {
             claim_gemm(P, a);
+        } else if (kGemm && kind == kMandel) {
+            claim_mandel(P, a);
         }
         if (exit_requested(ctl)) return kNone;
     }
@@ -1131,6 +1289,8 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
             mbar_init(&G.empty[i], n_cons);
         }
         fence_barrier_init();
+        G.mnext = 0;
+        for (uint32_t i = 0; i < kMaxItemsPerRound; ++i) G.msum[i] = 0;
     }
     if constexpr (kGemm) {
         if (producer) gemm_bars_init(G.gb, kPackTmemCols);   // GEMM barriers + tensor memory (warp-wide)
@@ -1210,13 +1370,21 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
             if (ni) {
                 // GEMM items first: short, and other CTAs may wait on the same job
                 for (uint32_t i = 0; i < ni;) {
-                    if (G.items[i] & kPackItemFlag) {
-                        drain_gemm_pack(P, gslots, G.items[i], bar_threads);
+                    const uint32_t it = G.items[i];
+                    if (it & kPackItemFlag) {
+                        drain_gemm_pack(P, gslots, it, bar_threads);
                         ++i;
+                    } else if (it & kMandelItemFlag) {
+                        // Mandelbrot bands: the round's bands are one pool
+                        // (the queue order puts a job's bands together)
+                        uint32_t e = i + 1;
+                        while (e < ni && (G.items[e] & kMandelItemFlag) && !(G.items[e] & kPackItemFlag)) ++e;
+                        drain_mandel_bands(P, G, &G.items[i], e - i, bar_threads);
+                        i = e;
                     } else {
                         // consecutive tiles run as one pipeline
                         uint32_t e = i + 1;
-                        while (e < ni && !(G.items[e] & kPackItemFlag)) ++e;
+                        while (e < ni && !(G.items[e] & (kPackItemFlag | kMandelItemFlag))) ++e;
                         drain_gemm_tiles(P, G, gslots, &G.items[i], e - i, gk, bar_threads);
                         i = e;
                     }

@@ -33,6 +33,10 @@ cudaError_t launch_gemm_one(const float *A, const float *B, float *C, uint32_t n
 int gemm_encode_tmap(void *out128, const void *base, uint32_t n, bool is_a);
 // A and B can be staged through tensor maps (n % 4 == 0, 16-byte aligned).
 bool gemm_tma_ok(const void *A, const void *B, uint32_t n);
+// One Mandelbrot message (per-message backend): one thread per pixel; sum and
+// blocks_done are scratch words, zero at rest and left zero.
+cudaError_t launch_mandel_one(const MandelDesc &d, uint64_t reply_addr, uint32_t reply_token,
+                              unsigned long long *sum, uint32_t *blocks_done, DevCtl *ctl, cudaStream_t stream);
 cudaError_t launch_debug_wait(const uint32_t *flag, uint64_t limit_ns, DevCtl *ctl, HostCtl *hctl,
                               cudaStream_t stream);
 // Prime table of the odd primes <= limit.  Allocates *primes/*pinv/*plim

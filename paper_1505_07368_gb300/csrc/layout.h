@@ -9,6 +9,7 @@
 //                     ring of them starting at ActorDesc::slot_base
 //   QCell[...]        ready queue (actor ids), free-batch queue, work queue
 //   FactorBatch[B]    messages swept together against the prime table
+//   GemmJob[272], MandelJob[256]   GEMM / Mandelbrot messages in the drain
 //   uint32_t x 3 x P  prime table: odd primes, their inverses mod 2^32 and
 //                     floor((2^32-1)/p), structure-of-arrays
 //   LogRow[L]         validation-mode handling log
@@ -81,6 +82,8 @@ struct GroupShared {
     uint32_t exit;
     uint32_t items[kMaxItemsPerRound];   // GEMM work items this CTA runs next
     uint32_t nitems;
+    uint32_t mnext;                      // Mandelbrot bands: next 32-pixel group of the round
+    unsigned long long msum[kMaxItemsPerRound];   // Mandelbrot bands: escape counts summed
 };
 constexpr uint32_t kDrainHeader = 1024;
 static_assert(sizeof(GroupShared) <= kDrainHeader, "drain header fits");
@@ -123,11 +126,41 @@ struct GemmDesc {
     uint32_t pad;
 };
 
+// Mandelbrot image job (the OpenCL actor experiment of Sec. 5): the pixels of
+// rows row0 .. row0+rows-1 of an image `width` wide, pixel (i, j) at
+// c = (x0 + i dx) + (y0 + j dy) i; out[(j - row0) * width + i] = its escape
+// count.  Same layout as caf_gpu_mandel_desc (40 bytes).
+struct MandelDesc {
+    uint64_t out;                  // uint32_t counts (device)
+    uint32_t width, rows, row0, max_iter;
+    float x0, y0, dx, dy;
+};
+static_assert(sizeof(MandelDesc) == 40, "MandelDesc is 40 bytes");
+constexpr uint32_t kMandelBand = 8192;               // pixels per band work item
+constexpr uint32_t kMandelMaxPixels = 1u << 24;      // per message: <= 2048 bands
+constexpr uint32_t kMandelMaxIter = 1u << 16;        // a band stays well inside the stall limit
+constexpr uint32_t kMandelMaxCoord = 1u << 24;       // width and row0 + rows: exact as float32
+constexpr uint32_t kMandelJobs = 256;                // Mandelbrot messages in flight in the drain
+constexpr uint32_t kMandelItemFlag = 0x4000u;        // work item: band (job << 16 | flag | band)
+
+// A Mandelbrot message being computed by the drain: its bands are items in
+// the work queue; the CTA that finishes the last one replies.
+struct alignas(64) MandelJob {
+    MandelDesc d;
+    uint32_t bands;                // band items of the job
+    uint32_t done;                 // bands finished (atomic)
+    uint64_t sum;                  // escape counts summed so far (atomic)
+    uint64_t reply_addr;
+    uint32_t reply_token;
+    uint32_t pad;
+};
+static_assert(sizeof(MandelJob) == 128, "MandelJob is 128 bytes");
+
 // actor lifecycle (Sec. 6: ready / waiting / running / done)
 enum : uint32_t { kWaiting = 0, kReady = 1, kRunning = 2, kDone = 3 };
 
 // kinds (mirror caf_gpu.h)
-enum : uint32_t { kFactor = 1, kGemmBf16 = 2, kGemmSplit = 3, kToken = 4, kSink = 5, kSource = 6 };
+enum : uint32_t { kFactor = 1, kGemmBf16 = 2, kGemmSplit = 3, kToken = 4, kSink = 5, kSource = 6, kMandel = 7 };
 enum : uint32_t { kMsgStart = 1 };
 enum : uint32_t { kActorMaster = 1 };
 
@@ -280,6 +313,7 @@ struct DevCtl {
     QueueHdr packq;                // GEMM pack items
     QueueHdr jobq;                 // free GemmJob records, small scratch class
     QueueHdr jobq_large;           // free GemmJob records, large scratch class
+    QueueHdr mjobq;                // free MandelJob records
 };
 
 // Host-visible control block (pinned, mapped).
@@ -335,6 +369,9 @@ struct DrainParams {
     uint8_t *pack_large;           // kGemmJobsLarge x kPackLargeBytes (record kGemmJobsSmall + i: i-th)
     uint32_t gemm;
     uint32_t pad1;
+    // Mandelbrot actors (run by the drain with the GEMM layout)
+    MandelJob *mjobs;
+    QCell *mjobq;
 };
 
 }  // namespace cafgpu

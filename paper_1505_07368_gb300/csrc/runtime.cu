@@ -18,6 +18,7 @@
 #include "../../include/caf_gpu.h"
 #include "kernels.h"
 #include "layout.h"
+#include "mandel.cuh"
 
 using namespace cafgpu;
 
@@ -65,6 +66,8 @@ struct caf_gpu_runtime {
     FactorBatch *d_batches = nullptr;
     uint32_t n_batches = 0;
     GemmJob *d_jobs = nullptr;
+    MandelJob *d_mjobs = nullptr;
+    QCell *d_mjobq = nullptr;
     QCell *d_jobq = nullptr, *d_jobq_large = nullptr;
     uint32_t jobq_cap = 0;
     uint8_t *d_pack_small = nullptr, *d_pack_large = nullptr;   // packed-operand scratch of the job records
@@ -86,6 +89,7 @@ struct caf_gpu_runtime {
     HostCtl *hctl = nullptr;
     Reply *replies = nullptr;
     GemmDesc *gemm_descs = nullptr;        // one per reply slot (host GEMM requests)
+    MandelDesc *mandel_descs = nullptr;    // one per reply slot (host Mandelbrot requests)
     IngressEntry *outbox = nullptr;
     uint32_t outbox_per_msg = 4;
     uint32_t outbox_msgs = 256;
@@ -153,6 +157,8 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.jobs = rt->d_jobs;
     p.jobq = rt->d_jobq;
     p.jobq_large = rt->d_jobq_large;
+    p.mjobs = rt->d_mjobs;
+    p.mjobq = rt->d_mjobq;
     p.pack_small = rt->d_pack_small;
     p.pack_large = rt->d_pack_large;
     p.gemm = rt->gemm_enabled ? 1u : 0u;
@@ -226,6 +232,11 @@ int check_msg(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *m, uint3
     }
     if ((m->kind == kSink || m->kind == kSource) && rt->backend != CAF_GPU_BACKEND_PERSISTENT)
         return CAF_GPU_EINVAL;
+    if (m->kind == kMandel) {
+        // the descriptor is read (copied) at the call
+        if (!m->u64) return CAF_GPU_EINVAL;
+        if (!mandel_desc_ok(*reinterpret_cast<const MandelDesc *>(m->u64))) return CAF_GPU_EINVAL;
+    }
     if (m->kind == kSource && m->u64 > 0xFFFFFFFFull) return CAF_GPU_EINVAL;
     if (m->kind == kToken) {
         uint32_t state = 0;
@@ -296,8 +307,22 @@ int submit_locked(caf_gpu_runtime *rt, uint32_t a, const caf_gpu_msg *m, uint64_
         rt->launches += 1;
         return 0;
     }
+    if (rt->backend == CAF_GPU_BACKEND_PER_MESSAGE_LAUNCH && m->kind == kMandel) {
+        const MandelDesc d = *reinterpret_cast<const MandelDesc *>(m->u64);
+        CK(launch_mandel_one(d, reply_addr, token, reinterpret_cast<unsigned long long *>(rt->d_scratch + 4),
+                             rt->d_scratch + 6, rt->d_ctl, rt->stream));
+        rt->launches += 1;
+        return 0;
+    }
     IngressEntry e{};
     uint64_t payload = m->u64;
+    if (m->kind == kMandel) {
+        if (!reply_addr) return CAF_GPU_EINVAL;
+        const size_t slot = (size_t)((reinterpret_cast<Reply *>(reply_addr)) - rt->replies);
+        MandelDesc *d = &rt->mandel_descs[slot];
+        *d = *reinterpret_cast<const MandelDesc *>(m->u64);
+        payload = (uint64_t)d;
+    }
     if (m->kind == kGemmBf16 || m->kind == kGemmSplit) {
         // the drain reads the operands through a descriptor kept with the reply slot
         if (!reply_addr) return CAF_GPU_EINVAL;
@@ -377,9 +402,12 @@ void free_runtime(caf_gpu_runtime *rt) {
     cudaFree(rt->d_jobs);
     cudaFree(rt->d_jobq);
     cudaFree(rt->d_jobq_large);
+    cudaFree(rt->d_mjobq);
+    cudaFree(rt->d_mjobs);
     cudaFree(rt->d_pack_small);
     cudaFree(rt->d_pack_large);
     if (rt->gemm_descs) cudaFreeHost(rt->gemm_descs);
+    if (rt->mandel_descs) cudaFreeHost(rt->mandel_descs);
     cudaFree(rt->d_primes);
     cudaFree(rt->d_pinv);
     cudaFree(rt->d_plim);
@@ -456,7 +484,8 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     rt->freeq_cap = next_pow2((uint64_t)rt->n_batches + 1);
     // every job's tiles, or its pack items, can be queued at once
     rt->workq_cap = next_pow2((uint64_t)kGemmJobsSmall * (kPackSmallMaxN / 128) * (kPackSmallMaxN / 128) +
-                              (uint64_t)kGemmJobsLarge * (kMaxDrainGemmN / 128) * (kMaxDrainGemmN / 128) + 1);
+                              (uint64_t)kGemmJobsLarge * (kMaxDrainGemmN / 128) * (kMaxDrainGemmN / 128) +
+                              (uint64_t)kMandelJobs * (kMandelMaxPixels / kMandelBand) + 1);
     rt->jobq_cap = next_pow2((uint64_t)kGemmJobs + 1);
     std::vector<uint32_t> none, all(rt->n_batches);
     for (uint32_t i = 0; i < rt->n_batches; ++i) all[i] = i;
@@ -474,6 +503,11 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     if ((r = init_queue(rt, &rt->d_jobq_large, rt->jobq_cap, &rt->d_ctl->jobq_large, jobs_large))) return r;
     CK(cudaMalloc(&rt->d_jobs, sizeof(GemmJob) * kGemmJobs));
     CK(cudaMemset(rt->d_jobs, 0, sizeof(GemmJob) * kGemmJobs));
+    std::vector<uint32_t> mjobs(kMandelJobs);
+    for (uint32_t i = 0; i < kMandelJobs; ++i) mjobs[i] = i;
+    if ((r = init_queue(rt, &rt->d_mjobq, next_pow2((uint64_t)kMandelJobs + 1), &rt->d_ctl->mjobq, mjobs))) return r;
+    CK(cudaMalloc(&rt->d_mjobs, sizeof(MandelJob) * kMandelJobs));
+    CK(cudaMemset(rt->d_mjobs, 0, sizeof(MandelJob) * kMandelJobs));
     if (c.validation_mode) {
         CK(cudaMalloc(&rt->d_log, sizeof(LogRow) * (size_t)c.log_capacity));
         CK(cudaMemset(rt->d_log, 0, sizeof(LogRow) * (size_t)c.log_capacity));
@@ -503,6 +537,8 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     memset(rt->replies, 0, sizeof(Reply) * (size_t)c.max_inflight_requests);
     CK(cudaHostAlloc(&rt->gemm_descs, sizeof(GemmDesc) * (size_t)c.max_inflight_requests, cudaHostAllocMapped));
     memset(rt->gemm_descs, 0, sizeof(GemmDesc) * (size_t)c.max_inflight_requests);
+    CK(cudaHostAlloc(&rt->mandel_descs, sizeof(MandelDesc) * (size_t)c.max_inflight_requests, cudaHostAllocMapped));
+    memset(rt->mandel_descs, 0, sizeof(MandelDesc) * (size_t)c.max_inflight_requests);
     CK(cudaHostAlloc(&rt->outbox, sizeof(IngressEntry) * rt->outbox_per_msg * rt->outbox_msgs,
                      cudaHostAllocMapped));
     memset(rt->outbox, 0, sizeof(IngressEntry) * rt->outbox_per_msg * rt->outbox_msgs);
@@ -574,14 +610,19 @@ int caf_gpu_runtime_destroy(caf_gpu_runtime *rt) {
 
 int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_cfg *cfg, caf_gpu_actor *out) {
     if (!rt || !out) return CAF_GPU_EINVAL;
-    if (kernel_id < kFactor || kernel_id > kSource) return CAF_GPU_EINVAL;
-    if ((kernel_id == kGemmBf16 || kernel_id == kGemmSplit) && !rt->gemm_enabled) {
-        // drains launched from now on carry tensor memory and the GEMM layout,
-        // and GEMM jobs need their packed-operand scratch
+    if (kernel_id < kFactor || kernel_id > kMandel) return CAF_GPU_EINVAL;
+    const bool gemm_kind = kernel_id == kGemmBf16 || kernel_id == kGemmSplit;
+    if ((gemm_kind && !rt->d_pack_small) || (kernel_id == kMandel && !rt->gemm_enabled)) {
+        // Drains launched from now on carry the work-item layout (tensor
+        // memory, GEMM and Mandelbrot items), and GEMM jobs need their
+        // packed-operand scratch.  Sync first: it stops the running drain, so
+        // no drain holds parameters without the scratch.  The scratch is
+        // keyed on its own pointer, not on the layout flag, which a
+        // MANDELBROT actor may have set first.
         int r = caf_gpu_sync(rt);
         if (r) return r;
         std::lock_guard<std::mutex> g(rt->mu);
-        if (!rt->d_pack_small) {
+        if (gemm_kind && !rt->d_pack_small) {
             if (cudaMalloc(&rt->d_pack_small, kPackSmallBytes * kGemmJobsSmall) != cudaSuccess) {
                 cudaGetLastError();
                 rt->d_pack_small = nullptr;
@@ -644,7 +685,8 @@ int caf_gpu_send(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *msg) 
     uint32_t a;
     int r = check_msg(rt, to, msg, &a);
     if (r) return r;
-    if (msg->kind == kGemmBf16 || msg->kind == kGemmSplit) return CAF_GPU_EINVAL;  // a GEMM needs a reply
+    // a GEMM or Mandelbrot message needs a reply: its descriptor lives in the reply slot
+    if (msg->kind == kGemmBf16 || msg->kind == kGemmSplit || msg->kind == kMandel) return CAF_GPU_EINVAL;
     {
         std::lock_guard<std::mutex> g(rt->mu);
         r = submit_locked(rt, a, msg, 0, 0);

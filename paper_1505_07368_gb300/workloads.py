@@ -29,7 +29,10 @@ restated for a single GPU:
   worker per ring, semiprimes with factors in [2^30, 2^31);
 * ``config5``: open-loop Poisson arrivals, 70 % factorization
   (log-uniform factors in [2^16, 2^31)) and 30 % split-BF16x3 GEMM
-  (n log-uniform in [32, 2048]).
+  (n log-uniform in [32, 2048]);
+* ``mandel_image`` / ``mandel_slices``: the geometry of the OpenCL actor
+  experiment's Mandelbrot image (1920 x 1080 pixels over the cut
+  [-0.5 - 0.7375i, 0.1 - 0.1375i]) and its split into row slices.
 """
 from __future__ import annotations
 
@@ -428,3 +431,23 @@ def integer_matrix(key, n: int, lo: int = -8, hi: int = 8) -> np.ndarray:
     """n x n float32 matrix of integers in [lo, hi] (exact in BF16)."""
     v = bounded(key, 0, n * n, 0, hi - lo + 1).astype(np.int64) + lo
     return v.astype(np.float32).reshape(n, n)
+
+
+# ---- the OpenCL actor experiment (Sec. 5, "Integrating OpenCL Actors") ----
+MANDEL_WIDTH, MANDEL_HEIGHT = 1920, 1080
+MANDEL_AREA = (-0.5, -0.7375, 0.1, -0.1375)      # (re min, im min, re max, im max)
+MANDEL_ITERS = (120, 1200)                       # the small and the large problem
+
+
+def mandel_image(width: int = MANDEL_WIDTH, height: int = MANDEL_HEIGHT, area=MANDEL_AREA):
+    """(x0, y0, dx, dy) as float32 values: pixel (i, j) lies at c = (x0 + i dx) + (y0 + j dy) i,
+    so the `width` x `height` pixels tile `area` from its lower-left corner."""
+    re0, im0, re1, im1 = area
+    f = np.float32
+    return f(re0), f(im0), f((re1 - re0) / width), f((im1 - im0) / height)
+
+
+def mandel_slices(height: int, parts: int):
+    """Split rows 0 .. height-1 into `parts` contiguous slices of near-equal size: [(row0, rows)]."""
+    edges = [(height * k) // parts for k in range(parts + 1)]
+    return [(edges[k], edges[k + 1] - edges[k]) for k in range(parts) if edges[k + 1] > edges[k]]

@@ -35,6 +35,8 @@ def test_struct_sizes():
     assert cafgpu.DMSG_DTYPE.itemsize == 32
     assert cafgpu.DREPLY_DTYPE.itemsize == 32
     assert cafgpu.GEMM_DESC_DTYPE.itemsize == 32
+    assert cafgpu.MANDEL_DESC_DTYPE.itemsize == 40
+    assert ctypes.sizeof(cafgpu.MandelDesc) == 40
     assert cafgpu.LOG_DTYPE.itemsize == 40
     assert cafgpu.SERVE_REQ_DTYPE.itemsize == 48
     assert cafgpu.SERVE_RESULT_DTYPE.itemsize == 48
