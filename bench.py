@@ -772,9 +772,11 @@ FP32_LANES_PER_SM = 128
 def run_mandel(args):
     """Mandelbrot actors (the OpenCL actor experiment, Sec. 5): the 1920 x 1080
     image of [-0.5 - 0.7375i, 0.1 - 0.1375i] at 120 and at 1200 iterations, sent
-    to one MANDELBROT actor as whole-image messages (100 per step, the paper's
-    100 runs) and as one message per row (10 images, 10,800 messages per step);
-    persistent drain against one kernel launch per message."""
+    as whole-image messages to one MANDELBROT actor (100 per step, the paper's
+    100 runs), and as one message per row to one actor per row (1080 actors,
+    10 images, 10,800 messages per step -- the one-actor-per-row split of the
+    paper's CPU Mandelbrot benchmark); persistent drain against one kernel
+    launch per message."""
     import torch
 
     import oracle
@@ -802,10 +804,13 @@ def run_mandel(args):
             d_desc = torch.from_numpy(desc.view(np.uint8).copy()).cuda()
             label = f"iter{max_iter}_{shape}"
             _note(f"mandel {label}: {count} messages")
-            with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=1, mailbox_capacity=1 << 14) as rt:
-                a = rt.spawn(C.MANDELBROT)
+            n_act = per_image                     # one actor per slice: 1 (whole images) or 1080 (rows)
+            cap = 128 if n_act == 1 else 16
+            with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=n_act, mailbox_capacity=cap) as rt:
+                acts = np.array([rt.spawn(C.MANDELBROT) for _ in range(n_act)], np.uint64)
+                actor_of = acts[np.tile(np.arange(per_image), images)]
                 m = np.zeros(count, C.DMSG_DTYPE)
-                m["actor"] = a - 1
+                m["actor"] = actor_of - 1
                 m["kind"] = C.MANDELBROT
                 m["u64"] = d_desc.data_ptr() + np.arange(count, dtype=np.uint64) * C.MANDEL_DESC_DTYPE.itemsize
                 m["sender_seq"] = np.arange(count)
@@ -845,7 +850,8 @@ def run_mandel(args):
                 lat = (rep_["t_done"].astype(np.int64) - np.int64(st["t_mark"])) / 1e6
                 t = float(np.mean(times))
                 ops = FP32_OPS_PER_ITER * float(counts_sum) * images
-                v = {"messages": count, "images": images, "ms_per_step": 1e3 * t, "msgs_per_s": count / t,
+                v = {"messages": count, "actors": n_act, "images": images, "ms_per_step": 1e3 * t,
+                     "msgs_per_s": count / t,
                      "images_per_s": images / t, "mpix_per_s": images * Wd * Hd / t / 1e6,
                      "mean_iterations": counts_sum / (Wd * Hd),
                      "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
@@ -857,7 +863,7 @@ def run_mandel(args):
                     msgs = (C.Msg * count)()
                     for i in range(count):
                         msgs[i] = C.Runtime.mandel_msg(ds[i], tag=i)
-                    actors = np.full(count, a, np.uint64)
+                    actors = actor_of
                     rt.await_batch(rt.request_batch(actors[:per_image], msgs), timeout_ns=AWAIT_NS)   # warm-up
                     pm = []
                     for _ in range(max(1, min(args.steps, 3))):

@@ -830,6 +830,59 @@ __device__ bool q_push_block(const DrainParams &P, QueueHdr *q, QCell *cells, ui
     return true;
 }
 
+// Warp-collective push of a run of items per lane: lane i pushes base_i | k
+// for k < count_i, lanes in lane order, all positions reserved with one
+// atomic add.  Position idx of the total belongs to the largest lane whose
+// exclusive prefix is <= idx (found by a binary search over the lanes).
+__device__ bool q_push_runs(const DrainParams &P, QueueHdr *q, QCell *cells, uint32_t base, uint32_t count) {
+    const uint32_t lane = lane_id();
+    uint32_t incl = count;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= (uint32_t)o) incl += v;
+    }
+    const uint32_t excl = incl - count;
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    if (total == 0) return true;
+    uint64_t pos0 = 0;
+    if (lane == 0) pos0 = add_u64(&q->enq, total);
+    pos0 = __shfl_sync(FULL, pos0, 0);
+    bool ok = true;
+    for (uint32_t at = 0; at < total; at += 32) {
+        const uint32_t idx = at + lane;
+        uint32_t o = 0;
+#pragma unroll
+        for (uint32_t step = 16; step; step >>= 1) {
+            const uint32_t cand = o + step;
+            const uint32_t e = __shfl_sync(FULL, excl, cand & 31u);
+            if (cand < 32 && e <= idx) o = cand;
+        }
+        const uint32_t ob = __shfl_sync(FULL, base, o);
+        const uint32_t oe = __shfl_sync(FULL, excl, o);
+        if (idx < total && ok) {
+            const uint64_t pos = pos0 + idx;
+            QCell *c = &cells[pos & q->mask];
+            if (ld_acquire_gpu(&c->seq) != pos) {
+                WaitClock w(P.wait_limit_ns);
+                while (ld_acquire_gpu(&c->seq) != pos) {
+                    if (!w.again()) { ok = false; break; }
+                }
+            }
+            if (ok) {
+                c->val = ob | (idx - oe);
+                st_release_gpu(&c->seq, pos + 1);
+            }
+        }
+    }
+    if (!__all_sync(FULL, ok)) {
+        if (lane == 0) fail(P, kErrWaitQueue, 28, total, base);
+        return false;
+    }
+    if (lane == 0) q_avail_add(q, total);
+    return true;
+}
+
 // Job record j's queue and packed-operand scratch.
 __device__ __forceinline__ bool job_small(uint32_t j) { return j < kGemmJobsSmall; }
 __device__ __forceinline__ uint8_t *job_scratch(const DrainParams &P, uint32_t j) {
@@ -1080,12 +1133,7 @@ __device__ __noinline__ void claim_mandel(const DrainParams &P, uint32_t a) {
         add_u64(&ctl->completed, bad);
     }
     __threadfence();
-    for (uint32_t i = 0; i < take; ++i) {
-        const uint32_t bi = __shfl_sync(FULL, bands, i);
-        const uint32_t ji = __shfl_sync(FULL, j, i);
-        if (!bi) continue;
-        if (!q_push_block(P, &ctl->workq, P.workq, (ji << 16) | kMandelItemFlag, bi)) return;
-    }
+    q_push_runs(P, &ctl->workq, P.workq, (j << 16) | kMandelItemFlag, bands);
 }
 
 // Item i of a round's `mine` (registers; no dynamic indexing).
@@ -1216,7 +1264,7 @@ __device__ uint32_t find_batch(const DrainParams &P) {
             run_source(P, a);
         } else if (kGemm && (kind == kGemmBf16 || kind == kGemmSplit)) {
             claim_gemm(P, a);
-        } else if (kGemm && kind == kMandel) {
+        } else if (kind == kMandel) {
             claim_mandel(P, a);
         }
         if (exit_requested(ctl)) return kNone;
@@ -1319,13 +1367,16 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
     GemmCounters gk{0, 0, 0, 0};
     uint64_t seen_completed = 0, seen_at = 0;   // completion watchdog (producer lane)
     uint32_t rounds = 0;
-    const bool gemm_cta = kGemm && !live0;
+    // work items (GEMM packs and tiles, Mandelbrot bands): the GEMM layout runs
+    // all three; without it (no GEMM actor) only Mandelbrot bands exist
+    const bool item_cta = (kGemm || P.mandel) && !live0;
     for (;;) {
         // ---- form a group: team leaders claim actors (skipped while the GEMM
         // tile queue already holds plenty of work for every CTA)
         if (!producer && team_ok && rank == 0 && held == kNone) {
             bool skip = false;
-            if (kGemm && lane == 0) skip = q_len(&ctl->workq) + q_len(&ctl->packq) > 2 * (int64_t)gridDim.x;
+            if ((kGemm || P.mandel) && lane == 0)
+                skip = q_len(&ctl->workq) + q_len(&ctl->packq) > 2 * (int64_t)gridDim.x;
             if (!__shfl_sync(FULL, skip, 0)) held = find_batch<kGemm>(P);
         }
         if (!producer && lane == 0) G.batch[ci] = (team_ok && rank == 0) ? held : kNone;
@@ -1337,9 +1388,18 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
             // lanes (one pop's latency); tiles first, so a job's tiles run
             // while its packed operands are still in L2
             uint32_t item = kNone;
-            if (gemm_cta && !ex && lane < P.gemm_items) {
+            // with fewer items queued than CTAs, each CTA tries one pop, so
+            // hundreds of producers do not all reserve (and undo) the last items
+            uint32_t npop = 0;
+            if (item_cta && !ex) {
+                int64_t av = 0;
+                if (lane == 0) av = q_len(&ctl->workq) + (kGemm ? q_len(&ctl->packq) : 0);
+                av = __shfl_sync(FULL, av, 0);
+                npop = av >= (int64_t)gridDim.x ? P.gemm_items : (av > 0 ? 1u : 0u);
+            }
+            if (lane < npop) {
                 int pr = q_try_pop(&ctl->workq, P.workq, &item, P.wait_limit_ns);
-                if (pr == 0) pr = q_try_pop(&ctl->packq, P.packq, &item, P.wait_limit_ns);
+                if (kGemm && pr == 0) pr = q_try_pop(&ctl->packq, P.packq, &item, P.wait_limit_ns);
                 if (pr < 0) fail(P, kErrWaitQueue, 24);
                 if (pr <= 0) item = kNone;
             }
@@ -1365,10 +1425,12 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
         }
         named_bar_sync(1, bar_threads);
         if (G.exit) break;
-        if constexpr (kGemm) {
-            const uint32_t ni = G.nitems;
-            if (ni) {
-                // GEMM items first: short, and other CTAs may wait on the same job
+        if (const uint32_t ni = G.nitems) {
+            // items first: short, and other CTAs may wait on the same job
+            if constexpr (!kGemm) {
+                // only Mandelbrot bands exist without the GEMM layout
+                drain_mandel_bands(P, G, &G.items[0], ni, bar_threads);
+            } else {
                 for (uint32_t i = 0; i < ni;) {
                     const uint32_t it = G.items[i];
                     if (it & kPackItemFlag) {
@@ -1389,10 +1451,10 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
                         i = e;
                     }
                 }
-                idle = false;
-                idle_ns = 256;
-                continue;
             }
+            idle = false;
+            idle_ns = 256;
+            continue;
         }
         uint32_t mine = kNone;
         if (!producer) mine = team_ok ? G.batch[team * wpb] : kNone;

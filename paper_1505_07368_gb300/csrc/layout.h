@@ -368,8 +368,8 @@ struct DrainParams {
     uint8_t *pack_small;           // kGemmJobsSmall x kPackSmallBytes (record j: j-th block)
     uint8_t *pack_large;           // kGemmJobsLarge x kPackLargeBytes (record kGemmJobsSmall + i: i-th)
     uint32_t gemm;
-    uint32_t pad1;
-    // Mandelbrot actors (run by the drain with the GEMM layout)
+    uint32_t mandel;               // Mandelbrot actors exist: every drain runs work items
+    // Mandelbrot job records
     MandelJob *mjobs;
     QCell *mjobq;
 };

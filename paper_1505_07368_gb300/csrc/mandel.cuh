@@ -29,29 +29,20 @@ namespace cafgpu {
 
 constexpr uint32_t kMandelUnroll = 8;
 
-__device__ __forceinline__ uint32_t mandel_count(float cx, float cy, uint32_t max_iter) {
-    float zr = 0.0f, zi = 0.0f;
-    uint32_t k = 0;
-    while (k + kMandelUnroll <= max_iter) {
-        const float sr = zr, si = zi;
-        bool esc = false;
-#pragma unroll
-        for (uint32_t u = 0; u < kMandelUnroll; ++u) {
-            const float x2 = __fmul_rn(zr, zr);
-            const float y2 = __fmul_rn(zi, zi);
-            esc |= __fadd_rn(x2, y2) > 4.0f;
-            const float xy = __fmul_rn(zr, zi);
-            zi = __fadd_rn(__fadd_rn(xy, xy), cy);
-            zr = __fadd_rn(__fsub_rn(x2, y2), cx);
-        }
-        if (esc) {
-            zr = sr;
-            zi = si;
-            break;
-        }
-        k += kMandelUnroll;
-    }
-    // one update at a time: the block that escaped, or the last max_iter % unroll
+// One update of z with its escape test folded into `esc` (no branch).
+__device__ __forceinline__ void mandel_step(float &zr, float &zi, float cx, float cy, bool &esc) {
+    const float x2 = __fmul_rn(zr, zr);
+    const float y2 = __fmul_rn(zi, zi);
+    esc |= __fadd_rn(x2, y2) > 4.0f;
+    const float xy = __fmul_rn(zr, zi);
+    zi = __fadd_rn(__fadd_rn(xy, xy), cy);
+    zr = __fadd_rn(__fsub_rn(x2, y2), cx);
+}
+
+// The count of c from state z after k updates, testing before each update:
+// used on the block that escaped, and on the last max_iter % unroll updates.
+__device__ __forceinline__ uint32_t mandel_single(float zr, float zi, float cx, float cy, uint32_t k,
+                                                  uint32_t max_iter) {
     while (k < max_iter) {
         const float x2 = __fmul_rn(zr, zr);
         const float y2 = __fmul_rn(zi, zi);
@@ -62,6 +53,24 @@ __device__ __forceinline__ uint32_t mandel_count(float cx, float cy, uint32_t ma
         ++k;
     }
     return k;
+}
+
+__device__ __forceinline__ uint32_t mandel_count(float cx, float cy, uint32_t max_iter) {
+    float zr = 0.0f, zi = 0.0f;
+    uint32_t k = 0;
+    while (k + kMandelUnroll <= max_iter) {
+        const float sr = zr, si = zi;
+        bool esc = false;
+#pragma unroll
+        for (uint32_t u = 0; u < kMandelUnroll; ++u) mandel_step(zr, zi, cx, cy, esc);
+        if (esc) {
+            zr = sr;
+            zi = si;
+            break;
+        }
+        k += kMandelUnroll;
+    }
+    return mandel_single(zr, zi, cx, cy, k, max_iter);
 }
 
 // c of pixel p of a job (row-major over its rows): one rounded product and

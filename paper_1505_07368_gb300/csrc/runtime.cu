@@ -72,6 +72,7 @@ struct caf_gpu_runtime {
     uint32_t jobq_cap = 0;
     uint8_t *d_pack_small = nullptr, *d_pack_large = nullptr;   // packed-operand scratch of the job records
     bool gemm_enabled = false;             // a GEMM actor exists: drains use the GEMM layout
+    bool mandel_enabled = false;           // a MANDELBROT actor exists: drains run work items
     unsigned grid_factor = 0, grid_mixed = 0;
     uint32_t *d_primes = nullptr, *d_pinv = nullptr, *d_plim = nullptr;
     uint32_t nprimes = 0;
@@ -162,6 +163,7 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.pack_small = rt->d_pack_small;
     p.pack_large = rt->d_pack_large;
     p.gemm = rt->gemm_enabled ? 1u : 0u;
+    p.mandel = rt->mandel_enabled ? 1u : 0u;
     return p;
 }
 
@@ -612,16 +614,16 @@ int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_c
     if (!rt || !out) return CAF_GPU_EINVAL;
     if (kernel_id < kFactor || kernel_id > kMandel) return CAF_GPU_EINVAL;
     const bool gemm_kind = kernel_id == kGemmBf16 || kernel_id == kGemmSplit;
-    if ((gemm_kind && !rt->d_pack_small) || (kernel_id == kMandel && !rt->gemm_enabled)) {
-        // Drains launched from now on carry the work-item layout (tensor
-        // memory, GEMM and Mandelbrot items), and GEMM jobs need their
-        // packed-operand scratch.  Sync first: it stops the running drain, so
-        // no drain holds parameters without the scratch.  The scratch is
-        // keyed on its own pointer, not on the layout flag, which a
-        // MANDELBROT actor may have set first.
+    if ((gemm_kind && !rt->gemm_enabled) || (kernel_id == kMandel && !rt->mandel_enabled)) {
+        // GEMM: drains launched from now on carry the GEMM layout (tensor
+        // memory, packs and tiles), and GEMM jobs need their packed-operand
+        // scratch.  MANDELBROT: drains launched from now on run work items
+        // (in either layout).  Sync first: it stops the running drain, so no
+        // drain runs with parameters that predate the actor.
         int r = caf_gpu_sync(rt);
         if (r) return r;
         std::lock_guard<std::mutex> g(rt->mu);
+        if (kernel_id == kMandel) rt->mandel_enabled = true;
         if (gemm_kind && !rt->d_pack_small) {
             if (cudaMalloc(&rt->d_pack_small, kPackSmallBytes * kGemmJobsSmall) != cudaSuccess) {
                 cudaGetLastError();
@@ -635,7 +637,7 @@ int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_c
                 return CAF_GPU_ENOMEM;
             }
         }
-        rt->gemm_enabled = true;
+        if (gemm_kind) rt->gemm_enabled = true;
     }
     caf_gpu_actor_cfg c{};
     if (cfg) c = *cfg;
