@@ -68,6 +68,10 @@ def parse_args(argv=None):
                          "GEMM, token-ring, serving and mailbox-traffic configurations")
     ap.add_argument("--no-autotune", action="store_true", help="use --factor-batch/--factor-warps as given")
     ap.add_argument("--requests", type=int, default=100_000, help="serve: requests in the trace")
+    ap.add_argument("--mandel-iters", default="120,1200", help="mandel: maximum iterations to run (comma list)")
+    ap.add_argument("--mandel-shapes", default="image,row", help="mandel: message shapes to run (image, row)")
+    ap.add_argument("--mandel-images", type=int, default=0,
+                    help="mandel: images per step (0: 100 as whole images, 10 as rows)")
     return ap.parse_args(argv)
 
 
@@ -790,8 +794,13 @@ def run_mandel(args):
     results = {}
     clocks = ClockSampler(physical_gpu(0))
     clocks.start()
-    for max_iter in W.MANDEL_ITERS:
+    iters = [int(x) for x in args.mandel_iters.split(",")]
+    shapes = [x.strip() for x in args.mandel_shapes.split(",")]
+    for max_iter in iters:
         for shape, images, rows_per_msg in (("image", 100, Hd), ("row", 10, 1)):
+            if shape not in shapes:
+                continue
+            images = args.mandel_images or images
             per_image = Hd // rows_per_msg
             count = images * per_image
             out = torch.zeros((images, Hd, Wd), dtype=torch.int32, device="cuda")
@@ -905,7 +914,7 @@ def run_mandel(args):
         done_iter += s_
         j += 1
     secs = time.perf_counter() - t0
-    head = results["iter1200_image"]
+    head = results.get("iter1200_image") or next(iter(results.values()))
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "Mandelbrot actor: 1920 x 1080 over [-0.5-0.7375i, 0.1-0.1375i], 120 and 1200 "

@@ -13,8 +13,10 @@
 // That makes the count a pure function of (cx, cy, max_iter), equal bit for
 // bit on any IEEE float32 machine that follows the same order.
 //
-// The loop runs kMandelUnroll updates per block with no branch between them,
-// folding the escape tests into one predicate.  A block in which some test
+// The loop runs blocks of kU updates with no branch between them, folding
+// the escape tests into one predicate (kU = 16 for max_iter >= 512, else 12:
+// a longer block amortises the loop, a shorter one wastes fewer updates after
+// an escape and leaves a shorter one-at-a-time tail; both are exact).  A block in which some test
 // fired is repeated from its saved start one update at a time, so the count
 // is the same as with a test before every update.  After an escape the block
 // may overflow to inf or NaN; the predicate already holds then (a NaN test is
@@ -26,8 +28,6 @@
 #include "layout.h"
 
 namespace cafgpu {
-
-constexpr uint32_t kMandelUnroll = 8;
 
 // One update of z with its escape test folded into `esc` (no branch).
 __device__ __forceinline__ void mandel_step(float &zr, float &zi, float cx, float cy, bool &esc) {
@@ -55,22 +55,28 @@ __device__ __forceinline__ uint32_t mandel_single(float zr, float zi, float cx, 
     return k;
 }
 
-__device__ __forceinline__ uint32_t mandel_count(float cx, float cy, uint32_t max_iter) {
+template <uint32_t kU>
+__device__ __forceinline__ uint32_t mandel_count_blocks(float cx, float cy, uint32_t max_iter) {
     float zr = 0.0f, zi = 0.0f;
     uint32_t k = 0;
-    while (k + kMandelUnroll <= max_iter) {
+    while (k + kU <= max_iter) {
         const float sr = zr, si = zi;
         bool esc = false;
 #pragma unroll
-        for (uint32_t u = 0; u < kMandelUnroll; ++u) mandel_step(zr, zi, cx, cy, esc);
+        for (uint32_t u = 0; u < kU; ++u) mandel_step(zr, zi, cx, cy, esc);
         if (esc) {
             zr = sr;
             zi = si;
             break;
         }
-        k += kMandelUnroll;
+        k += kU;
     }
     return mandel_single(zr, zi, cx, cy, k, max_iter);
+}
+
+// max_iter is the same for every pixel of a job, so the choice does not diverge.
+__device__ __forceinline__ uint32_t mandel_count(float cx, float cy, uint32_t max_iter) {
+    return max_iter >= 512 ? mandel_count_blocks<16>(cx, cy, max_iter) : mandel_count_blocks<12>(cx, cy, max_iter);
 }
 
 // c of pixel p of a job (row-major over its rows): one rounded product and

@@ -68,8 +68,11 @@ def rt_actor(request):
     (333, 1, 1, 65536),        # one row, the largest max_iter
     (128, 128, 4, 0),          # max_iter 0: every count 0
     (96, 64, 2, 1),
-    (700, 40, 1, 8),           # max_iter equal to one unrolled block
-    (700, 40, 1, 9),
+    (700, 40, 1, 12),          # max_iter equal to one block of 12 updates
+    (700, 40, 1, 13),
+    (300, 30, 1, 511),         # the last max_iter with blocks of 12
+    (300, 30, 1, 512),         # the first with blocks of 16
+    (300, 30, 1, 528),
 ])
 def test_edge_region_bit_exact(rt_actor, width, height, parts, max_iter):
     rt, a = rt_actor
