@@ -69,7 +69,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="use --factor-batch/--factor-warps as given")
     ap.add_argument("--requests", type=int, default=100_000, help="serve: requests in the trace")
     ap.add_argument("--mandel-iters", default="120,1200", help="mandel: maximum iterations to run (comma list)")
-    ap.add_argument("--mandel-shapes", default="image,row", help="mandel: message shapes to run (image, row)")
+    ap.add_argument("--mandel-shapes", default="single,image,row",
+                    help="mandel: message shapes to run (single: one image per step; image; row)")
     ap.add_argument("--mandel-images", type=int, default=0,
                     help="mandel: images per step (0: 100 as whole images, 10 as rows)")
     return ap.parse_args(argv)
@@ -776,9 +777,10 @@ FP32_LANES_PER_SM = 128
 def run_mandel(args):
     """Mandelbrot actors (the OpenCL actor experiment, Sec. 5): the 1920 x 1080
     image of [-0.5 - 0.7375i, 0.1 - 0.1375i] at 120 and at 1200 iterations, sent
-    as whole-image messages to one MANDELBROT actor (100 per step, the paper's
-    100 runs), and as one message per row to one actor per row (1080 actors,
-    10 images, 10,800 messages per step -- the one-actor-per-row split of the
+    as one whole-image message per step (the paper's per-run time), as 100
+    whole-image messages to one MANDELBROT actor (the paper's 100 runs at
+    once), and as one message per row to one actor per row (1080 actors, 10
+    images, 10,800 messages per step -- the one-actor-per-row split of the
     paper's CPU Mandelbrot benchmark); persistent drain against one kernel
     launch per message."""
     import torch
@@ -797,10 +799,11 @@ def run_mandel(args):
     iters = [int(x) for x in args.mandel_iters.split(",")]
     shapes = [x.strip() for x in args.mandel_shapes.split(",")]
     for max_iter in iters:
-        for shape, images, rows_per_msg in (("image", 100, Hd), ("row", 10, 1)):
+        for shape, images, rows_per_msg in (("single", 1, Hd), ("image", 100, Hd), ("row", 10, 1)):
             if shape not in shapes:
                 continue
-            images = args.mandel_images or images
+            if shape != "single":
+                images = args.mandel_images or images
             per_image = Hd // rows_per_msg
             count = images * per_image
             out = torch.zeros((images, Hd, Wd), dtype=torch.int32, device="cuda")
@@ -833,7 +836,8 @@ def run_mandel(args):
                 rt.stream_sync()
                 rt.stats()
                 times = []
-                for _ in range(args.steps):
+                reps = max(args.steps, 20) if shape == "single" else args.steps   # sub-ms steps: more samples
+                for _ in range(reps):
                     with torch.cuda.stream(stream):
                         flush.add_(1.0)
                     e0, e1 = _events(stream)
@@ -875,7 +879,7 @@ def run_mandel(args):
                     actors = actor_of
                     rt.await_batch(rt.request_batch(actors[:per_image], msgs), timeout_ns=AWAIT_NS)   # warm-up
                     pm = []
-                    for _ in range(max(1, min(args.steps, 3))):
+                    for _ in range(reps if shape == "single" else max(1, min(args.steps, 3))):
                         with torch.cuda.stream(stream):
                             flush.add_(1.0)
                         e0, e1 = _events(stream)

@@ -1076,7 +1076,11 @@ __device__ __noinline__ void drain_gemm_tiles(const DrainParams &P, GroupShared 
 // ---------------------------------------------------------------------------
 // Claim a Mandelbrot actor: take up to 32 messages (as many as there are free
 // job records), copy each message's descriptor into its job and queue the
-// job's bands (kMandelBand pixels each) as work items.
+// job's bands as work items.  The claim's jobs together are cut into about
+// two bands per CTA of the grid, in proportion to their pixels, so a single
+// large image fills every SM; bands stay within [kMandelBandMin,
+// kMandelBandMax] pixels (large bands when the claim brings plenty of work:
+// each band costs a round's pop, barrier and count update).
 __device__ __noinline__ void claim_mandel(const DrainParams &P, uint32_t a) {
     const uint32_t lane = lane_id();
     DevCtl *ctl = P.ctl;
@@ -1108,15 +1112,25 @@ __device__ __noinline__ void claim_mandel(const DrainParams &P, uint32_t a) {
     release_actor(P, a, head + take);
     uint32_t bands = 0;
     bool valid = false;
+    MandelDesc d{};
     if (lane < take) {
         const MandelDesc *dp = reinterpret_cast<const MandelDesc *>(m.payload);
-        MandelDesc d{};
         if (dp) d = *dp;
         valid = dp && mandel_desc_ok(d);
+    }
+    const uint64_t claim_px = warp_sum_u64(valid ? (uint64_t)d.width * d.rows : 0ull);
+    if (lane < take) {
         if (valid) {
             MandelJob *J = &P.mjobs[j];
             J->d = d;
-            bands = (d.width * d.rows + kMandelBand - 1) / kMandelBand;
+            const uint32_t pixels = d.width * d.rows;
+            const uint64_t tq = (2ull * gridDim.x * pixels + claim_px - 1) / claim_px;
+            const uint32_t target = tq < kMandelMaxBands ? (uint32_t)tq : kMandelMaxBands;
+            const uint32_t nb = max((pixels + kMandelBandMax - 1) / kMandelBandMax,
+                                    min((pixels + kMandelBandMin - 1) / kMandelBandMin, target));
+            const uint32_t band_px = ((pixels + nb - 1) / nb + 31u) & ~31u;
+            bands = (pixels + band_px - 1) / band_px;
+            J->band_px = band_px;
             J->bands = bands;
             J->done = 0;
             J->sum = 0;
@@ -1136,12 +1150,13 @@ __device__ __noinline__ void claim_mandel(const DrainParams &P, uint32_t a) {
     q_push_runs(P, &ctl->workq, P.workq, (j << 16) | kMandelItemFlag, bands);
 }
 
-// Item i of a round's `mine` (registers; no dynamic indexing).
-__device__ __forceinline__ uint32_t pick_item(const uint32_t (&mine)[kMaxItemsPerRound], uint32_t i) {
-    uint32_t v = mine[0];
+// Entry i of a small register array (no dynamic indexing, so no local memory).
+template <uint32_t N>
+__device__ __forceinline__ uint32_t pick_item(const uint32_t (&a)[N], uint32_t i) {
+    uint32_t v = a[0];
 #pragma unroll
-    for (uint32_t k = 1; k < kMaxItemsPerRound; ++k)
-        if (k == i) v = mine[k];
+    for (uint32_t k = 1; k < N; ++k)
+        if (k == i) v = a[k];
     return v;
 }
 
@@ -1154,14 +1169,19 @@ __device__ __forceinline__ uint32_t pick_item(const uint32_t (&mine)[kMaxItemsPe
 // again after the closing barrier, before it reaches the next round's.
 __device__ __noinline__ void drain_mandel_bands(const DrainParams &P, GroupShared &G, const uint32_t *items,
                                                 uint32_t count, uint32_t bar_threads) {
-    constexpr uint32_t kGroups = kMandelBand / 32;
     const uint32_t lane = lane_id();
     uint32_t mine[kMaxItemsPerRound];
+    uint32_t first[kMaxItemsPerRound + 1];     // first group of each band in the pool
+    first[0] = 0;
 #pragma unroll
-    for (uint32_t i = 0; i < kMaxItemsPerRound; ++i) mine[i] = i < count ? items[i] : 0u;
-    const uint32_t total = count * kGroups;
+    for (uint32_t i = 0; i < kMaxItemsPerRound; ++i) {
+        mine[i] = i < count ? items[i] : 0u;
+        const uint32_t groups = i < count ? P.mjobs[mine[i] >> 16].band_px / 32u : 0u;
+        first[i + 1] = first[i] + groups;
+    }
+    const uint32_t total = first[kMaxItemsPerRound];
     uint32_t cur = kNone;                  // band whose descriptor is in registers
-    uint32_t base = 0;                     // its first pixel
+    uint32_t base = 0, gbase = 0;          // its first pixel and first group
     MandelDesc d{};
     uint32_t pixels = 0;
     unsigned long long acc = 0;            // this lane's count sum for band `cur`
@@ -1169,8 +1189,16 @@ __device__ __noinline__ void drain_mandel_bands(const DrainParams &P, GroupShare
         uint32_t g = 0;
         if (lane == 0) g = atomicAdd(&G.mnext, 1u);
         g = __shfl_sync(FULL, g, 0);
-        const uint32_t b = g < total ? g / kGroups : kNone;
-        if (b != cur) {
+        uint32_t b = kNone;
+        if (g < total) {
+            b = 0;
+#pragma unroll
+            for (uint32_t i = 1; i < kMaxItemsPerRound; ++i)
+                if (g >= first[i]) b = i;
+        }
+        // (a warp whose first group is already past the pool's end leaves
+        // too: cur is still kNone then)
+        if (b != cur || b == kNone) {
             if (cur != kNone) {
                 const unsigned long long s = warp_sum_u64(acc);
                 if (lane == 0 && s) atomicAdd(&G.msum[cur], s);
@@ -1179,13 +1207,15 @@ __device__ __noinline__ void drain_mandel_bands(const DrainParams &P, GroupShare
             cur = b;
             if (b == kNone) break;
             const uint32_t it = pick_item(mine, b);
-            d = P.mjobs[it >> 16].d;
+            const MandelJob *J = &P.mjobs[it >> 16];
+            d = J->d;
             pixels = d.width * d.rows;
-            base = (it & (kMandelItemFlag - 1u)) * kMandelBand;
+            base = (it & (kMandelItemFlag - 1u)) * J->band_px;
+            gbase = pick_item(first, b);
         }
         // long bands (max_iter up to 65536) keep the stall detector fed
         if (lane == 0 && (g & 15u) == 0) heartbeat(P);
-        const uint32_t p = base + (g % kGroups) * 32u + lane;
+        const uint32_t p = base + (g - gbase) * 32u + lane;
         if (p < pixels) {
             float cx, cy;
             mandel_c(d, p, cx, cy);
@@ -1395,7 +1425,16 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
                 int64_t av = 0;
                 if (lane == 0) av = q_len(&ctl->workq) + (kGemm ? q_len(&ctl->packq) : 0);
                 av = __shfl_sync(FULL, av, 0);
-                npop = av >= (int64_t)gridDim.x ? P.gemm_items : (av > 0 ? 1u : 0u);
+                if (kGemm) {
+                    // GEMM tile runs want full rounds while the queue is not short
+                    npop = av >= (int64_t)gridDim.x ? P.gemm_items : (av > 0 ? 1u : 0u);
+                } else {
+                    // Mandelbrot bands only: an even share, so the last bands of
+                    // a step spread over every CTA
+                    const int64_t share = av / (int64_t)gridDim.x;
+                    npop = share >= (int64_t)P.gemm_items ? P.gemm_items
+                                                          : (share > 0 ? (uint32_t)share : (av > 0 ? 1u : 0u));
+                }
             }
             if (lane < npop) {
                 int pr = q_try_pop(&ctl->workq, P.workq, &item, P.wait_limit_ns);

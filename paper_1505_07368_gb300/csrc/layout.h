@@ -136,8 +136,12 @@ struct MandelDesc {
     float x0, y0, dx, dy;
 };
 static_assert(sizeof(MandelDesc) == 40, "MandelDesc is 40 bytes");
-constexpr uint32_t kMandelBand = 8192;               // pixels per band work item
-constexpr uint32_t kMandelMaxPixels = 1u << 24;      // per message: <= 2048 bands
+// A job's band size is chosen at its claim: about two bands per CTA of the
+// running grid, within [kMandelBandMin, kMandelBandMax] pixels, a multiple of 32.
+constexpr uint32_t kMandelBandMin = 2048;
+constexpr uint32_t kMandelBandMax = 8192;
+constexpr uint32_t kMandelMaxBands = 2048;           // bands of one job, at most
+constexpr uint32_t kMandelMaxPixels = 1u << 24;      // per message
 constexpr uint32_t kMandelMaxIter = 1u << 16;        // a band stays well inside the stall limit
 constexpr uint32_t kMandelMaxCoord = 1u << 24;       // width and row0 + rows: exact as float32
 constexpr uint32_t kMandelJobs = 256;                // Mandelbrot messages in flight in the drain
@@ -152,9 +156,10 @@ struct alignas(64) MandelJob {
     uint64_t sum;                  // escape counts summed so far (atomic)
     uint64_t reply_addr;
     uint32_t reply_token;
-    uint32_t pad;
+    uint32_t band_px;              // pixels per band (a multiple of 32)
 };
 static_assert(sizeof(MandelJob) == 128, "MandelJob is 128 bytes");
+static_assert(kMandelMaxPixels / kMandelBandMax <= kMandelMaxBands, "large jobs fit the band limit");
 
 // actor lifecycle (Sec. 6: ready / waiting / running / done)
 enum : uint32_t { kWaiting = 0, kReady = 1, kRunning = 2, kDone = 3 };

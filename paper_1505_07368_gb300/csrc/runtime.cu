@@ -487,7 +487,7 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     // every job's tiles, or its pack items, can be queued at once
     rt->workq_cap = next_pow2((uint64_t)kGemmJobsSmall * (kPackSmallMaxN / 128) * (kPackSmallMaxN / 128) +
                               (uint64_t)kGemmJobsLarge * (kMaxDrainGemmN / 128) * (kMaxDrainGemmN / 128) +
-                              (uint64_t)kMandelJobs * (kMandelMaxPixels / kMandelBand) + 1);
+                              (uint64_t)kMandelJobs * kMandelMaxBands + 1);
     rt->jobq_cap = next_pow2((uint64_t)kGemmJobs + 1);
     std::vector<uint32_t> none, all(rt->n_batches);
     for (uint32_t i = 0; i < rt->n_batches; ++i) all[i] = i;
