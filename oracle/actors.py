@@ -20,6 +20,12 @@ receives 0 terminates.  Readings taken where the paper is silent:
 * the ring master (actor 0) sends one factorization request to its ring's
   worker when it starts and one more for every token value v > 0 it
   receives.
+
+Actor creation (Sec. 5, "Overhead of Actor Creation"): 2^N is computed by
+recursive creation; an actor with counter N > 0 spawns two actors with
+counter N - 1 and waits for their results, an actor with counter 0 answers
+1.  Readings: a parent answers the sum of its children's results and then
+terminates; every spawned actor terminates after answering.
 """
 from __future__ import annotations
 
@@ -152,3 +158,57 @@ def source_streams(sources):
             totals[t] = (cnt + 1, (tot + v) % (1 << 64))
     return (np.asarray(rec, np.int64), np.asarray(snd, np.int64), np.asarray(seq, np.int64),
             np.asarray(val, np.uint64), totals)
+
+
+def fork_tree(n: int):
+    """Run the recursive-creation computation of 2^n as actors exchanging
+    messages, one message at a time in arrival order (Sec. 5, "Overhead of
+    Actor Creation").
+
+    The root (counter n) gets one start message.  An actor's start message
+    with counter c > 0 spawns two actors and sends each a start message with
+    counter c - 1; with c = 0 the actor answers 1 at once.  A result message
+    adds its value to the actor's sum; after the second result the actor
+    answers the sum.  Answering sends a result message to the parent (the
+    root's answer is the computation's result) and terminates the actor.
+
+    Returns {"result", "spawned", "messages", "live_after"}: the root's
+    answer, the actors spawned (the root not counted), the messages handled
+    (start and result messages, including the root's start) and the spawned
+    actors still alive at the end."""
+    parent = {0: None}
+    pending = {0: 0}
+    total = {0: 0}
+    queue = deque([(0, "start", n)])
+    spawned = messages = 0
+    result = None
+    next_id = 1
+
+    def answer(a, value):
+        nonlocal result
+        if parent[a] is None:
+            result = value
+        else:
+            queue.append((parent[a], "result", value))
+            del parent[a], pending[a], total[a]
+
+    while queue:
+        a, kind, v = queue.popleft()
+        messages += 1
+        if kind == "start":
+            if v == 0:
+                answer(a, 1)
+                continue
+            for _ in range(2):
+                c = next_id
+                next_id += 1
+                parent[c], pending[c], total[c] = a, 0, 0
+                spawned += 1
+                queue.append((c, "start", v - 1))
+            pending[a], total[a] = 2, 0
+        else:
+            total[a] += v
+            pending[a] -= 1
+            if pending[a] == 0:
+                answer(a, total[a])
+    return {"result": result, "spawned": spawned, "messages": messages, "live_after": len(parent) - 1}

@@ -86,3 +86,22 @@ def test_source_streams_closed_form():
         rows = snd == s
         assert list(seq[rows]) == list(range(c))
         assert all(int(v) >> 32 == s and int(v) & 0xFFFFFFFF == k for v, k in zip(val[rows], seq[rows]))
+
+
+def test_fork_tree_by_hand():
+    # n = 1: the root spawns two actors with counter 0; each answers 1; the
+    # root handles its start and two results and answers 2
+    assert actors.fork_tree(1) == {"result": 2, "spawned": 2, "messages": 5, "live_after": 0}
+    assert actors.fork_tree(0) == {"result": 1, "spawned": 0, "messages": 1, "live_after": 0}
+
+
+def test_fork_tree_closed_form():
+    # a full binary tree of depth n: 2^n leaves answer 1 each, so the root answers
+    # 2^n; it has 2^(n+1) - 1 nodes (the root is not spawned); each of the
+    # 2^n - 1 inner nodes handles 3 messages and each leaf 1
+    for n in range(0, 13):
+        r = actors.fork_tree(n)
+        assert r["result"] == 2 ** n
+        assert r["spawned"] == 2 ** (n + 1) - 2
+        assert r["messages"] == 3 * (2 ** n - 1) + 2 ** n == 2 ** (n + 2) - 3
+        assert r["live_after"] == 0
