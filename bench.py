@@ -62,12 +62,13 @@ def parse_args(argv=None):
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--max-messages", type=int, default=None, help="truncate the workload (profiling)")
-    ap.add_argument("--workload", choices=["factor", "gemm", "ring", "serve", "mailbox", "small", "mandel"],
+    ap.add_argument("--workload", choices=["factor", "gemm", "ring", "serve", "mailbox", "small", "mandel", "spawn"],
                     default="factor",
                     help="factor: the batched-factorization line (default); the others measure the "
                          "GEMM, token-ring, serving and mailbox-traffic configurations")
     ap.add_argument("--no-autotune", action="store_true", help="use --factor-batch/--factor-warps as given")
     ap.add_argument("--requests", type=int, default=100_000, help="serve: requests in the trace")
+    ap.add_argument("--fork-n", type=int, default=20, help="spawn: recursion counter n (2^(n+1) - 2 spawns per step)")
     ap.add_argument("--mandel-iters", default="120,1200", help="mandel: maximum iterations to run (comma list)")
     ap.add_argument("--mandel-shapes", default="single,image,row",
                     help="mandel: message shapes to run (single: one image per step; image; row)")
@@ -933,6 +934,73 @@ def run_mandel(args):
     return 0
 
 
+def run_spawn(args):
+    """Actor creation (Sec. 5, "Overhead of Actor Creation"): one FORK root computes
+    2^n by recursive creation, every actor spawned on the device from the pool and
+    recycled; one device-resident start message per step."""
+    import torch
+
+    from oracle import actors as OA
+    from paper_1505_07368_gb300 import cafgpu as C
+    torch.cuda.set_device(0)
+    n = args.fork_n
+    spawns = (2 << n) - 2
+    msgs = (4 << n) - 3                    # start and result messages per step
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    # per spawned actor: its 128 B record written, one start and one result slot
+    # (64 B each) written and read
+    bytes_per_actor = 128 + 2 * 128
+    clocks = ClockSampler(physical_gpu(0))
+    with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=4, fork_pool=max(1 << 21, spawns)) as rt:
+        root = rt.spawn(C.FORK)
+        m = np.zeros(1, C.DMSG_DTYPE)
+        m["actor"], m["kind"], m["u64"] = root - 1, C.FORK, n
+        d_m = torch.from_numpy(m.view(np.uint8).copy()).cuda()
+        d_r = torch.zeros(32, dtype=torch.uint8, device="cuda")
+        stream = torch.cuda.ExternalStream(rt.stream())
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            rt.request_batch_device(d_m.data_ptr(), 1, d_r.data_ptr())
+        rt.stream_sync()
+        rt.stats()
+        clocks.start()
+        times = []
+        for _ in range(args.steps):
+            e0, e1 = _events(stream)
+            e0.record(stream)
+            rt.request_batch_device(d_m.data_ptr(), 1, d_r.data_ptr())
+            e1.record(stream)
+            rt.stream_sync()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        clk = clocks.stop()
+        st = rt.stats()
+        rep_ = d_r.cpu().numpy().view(C.DREPLY_DTYPE)
+        if (rep_["status"][0], rep_["r0"][0], rep_["r1"][0]) != (0, 1 << n, spawns):
+            raise SystemExit(f"bench: spawn: wrong reply {rep_}")
+        if st["device_spawns"] != args.steps * spawns or st["messages"] != args.steps * msgs:
+            raise SystemExit(f"bench: spawn: counters {st}")
+    t = float(np.mean(times))
+    # CPU baseline: the oracle's message-by-message simulation, one core, n = 16
+    t0 = time.perf_counter()
+    ref = OA.fork_tree(16)
+    ct = time.perf_counter() - t0
+    print(json.dumps({
+        "metric": METRIC, "unit": "actors spawned/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"actor creation: 2^{n} by recursive spawning, {spawns} device spawns and {msgs} "
+                               f"messages per step, one FORK root, pool of {max(1 << 21, spawns)} records"},
+        "value": spawns / t, "ms_per_step": 1e3 * t, "msgs_per_s": msgs / t,
+        "roofline": {"bound": "hbm", "achieved": bytes_per_actor * spawns / t / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": bytes_per_actor * spawns / t / 1e9 / hbm, "bytes_per_actor": bytes_per_actor,
+                     "note": "record and mailbox bytes per spawned actor; the path is bound by atomics and "
+                             "queue latency, not by this traffic"},
+        "gpu_launches": st["launches"], "clocks": clk,
+        "cpu_baseline": {"value": ref["spawned"] / ct, "unit": "actors spawned/s", "cores": 1, "kind": "oracle",
+                         "sample": f"n = 16 ({ref['spawned']} spawns) in {ct:.2f} s, message-by-message simulation"}}))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -949,6 +1017,8 @@ def main(argv=None):
         return run_small(args)
     if args.workload == "mandel":
         return run_mandel(args)
+    if args.workload == "spawn":
+        return run_spawn(args)
     return run_ours(args)
 
 

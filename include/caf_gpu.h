@@ -55,6 +55,7 @@ extern "C" {
 #define CAF_GPU_SINK                5u  /* counts what it receives (stateful)        */
 #define CAF_GPU_SOURCE              6u  /* sends a stream of messages to a sink      */
 #define CAF_GPU_MANDELBROT          7u  /* escape counts of an image's rows          */
+#define CAF_GPU_FORK                8u  /* recursive actor creation (spawns on the device) */
 /* SINK and SOURCE are the two ends of the paper's mailbox experiment (Sec. 5,
  * "Mailbox Performance in N:1 Communication Scenario": many senders, one
  * receiver).  A SINK handles each message (u64 value v) by adding 1 to its
@@ -86,6 +87,25 @@ extern "C" {
  * aligned; other descriptors are EINVAL at the call (host messages) or get
  * reply status CAF_GPU_REPLY_REJECTED (device batches).  A message needs a
  * reply (caf_gpu_send returns EINVAL). */
+
+/* FORK is the actor of the paper's actor-creation benchmark (Sec. 5,
+ * "Overhead of Actor Creation": 2^n computed by recursively creating actors).
+ * A message u64 = n (0 <= n <= 30) to a FORK actor spawned by the host (the
+ * root) starts a computation: an actor with counter c > 0 spawns two FORK
+ * actors with counter c - 1 on the device and waits for their results; an
+ * actor with counter 0 answers 1; a parent answers the sum of its two
+ * children's results and terminates.  The root's reply is (r0, r1) =
+ * (2^n, actors spawned = 2^(n+1) - 2).  Spawned actors come from a device
+ * pool of cfg.fork_pool actor records (made at the first FORK spawn); a
+ * terminated actor's record returns to the pool, so repeated computations
+ * recycle the same records.  A message is EINVAL at the call (REJECTED in a
+ * device batch) when its tree, 2^(n+1) - 2 actors, exceeds the pool; the
+ * trees in flight at once share the pool, and a spawn that finds it empty
+ * waits, bounded by wait_limit_ns (then CAF_GPU_EWAITLIMIT).  A root handles
+ * one computation at a time: a start message that reaches it while it waits
+ * for results gets CAF_GPU_REPLY_REJECTED.  Spawn the first FORK actor before
+ * recording any CUDA graph (ESTATE after one): making the pool moves the
+ * actor table.  Persistent backend only. */
 
 /* ---- backends ----------------------------------------------------------- */
 #define CAF_GPU_BACKEND_PERSISTENT          0  /* one persistent kernel drains all mailboxes */
@@ -129,7 +149,7 @@ typedef struct {
     uint32_t log_capacity;          /* log rows (default 1 << 20)                             */
     void    *cuda_stream;           /* cudaStream_t for all work; NULL = runtime's own stream */
     uint32_t gemm_items_per_round;  /* GEMM work items a drain CTA takes per round, 1..8 (4)   */
-    uint32_t pad;
+    uint32_t fork_pool;             /* FORK actors the device may hold at once (2^21)          */
 } caf_gpu_runtime_cfg;
 
 /* Per-actor configuration for caf_gpu_spawn (may be NULL for defaults). */
@@ -165,7 +185,8 @@ typedef struct {
     int32_t  status;                /* CAF_GPU_REPLY_*                                         */
     uint32_t kind;
     uint64_t r0, r1;                /* FACTOR_U64: (p, q) with p <= q; GEMM: (0, n);           */
-                                    /* MANDELBROT: (pixels, sum of the escape counts)          */
+                                    /* MANDELBROT: (pixels, sum of the escape counts);         */
+                                    /* FORK: (2^n, actors spawned)                             */
     uint64_t t_done;                /* device clock when the reply was written (ns)            */
 } caf_gpu_reply;
 
@@ -236,6 +257,7 @@ typedef struct {
     uint32_t pad;
     uint64_t diag[2];               /* values the expired wait saw (for diagnosis)              */
     uint64_t t_mark;                /* device clock of the last caf_gpu_mark (ns)               */
+    uint64_t device_spawns;         /* FORK actors spawned on the device                        */
 } caf_gpu_stats;
 
 /* Create a runtime on the current CUDA device.  Builds the prime table used by

@@ -19,7 +19,7 @@ from . import _build
 
 # ---- constants (caf_gpu.h) ------------------------------------------------
 OK, EINVAL, ENOMEM, EAGAIN, ETIMEDOUT, EDEAD, EWAITLIMIT, ESTATE, ECUDA = 0, -1, -2, -3, -4, -5, -6, -7, -8
-FACTOR_U64, GEMM_BF16, GEMM_SPLIT_BF16X3, RING_TOKEN, SINK, SOURCE, MANDELBROT = 1, 2, 3, 4, 5, 6, 7
+FACTOR_U64, GEMM_BF16, GEMM_SPLIT_BF16X3, RING_TOKEN, SINK, SOURCE, MANDELBROT, FORK = 1, 2, 3, 4, 5, 6, 7, 8
 BACKEND_PERSISTENT, BACKEND_PER_MESSAGE_LAUNCH = 0, 1
 REPLY_OK, REPLY_NOFACTOR, REPLY_DEAD, REPLY_REJECTED = 0, 1, 2, 3
 MSG_START = 1
@@ -52,7 +52,7 @@ class RuntimeCfg(ctypes.Structure):
                 ("wait_limit_ns", ctypes.c_uint64), ("idle_exit_ns", ctypes.c_uint64),
                 ("validation_mode", ctypes.c_uint32), ("log_capacity", ctypes.c_uint32),
                 ("cuda_stream", ctypes.c_void_p), ("gemm_items_per_round", ctypes.c_uint32),
-                ("pad", ctypes.c_uint32)]
+                ("fork_pool", ctypes.c_uint32)]
 
 
 class ActorCfg(ctypes.Structure):
@@ -86,7 +86,8 @@ class Stats(ctypes.Structure):
                 ("device_sends", ctypes.c_uint64), ("claims", ctypes.c_uint64),
                 ("factor_items", ctypes.c_uint64), ("prime_tests", ctypes.c_uint64),
                 ("gemm_tiles", ctypes.c_uint64), ("error_word", ctypes.c_uint32), ("pad", ctypes.c_uint32),
-                ("diag0", ctypes.c_uint64), ("diag1", ctypes.c_uint64), ("t_mark", ctypes.c_uint64)]
+                ("diag0", ctypes.c_uint64), ("diag1", ctypes.c_uint64), ("t_mark", ctypes.c_uint64),
+                ("device_spawns", ctypes.c_uint64)]
 
 
 SERVE_REQ_DTYPE = np.dtype([("actor", "<u8"), ("t_arrival", "<f8"), ("u64", "<u8"), ("n", "<u4"), ("pad", "<u4"),

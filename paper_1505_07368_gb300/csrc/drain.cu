@@ -707,6 +707,162 @@ __device__ void run_source(const DrainParams &P, uint32_t a) {
     release_actor(P, a, head + 1);
 }
 
+// ---------------------------------------------------------------------------
+// FORK actors: recursive actor creation (Sec. 5, "Overhead of Actor
+// Creation": 2^n computed by actors that each spawn two actors with counter
+// n - 1 and wait for their results).  Spawned actors come from a device pool
+// of actor ids with fixed 4-slot mailboxes; an actor that has answered
+// terminates and its id goes back to the pool, so repeated computations
+// recycle the same records.  A result message carries the child's value in
+// its low and the actors spawned below it in its high 32 bits.
+// ---------------------------------------------------------------------------
+// Lane 0: take a free pool id, waiting (bounded) while the pool is empty.
+__device__ uint32_t fork_take_id(const DrainParams &P) {
+    uint32_t id = kNone;
+    WaitClock w(P.wait_limit_ns);
+    for (;;) {
+        const int pr = q_try_pop(&P.ctl->forkq, P.forkq, &id, P.wait_limit_ns);
+        if (pr > 0) return id;
+        if (pr < 0 || !w.again()) {
+            fail(P, kErrWaitQueue, 29, 0, 0);
+            return kNone;
+        }
+        __nanosleep(64);
+    }
+}
+
+// Answer (value, spawned below) to the parent, or to the root's requester.
+__device__ bool fork_answer(const DrainParams &P, uint32_t a, uint64_t value, uint64_t spawned) {
+    ActorDesc *A = &P.actors[a];
+    const uint32_t parent = A->next;
+    if (parent == kNone) {
+        if (lane_id() == 0) write_reply(A->fork_reply, 0, value, spawned, 0, A->fork_token);
+        __syncwarp();
+        return true;
+    }
+    MsgData r{};
+    r.payload = (value & 0xFFFFFFFFull) | (spawned << 32);
+    r.kind = kFork | (kMsgResult << 16);
+    r.sender = 0x80000000u | a;
+    if (lane_id() == 0) add_u64(&P.ctl->device_sends, 1);
+    return warp_enqueue(P, lane_id() == 0, parent, r);
+}
+
+// Claimed FORK actor `a`: handle its published messages in mailbox order.  A
+// start message with counter c answers 1 when c = 0; otherwise it spawns two
+// pool actors (parent a, counter c - 1) and sends each a start message.  A
+// result adds to the actor's sum; the second one answers (sum, 2 + spawned
+// below).  A pool actor terminates after answering and returns its id to the
+// pool; a root (spawned by the host) stays for the next computation.  A start
+// message that reaches a root still waiting for results is rejected.
+__device__ void run_fork(const DrainParams &P, uint32_t a) {
+    const uint32_t lane = lane_id();
+    ActorDesc *A = &P.actors[a];
+    const bool pooled = a >= P.fork_base && a - P.fork_base < P.fork_pool;
+    if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
+    __syncwarp();
+    const uint64_t head = *((volatile uint64_t *)&A->head);
+    const uint64_t tail = ld_acquire_gpu(&A->tail);
+    uint64_t avail = tail - head;
+    if (P.max_claim && avail > P.max_claim) avail = P.max_claim;
+    if (lane == 0) add_u64(&P.ctl->claims, 1);
+    MsgData m{};
+    const uint32_t got = avail ? warp_dequeue(P, a, head, avail < 32 ? (uint32_t)avail : 32u, m) : 0u;
+    int32_t pending = A->user_state;
+    uint64_t sum = A->sink_sum, spawned = A->sink_count;
+    bool ok = true, ended = false;
+    for (uint32_t i = 0; i < got && ok; ++i) {
+        const uint64_t v = __shfl_sync(FULL, m.payload, i);
+        const uint32_t kind = __shfl_sync(FULL, m.kind, i);
+        const uint64_t reply_addr = __shfl_sync(FULL, m.reply_addr, i);
+        const uint32_t token = __shfl_sync(FULL, m.reply_token, i);
+        const uint64_t tag = __shfl_sync(FULL, m.tag, i);
+        if (!((kind >> 16) & kMsgResult)) {
+            if (pending != 0 || ended) {
+                if (lane == 0) write_reply(reply_addr, 3, 0, 0, tag, token);
+                continue;
+            }
+            if (!pooled && lane == 0) {
+                A->fork_reply = reply_addr;
+                A->fork_token = token;
+            }
+            __syncwarp();
+            if (v == 0) {
+                ok = fork_answer(P, a, 1, 0);
+                ended = pooled;          // a root takes its next start message
+                continue;
+            }
+            // spawn two children: lanes 0 and 1 each take a pool id and set it up
+            uint32_t c = kNone;
+            if (lane < 2) {
+                c = fork_take_id(P);
+                if (c != kNone) {
+                    ActorDesc *C = &P.actors[c];
+                    C->next = a;
+                    C->user_state = 0;
+                    C->sink_sum = 0;
+                    C->sink_count = 0;
+                    C->fork_reply = 0;
+                    *((volatile uint32_t *)&C->state) = kWaiting;
+                }
+            }
+            if (__any_sync(FULL, lane < 2 && c == kNone)) {
+                ok = false;
+                break;
+            }
+            __threadfence();
+            MsgData s{};
+            s.payload = v - 1;
+            s.kind = kFork;
+            s.sender = 0x80000000u | a;
+            s.sender_seq = lane;
+            s.tag = tag;
+            if (lane == 0) {
+                add_u64(&P.ctl->device_sends, 2);
+                add_u64(&P.ctl->device_spawns, 2);
+            }
+            ok = warp_enqueue(P, lane < 2, c, s);
+            pending = 2;
+            sum = 0;
+            spawned = 0;
+        } else {
+            sum += v & 0xFFFFFFFFull;
+            spawned += v >> 32;
+            if (--pending == 0) {
+                ok = fork_answer(P, a, sum, spawned + 2);
+                ended = pooled;
+                sum = 0;
+                spawned = 0;
+            }
+        }
+    }
+    if (lane == 0) {
+        if (ended) {
+            // a pool actor that has answered terminates
+            A->user_state = 0;
+            A->sink_sum = 0;
+            A->sink_count = 0;
+            *((volatile uint32_t *)&A->state) = kDone;
+        } else {
+            A->user_state = pending;
+            A->sink_sum = sum;
+            A->sink_count = spawned;
+        }
+        __threadfence();
+        add_u64(&P.ctl->messages, got);
+        add_u64(&P.ctl->completed, got);
+    }
+    __syncwarp();
+    release_actor(P, a, head + got);
+    if (ended && pooled && lane == 0) {
+        // every message of this incarnation is handled and the claim is
+        // released: the id can serve a new actor
+        __threadfence();
+        if (!q_push(&P.ctl->forkq, P.forkq, a, P.wait_limit_ns)) fail(P, kErrWaitQueue, 30);
+    }
+    __syncwarp();
+}
+
 // Answer a message that cannot be handled (unknown actor, kind mismatch,
 // terminated receiver, n out of range).
 __device__ __forceinline__ void reject(uint64_t reply_addr, uint32_t token, uint64_t tag, int32_t status) {
@@ -720,6 +876,13 @@ __device__ __forceinline__ bool message_ok(const DrainParams &P, uint32_t a, uin
     if ((kind & 0xFFFFu) != A->kind) { *why = 3; return false; }
     if (*((volatile const uint32_t *)&A->state) == kDone) { *why = 2; return false; }
     if ((kind & 0xFFFFu) == kFactor && payload > P.max_n) { *why = 3; return false; }
+    if ((kind & 0xFFFFu) == kFork) {
+        // a start message whose tree fits the pool; results come only from children
+        if (((kind >> 16) & kMsgResult) || payload > kForkMaxN || (2ull << payload) - 2 > P.fork_pool) {
+            *why = 3;
+            return false;
+        }
+    }
     return true;
 }
 
@@ -1296,6 +1459,8 @@ __device__ uint32_t find_batch(const DrainParams &P) {
             claim_gemm(P, a);
         } else if (kind == kMandel) {
             claim_mandel(P, a);
+        } else if (kind == kFork) {
+            run_fork(P, a);
         }
         if (exit_requested(ctl)) return kNone;
     }
@@ -1674,6 +1839,24 @@ __global__ void k_reset_actors(ActorDesc *actors, uint32_t n_actors) {
     } else if (A->kind == kSink) {
         A->sink_count = 0;
         A->sink_sum = 0;
+    } else if (A->kind == kFork) {
+        A->user_state = 0;
+        A->sink_count = 0;
+        A->sink_sum = 0;
+    }
+}
+
+// Set up the FORK actor pool: ids base .. base + count - 1, free (DONE), each
+// with kForkSlots mailbox slots starting at slot0 + kForkSlots * i.
+__global__ void k_fork_pool_init(ActorDesc *actors, uint32_t base, uint32_t count, uint64_t slot0) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        ActorDesc d{};
+        d.kind = kFork;
+        d.state = kDone;
+        d.cap_mask = kForkSlots - 1;
+        d.slot_base = slot0 + (uint64_t)kForkSlots * i;
+        d.next = kNone;
+        actors[base + i] = d;
     }
 }
 
@@ -1842,6 +2025,12 @@ cudaError_t launch_drain(const DrainParams &p, unsigned grid, cudaStream_t strea
         k_drain<true><<<grid, kThreads, kDrainSmemMixed, stream>>>(p);
     else
         k_drain<false><<<grid, kThreads, kDrainSmemFactor, stream>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fork_pool_init(ActorDesc *actors, uint32_t base, uint32_t count, uint64_t slot0,
+                                  cudaStream_t stream) {
+    k_fork_pool_init<<<1024, 256, 0, stream>>>(actors, base, count, slot0);
     return cudaGetLastError();
 }
 

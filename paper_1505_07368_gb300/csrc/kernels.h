@@ -21,6 +21,9 @@ cudaError_t launch_token_one(ActorDesc *actors, uint32_t a, uint32_t kind, int32
                              uint64_t reply_addr, uint32_t reply_token, IngressEntry *outbox,
                              DevCtl *ctl, cudaStream_t stream);
 cudaError_t launch_reset_actors(ActorDesc *actors, uint32_t n_actors, cudaStream_t stream);
+// FORK actor pool: `count` free records from actor index `base`, mailboxes from slot `slot0`.
+cudaError_t launch_fork_pool_init(ActorDesc *actors, uint32_t base, uint32_t count, uint64_t slot0,
+                                  cudaStream_t stream);
 // One GEMM message, C = A * B (n x n FP32), BF16 or split-BF16x3 on tcgen05;
 // scratch[0] must be 0 at rest.
 cudaError_t launch_gemm_one(const float *A, const float *B, float *C, uint32_t n, bool split, uint64_t reply_addr,

@@ -165,8 +165,12 @@ static_assert(kMandelMaxPixels / kMandelBandMax <= kMandelMaxBands, "large jobs 
 enum : uint32_t { kWaiting = 0, kReady = 1, kRunning = 2, kDone = 3 };
 
 // kinds (mirror caf_gpu.h)
-enum : uint32_t { kFactor = 1, kGemmBf16 = 2, kGemmSplit = 3, kToken = 4, kSink = 5, kSource = 6, kMandel = 7 };
-enum : uint32_t { kMsgStart = 1 };
+enum : uint32_t { kFactor = 1, kGemmBf16 = 2, kGemmSplit = 3, kToken = 4, kSink = 5, kSource = 6, kMandel = 7,
+                  kFork = 8 };
+enum : uint32_t { kMsgStart = 1, kMsgResult = 2 };
+// FORK: the largest recursion counter (2^n and 2^(n+1) - 2 fit in 32 bits)
+constexpr uint32_t kForkMaxN = 30;
+constexpr uint32_t kForkSlots = 4;         // mailbox of a pool actor: a start and two results
 enum : uint32_t { kActorMaster = 1 };
 
 // error codes in DevCtl::error_word (low byte) -- high bits carry the site
@@ -218,12 +222,14 @@ struct ActorDesc {                 // 128 bytes
     uint32_t flags;
     uint64_t slot_base;            // first Slot of this actor's ring
     uint64_t head;                 // consumer position (written by the claim holder only)
-    uint64_t sink_count;           // SINK: messages handled (claim holder only)
-    uint64_t sink_sum;             // SINK: sum of their values
-    uint64_t pad_a[2];
+    uint64_t sink_count;           // SINK: messages handled (claim holder only); FORK: actors spawned below
+    uint64_t sink_sum;             // SINK: sum of their values; FORK: children's results so far
+    uint64_t fork_reply;           // FORK root: reply record of the running computation
+    uint32_t fork_token;           // FORK root: its reply token
+    uint32_t pad_a;
     uint64_t tail;                 // producer ticket (atomic add)
-    int32_t user_state;
-    uint32_t next;                 // ring successor
+    int32_t user_state;            // TOKEN: last token; FORK: results still awaited
+    uint32_t next;                 // TOKEN: ring successor; FORK: parent (kNone for a root)
     uint32_t worker;               // ring master: factor worker
     uint32_t factor_count;         // ring master: number of n values
     uint64_t factor_n;             // ring master: const uint64_t* (device)
@@ -311,7 +317,8 @@ struct DevCtl {
     uint64_t t_mark;               // %globaltimer written by k_mark
     // statistics
     uint64_t claims, factor_items, prime_tests, gemm_tiles, device_sends, messages;
-    uint64_t pad3[5];
+    uint64_t device_spawns;        // FORK actors spawned on the device
+    uint64_t pad3[4];
     QueueHdr readyq;
     QueueHdr freeq;
     QueueHdr workq;                // GEMM tile items (taken before pack items)
@@ -319,6 +326,7 @@ struct DevCtl {
     QueueHdr jobq;                 // free GemmJob records, small scratch class
     QueueHdr jobq_large;           // free GemmJob records, large scratch class
     QueueHdr mjobq;                // free MandelJob records
+    QueueHdr forkq;                // free ids of the FORK actor pool
 };
 
 // Host-visible control block (pinned, mapped).
@@ -377,6 +385,10 @@ struct DrainParams {
     // Mandelbrot job records
     MandelJob *mjobs;
     QCell *mjobq;
+    // FORK actor pool: ids fork_base .. fork_base + fork_pool - 1, free ids in forkq
+    QCell *forkq;
+    uint32_t fork_base;
+    uint32_t fork_pool;
 };
 
 }  // namespace cafgpu

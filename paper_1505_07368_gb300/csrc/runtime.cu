@@ -68,6 +68,9 @@ struct caf_gpu_runtime {
     GemmJob *d_jobs = nullptr;
     MandelJob *d_mjobs = nullptr;
     QCell *d_mjobq = nullptr;
+    QCell *d_forkq = nullptr;              // free ids of the FORK actor pool
+    uint32_t fork_base = 0, fork_pool = 0; // pool ids fork_base .. fork_base + fork_pool - 1 (0: no pool yet)
+    bool graphs_made = false;              // a CUDA graph holds the current table addresses
     QCell *d_jobq = nullptr, *d_jobq_large = nullptr;
     uint32_t jobq_cap = 0;
     uint8_t *d_pack_small = nullptr, *d_pack_large = nullptr;   // packed-operand scratch of the job records
@@ -160,6 +163,9 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.jobq_large = rt->d_jobq_large;
     p.mjobs = rt->d_mjobs;
     p.mjobq = rt->d_mjobq;
+    p.forkq = rt->d_forkq;
+    p.fork_base = rt->fork_base;
+    p.fork_pool = rt->fork_pool;
     p.pack_small = rt->d_pack_small;
     p.pack_large = rt->d_pack_large;
     p.gemm = rt->gemm_enabled ? 1u : 0u;
@@ -234,6 +240,11 @@ int check_msg(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *m, uint3
     }
     if ((m->kind == kSink || m->kind == kSource) && rt->backend != CAF_GPU_BACKEND_PERSISTENT)
         return CAF_GPU_EINVAL;
+    if (m->kind == kFork) {
+        // a computation whose tree fits the device actor pool; persistent backend only
+        if (rt->backend != CAF_GPU_BACKEND_PERSISTENT) return CAF_GPU_EINVAL;
+        if (m->flags || m->u64 > kForkMaxN || (2ull << m->u64) - 2 > rt->fork_pool) return CAF_GPU_EINVAL;
+    }
     if (m->kind == kMandel) {
         // the descriptor is read (copied) at the call
         if (!m->u64) return CAF_GPU_EINVAL;
@@ -406,6 +417,7 @@ void free_runtime(caf_gpu_runtime *rt) {
     cudaFree(rt->d_jobq_large);
     cudaFree(rt->d_mjobq);
     cudaFree(rt->d_mjobs);
+    cudaFree(rt->d_forkq);
     cudaFree(rt->d_pack_small);
     cudaFree(rt->d_pack_large);
     if (rt->gemm_descs) cudaFreeHost(rt->gemm_descs);
@@ -442,6 +454,8 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     if (!c.idle_exit_ns) c.idle_exit_ns = 2000000ull;
     if (!c.log_capacity) c.log_capacity = 1u << 20;
     if (!c.gemm_items_per_round) c.gemm_items_per_round = 4;
+    if (!c.fork_pool) c.fork_pool = 1u << 21;
+    if ((uint64_t)c.max_actors + c.fork_pool >= (1ull << 31)) return CAF_GPU_EINVAL;
     if (c.gemm_items_per_round > kMaxItemsPerRound) return CAF_GPU_EINVAL;
     if (!is_pow2(c.mailbox_capacity) || !is_pow2(c.ingress_capacity)) return CAF_GPU_EINVAL;
     if (c.factor_batch > kFactorKMax || c.ctas_per_sm > 4) return CAF_GPU_EINVAL;
@@ -610,9 +624,62 @@ int caf_gpu_runtime_destroy(caf_gpu_runtime *rt) {
     return r == CAF_GPU_EWAITLIMIT ? 0 : r;
 }
 
+// The FORK actor pool (first FORK spawn): grow the actor table by the pool's
+// records and the slot array by their 4-slot mailboxes, copying what exists,
+// and fill the free-id queue.  Caller holds rt->mu, and no drain runs.
+int make_fork_pool(caf_gpu_runtime *rt) {
+    if (rt->graphs_made) return CAF_GPU_ESTATE;   // a graph would keep the old addresses
+    const uint32_t pool = rt->cfg.fork_pool;
+    const uint32_t base = rt->cfg.max_actors;
+    const uint64_t n_act = (uint64_t)base + pool;
+    const uint64_t n_slots = rt->n_slots + (uint64_t)kForkSlots * pool;
+    ActorDesc *actors = nullptr;
+    Slot *slots = nullptr;
+    if (cudaMalloc(&actors, sizeof(ActorDesc) * n_act) != cudaSuccess) {
+        cudaGetLastError();
+        return CAF_GPU_ENOMEM;
+    }
+    if (cudaMalloc(&slots, sizeof(Slot) * n_slots) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(actors);
+        return CAF_GPU_ENOMEM;
+    }
+    CK(cudaMemcpyAsync(actors, rt->d_actors, sizeof(ActorDesc) * base, cudaMemcpyDeviceToDevice, rt->setup));
+    CK(cudaMemcpyAsync(slots, rt->d_slots, sizeof(Slot) * rt->n_slots, cudaMemcpyDeviceToDevice, rt->setup));
+    CK(cudaMemsetAsync(slots + rt->n_slots, 0, sizeof(Slot) * (n_slots - rt->n_slots), rt->setup));
+    CK(launch_fork_pool_init(actors, base, pool, rt->n_slots, rt->setup));
+    std::vector<uint32_t> ids(pool);
+    for (uint32_t i = 0; i < pool; ++i) ids[i] = base + i;
+    int r = init_queue(rt, &rt->d_forkq, (uint32_t)next_pow2((uint64_t)pool + 1), &rt->d_ctl->forkq, ids);
+    if (r) return r;
+    // the ready queue holds each actor at most once (it is pushed on the
+    // waiting -> ready transition only): make room for the pool.  No drain
+    // runs, so every actor is parked and the queue is empty.
+    QCell *readyq = nullptr;
+    const uint32_t readyq_cap = (uint32_t)next_pow2(n_act + 1);
+    if ((r = init_queue(rt, &readyq, readyq_cap, &rt->d_ctl->readyq, {}))) return r;
+    cudaFree(rt->d_readyq);
+    rt->d_readyq = readyq;
+    rt->readyq_cap = readyq_cap;
+    CK(cudaStreamSynchronize(rt->setup));
+    cudaFree(rt->d_actors);
+    cudaFree(rt->d_slots);
+    rt->d_actors = actors;
+    rt->d_slots = slots;     // rt->n_slots stays the host actors' region; the pool's slots follow it
+    rt->fork_base = base;
+    rt->fork_pool = pool;
+    return 0;
+}
+
 int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_cfg *cfg, caf_gpu_actor *out) {
     if (!rt || !out) return CAF_GPU_EINVAL;
-    if (kernel_id < kFactor || kernel_id > kMandel) return CAF_GPU_EINVAL;
+    if (kernel_id < kFactor || kernel_id > kFork) return CAF_GPU_EINVAL;
+    if (kernel_id == kFork && !rt->fork_pool) {
+        int r = caf_gpu_sync(rt);   // stops the running drain: it holds the old table addresses
+        if (r) return r;
+        std::lock_guard<std::mutex> g(rt->mu);
+        if ((r = make_fork_pool(rt))) return r;
+    }
     const bool gemm_kind = kernel_id == kGemmBf16 || kernel_id == kGemmSplit;
     if ((gemm_kind && !rt->gemm_enabled) || (kernel_id == kMandel && !rt->mandel_enabled)) {
         // GEMM: drains launched from now on carry the GEMM layout (tensor
@@ -667,6 +734,7 @@ int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_c
         d.init_state = c.init_state;
         d.user_state = c.init_state;
     }
+    if (kernel_id == kFork) d.next = kNone;   // a root: its answer is the computation's reply
     if (kernel_id == kSource) {
         // the target must be an existing SINK
         if (c.next == 0 || c.next > rt->n_actors || rt->actors[c.next - 1].kind != kSink) return CAF_GPU_EINVAL;
@@ -888,6 +956,7 @@ int caf_gpu_stats_read(caf_gpu_runtime *rt, caf_gpu_stats *out) {
     out->factor_items = c.factor_items - l.factor_items;
     out->prime_tests = c.prime_tests - l.prime_tests;
     out->gemm_tiles = c.gemm_tiles - l.gemm_tiles;
+    out->device_spawns = c.device_spawns - l.device_spawns;
     out->error_word = c.error_word;
     out->pad = 0;
     out->diag[0] = c.diag[0];
@@ -1126,6 +1195,7 @@ int caf_gpu_graph_end(caf_gpu_runtime *rt, caf_gpu_graph **out) {
         return CAF_GPU_ECUDA;
     }
     *out = gr;
+    rt->graphs_made = true;
     return 0;
 }
 

@@ -43,6 +43,7 @@ def test_struct_sizes():
     assert ctypes.sizeof(cafgpu.ServeCfg) == 32
     assert ctypes.sizeof(cafgpu.ServeStats) == 32
     assert ctypes.sizeof(cafgpu.RuntimeCfg) == 88
+    assert ctypes.sizeof(cafgpu.Stats) == 96
 
 
 def test_strerror_without_gpu():
