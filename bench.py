@@ -68,6 +68,8 @@ def parse_args(argv=None):
                          "GEMM, token-ring, serving and mailbox-traffic configurations")
     ap.add_argument("--no-autotune", action="store_true", help="use --factor-batch/--factor-warps as given")
     ap.add_argument("--requests", type=int, default=100_000, help="serve: requests in the trace")
+    ap.add_argument("--scheduler", choices=["global", "steal"], default="global",
+                    help="ready-actor scheduler (factor, ring, mailbox, spawn): one global queue or work stealing")
     ap.add_argument("--fork-n", type=int, default=20, help="spawn: recursion counter n (2^(n+1) - 2 spawns per step)")
     ap.add_argument("--mandel-iters", default="120,1200", help="mandel: maximum iterations to run (comma list)")
     ap.add_argument("--mandel-shapes", default="single,image,row",
@@ -272,7 +274,7 @@ def run_ours(args):
         tuned = {"best": best, "measured": [[c, round(t * 1e3, 2)] for c, t in table] or "cached"}
     rt = C.Runtime(max_factor_n=(1 << 56) - 1, max_actors=wl.n_actors, mailbox_capacity=512,
                    ingress_capacity=1 << 17, max_inflight_requests=1 << 17, factor_batch=args.factor_batch,
-                   factor_warps=args.factor_warps, ctas_per_sm=args.ctas_per_sm)
+                   factor_warps=args.factor_warps, ctas_per_sm=args.ctas_per_sm, scheduler=_sched(args))
     for _ in range(wl.n_actors):
         rt.spawn(C.FACTOR_U64)
     m = np.zeros(count, C.DMSG_DTYPE)
@@ -361,7 +363,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "messages": count, "actors": wl.n_actors,
                    "factor_batch": args.factor_batch, "factor_warps": args.factor_warps,
-                   "ctas_per_sm": args.ctas_per_sm, "l2": "flushed between steps (256 MiB write)",
+                   "ctas_per_sm": args.ctas_per_sm, "scheduler": args.scheduler,
+                   "l2": "flushed between steps (256 MiB write)",
                    "timing": "CUDA events on the runtime stream, per step",
                    "autotune": tuned if tuned else "off"},
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
@@ -441,6 +444,10 @@ def run_ours(args):
 # other configurations (measurement lines for the record; the default line is
 # the default batched-factorization workload)
 # ---------------------------------------------------------------------------
+def _sched(args) -> int:
+    return 1 if getattr(args, "scheduler", "global") == "steal" else 0
+
+
 def _note(msg):
     print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
@@ -567,7 +574,7 @@ def run_ring(args):
     R, L, rounds = wl.n_rings, wl.ring_len, wl.n.shape[1]
     out = {}
     for label, with_factor in (("tokens_only", False), ("mixed", True)):
-        with C.Runtime(max_actors=R * (L + 1)) as rt:
+        with C.Runtime(max_actors=R * (L + 1), scheduler=_sched(args)) as rt:
             d_n = torch.from_numpy(wl.n.astype(np.uint64).reshape(-1).copy()).cuda()
             d_rep = torch.zeros(R * rounds * 32, dtype=torch.uint8, device="cuda")
             masters = []
@@ -728,7 +735,7 @@ def run_mailbox(args):
     for label, n_src, n_sink, per in (("n_to_1", 100, 1, 20_000), ("pairs", 1024, 1024, 2_000)):
         # the slot pool is max_actors x the default capacity: the sinks' size
         sink_cap = 1 << 14 if n_sink == 1 else 4096
-        with C.Runtime(max_actors=n_src + n_sink, mailbox_capacity=sink_cap) as rt:
+        with C.Runtime(max_actors=n_src + n_sink, mailbox_capacity=sink_cap, scheduler=_sched(args)) as rt:
             sinks = [rt.spawn(C.SINK) for _ in range(n_sink)]
             srcs = [rt.spawn(C.SOURCE, next=sinks[i % n_sink], mailbox_capacity=4) for i in range(n_src)]
             m = np.zeros(n_src, C.DMSG_DTYPE)
@@ -952,7 +959,8 @@ def run_spawn(args):
     # (64 B each) written and read
     bytes_per_actor = 128 + 2 * 128
     clocks = ClockSampler(physical_gpu(0))
-    with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=4, fork_pool=max(1 << 21, spawns)) as rt:
+    with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=4, fork_pool=max(1 << 21, spawns),
+                   scheduler=_sched(args)) as rt:
         root = rt.spawn(C.FORK)
         m = np.zeros(1, C.DMSG_DTYPE)
         m["actor"], m["kind"], m["u64"] = root - 1, C.FORK, n
@@ -989,7 +997,8 @@ def run_spawn(args):
         "metric": METRIC, "unit": "actors spawned/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "dtype": "u32", "data": "synthetic",
         "config": {"workload": f"actor creation: 2^{n} by recursive spawning, {spawns} device spawns and {msgs} "
-                               f"messages per step, one FORK root, pool of {max(1 << 21, spawns)} records"},
+                               f"messages per step, one FORK root, pool of {max(1 << 21, spawns)} records",
+                   "scheduler": args.scheduler},
         "value": spawns / t, "ms_per_step": 1e3 * t, "msgs_per_s": msgs / t,
         "roofline": {"bound": "hbm", "achieved": bytes_per_actor * spawns / t / 1e9, "peak": hbm, "unit": "GB/s",
                      "frac": bytes_per_actor * spawns / t / 1e9 / hbm, "bytes_per_actor": bytes_per_actor,

@@ -111,6 +111,11 @@ extern "C" {
 #define CAF_GPU_BACKEND_PERSISTENT          0  /* one persistent kernel drains all mailboxes */
 #define CAF_GPU_BACKEND_PER_MESSAGE_LAUNCH  1  /* one kernel launch per message (comparator)  */
 
+/* ---- schedulers (Sec. 6.2) ------------------------------------------------ */
+#define CAF_GPU_SCHED_GLOBAL  0u   /* one device-wide queue of ready actors                      */
+#define CAF_GPU_SCHED_STEAL   1u   /* a queue per worker CTA: the actors a CTA wakes go to its    */
+                                   /* own queue; an idle CTA steals from others (work stealing)  */
+
 /* ---- reply status ------------------------------------------------------- */
 #define CAF_GPU_REPLY_OK        0  /* factor: n = r0 * r1 with r0 the smallest divisor >= 2 */
 #define CAF_GPU_REPLY_NOFACTOR  1  /* factor: no divisor d >= 2 with d*d <= n; (r0, r1) = (1, n) */
@@ -150,6 +155,8 @@ typedef struct {
     void    *cuda_stream;           /* cudaStream_t for all work; NULL = runtime's own stream */
     uint32_t gemm_items_per_round;  /* GEMM work items a drain CTA takes per round, 1..8 (4)   */
     uint32_t fork_pool;             /* FORK actors the device may hold at once (2^21)          */
+    uint32_t scheduler;             /* ready actors: CAF_GPU_SCHED_* (global queue)            */
+    uint32_t pad;
 } caf_gpu_runtime_cfg;
 
 /* Per-actor configuration for caf_gpu_spawn (may be NULL for defaults). */

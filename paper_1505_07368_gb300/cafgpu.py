@@ -21,6 +21,7 @@ from . import _build
 OK, EINVAL, ENOMEM, EAGAIN, ETIMEDOUT, EDEAD, EWAITLIMIT, ESTATE, ECUDA = 0, -1, -2, -3, -4, -5, -6, -7, -8
 FACTOR_U64, GEMM_BF16, GEMM_SPLIT_BF16X3, RING_TOKEN, SINK, SOURCE, MANDELBROT, FORK = 1, 2, 3, 4, 5, 6, 7, 8
 BACKEND_PERSISTENT, BACKEND_PER_MESSAGE_LAUNCH = 0, 1
+SCHED_GLOBAL, SCHED_STEAL = 0, 1
 REPLY_OK, REPLY_NOFACTOR, REPLY_DEAD, REPLY_REJECTED = 0, 1, 2, 3
 MSG_START = 1
 ACTOR_MASTER = 1
@@ -52,7 +53,7 @@ class RuntimeCfg(ctypes.Structure):
                 ("wait_limit_ns", ctypes.c_uint64), ("idle_exit_ns", ctypes.c_uint64),
                 ("validation_mode", ctypes.c_uint32), ("log_capacity", ctypes.c_uint32),
                 ("cuda_stream", ctypes.c_void_p), ("gemm_items_per_round", ctypes.c_uint32),
-                ("fork_pool", ctypes.c_uint32)]
+                ("fork_pool", ctypes.c_uint32), ("scheduler", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 class ActorCfg(ctypes.Structure):

@@ -59,6 +59,42 @@ __device__ __forceinline__ void heartbeat(const DrainParams &P) {
     *((volatile uint64_t *)&P.ctl->heartbeat) = globaltimer();
 }
 
+// Ready actors (Sec. 6.2: the scheduler).  By default one global queue.  With
+// work stealing (P.steal) every CTA has its own queue: the actors a CTA wakes
+// go to its queue (to the global one when it is nearly full), and a worker
+// pops its CTA's queue first, then the global one (host messages, overflow),
+// then tries a few other CTAs' queues.  Only the owning CTA pushes to a local
+// queue, so kLocalQueueSlack bounds the pushes in flight past the check.
+__device__ __forceinline__ bool ready_push(const DrainParams &P, uint32_t a) {
+    if (P.steal) {
+        QueueHdr *q = &P.localq_hdr[blockIdx.x];
+        const uint64_t used = ld_relaxed_gpu(&q->enq) - ld_relaxed_gpu(&q->deq);
+        if (used + kLocalQueueSlack < P.localq_cap)
+            return q_push(q, P.localq + (size_t)blockIdx.x * P.localq_cap, a, P.wait_limit_ns);
+    }
+    return q_push(&P.ctl->readyq, P.readyq, a, P.wait_limit_ns);
+}
+
+// Lane 0: the next ready actor (1), none (0), or an expired wait (-1).  `rng`
+// is the caller's victim generator (a linear congruential step per try).
+__device__ int ready_pop(const DrainParams &P, uint32_t *a, uint32_t &rng) {
+    if (P.steal) {
+        const int pr = q_try_pop(&P.localq_hdr[blockIdx.x], P.localq + (size_t)blockIdx.x * P.localq_cap, a,
+                                 P.wait_limit_ns);
+        if (pr != 0) return pr;
+    }
+    const int pr = q_try_pop(&P.ctl->readyq, P.readyq, a, P.wait_limit_ns);
+    if (pr != 0 || !P.steal || gridDim.x < 2) return pr;
+    for (uint32_t k = 0; k < kStealTries; ++k) {
+        rng = rng * 1664525u + 1013904223u;
+        const uint32_t v = (rng >> 8) % gridDim.x;
+        if (v == blockIdx.x) continue;
+        const int ps = q_try_pop(&P.localq_hdr[v], P.localq + (size_t)v * P.localq_cap, a, P.wait_limit_ns);
+        if (ps != 0) return ps;
+    }
+    return 0;
+}
+
 // Warp-collective enqueue: every lane with `valid` holds one message for
 // actor `a`; lanes are in send order.  Messages that fit are published, the
 // receiver is woken, and only then do lanes whose slot is still occupied wait
@@ -109,7 +145,7 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
         if (valid && (int)lane == leader) {
             if (cas_u32(&A->state, kWaiting, kReady) == kWaiting) {
                 if (handoff) woke = true;
-                else qok = q_push(&P.ctl->readyq, P.readyq, a, P.wait_limit_ns);
+                else qok = ready_push(P, a);
             }
         }
         if (handoff) {
@@ -140,7 +176,7 @@ __device__ void release_actor(const DrainParams &P, uint32_t a, uint64_t new_hea
             asm volatile("fence.sc.gpu;" ::: "memory");
             if (ld_relaxed_gpu(&A->tail) != new_head &&
                 cas_u32(&A->state, kWaiting, kReady) == kWaiting) {
-                if (!q_push(&P.ctl->readyq, P.readyq, a, P.wait_limit_ns)) fail(P, kErrWaitQueue, 3);
+                if (!ready_push(P, a)) fail(P, kErrWaitQueue, 3);
             }
         }
     }
@@ -599,7 +635,7 @@ __device__ void claim_ring(const DrainParams &P, uint32_t a) {
         cur = run_ring_actor(P, cur);
         if ((i & 255) == 0 && lane_id() == 0) heartbeat(P);
     }
-    if (cur != kNone && lane_id() == 0 && !q_push(&P.ctl->readyq, P.readyq, cur, P.wait_limit_ns))
+    if (cur != kNone && lane_id() == 0 && !ready_push(P, cur))
         fail(P, kErrWaitQueue, 18);
     __syncwarp();
 }
@@ -1417,14 +1453,14 @@ __device__ __noinline__ void drain_mandel_bands(const DrainParams &P, GroupShare
 // factor actors into a fresh batch record, and run ring-token actors on the
 // way (a few at most, so the group forms quickly).
 template <bool kGemm>
-__device__ uint32_t find_batch(const DrainParams &P) {
+__device__ uint32_t find_batch(const DrainParams &P, uint32_t &rng) {
     const uint32_t lane = lane_id();
     DevCtl *ctl = P.ctl;
     for (int attempt = 0; attempt < 4; ++attempt) {
         uint32_t a = 0;
         bool got = false;
         if (lane == 0) {
-            const int pr = q_try_pop(&ctl->readyq, P.readyq, &a, P.wait_limit_ns);
+            const int pr = ready_pop(P, &a, rng);
             if (pr < 0) fail(P, kErrWaitQueue, 22);
             got = pr > 0;
         }
@@ -1443,7 +1479,7 @@ __device__ uint32_t find_batch(const DrainParams &P) {
             gb = __shfl_sync(FULL, gb, 0);
             if (!gb) {
                 // no batch record free: leave the actor READY for later
-                if (lane == 0 && !q_push(&ctl->readyq, P.readyq, a, P.wait_limit_ns)) fail(P, kErrWaitQueue, 7);
+                if (lane == 0 && !ready_push(P, a)) fail(P, kErrWaitQueue, 7);
                 __syncwarp();
                 return kNone;
             }
@@ -1559,6 +1595,7 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
     uint64_t idle_start = 0;
     uint32_t idle_ns = 256;
     uint32_t held = kNone;                 // a team leader's claimed batch, kept across GEMM tiles
+    uint32_t rng = (blockIdx.x * kWarpsPerCta + warp) * 2654435761u + 1u;   // steal victims
     GemmCounters gk{0, 0, 0, 0};
     uint64_t seen_completed = 0, seen_at = 0;   // completion watchdog (producer lane)
     uint32_t rounds = 0;
@@ -1572,7 +1609,7 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
             bool skip = false;
             if ((kGemm || P.mandel) && lane == 0)
                 skip = q_len(&ctl->workq) + q_len(&ctl->packq) > 2 * (int64_t)gridDim.x;
-            if (!__shfl_sync(FULL, skip, 0)) held = find_batch<kGemm>(P);
+            if (!__shfl_sync(FULL, skip, 0)) held = find_batch<kGemm>(P, rng);
         }
         if (!producer && lane == 0) G.batch[ci] = (team_ok && rank == 0) ? held : kNone;
         if (producer) {

@@ -389,6 +389,15 @@ struct DrainParams {
     QCell *forkq;
     uint32_t fork_base;
     uint32_t fork_pool;
+    // work stealing (steal != 0): CTA b's ready queue is localq_hdr[b] with
+    // cells localq[b * localq_cap ..]
+    QueueHdr *localq_hdr;
+    QCell *localq;
+    uint32_t localq_cap;
+    uint32_t steal;
 };
+constexpr uint32_t kLocalQueueCap = 4096;     // ready actors per CTA queue
+constexpr uint32_t kLocalQueueSlack = 1024;   // room kept for the CTA's concurrent pushes (9 warps x 32 wakes)
+constexpr uint32_t kStealTries = 4;           // victims a worker tries per empty pop
 
 }  // namespace cafgpu

@@ -71,6 +71,8 @@ struct caf_gpu_runtime {
     QCell *d_forkq = nullptr;              // free ids of the FORK actor pool
     uint32_t fork_base = 0, fork_pool = 0; // pool ids fork_base .. fork_base + fork_pool - 1 (0: no pool yet)
     bool graphs_made = false;              // a CUDA graph holds the current table addresses
+    QueueHdr *d_localq_hdr = nullptr;      // work stealing: a ready queue per CTA
+    QCell *d_localq = nullptr;
     QCell *d_jobq = nullptr, *d_jobq_large = nullptr;
     uint32_t jobq_cap = 0;
     uint8_t *d_pack_small = nullptr, *d_pack_large = nullptr;   // packed-operand scratch of the job records
@@ -164,6 +166,10 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.mjobs = rt->d_mjobs;
     p.mjobq = rt->d_mjobq;
     p.forkq = rt->d_forkq;
+    p.localq_hdr = rt->d_localq_hdr;
+    p.localq = rt->d_localq;
+    p.localq_cap = kLocalQueueCap;
+    p.steal = rt->d_localq ? 1u : 0u;
     p.fork_base = rt->fork_base;
     p.fork_pool = rt->fork_pool;
     p.pack_small = rt->d_pack_small;
@@ -418,6 +424,8 @@ void free_runtime(caf_gpu_runtime *rt) {
     cudaFree(rt->d_mjobq);
     cudaFree(rt->d_mjobs);
     cudaFree(rt->d_forkq);
+    cudaFree(rt->d_localq_hdr);
+    cudaFree(rt->d_localq);
     cudaFree(rt->d_pack_small);
     cudaFree(rt->d_pack_large);
     if (rt->gemm_descs) cudaFreeHost(rt->gemm_descs);
@@ -455,6 +463,7 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     if (!c.log_capacity) c.log_capacity = 1u << 20;
     if (!c.gemm_items_per_round) c.gemm_items_per_round = 4;
     if (!c.fork_pool) c.fork_pool = 1u << 21;
+    if (c.scheduler > CAF_GPU_SCHED_STEAL) return CAF_GPU_EINVAL;
     if ((uint64_t)c.max_actors + c.fork_pool >= (1ull << 31)) return CAF_GPU_EINVAL;
     if (c.gemm_items_per_round > kMaxItemsPerRound) return CAF_GPU_EINVAL;
     if (!is_pow2(c.mailbox_capacity) || !is_pow2(c.ingress_capacity)) return CAF_GPU_EINVAL;
@@ -527,6 +536,25 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     if (c.validation_mode) {
         CK(cudaMalloc(&rt->d_log, sizeof(LogRow) * (size_t)c.log_capacity));
         CK(cudaMemset(rt->d_log, 0, sizeof(LogRow) * (size_t)c.log_capacity));
+    }
+    if (c.scheduler == CAF_GPU_SCHED_STEAL) {
+        // one queue per CTA of the larger grid; cell i of a queue starts free for position i
+        const uint32_t nq = std::max(rt->grid_factor, rt->grid_mixed);
+        CK(cudaMalloc(&rt->d_localq_hdr, sizeof(QueueHdr) * nq));
+        CK(cudaMalloc(&rt->d_localq, sizeof(QCell) * (size_t)nq * kLocalQueueCap));
+        std::vector<QueueHdr> hdr(nq);
+        for (auto &h : hdr) {
+            memset(&h, 0, sizeof(h));
+            h.mask = kLocalQueueCap - 1;
+        }
+        std::vector<QCell> cells((size_t)nq * kLocalQueueCap);
+        for (size_t i = 0; i < cells.size(); ++i) {
+            cells[i].seq = i % kLocalQueueCap;
+            cells[i].val = 0;
+            cells[i].pad = 0;
+        }
+        CK(cudaMemcpy(rt->d_localq_hdr, hdr.data(), sizeof(QueueHdr) * nq, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(rt->d_localq, cells.data(), sizeof(QCell) * cells.size(), cudaMemcpyHostToDevice));
     }
     CK(cudaMalloc(&rt->d_scratch, 64));
     CK(cudaMemset(rt->d_scratch, 0, 64));

@@ -42,7 +42,7 @@ def test_struct_sizes():
     assert cafgpu.SERVE_RESULT_DTYPE.itemsize == 48
     assert ctypes.sizeof(cafgpu.ServeCfg) == 32
     assert ctypes.sizeof(cafgpu.ServeStats) == 32
-    assert ctypes.sizeof(cafgpu.RuntimeCfg) == 88
+    assert ctypes.sizeof(cafgpu.RuntimeCfg) == 96
     assert ctypes.sizeof(cafgpu.Stats) == 96
 
 
