@@ -75,6 +75,18 @@ __device__ __forceinline__ bool ready_push(const DrainParams &P, uint32_t a) {
     return q_push(&P.ctl->readyq, P.readyq, a, P.wait_limit_ns);
 }
 
+// Steal an actor from up to kStealTries random other CTAs' queues.
+__device__ __noinline__ int ready_steal(const DrainParams &P, uint32_t *a, uint32_t &rng) {
+    for (uint32_t k = 0; k < kStealTries; ++k) {
+        rng = rng * 1664525u + 1013904223u;
+        const uint32_t v = (rng >> 8) % gridDim.x;
+        if (v == blockIdx.x) continue;
+        const int ps = q_try_pop(&P.localq_hdr[v], P.localq + (size_t)v * P.localq_cap, a, P.wait_limit_ns);
+        if (ps != 0) return ps;
+    }
+    return 0;
+}
+
 // Lane 0: the next ready actor (1), none (0), or an expired wait (-1).  `rng`
 // is the caller's victim generator (a linear congruential step per try).
 __device__ int ready_pop(const DrainParams &P, uint32_t *a, uint32_t &rng) {
@@ -85,14 +97,7 @@ __device__ int ready_pop(const DrainParams &P, uint32_t *a, uint32_t &rng) {
     }
     const int pr = q_try_pop(&P.ctl->readyq, P.readyq, a, P.wait_limit_ns);
     if (pr != 0 || !P.steal || gridDim.x < 2) return pr;
-    for (uint32_t k = 0; k < kStealTries; ++k) {
-        rng = rng * 1664525u + 1013904223u;
-        const uint32_t v = (rng >> 8) % gridDim.x;
-        if (v == blockIdx.x) continue;
-        const int ps = q_try_pop(&P.localq_hdr[v], P.localq + (size_t)v * P.localq_cap, a, P.wait_limit_ns);
-        if (ps != 0) return ps;
-    }
-    return 0;
+    return ready_steal(P, a, rng);
 }
 
 // Warp-collective enqueue: every lane with `valid` holds one message for
@@ -657,7 +662,7 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 // Claimed SINK `a`: take up to kSinkChunk messages, 32 per dequeue; each adds
 // 1 to the count and its value to the sum; a request's reply is (count after
 // it, value).
-__device__ void run_sink(const DrainParams &P, uint32_t a) {
+__device__ __noinline__ void run_sink(const DrainParams &P, uint32_t a) {
     const uint32_t lane = lane_id();
     ActorDesc *A = &P.actors[a];
     if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
@@ -696,7 +701,7 @@ __device__ void run_sink(const DrainParams &P, uint32_t a) {
 // c in the low and k0 in the high 32 bits: send up to kSourceChunk messages
 // (k0 + i) to the target SINK, 32 per warp-wide enqueue, then either send the
 // continuation (c', k0') to itself or, when all are sent, reply (total, 0).
-__device__ void run_source(const DrainParams &P, uint32_t a) {
+__device__ __noinline__ void run_source(const DrainParams &P, uint32_t a) {
     const uint32_t lane = lane_id();
     ActorDesc *A = &P.actors[a];
     if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
@@ -791,7 +796,7 @@ __device__ bool fork_answer(const DrainParams &P, uint32_t a, uint64_t value, ui
 // below).  A pool actor terminates after answering and returns its id to the
 // pool; a root (spawned by the host) stays for the next computation.  A start
 // message that reaches a root still waiting for results is rejected.
-__device__ void run_fork(const DrainParams &P, uint32_t a) {
+__device__ __noinline__ void run_fork(const DrainParams &P, uint32_t a) {
     const uint32_t lane = lane_id();
     ActorDesc *A = &P.actors[a];
     const bool pooled = a >= P.fork_base && a - P.fork_base < P.fork_pool;
