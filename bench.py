@@ -70,9 +70,6 @@ def parse_args(argv=None):
     ap.add_argument("--requests", type=int, default=100_000, help="serve: requests in the trace")
     ap.add_argument("--scheduler", choices=["global", "steal"], default="global",
                     help="ready-actor scheduler (factor, ring, mailbox, spawn): one global queue or work stealing")
-    ap.add_argument("--leader-warps", type=int, default=1,
-                    help="spawn, mailbox: warps per team (1: every consumer warp claims actors; there are no "
-                         "factor batches to share)")
     ap.add_argument("--fork-n", type=int, default=20, help="spawn: recursion counter n (2^(n+1) - 2 spawns per step)")
     ap.add_argument("--mandel-iters", default="120,1200", help="mandel: maximum iterations to run (comma list)")
     ap.add_argument("--mandel-shapes", default="single,image,row",
@@ -738,8 +735,7 @@ def run_mailbox(args):
     for label, n_src, n_sink, per in (("n_to_1", 100, 1, 20_000), ("pairs", 1024, 1024, 2_000)):
         # the slot pool is max_actors x the default capacity: the sinks' size
         sink_cap = 1 << 14 if n_sink == 1 else 4096
-        with C.Runtime(max_actors=n_src + n_sink, mailbox_capacity=sink_cap, scheduler=_sched(args),
-                       factor_warps=args.leader_warps) as rt:
+        with C.Runtime(max_actors=n_src + n_sink, mailbox_capacity=sink_cap, scheduler=_sched(args)) as rt:
             sinks = [rt.spawn(C.SINK) for _ in range(n_sink)]
             srcs = [rt.spawn(C.SOURCE, next=sinks[i % n_sink], mailbox_capacity=4) for i in range(n_src)]
             m = np.zeros(n_src, C.DMSG_DTYPE)
@@ -964,7 +960,7 @@ def run_spawn(args):
     bytes_per_actor = 128 + 2 * 128
     clocks = ClockSampler(physical_gpu(0))
     with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=4, fork_pool=max(1 << 21, spawns),
-                   scheduler=_sched(args), factor_warps=args.leader_warps) as rt:
+                   scheduler=_sched(args)) as rt:
         root = rt.spawn(C.FORK)
         m = np.zeros(1, C.DMSG_DTYPE)
         m["actor"], m["kind"], m["u64"] = root - 1, C.FORK, n
@@ -1002,7 +998,8 @@ def run_spawn(args):
         "higher_is_better": True, "dtype": "u32", "data": "synthetic",
         "config": {"workload": f"actor creation: 2^{n} by recursive spawning, {spawns} device spawns and {msgs} "
                                f"messages per step, one FORK root, pool of {max(1 << 21, spawns)} records",
-                   "scheduler": args.scheduler, "warps_per_team": args.leader_warps},
+                   "scheduler": args.scheduler,
+                   "warps_per_team": "1 (the runtime's choice when no factor actor exists)"},
         "value": spawns / t, "ms_per_step": 1e3 * t, "msgs_per_s": msgs / t,
         "roofline": {"bound": "hbm", "achieved": bytes_per_actor * spawns / t / 1e9, "peak": hbm, "unit": "GB/s",
                      "frac": bytes_per_actor * spawns / t / 1e9 / hbm, "bytes_per_actor": bytes_per_actor,

@@ -78,6 +78,7 @@ struct caf_gpu_runtime {
     uint8_t *d_pack_small = nullptr, *d_pack_large = nullptr;   // packed-operand scratch of the job records
     bool gemm_enabled = false;             // a GEMM actor exists: drains use the GEMM layout
     bool mandel_enabled = false;           // a MANDELBROT actor exists: drains run work items
+    uint32_t n_factor_actors = 0;          // FACTOR actors spawned (teams of factor_warps need them)
     unsigned grid_factor = 0, grid_mixed = 0;
     uint32_t *d_primes = nullptr, *d_pinv = nullptr, *d_plim = nullptr;
     uint32_t nprimes = 0;
@@ -148,7 +149,9 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.plim = rt->d_plim;
     p.nprimes = rt->nprimes;
     p.factor_k = rt->cfg.factor_batch;
-    p.factor_w = rt->cfg.factor_warps;
+    // warps share factor batches in teams; without factor actors every
+    // consumer warp leads its own team, so every warp claims actors
+    p.factor_w = rt->n_factor_actors ? rt->cfg.factor_warps : 1u;
     p.max_claim = rt->cfg.max_msgs_per_claim;
     p.gemm_items = rt->cfg.gemm_items_per_round;
     p.max_n = rt->cfg.max_factor_n;
@@ -763,6 +766,7 @@ int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_c
         d.user_state = c.init_state;
     }
     if (kernel_id == kFork) d.next = kNone;   // a root: its answer is the computation's reply
+    if (kernel_id == kFactor) ++rt->n_factor_actors;
     if (kernel_id == kSource) {
         // the target must be an existing SINK
         if (c.next == 0 || c.next > rt->n_actors || rt->actors[c.next - 1].kind != kSink) return CAF_GPU_EINVAL;
