@@ -666,35 +666,43 @@ int make_fork_pool(caf_gpu_runtime *rt) {
     const uint64_t n_slots = rt->n_slots + (uint64_t)kForkSlots * pool;
     ActorDesc *actors = nullptr;
     Slot *slots = nullptr;
-    if (cudaMalloc(&actors, sizeof(ActorDesc) * n_act) != cudaSuccess) {
-        cudaGetLastError();
-        return CAF_GPU_ENOMEM;
-    }
-    if (cudaMalloc(&slots, sizeof(Slot) * n_slots) != cudaSuccess) {
+    QCell *forkq = nullptr, *readyq = nullptr;
+    // on any failure, free what this call made; the runtime keeps its old table
+    auto fail_with = [&](int code) {
         cudaGetLastError();
         cudaFree(actors);
-        return CAF_GPU_ENOMEM;
-    }
-    CK(cudaMemcpyAsync(actors, rt->d_actors, sizeof(ActorDesc) * base, cudaMemcpyDeviceToDevice, rt->setup));
-    CK(cudaMemcpyAsync(slots, rt->d_slots, sizeof(Slot) * rt->n_slots, cudaMemcpyDeviceToDevice, rt->setup));
-    CK(cudaMemsetAsync(slots + rt->n_slots, 0, sizeof(Slot) * (n_slots - rt->n_slots), rt->setup));
-    CK(launch_fork_pool_init(actors, base, pool, rt->n_slots, rt->setup));
+        cudaFree(slots);
+        cudaFree(forkq);
+        cudaFree(readyq);
+        return code;
+    };
+    if (cudaMalloc(&actors, sizeof(ActorDesc) * n_act) != cudaSuccess) return fail_with(CAF_GPU_ENOMEM);
+    if (cudaMalloc(&slots, sizeof(Slot) * n_slots) != cudaSuccess) return fail_with(CAF_GPU_ENOMEM);
+    if (cudaMemcpyAsync(actors, rt->d_actors, sizeof(ActorDesc) * base, cudaMemcpyDeviceToDevice, rt->setup) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(slots, rt->d_slots, sizeof(Slot) * rt->n_slots, cudaMemcpyDeviceToDevice, rt->setup) !=
+            cudaSuccess ||
+        cudaMemsetAsync(slots + rt->n_slots, 0, sizeof(Slot) * (n_slots - rt->n_slots), rt->setup) != cudaSuccess ||
+        launch_fork_pool_init(actors, base, pool, rt->n_slots, rt->setup) != cudaSuccess ||
+        cudaStreamSynchronize(rt->setup) != cudaSuccess)
+        return fail_with(CAF_GPU_ECUDA);
+    // the free-id queue, and a ready queue that holds every actor once (an
+    // actor is pushed on the waiting -> ready transition only).  No drain
+    // runs, so every actor is parked and the old ready queue is empty.  If the
+    // second fails, the first's header is left unused (fork_pool stays 0).
+    const uint32_t forkq_cap = (uint32_t)next_pow2((uint64_t)pool + 1);
+    const uint32_t readyq_cap = (uint32_t)next_pow2(n_act + 1);
     std::vector<uint32_t> ids(pool);
     for (uint32_t i = 0; i < pool; ++i) ids[i] = base + i;
-    int r = init_queue(rt, &rt->d_forkq, (uint32_t)next_pow2((uint64_t)pool + 1), &rt->d_ctl->forkq, ids);
-    if (r) return r;
-    // the ready queue holds each actor at most once (it is pushed on the
-    // waiting -> ready transition only): make room for the pool.  No drain
-    // runs, so every actor is parked and the queue is empty.
-    QCell *readyq = nullptr;
-    const uint32_t readyq_cap = (uint32_t)next_pow2(n_act + 1);
-    if ((r = init_queue(rt, &readyq, readyq_cap, &rt->d_ctl->readyq, {}))) return r;
+    int r = init_queue(rt, &forkq, forkq_cap, &rt->d_ctl->forkq, ids);
+    if (r) return fail_with(r);
+    if ((r = init_queue(rt, &readyq, readyq_cap, &rt->d_ctl->readyq, {}))) return fail_with(r);
     cudaFree(rt->d_readyq);
-    rt->d_readyq = readyq;
-    rt->readyq_cap = readyq_cap;
-    CK(cudaStreamSynchronize(rt->setup));
     cudaFree(rt->d_actors);
     cudaFree(rt->d_slots);
+    rt->d_readyq = readyq;
+    rt->readyq_cap = readyq_cap;
+    rt->d_forkq = forkq;
     rt->d_actors = actors;
     rt->d_slots = slots;     // rt->n_slots stays the host actors' region; the pool's slots follow it
     rt->fork_base = base;

@@ -58,3 +58,23 @@ def test_create_without_gpu_fails_loudly():
     with pytest.raises(cafgpu.CafGpuError) as e:
         cafgpu.Runtime(max_factor_n=1 << 20)
     assert e.value.code == cafgpu.ECUDA
+
+
+def test_header_constants_match_binding():
+    src = open(HEADER).read()
+    defs = dict(re.findall(r"#define\s+CAF_GPU_(\w+)\s+\(?(-?\d+)u?\)?", src))
+    want = {
+        "FACTOR_U64": cafgpu.FACTOR_U64, "GEMM_BF16": cafgpu.GEMM_BF16,
+        "GEMM_SPLIT_BF16X3": cafgpu.GEMM_SPLIT_BF16X3, "RING_TOKEN": cafgpu.RING_TOKEN,
+        "SINK": cafgpu.SINK, "SOURCE": cafgpu.SOURCE, "MANDELBROT": cafgpu.MANDELBROT, "FORK": cafgpu.FORK,
+        "SCHED_GLOBAL": cafgpu.SCHED_GLOBAL, "SCHED_STEAL": cafgpu.SCHED_STEAL,
+        "BACKEND_PERSISTENT": cafgpu.BACKEND_PERSISTENT,
+        "BACKEND_PER_MESSAGE_LAUNCH": cafgpu.BACKEND_PER_MESSAGE_LAUNCH,
+        "REPLY_OK": cafgpu.REPLY_OK, "REPLY_NOFACTOR": cafgpu.REPLY_NOFACTOR,
+        "REPLY_DEAD": cafgpu.REPLY_DEAD, "REPLY_REJECTED": cafgpu.REPLY_REJECTED,
+        "EINVAL": cafgpu.EINVAL, "ENOMEM": cafgpu.ENOMEM, "EAGAIN": cafgpu.EAGAIN,
+        "ETIMEDOUT": cafgpu.ETIMEDOUT, "EDEAD": cafgpu.EDEAD, "EWAITLIMIT": cafgpu.EWAITLIMIT,
+        "ESTATE": cafgpu.ESTATE, "ECUDA": cafgpu.ECUDA,
+    }
+    for name, value in want.items():
+        assert int(defs[name]) == value, name
