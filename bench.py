@@ -619,6 +619,30 @@ def run_ring(args):
             msgs = R * (hops + 1) + (R * rounds if with_factor else 0)
             out[label] = {"ms_per_step": 1e3 * t, "msgs_per_s": msgs / t, "ns_per_hop": 1e9 * t / hops,
                           "messages": msgs}
+            if not args.skip_per_message:
+                # the same workload with one kernel launch per message: the host sends
+                # each master its start message and launches the messages each wave
+                # produces until none is left (one run; it takes seconds)
+                rt.set_backend(C.BACKEND_PER_MESSAGE_LAUNCH)
+                rt.reset_actors()
+                d_rep.zero_()
+                rt.stream_sync()
+                torch.cuda.synchronize()
+                rt.stats()                 # restart the launch count
+                t0 = time.perf_counter()
+                for mst in masters:
+                    rt.send(mst, C.Runtime.msg(C.RING_TOKEN, wl.token, flags=C.MSG_START))
+                rt.sync()
+                tp = time.perf_counter() - t0
+                launches = rt.stats()["launches"]
+                if with_factor:
+                    rep_ = d_rep.cpu().numpy().view(C.DREPLY_DTYPE).reshape(R, rounds)
+                    n_ = wl.n.astype(np.uint64)
+                    if not (np.all(rep_["status"] == 0) and np.array_equal(rep_["r0"] * rep_["r1"], n_)):
+                        raise SystemExit("bench: ring: per-message factor replies wrong")
+                out[label]["per_message_launch"] = {"ms": 1e3 * tp, "msgs_per_s": msgs / tp, "launches": launches,
+                                                    "speedup_persistent": tp / t,
+                                                    "timing": "host wall clock around the sends and caf_gpu_sync"}
     print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "token rings (64 x 128, token 1000) + "
                       "8 factorization requests per ring, captured CUDA graph", "steps": args.steps,
                       "results": out, "value": out["mixed"]["msgs_per_s"]}))
