@@ -588,6 +588,10 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a) {
     uint64_t head = *((volatile uint64_t *)&A->head);
     const uint64_t tail = ld_acquire_gpu(&A->tail);
     uint64_t take = tail - head;
+    // tail counts tickets a sender may not have published yet; a ticket at or
+    // past head + capacity waits for room that this claim only releases at
+    // its end, so a claim never goes past one mailbox's worth
+    if (take > (uint64_t)A->cap_mask + 1) take = (uint64_t)A->cap_mask + 1;
     if (P.max_claim && take > P.max_claim) take = P.max_claim;
     if (lane == 0) add_u64(&P.ctl->claims, 1);
     for (uint64_t i = 0; i < take; ++i) {
@@ -671,6 +675,10 @@ __device__ __noinline__ void run_sink(const DrainParams &P, uint32_t a) {
     const uint64_t tail = ld_acquire_gpu(&A->tail);
     uint64_t left = tail - head;
     if (left > kSinkChunk) left = kSinkChunk;
+    // tail counts tickets a sender may not have published yet; a ticket at or
+    // past head + capacity waits for room that this claim only releases at
+    // its end, so a claim never goes past one mailbox's worth
+    if (left > (uint64_t)A->cap_mask + 1) left = (uint64_t)A->cap_mask + 1;
     if (P.max_claim && left > P.max_claim) left = P.max_claim;
     if (lane == 0) add_u64(&P.ctl->claims, 1);
     uint64_t count = A->sink_count, sum = A->sink_sum, handled = 0;
