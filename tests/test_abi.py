@@ -78,3 +78,16 @@ def test_header_constants_match_binding():
     }
     for name, value in want.items():
         assert int(defs[name]) == value, name
+
+
+@pytest.mark.parametrize("bad", [
+    {"factor_warps": 3}, {"factor_batch": 17}, {"ctas_per_sm": 5}, {"mailbox_capacity": 48},
+    {"ingress_capacity": 1000}, {"max_factor_n": 1 << 62}, {"gemm_items_per_round": 9},
+    {"scheduler": 2}, {"max_actors": (1 << 24) + 1}, {"max_actors": 1 << 20, "fork_pool": (1 << 31) - (1 << 20)},
+])
+def test_bad_runtime_settings_rejected_before_any_cuda_call(bad):
+    # the settings are checked before the runtime touches the device, so this
+    # holds with or without a GPU
+    with pytest.raises(cafgpu.CafGpuError) as e:
+        cafgpu.Runtime(**bad)
+    assert e.value.code == cafgpu.EINVAL, bad
