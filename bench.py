@@ -70,6 +70,9 @@ def parse_args(argv=None):
     ap.add_argument("--requests", type=int, default=100_000, help="serve: requests in the trace")
     ap.add_argument("--scheduler", choices=["global", "steal"], default="global",
                     help="ready-actor scheduler (factor, ring, mailbox, spawn): one global queue or work stealing")
+    ap.add_argument("--factor-split", type=int, default=0,
+                    help="factor, ring, serve: split large factor batches over idle teams, up to this many "
+                         "segments (0: off)")
     ap.add_argument("--fork-n", type=int, default=20, help="spawn: recursion counter n (2^(n+1) - 2 spawns per step)")
     ap.add_argument("--mandel-iters", default="120,1200", help="mandel: maximum iterations to run (comma list)")
     ap.add_argument("--mandel-shapes", default="single,image,row",
@@ -274,7 +277,8 @@ def run_ours(args):
         tuned = {"best": best, "measured": [[c, round(t * 1e3, 2)] for c, t in table] or "cached"}
     rt = C.Runtime(max_factor_n=(1 << 56) - 1, max_actors=wl.n_actors, mailbox_capacity=512,
                    ingress_capacity=1 << 17, max_inflight_requests=1 << 17, factor_batch=args.factor_batch,
-                   factor_warps=args.factor_warps, ctas_per_sm=args.ctas_per_sm, scheduler=_sched(args))
+                   factor_warps=args.factor_warps, ctas_per_sm=args.ctas_per_sm, scheduler=_sched(args),
+                   factor_split=args.factor_split)
     for _ in range(wl.n_actors):
         rt.spawn(C.FACTOR_U64)
     m = np.zeros(count, C.DMSG_DTYPE)
@@ -363,7 +367,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "messages": count, "actors": wl.n_actors,
                    "factor_batch": args.factor_batch, "factor_warps": args.factor_warps,
-                   "ctas_per_sm": args.ctas_per_sm, "scheduler": args.scheduler,
+                   "ctas_per_sm": args.ctas_per_sm, "scheduler": args.scheduler, "factor_split": args.factor_split,
                    "l2": "flushed between steps (256 MiB write)",
                    "timing": "CUDA events on the runtime stream, per step",
                    "autotune": tuned if tuned else "off"},
@@ -574,7 +578,7 @@ def run_ring(args):
     R, L, rounds = wl.n_rings, wl.ring_len, wl.n.shape[1]
     out = {}
     for label, with_factor in (("tokens_only", False), ("mixed", True)):
-        with C.Runtime(max_actors=R * (L + 1), scheduler=_sched(args)) as rt:
+        with C.Runtime(max_actors=R * (L + 1), scheduler=_sched(args), factor_split=args.factor_split) as rt:
             d_n = torch.from_numpy(wl.n.astype(np.uint64).reshape(-1).copy()).cuda()
             d_rep = torch.zeros(R * rounds * 32, dtype=torch.uint8, device="cuda")
             masters = []
@@ -645,6 +649,7 @@ def run_ring(args):
                                                     "timing": "host wall clock around the sends and caf_gpu_sync"}
     print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "token rings (64 x 128, token 1000) + "
                       "8 factorization requests per ring, captured CUDA graph", "steps": args.steps,
+                      "factor_split": args.factor_split,
                       "results": out, "value": out["mixed"]["msgs_per_s"]}))
     return 0
 
@@ -679,7 +684,7 @@ def run_serve(args):
         return reqs
 
     with C.Runtime(max_actors=n_f + n_g, mailbox_capacity=256, max_inflight_requests=1 << 17,
-                   ingress_capacity=1 << 17) as rt:
+                   ingress_capacity=1 << 17, factor_split=args.factor_split) as rt:
         af = [rt.spawn(C.FACTOR_U64) for _ in range(n_f)]
         ag = [rt.spawn(C.GEMM_SPLIT_BF16X3) for _ in range(n_g)]
         closed = trace(base_wl, af, ag)

@@ -157,7 +157,9 @@ typedef struct {
     uint32_t gemm_items_per_round;  /* GEMM work items a drain CTA takes per round, 1..8 (4)   */
     uint32_t fork_pool;             /* FORK actors the device may hold at once (2^21)          */
     uint32_t scheduler;             /* ready actors: CAF_GPU_SCHED_* (global queue)            */
-    uint32_t pad;
+    uint32_t factor_split;          /* 0 or 1: off; else a large factor batch is split into up */
+                                    /* to this many (<= 32) segments that idle teams in other  */
+                                    /* CTAs sweep                                               */
 } caf_gpu_runtime_cfg;
 
 /* Per-actor configuration for caf_gpu_spawn (may be NULL for defaults). */

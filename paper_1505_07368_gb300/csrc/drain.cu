@@ -345,16 +345,88 @@ __device__ void group_produce(const DrainParams &P, GroupShared &G, TableTile *r
     }
 }
 
-// Consumer warp: sweep batch b (kNone: only keep the ring moving) over the
-// streamed tiles.  A team of `wpb` warps shares one batch; member `r` tests
-// the chunks u of each tile with u % wpb == r, and members drop messages that
-// another member has already decided below their position.
+// Table producer (one lane of the producer warp): streams, in increasing
+// order, every table tile some team of the group needs, until none is needed
+// or no consumer holds a message.  Tile i is needed by a team whose batch
+// reaches it and, for a segment s of a batch split into S, has i % S == s.
+// Without split batches this is tiles 0, 1, ... up to the largest bound.
+// Each stage carries its tile index; the stream ends with a stage that
+// carries kNone and no data (its full barrier is completed by a plain
+// arrive).  `t` counts ring tiles over the whole kernel; stage = t % kStages,
+// use = t / kStages.
+__device__ void group_produce_split(const DrainParams &P, GroupShared &G, TableTile *ring, uint32_t &t,
+                              uint32_t n_cons, uint32_t wpb) {
+    uint32_t tS[kConsumerWarps], ts[kConsumerWarps], tl[kConsumerWarps];
+    uint32_t nt = 0, lim = 0;
+    bool split = false;
+    for (uint32_t tb = 0; (tb + 1) * wpb <= n_cons; ++tb) {
+        const uint32_t enc = G.batch[tb * wpb];
+        if (enc == kNone) continue;
+        const FactorBatch *B = &P.batches[enc & 0xFFFFFFu];
+        const uint32_t S = B->segs > 1 ? B->segs : 1u;
+        tS[nt] = S;
+        ts[nt] = (enc >> 24) % S;
+        tl[nt] = (B->maxbound + kTile - 1) / kTile;
+        lim = max(lim, tl[nt]);
+        split |= S > 1;
+        ++nt;
+    }
+    bool ok = true;
+    uint32_t cur = 0;
+    for (;; ++t) {
+        const uint32_t st = t % kStages;
+        const uint32_t use = t / kStages;
+        if (use >= 1 && ok) ok = mbar_wait_bounded(P, &G.empty[st], (use - 1) & 1u, 12);
+        uint32_t idx = kNone;
+        if (ok && *((volatile uint32_t *)&G.active) != 0) {
+            if (!split) {
+                if (cur < lim) idx = cur;
+            } else {
+                for (uint32_t k = 0; k < nt; ++k) {
+                    const uint32_t i = cur + (ts[k] + tS[k] - cur % tS[k]) % tS[k];   // first i >= cur in segment
+                    if (i < tl[k] && i < idx) idx = i;
+                }
+            }
+        }
+        *((volatile uint32_t *)&G.tile_idx[st]) = idx;
+        if (idx == kNone) {
+            mbar_arrive(&G.full[st]);
+            ++t;
+            return;
+        }
+        cur = idx + 1;
+        const uint32_t i0 = idx * kTile;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&G.full[st], 3 * kTile * 4);
+        bulk_g2s(ring[st].p, P.primes + i0, kTile * 4, &G.full[st]);
+        bulk_g2s(ring[st].pinv, P.pinv + i0, kTile * 4, &G.full[st]);
+        bulk_g2s(ring[st].plim, P.plim + i0, kTile * 4, &G.full[st]);
+    }
+}
+
+// Consumer warp: sweep held batch `enc` ((segment << 24) | batch record;
+// kNone: only keep the ring moving) over the streamed tiles of its segment.
+// A team of `wpb` warps shares one batch; member `r` tests the chunks u of
+// each tile with u % wpb == r, and members drop messages that another member,
+// of any segment, has already decided below their position.  (A segment may
+// see tiles past its messages' bounds that another team needs: they are
+// tested only until the bound check drops the messages, and a hit at or past
+// a message's bound is no divisor below its square root.)
 constexpr uint32_t kSweepPrimes = 4;   // chunks (primes per lane) tested per step
 static_assert((kTile / 32) % (kSweepPrimes * kConsumerWarps) == 0, "a tile splits into steps for any team size");
+// kSplit: the drain splits batches (the stream carries tile indices); else
+// the sequential stream of group_produce, whose end is G.final_tile.
+template <bool kSplit>
 __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableTile *ring, uint32_t &t,
-                              uint32_t b, uint32_t r, uint32_t wpb) {
+                              uint32_t enc, uint32_t r, uint32_t wpb) {
     const uint32_t lane = lane_id();
+    const uint32_t b = (!kSplit || enc == kNone) ? enc : (enc & 0xFFFFFFu);
     FactorBatch *B = (b != kNone) ? &P.batches[b] : nullptr;
+    uint32_t segs = 1, seg = 0;
+    if constexpr (kSplit) {
+        segs = (B && B->segs > 1) ? B->segs : 1u;
+        seg = enc == kNone ? 0u : (enc >> 24) % segs;
+    }
     SweepRegs s;
     sweep_init(s);
     if (B) {
@@ -387,15 +459,26 @@ __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableT
         const uint32_t st = t % kStages;
         const bool ok = mbar_wait_bounded(P, &G.full[st], (t / kStages) & 1u, 13);
         if (!__all_sync(FULL, ok)) break;
-        const uint32_t fin = *((volatile uint32_t *)&G.final_tile);
-        if (i >= fin) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&G.empty[st]);
-            ++t;
-            break;
+        uint32_t tile = i;
+        if constexpr (kSplit) {
+            tile = *((volatile uint32_t *)&G.tile_idx[st]);
+            if (tile == kNone) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&G.empty[st]);
+                ++t;
+                break;
+            }
+        } else {
+            const uint32_t fin = *((volatile uint32_t *)&G.final_tile);
+            if (i >= fin) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&G.empty[st]);
+                ++t;
+                break;
+            }
         }
-        if (s.k > 0) {
-            const uint32_t start = i * kTile;
+        if (s.k > 0 && (!kSplit || segs == 1 || tile % segs == seg)) {
+            const uint32_t start = tile * kTile;
             // teammates' hits (lane j: message j), read now and applied after
             // this tile so the load's latency overlaps the tests; a stale
             // value only costs tests
@@ -483,6 +566,7 @@ __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableT
 // Claim a factor actor: move up to K messages into batch b.  Returns b when
 // the batch needs a sweep (the caller's team runs it), kNone when every
 // message was answered at once or nothing could be taken.
+template <bool kSplit>
 __device__ uint32_t claim_factor(const DrainParams &P, uint32_t a, uint32_t b) {
     const uint32_t lane = lane_id();
     ActorDesc *A = &P.actors[a];
@@ -518,11 +602,25 @@ __device__ uint32_t claim_factor(const DrainParams &P, uint32_t a, uint32_t b) {
     }
     const uint32_t even_mask = __ballot_sync(FULL, lane < take && even);
     const uint32_t maxb = __reduce_max_sync(FULL, lane < take ? pb : 0u);
+    // split a large batch over the teams that would otherwise idle: the
+    // device's teams against the batch records in use
+    uint32_t segs = 1;
+    const uint32_t tiles = (maxb + kTile - 1) / kTile;
+    if (kSplit && P.split > 1 && tiles >= kSplitMinTiles) {
+        int64_t in_use = 0;
+        if (lane == 0) in_use = (int64_t)P.n_batches - q_len(&P.ctl->freeq);
+        in_use = __shfl_sync(FULL, in_use, 0);
+        const uint32_t teams = gridDim.x * (kConsumerWarps / P.factor_w);
+        const uint32_t idle = in_use >= 1 ? teams / (uint32_t)in_use : teams;
+        segs = min(min(min(P.split, kSplitMax), tiles / kSplitTilesPerSeg), idle);
+        if (segs < 2) segs = 1;
+    }
     if (lane == 0) {
         B->count = take;
         B->even_mask = even_mask;
         B->maxbound = maxb;
-        B->items_left = P.factor_w;
+        B->segs = segs;
+        B->items_left = P.factor_w * segs;
         add_u64(&P.ctl->claims, 1);
     }
     __syncwarp();
@@ -530,7 +628,17 @@ __device__ uint32_t claim_factor(const DrainParams &P, uint32_t a, uint32_t b) {
         finalize_batch(P, b);
         return kNone;
     }
-    return b;
+    if (kSplit && segs > 1) {
+        // the record is complete before any segment can be taken
+        __threadfence();
+        bool ok = true;
+        if (lane >= 1 && lane < segs) ok = q_push(&P.ctl->segq, P.segq, (lane << 24) | b, P.wait_limit_ns);
+        if (!__all_sync(FULL, ok)) {
+            if (!ok) fail(P, kErrWaitQueue, 33);
+            return kNone;
+        }
+    }
+    return b;   // segment 0 for the claiming team
 }
 
 // ---------------------------------------------------------------------------
@@ -1465,10 +1573,21 @@ __device__ __noinline__ void drain_mandel_bands(const DrainParams &P, GroupShare
 // A team leader looks for a factor batch to sweep: pop ready actors, claim
 // factor actors into a fresh batch record, and run ring-token actors on the
 // way (a few at most, so the group forms quickly).
-template <bool kGemm>
+template <bool kGemm, bool kSplit>
 __device__ uint32_t find_batch(const DrainParams &P, uint32_t &rng) {
     const uint32_t lane = lane_id();
     DevCtl *ctl = P.ctl;
+    if (kSplit) {
+        // a segment of a split batch waiting for a team comes first
+        uint32_t item = kNone;
+        if (lane == 0) {
+            const int pr = q_try_pop(&ctl->segq, P.segq, &item, P.wait_limit_ns);
+            if (pr < 0) fail(P, kErrWaitQueue, 34);
+            if (pr <= 0) item = kNone;
+        }
+        item = __shfl_sync(FULL, item, 0);
+        if (item != kNone) return item;
+    }
     for (int attempt = 0; attempt < 4; ++attempt) {
         uint32_t a = 0;
         bool got = false;
@@ -1496,7 +1615,7 @@ __device__ uint32_t find_batch(const DrainParams &P, uint32_t &rng) {
                 __syncwarp();
                 return kNone;
             }
-            const uint32_t r = claim_factor(P, a, __shfl_sync(FULL, b, 0));
+            const uint32_t r = claim_factor<kSplit>(P, a, __shfl_sync(FULL, b, 0));
             if (r != kNone) return r;
         } else if (kind == kToken) {
             claim_ring(P, a);
@@ -1554,7 +1673,9 @@ __device__ void agent_loop(const DrainParams &P) {
 // sweeps its batch against it, so one pass over the table serves up to
 // kConsumerWarps * K messages.  With the live host ring, warp 0 of CTA 0 is
 // the ingress warp and takes no part in groups.
-template <bool kGemm>
+// kSplit: the instantiation for a runtime that splits large factor batches
+// (its own kernel, so the sequential sweep's code is the same without it).
+template <bool kGemm, bool kSplit>
 __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P) {
     extern __shared__ __align__(128) uint8_t drain_smem[];
     uint8_t *base = drain_smem + ((1024u - (smem_u32(drain_smem) & 1023u)) & 1023u);
@@ -1622,7 +1743,7 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
             bool skip = false;
             if ((kGemm || P.mandel) && lane == 0)
                 skip = q_len(&ctl->workq) + q_len(&ctl->packq) > 2 * (int64_t)gridDim.x;
-            if (!__shfl_sync(FULL, skip, 0)) held = find_batch<kGemm>(P, rng);
+            if (!__shfl_sync(FULL, skip, 0)) held = find_batch<kGemm, kSplit>(P, rng);
         }
         if (!producer && lane == 0) G.batch[ci] = (team_ok && rank == 0) ? held : kNone;
         if (producer) {
@@ -1717,10 +1838,10 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
             for (uint32_t i = 0; i < n_cons; ++i) {
                 const uint32_t tb = i / wpb;
                 if ((tb + 1) * wpb > n_cons) continue;
-                const uint32_t b = G.batch[tb * wpb];
-                if (b == kNone) continue;
+                const uint32_t enc = G.batch[tb * wpb];
+                if (enc == kNone) continue;
                 ++active;
-                limit = max(limit, P.batches[b].maxbound);
+                limit = max(limit, P.batches[enc & 0xFFFFFFu].maxbound);
             }
             G.active = active;
             G.limit_tiles = (limit + kTile - 1) / kTile;
@@ -1756,10 +1877,13 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
         // ---- sweep
         if (producer) {
             uint32_t tt = t;
-            if (lane == 0) group_produce(P, G, ring, tt);
+            if (lane == 0) {
+                if constexpr (kSplit) group_produce_split(P, G, ring, tt, n_cons, wpb);
+                else group_produce(P, G, ring, tt);
+            }
             t = __shfl_sync(FULL, tt, 0);
         } else {
-            group_consume(P, G, ring, t, mine, rank, wpb);
+            group_consume<kSplit>(P, G, ring, t, mine, rank, wpb);
         }
         held = kNone;
         named_bar_sync(1, bar_threads);
@@ -2054,9 +2178,14 @@ namespace cafgpu {
 static cudaError_t drain_attr() {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_drain<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDrainSmemFactor);
+    cudaError_t e = cudaFuncSetAttribute(k_drain<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kDrainSmemFactor);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_drain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDrainSmemMixed);
+        e = cudaFuncSetAttribute(k_drain<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDrainSmemMixed);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_drain<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDrainSmemFactor);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_drain<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDrainSmemMixed);
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -2064,17 +2193,34 @@ static cudaError_t drain_attr() {
 cudaError_t drain_occupancy(bool gemm, int *ctas_per_sm) {
     cudaError_t e = drain_attr();
     if (e != cudaSuccess) return e;
-    if (gemm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain<true>, kThreads, kDrainSmemMixed);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain<false>, kThreads, kDrainSmemFactor);
+    // the split instantiations have the same launch bounds and shared memory
+    int split_fit = 0;
+    cudaError_t e2;
+    if (gemm) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain<true, false>, kThreads, kDrainSmemMixed);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&split_fit, k_drain<true, true>, kThreads, kDrainSmemMixed);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain<false, false>, kThreads,
+                                                          kDrainSmemFactor);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&split_fit, k_drain<false, true>, kThreads,
+                                                           kDrainSmemFactor);
+    }
+    if (e == cudaSuccess && e2 == cudaSuccess && split_fit < *ctas_per_sm) *ctas_per_sm = split_fit;
+    return e != cudaSuccess ? e : e2;
 }
 
 cudaError_t launch_drain(const DrainParams &p, unsigned grid, cudaStream_t stream) {
     cudaError_t e = drain_attr();
     if (e != cudaSuccess) return e;
-    if (p.gemm)
-        k_drain<true><<<grid, kThreads, kDrainSmemMixed, stream>>>(p);
+    const bool split = p.split > 1;
+    if (p.gemm && split)
+        k_drain<true, true><<<grid, kThreads, kDrainSmemMixed, stream>>>(p);
+    else if (p.gemm)
+        k_drain<true, false><<<grid, kThreads, kDrainSmemMixed, stream>>>(p);
+    else if (split)
+        k_drain<false, true><<<grid, kThreads, kDrainSmemFactor, stream>>>(p);
     else
-        k_drain<false><<<grid, kThreads, kDrainSmemFactor, stream>>>(p);
+        k_drain<false, false><<<grid, kThreads, kDrainSmemFactor, stream>>>(p);
     return cudaGetLastError();
 }
 

@@ -77,7 +77,8 @@ struct GroupShared {
     GemmBars gb;
     uint32_t batch[kConsumerWarps];
     uint32_t limit_tiles;          // tiles needed by the group's largest bound
-    uint32_t final_tile;           // tile index at which the group's stream ends
+    uint32_t final_tile;           // tile index at which the group's sequential stream ends
+    uint32_t tile_idx[kStages];    // split batches: table tile in each stage (kNone: the stream ended)
     uint32_t active;               // consumer warps still holding messages
     uint32_t exit;
     uint32_t items[kMaxItemsPerRound];   // GEMM work items this CTA runs next
@@ -279,7 +280,7 @@ static_assert(sizeof(IngressEntry) == 64, "IngressEntry is 64 bytes");
 
 struct FactorBatch {
     uint32_t count;                // messages in the batch
-    uint32_t items_left;           // work items not yet finished
+    uint32_t items_left;           // sweeps (team members x segments) not yet finished
     uint32_t maxbound;             // max over messages of pbound
     uint32_t even_mask;            // messages answered by d = 2
     uint64_t n[kFactorKMax];
@@ -288,7 +289,14 @@ struct FactorBatch {
     uint64_t reply_addr[kFactorKMax];
     uint32_t reply_token[kFactorKMax];
     uint64_t tag[kFactorKMax];
+    uint32_t segs;                 // segments: segment s sweeps the table tiles i with i % segs == s
+    uint32_t pad;
 };
+// A large batch may be split into segments swept by idle teams in any CTA
+// (the factor_split setting); a held batch is (segment << 24) | batch record.
+constexpr uint32_t kSplitMax = 32;          // segments of one batch, at most
+constexpr uint32_t kSplitMinTiles = 256;    // a batch reaching fewer tiles is not split
+constexpr uint32_t kSplitTilesPerSeg = 64;  // at least this many tiles per segment
 
 struct LogRow {                    // same layout as caf_gpu_log_row
     uint32_t actor;
@@ -327,6 +335,7 @@ struct DevCtl {
     QueueHdr jobq_large;           // free GemmJob records, large scratch class
     QueueHdr mjobq;                // free MandelJob records
     QueueHdr forkq;                // free ids of the FORK actor pool
+    QueueHdr segq;                 // segments of split factor batches, waiting for a team
 };
 
 // Host-visible control block (pinned, mapped).
@@ -395,6 +404,10 @@ struct DrainParams {
     QCell *localq;
     uint32_t localq_cap;
     uint32_t steal;
+    // split factor batches (split > 1: at most that many segments per batch)
+    QCell *segq;
+    uint32_t split;
+    uint32_t n_batches;            // batch records (those not in freeq are in use)
 };
 constexpr uint32_t kLocalQueueCap = 4096;     // ready actors per CTA queue
 constexpr uint32_t kLocalQueueSlack = 1024;   // room kept for the CTA's concurrent pushes (9 warps x 32 wakes)

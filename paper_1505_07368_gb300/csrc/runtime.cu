@@ -69,6 +69,7 @@ struct caf_gpu_runtime {
     MandelJob *d_mjobs = nullptr;
     QCell *d_mjobq = nullptr;
     QCell *d_forkq = nullptr;              // free ids of the FORK actor pool
+    QCell *d_segq = nullptr;               // segments of split factor batches
     uint32_t fork_base = 0, fork_pool = 0; // pool ids fork_base .. fork_base + fork_pool - 1 (0: no pool yet)
     bool graphs_made = false;              // a CUDA graph holds the current table addresses
     QueueHdr *d_localq_hdr = nullptr;      // work stealing: a ready queue per CTA
@@ -169,6 +170,9 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.mjobs = rt->d_mjobs;
     p.mjobq = rt->d_mjobq;
     p.forkq = rt->d_forkq;
+    p.segq = rt->d_segq;
+    p.split = rt->cfg.factor_split;
+    p.n_batches = rt->n_batches;
     p.localq_hdr = rt->d_localq_hdr;
     p.localq = rt->d_localq;
     p.localq_cap = kLocalQueueCap;
@@ -427,6 +431,7 @@ void free_runtime(caf_gpu_runtime *rt) {
     cudaFree(rt->d_mjobq);
     cudaFree(rt->d_mjobs);
     cudaFree(rt->d_forkq);
+    cudaFree(rt->d_segq);
     cudaFree(rt->d_localq_hdr);
     cudaFree(rt->d_localq);
     cudaFree(rt->d_pack_small);
@@ -467,6 +472,7 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     if (!c.gemm_items_per_round) c.gemm_items_per_round = 4;
     if (!c.fork_pool) c.fork_pool = 1u << 21;
     if (c.scheduler > CAF_GPU_SCHED_STEAL) return CAF_GPU_EINVAL;
+    if (c.factor_split > kSplitMax) return CAF_GPU_EINVAL;
     if ((uint64_t)c.max_actors + c.fork_pool >= (1ull << 31)) return CAF_GPU_EINVAL;
     if (c.gemm_items_per_round > kMaxItemsPerRound) return CAF_GPU_EINVAL;
     if (!is_pow2(c.mailbox_capacity) || !is_pow2(c.ingress_capacity)) return CAF_GPU_EINVAL;
@@ -529,6 +535,10 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     for (uint32_t i = 0; i < kGemmJobsLarge; ++i) jobs_large[i] = kGemmJobsSmall + i;
     if ((r = init_queue(rt, &rt->d_jobq, rt->jobq_cap, &rt->d_ctl->jobq, jobs_small))) return r;
     if ((r = init_queue(rt, &rt->d_jobq_large, rt->jobq_cap, &rt->d_ctl->jobq_large, jobs_large))) return r;
+    // every batch record split at once still fits
+    if ((r = init_queue(rt, &rt->d_segq, (uint32_t)next_pow2((uint64_t)rt->n_batches * kSplitMax + 1),
+                        &rt->d_ctl->segq, none)))
+        return r;
     CK(cudaMalloc(&rt->d_jobs, sizeof(GemmJob) * kGemmJobs));
     CK(cudaMemset(rt->d_jobs, 0, sizeof(GemmJob) * kGemmJobs));
     std::vector<uint32_t> mjobs(kMandelJobs);

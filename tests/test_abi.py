@@ -84,6 +84,7 @@ def test_header_constants_match_binding():
     {"factor_warps": 3}, {"factor_batch": 17}, {"ctas_per_sm": 5}, {"mailbox_capacity": 48},
     {"ingress_capacity": 1000}, {"max_factor_n": 1 << 62}, {"gemm_items_per_round": 9},
     {"scheduler": 2}, {"max_actors": (1 << 24) + 1}, {"max_actors": 1 << 20, "fork_pool": (1 << 31) - (1 << 20)},
+    {"factor_split": 33},
 ])
 def test_bad_runtime_settings_rejected_before_any_cuda_call(bad):
     # the settings are checked before the runtime touches the device, so this
