@@ -11,7 +11,7 @@ Functions and the passages they follow:
   of the factorization side load of the mixed benchmark (Sec. 5, "Mixed
   Operations Under Work Load"): smallest d >= 2 with d*d <= n and d | n.
 * ``check_certificate`` / ``is_prime`` -- p*q == n, p <= q, p and q prime.
-* ``gemm_f64`` / ``gemm_entry`` -- the matrix product of the OpenCL actor
+* ``gemm_f64`` / ``gemm_rows`` / ``gemm_entry`` -- the matrix product of the OpenCL actor
   example (Sec. 3.6) in float64 from float32 inputs.
 * ``rel_frobenius`` -- relative Frobenius error in float64.
 * ``mandel_point`` / ``mandel_rows`` -- escape counts of the Mandelbrot
@@ -64,6 +64,9 @@ def lib():
         L.oracle_check_certificate.restype = ctypes.c_int32
         L.oracle_gemm_f64.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         L.oracle_gemm_f64.restype = None
+        L.oracle_gemm_rows.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.c_int64, ctypes.c_void_p]
+        L.oracle_gemm_rows.restype = None
         L.oracle_gemm_entry.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                         ctypes.c_int64, ctypes.c_int64]
         L.oracle_gemm_entry.restype = ctypes.c_double
@@ -114,6 +117,20 @@ def gemm_f64(A: np.ndarray, B: np.ndarray) -> np.ndarray:
     C = np.empty((n, n), dtype=np.float64)
     lib().oracle_gemm_f64(A.ctypes.data, B.ctypes.data, n, C.ctypes.data)
     return C
+
+
+def gemm_rows(A: np.ndarray, B: np.ndarray, rows) -> np.ndarray:
+    """Rows ``rows`` of ``gemm_f64(A, B)`` (float64, shape (len(rows), n)), each
+    computed as ``gemm_f64`` computes it; for products too large to form whole."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    n = A.shape[0]
+    assert A.shape == (n, n) and B.shape == (n, n)
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    assert r.ndim == 1 and (r.size == 0 or (r.min() >= 0 and r.max() < n))
+    out = np.empty((r.size, n), dtype=np.float64)
+    lib().oracle_gemm_rows(A.ctypes.data, B.ctypes.data, n, r.ctypes.data, r.size, out.ctypes.data)
+    return out
 
 
 def gemm_entry(A: np.ndarray, B: np.ndarray, i: int, j: int) -> float:
