@@ -130,7 +130,9 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
     bool pending = valid;
     WaitClock w(P.wait_limit_ns);
     for (;;) {
-        if (pending && t - *((volatile uint64_t *)&A->head) <= mask) {
+        // acquire: pairs with the consumer's release of head, so the slot's
+        // previous message has been read before this write replaces it
+        if (pending && t - ld_acquire_gpu(&A->head) <= mask) {
             Slot *s = &P.slots[A->slot_base + (t & mask)];
             s->payload = m.payload;
             s->reply_addr = m.reply_addr;
@@ -148,7 +150,7 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
         bool qok = true;
         bool woke = false;
         if (valid && (int)lane == leader) {
-            if (cas_u32(&A->state, kWaiting, kReady) == kWaiting) {
+            if (cas_acq_rel_gpu(&A->state, kWaiting, kReady) == kWaiting) {
                 if (handoff) woke = true;
                 else qok = ready_push(P, a);
             }
@@ -172,12 +174,18 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
 }
 
 // Park or re-queue an actor after its claim (warp-collective; lane 0 acts).
+// The warp barrier orders every lane's slot reads before lane 0's release
+// store of the new head: a producer that sees that head (acquire) may
+// overwrite those slots.  The exchange to WAITING is a release as well, so a
+// producer whose acquire-CAS wakes the actor passes the head on to the next
+// claim through the ready queue.
 __device__ void release_actor(const DrainParams &P, uint32_t a, uint64_t new_head) {
+    __syncwarp();
     if (lane_id() == 0) {
         ActorDesc *A = &P.actors[a];
-        *((volatile uint64_t *)&A->head) = new_head;
+        st_release_gpu(&A->head, new_head);
         if (*((volatile uint32_t *)&A->state) != kDone) {
-            atomicExch(reinterpret_cast<unsigned int *>(&A->state), kWaiting);
+            exch_release_gpu(&A->state, kWaiting);
             asm volatile("fence.sc.gpu;" ::: "memory");
             if (ld_relaxed_gpu(&A->tail) != new_head &&
                 cas_u32(&A->state, kWaiting, kReady) == kWaiting) {
