@@ -21,6 +21,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "isqrt.h"
 
 namespace cafgpu {
 
@@ -32,13 +33,6 @@ __device__ __forceinline__ bool mont_divides(uint64_t n, uint32_t nlneg, uint32_
     return m1 <= plim;
 }
 
-// floor(sqrt(n)) for n < 2^62, exact.
-__device__ __forceinline__ uint64_t isqrt_u64(uint64_t n) {
-    uint64_t s = (uint64_t)sqrt((double)n);
-    while (s * s > n) --s;
-    while ((s + 1) * (s + 1) <= n) ++s;
-    return s;
-}
 
 // Number of table primes <= x (table sorted increasingly, odd primes).
 __device__ __forceinline__ uint32_t primes_le(const uint32_t *primes, uint32_t nprimes, uint64_t x) {

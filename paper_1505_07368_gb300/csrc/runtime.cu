@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/caf_gpu.h"
+#include "isqrt.h"
 #include "kernels.h"
 #include "layout.h"
 #include "mandel.cuh"
@@ -577,9 +578,7 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     CK(cudaMemset(rt->d_zero, 0, 64));
 
     // prime table: odd primes up to floor(sqrt(max_factor_n))
-    uint64_t lim = (uint64_t)std::sqrt((double)c.max_factor_n);
-    while (lim * lim > c.max_factor_n) --lim;
-    while ((lim + 1) * (lim + 1) <= c.max_factor_n) ++lim;
+    const uint64_t lim = isqrt_u64(c.max_factor_n);
     rt->prime_limit = lim;
     CK(build_prime_table(lim, kRangePrimes + 64, &rt->d_primes, &rt->d_pinv, &rt->d_plim, &rt->nprimes,
                          rt->setup));
