@@ -472,7 +472,9 @@ int caf_gpu_serve_run(caf_gpu_runtime *rt, const caf_gpu_serve_req *reqs, uint32
  * (device memory): status CAF_GPU_REPLY_OK with (r0, r1) = (smallest divisor
  * d >= 2 with d*d <= n, n/d), CAF_GPU_REPLY_NOFACTOR with (1, n), or
  * CAF_GPU_REPLY_REJECTED for n >= 2^62.  The results equal those of a
- * FACTOR_U64 actor.  Work is enqueued on `stream` (cudaStream_t, NULL = the
+ * FACTOR_U64 actor of a runtime with the default max_factor_n (2^62 - 1); a
+ * runtime created with a smaller limit refuses larger n, which this call
+ * still factors.  Work is enqueued on `stream` (cudaStream_t, NULL = the
  * legacy default stream) and the call returns at once; the replies are
  * complete when the stream reaches this point.  The caller owns both arrays.
  *
@@ -481,7 +483,9 @@ int caf_gpu_serve_run(caf_gpu_runtime *rt, const caf_gpu_serve_req *reqs, uint32
  * library, which every GPU that loads the library holds until the process
  * exits.  The first call on each device looks up that array's device address
  * (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  All calls share the array, so calls whose work overlaps
+ * any stream capture.  The address is kept for the life of the process, so
+ * the device's primary context must not be reset (cudaDeviceReset) after the
+ * first call.  All calls share the array, so calls whose work overlaps
  * on the GPU (other streams, other threads) race and must not be issued; each
  * call resets the words it uses before its kernel runs.
  *

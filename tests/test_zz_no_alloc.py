@@ -5,7 +5,8 @@ allocator owns the GPU's memory, latency-critical paths, programs that forbid
 allocation after start-up).  This test calls it through the C ABI, twice in a
 row with different numbers (so a stale scratch word from the first call would
 show in the second), and requires the same replies as the runtime's device
-batch entry point.  The file is named to be collected last.
+batch entry point and as the CPU oracle's trial division.  The file is named
+to be collected last.
 """
 import numpy as np
 import pytest
@@ -13,6 +14,7 @@ import pytest
 from paper_1505_07368_gb300 import cafgpu as C
 from paper_1505_07368_gb300 import workloads as W
 
+import oracle
 from helpers import device_batch
 
 pytestmark = pytest.mark.gpu
@@ -20,6 +22,21 @@ pytestmark = pytest.mark.gpu
 MAX40 = (1 << 40) - 1
 EDGE = [0, 1, 2, 3, 4, 5, 8, 9, 15, 25, 49, 97 * 97, 1 << 39, MAX40, 1048573 * 1048573,
         1048573 * 1048571, 1048573, 999983 * 2, 3 * 1048573, (1 << 40) - 87]
+
+
+def _largest_primes_below(x: int, k: int):
+    out, c = [], x - 1 if x % 2 == 0 else x - 2
+    while len(out) < k:
+        if oracle.is_prime(c):
+            out.append(c)
+        c -= 2
+    return out
+
+
+# odd primes just below 2^40 (every candidate up to the root is tried) and
+# squares of the primes just below 2^20 (the divisor is the root itself)
+PRIMES40 = _largest_primes_below(1 << 40, 4)
+SQUARES40 = [p * p for p in _largest_primes_below(1 << 20, 4)]
 
 
 def _static_call(values: np.ndarray) -> np.ndarray:
@@ -35,8 +52,9 @@ def _static_call(values: np.ndarray) -> np.ndarray:
 
 def test_no_alloc_entry_matches_runtime_entry_on_two_calls():
     wl = W.config1()
-    first = np.concatenate([wl.n[:200], np.array(EDGE, dtype=np.uint64)])
-    second = np.concatenate([np.array(EDGE[::-1], dtype=np.uint64), wl.n[::-1][:150]])
+    extra = np.array(EDGE + PRIMES40 + SQUARES40, dtype=np.uint64)
+    first = np.concatenate([wl.n[:200], extra])
+    second = np.concatenate([extra[::-1], wl.n[::-1][:150]])
     with C.Runtime(max_factor_n=MAX40, max_actors=4) as rt:
         a = rt.spawn(C.FACTOR_U64)
         want = [device_batch(rt, np.full(v.size, a - 1, np.uint32), C.FACTOR_U64, v) for v in (first, second)]
@@ -46,6 +64,22 @@ def test_no_alloc_entry_matches_runtime_entry_on_two_calls():
         assert np.array_equal(got["status"], ref["status"])
         assert np.array_equal(got["r0"], ref["r0"])
         assert np.array_equal(got["r1"], ref["r1"])
+        st, p, q = oracle.factor_batch(values)
+        assert np.array_equal(got["status"], st)
+        assert np.array_equal(got["r0"], p) and np.array_equal(got["r1"], q)
+
+
+def test_no_alloc_entry_beyond_the_runtime_default_range():
+    # n up to 2^50 and values at and past the 2^62 limit, against the oracle
+    big = _largest_primes_below(1 << 50, 2) + [((1 << 25) - 39) * ((1 << 25) - 39), (1 << 62) - 2,
+                                                 3 * ((1 << 60) + 1)]
+    values = np.array(big, dtype=np.uint64)
+    got = _static_call(values)
+    st, p, q = oracle.factor_batch(values)
+    assert np.array_equal(got["status"], st)
+    assert np.array_equal(got["r0"], p) and np.array_equal(got["r1"], q)
+    rej = _static_call(np.array([1 << 62, (1 << 64) - 1], dtype=np.uint64))
+    assert np.all(rej["status"] == C.REPLY_REJECTED)
 
 
 def test_no_alloc_entry_rejects_oversize_batch():
