@@ -44,7 +44,6 @@ UNIT = "msgs/s"
 WORKLOAD = ("batched factorization actors: 1024 actors, geometric(mean 64) mailbox lengths, "
             "semiprimes with prime factors in [2^24, 2^28), one persistent launch per step")
 L2_FLUSH_BYTES = 256 << 20
-SM_COUNT = 152
 IMAD_PER_SM_CLK = 64          # 32-bit integer multiply(-add) lanes per SM per clock
 MULS_PER_TEST = 3             # the Montgomery divisibility test: m0, n + m0*p, m1
 
@@ -52,7 +51,7 @@ MULS_PER_TEST = 3             # the Montgomery divisibility test: m0, n + m0*p, 
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--factor-batch", type=int, default=16)
@@ -67,7 +66,7 @@ def parse_args(argv=None):
                     help="factor: the batched-factorization line (default); the others measure the "
                          "GEMM, token-ring, serving and mailbox-traffic configurations")
     ap.add_argument("--no-autotune", action="store_true", help="use --factor-batch/--factor-warps as given")
-    ap.add_argument("--requests", type=int, default=100_000, help="serve: requests in the trace")
+    ap.add_argument("--requests", type=int, default=1_000_000, help="serve: requests in the trace")
     ap.add_argument("--scheduler", choices=["global", "steal"], default="global",
                     help="ready-actor scheduler (factor, ring, mailbox, spawn): one global queue or work stealing")
     ap.add_argument("--factor-split", type=int, default=0,
@@ -185,6 +184,29 @@ def measured_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         return {}
+
+
+# two-sided 95 % quantiles of Student's t distribution, degrees of freedom 1..30
+_T975 = (12.706, 4.303, 3.182, 2.776, 2.571, 2.447, 2.365, 2.306, 2.262, 2.228, 2.201, 2.179, 2.160, 2.145,
+         2.131, 2.120, 2.110, 2.101, 2.093, 2.086, 2.080, 2.074, 2.069, 2.064, 2.060, 2.056, 2.052, 2.048,
+         2.045, 2.042)
+
+
+def timing_stats(times_s, units_per_step=None):
+    """Per-step times (seconds) -> mean, sample standard deviation and the 95 %
+    confidence interval of the mean (Student's t), in ms; with units_per_step,
+    also the interval of the rate units / mean time."""
+    x = np.asarray(times_s, dtype=np.float64) * 1e3
+    n = int(x.size)
+    out = {"runs": n, "mean_ms": float(x.mean()), "min_ms": float(x.min()), "max_ms": float(x.max())}
+    if n >= 2:
+        sd = float(x.std(ddof=1))
+        hw = (_T975[n - 2] if n - 1 <= len(_T975) else 1.96) * sd / np.sqrt(n)
+        out.update({"std_ms": sd, "ci95_ms": [out["mean_ms"] - hw, out["mean_ms"] + hw], "ci95_halfwidth_ms": hw})
+        if units_per_step is not None and out["mean_ms"] - hw > 0:
+            out["rate_ci95"] = [units_per_step / ((out["mean_ms"] + hw) * 1e-3),
+                                units_per_step / ((out["mean_ms"] - hw) * 1e-3)]
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -345,13 +367,14 @@ def run_ours(args):
     tests_alg = float(odd_prime_counts(wl.p).sum())
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tops = SM_COUNT * IMAD_PER_SM_CLK * sm_max * 1e6 / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tops = sm_count * IMAD_PER_SM_CLK * sm_max * 1e6 / 1e12
     achieved_tops = MULS_PER_TEST * tests_alg / (dev_s / args.steps) / 1e12
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tmul/s",
                 "frac": achieved_tops / peak_tops, "traffic": None,
                 "kernel": "k_drain", "algorithmic_tests_per_step": tests_alg,
                 "executed_tests_per_step": st["prime_tests"] / args.steps,
-                "peak_basis": f"{SM_COUNT} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz (sm_max_mhz of measured)"}
+                "peak_basis": f"{sm_count} SMs (device attribute) x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz (sm_max_mhz of measured)"}
     # what the test's own instruction mix can reach on this GPU (measured after
     # the timed steps): its high multiply runs at a lower rate than the low one
     rates = C.measure_mul_rates()
@@ -371,6 +394,7 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MiB write)",
                    "timing": "CUDA events on the runtime stream, per step",
                    "autotune": tuned if tuned else "off"},
+        "timing_stats": timing_stats(np.asarray(step_ms) / 1e3, units_per_step=float(count)),
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
                        "max": float(lat_ms.max()), "from": "step start (device clock) to reply written"},
         "gpu_launches": st["launches"],
@@ -533,7 +557,7 @@ def run_gemm(args):
             lat = (rep["t_done"].astype(np.int64) - np.int64(st["t_mark"])) / 1e6
             t = float(np.mean(times))
             mult = 3.0 if kind == C.GEMM_SPLIT_BF16X3 else 1.0
-            v = {"value": wl.count / t, "ms_per_step": 1e3 * t,
+            v = {"value": wl.count / t, "ms_per_step": 1e3 * t, "timing_stats": timing_stats(times, wl.count),
                  "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
                  "roofline": {
                      "hbm": {"achieved": alg_bytes / t / 1e9, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
@@ -621,7 +645,8 @@ def run_ring(args):
             t = float(np.mean(times))
             hops = L + wl.token            # deliveries per ring (the 0 travels once around)
             msgs = R * (hops + 1) + (R * rounds if with_factor else 0)
-            out[label] = {"ms_per_step": 1e3 * t, "msgs_per_s": msgs / t, "ns_per_hop": 1e9 * t / hops,
+            out[label] = {"ms_per_step": 1e3 * t, "timing_stats": timing_stats(times, msgs),
+                          "msgs_per_s": msgs / t, "ns_per_hop": 1e9 * t / hops,
                           "messages": msgs}
             if not args.skip_per_message:
                 # the same workload with one kernel launch per message: the host sends
@@ -664,12 +689,63 @@ def run_serve(args):
     torch.cuda.set_device(0)
     count = args.requests
     n_f, n_g = 2048, 1024
-    base_wl = W.config5(n_requests=count, rate=1e6, pool_elems=1 << 24)
-    pool = torch.from_numpy(W.gemm_pool(base_wl.pool_seed, base_wl.pool_elems)).cuda()
+    pool_elems = 1 << 28            # 1 GiB of operands: larger than L2, so the GEMMs read HBM
+    _note(f"serve: drawing the {count}-request trace and a {pool_elems * 4 >> 20} MiB operand pool")
+    base_wl = W.config5(n_requests=count, rate=1e6, pool_elems=pool_elems)
+    pool_np = W.gemm_pool(base_wl.pool_seed, base_wl.pool_elems)
+    pool = torch.from_numpy(pool_np).cuda()
     arena_bytes = 4 << 30
     arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
     result = {"metric": METRIC, "unit": UNIT, "requests": count,
-              "workload": "serving: Poisson arrivals, 70% factor / 30% split GEMM, 8 GB budget"}
+              "workload": "serving: Poisson arrivals, 70% factor / 30% split GEMM, 8 GB budget",
+              "operand_pool_bytes": pool_elems * 4, "checks": {}}
+
+    def check(res, wl, label):
+        """Every reply: status, factors against the generator's primes, GEMM size;
+        split-GEMM error on a seeded sample of the results still intact in the
+        arena (a later result may reuse an earlier one's bytes), large n included."""
+        isf = wl.kind == C.FACTOR_U64
+        bad = int(np.count_nonzero(res["status"] != 0))
+        fi = np.nonzero(isf)[0]
+        gi = np.nonzero(~isf)[0]
+        bad_f = int(np.count_nonzero((res["r0"][fi] != wl.p[fi]) | (res["r1"][fi] != wl.q[fi])))
+        bad_g = int(np.count_nonzero(res["r1"][gi] != wl.size[gi].astype(np.uint64)))
+        page = 1 << 12
+        taken = np.zeros(arena_bytes // page + 1, dtype=bool)
+        intact_big, intact = [], []
+        for i in gi[::-1]:
+            n = int(wl.size[i])
+            lo = int(res["c_offset"][i]) // page
+            hi = (int(res["c_offset"][i]) + 4 * n * n - 1) // page + 1
+            if not taken[lo:hi].any():
+                (intact_big if n > 1024 else intact).append(i)
+            taken[lo:hi] = True
+            if len(intact_big) >= 6 and len(intact) >= 400:
+                break
+        rng = np.random.default_rng(1505_07368)
+        sample = intact_big[:6] + list(rng.choice(intact, size=min(18, len(intact)), replace=False))
+        worst = 0.0
+        for i in sample:
+            n = int(wl.size[i])
+            rows = np.unique(rng.integers(0, n, size=24))
+            off = int(res["c_offset"][i])
+            got = arena[off:off + 4 * n * n].view(torch.float32).view(n, n)[torch.from_numpy(rows).cuda()]
+            got = got.cpu().numpy().astype(np.float64)
+            A = pool_np[wl.a_off[i]:wl.a_off[i] + n * n].reshape(n, n)
+            B = pool_np[wl.b_off[i]:wl.b_off[i] + n * n].reshape(n, n)
+            want = A[rows].astype(np.float64) @ B.astype(np.float64)
+            err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+            worst = max(worst, err)
+        result["checks"][label] = {
+            "replies": int(res.size), "bad_status": bad, "bad_factors": bad_f, "factor_replies": int(fi.size),
+            "bad_gemm_replies": bad_g, "gemm_replies": int(gi.size),
+            "gemm_error_sample": {"messages": len(sample), "large_n": len(intact_big[:6]),
+                                  "sizes": sorted(int(wl.size[i]) for i in sample),
+                                  "worst_rel_frobenius": worst, "bound": 1e-5,
+                                  "reference": "float64 numpy product of the float32 operands, 24 sampled rows"}}
+        if bad or bad_f or bad_g or worst > 1e-5 or not intact_big:
+            print(json.dumps(result["checks"][label]), file=sys.stderr)
+            raise SystemExit(f"bench: serve {label}: replies fail the check")
 
     def trace(wl, actors_f, actors_g):
         reqs = np.zeros(wl.count, C.SERVE_REQ_DTYPE)
@@ -690,15 +766,21 @@ def run_serve(args):
         closed = trace(base_wl, af, ag)
         closed["t_arrival"] = 0.0
         torch.cuda.synchronize()
+        _note("serve: closed loop")
         res, st = rt.serve_run(closed, arena.data_ptr(), arena_bytes, mem_budget_bytes=8 << 30)
+        torch.cuda.synchronize()
+        check(res, base_wl, "closed_loop")
         capacity = count / st["wall_s"]
         result["closed_loop"] = {"msgs_per_s": capacity, "wall_s": st["wall_s"]}
         lam = 0.8 * capacity
-        wl = W.config5(n_requests=count, rate=lam, pool_elems=1 << 24)
+        wl = W.config5(n_requests=count, rate=lam, pool_elems=pool_elems)
         reqs = trace(wl, af, ag)
         for backend, label in ((C.BACKEND_PERSISTENT, "persistent"), (C.BACKEND_PER_MESSAGE_LAUNCH, "per_message_launch")):
+            _note(f"serve: open loop, {label}")
             rt.set_backend(backend)
             res, st = rt.serve_run(reqs, arena.data_ptr(), arena_bytes, mem_budget_bytes=8 << 30)
+            torch.cuda.synchronize()
+            check(res, wl, label)
             lat = (res["t_done"] - wl.t) * 1e3
             result[label] = {"rate_offered": lam, "msgs_per_s": count / st["wall_s"],
                              "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -738,6 +820,7 @@ def run_small(args):
                 raise SystemExit(f"bench: small {label}: wrong factors")
             t = float(np.mean(times))
             out[label] = {"msgs_per_s": wl.count / t, "ms_per_step": 1e3 * t,
+                          "timing_stats": timing_stats(times, wl.count),
                           "launches_per_step": rt.stats()["launches"] / (args.warmup + args.steps)}
     rate, done, secs = cpu_oracle_rate(wl, args.cpu_seconds)
     print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "plain small case: 1 actor, 1 mailbox, 256 "
@@ -796,6 +879,7 @@ def run_mailbox(args):
             t = float(np.mean(times))
             msgs = n_src * per
             out[label] = {"sources": n_src, "sinks": n_sink, "messages": msgs, "ms_per_step": 1e3 * t,
+                          "timing_stats": timing_stats(times, msgs),
                           "msgs_per_s": msgs / t,
                           "roofline": {"bound": "hbm", "achieved": slot_bytes * msgs / t / 1e9, "peak": hbm,
                                        "unit": "GB/s", "frac": slot_bytes * msgs / t / 1e9 / hbm,
@@ -901,6 +985,7 @@ def run_mandel(args):
                 t = float(np.mean(times))
                 ops = FP32_OPS_PER_ITER * float(counts_sum) * images
                 v = {"messages": count, "actors": n_act, "images": images, "ms_per_step": 1e3 * t,
+                     "timing_stats": timing_stats(times, count),
                      "msgs_per_s": count / t,
                      "images_per_s": images / t, "mpix_per_s": images * Wd * Hd / t / 1e6,
                      "mean_iterations": counts_sum / (Wd * Hd),
@@ -937,7 +1022,7 @@ def run_mandel(args):
             torch.cuda.empty_cache()
     clk = clocks.stop()
     mhz = clk.get("sm_max_mhz") or 2070.0
-    nominal = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
+    nominal = torch.cuda.get_device_properties(0).multi_processor_count * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
     for v in results.values():
         v["roofline"] = {"bound": "alu", "achieved": v["fp32_tops"], "peak": nominal, "unit": "TFLOP/s",
                          "frac": v["fp32_tops"] / nominal, "measured_fp32_tops": fp32_rate / 1e12,
@@ -1029,7 +1114,8 @@ def run_spawn(args):
                                f"messages per step, one FORK root, pool of {max(1 << 21, spawns)} records",
                    "scheduler": args.scheduler,
                    "warps_per_team": "1 (the runtime's choice when no factor actor exists)"},
-        "value": spawns / t, "ms_per_step": 1e3 * t, "msgs_per_s": msgs / t,
+        "value": spawns / t, "ms_per_step": 1e3 * t, "timing_stats": timing_stats(times, spawns),
+        "msgs_per_s": msgs / t,
         "roofline": {"bound": "hbm", "achieved": bytes_per_actor * spawns / t / 1e9, "peak": hbm, "unit": "GB/s",
                      "frac": bytes_per_actor * spawns / t / 1e9 / hbm, "bytes_per_actor": bytes_per_actor,
                      "note": "record and mailbox bytes per spawned actor; the path is bound by atomics and "
