@@ -104,34 +104,49 @@ def check_mailbox_log(actor, sender, sender_seq, log_actor, log_msg, log_stamp,
     return errs
 
 
-def simulate_rings(n_rings: int, ring_len: int, token: int):
-    """Run every ring to termination.
+def simulate_rings(n_rings: int, ring_len: int, token: int, incarnations: int = 1):
+    """Run every ring to termination, ``incarnations`` times.
+
+    The mixed benchmark's rings are "re-created 4 times" (Sec. 5, "Mixed
+    Operations Under Work Load").  Reading: an incarnation is the ring run to
+    termination as below; the master then creates the ring anew (new member
+    actors, the master itself kept) and starts it with the same token, until
+    ``incarnations`` have run; it terminates after the last.  A master sends
+    one factorization request when an incarnation starts and one per token
+    v > 0 it receives.
 
     Returns a list with one dict per ring: ``trace`` is the list of
-    (receiver, value) deliveries in order, ``requests`` the number of
+    (receiver, value) deliveries in order over all incarnations (receiver =
+    position in the ring, the master at 0), ``incarnation_starts`` the index
+    in ``trace`` where each incarnation begins, ``requests`` the number of
     factorization requests the master sent, ``request_after`` the number of
     deliveries seen before each request.
     """
     rings = []
     for _ in range(n_rings):
-        done = [False] * ring_len
         trace = []
-        req_after = [0]          # the master's request at start
-        pending = deque([(1 % ring_len, token)])
-        while pending:
-            r, v = pending.popleft()
-            trace.append((r, v))
-            succ = (r + 1) % ring_len
-            if v > 0:
-                if r == 0:
-                    req_after.append(len(trace))
-                pending.append((succ, v - 1))
-            else:
-                done[r] = True
-                if not done[succ]:
-                    pending.append((succ, 0))
-        assert all(done)
-        rings.append({"trace": trace, "requests": len(req_after), "request_after": req_after})
+        req_after = []
+        starts = []
+        for _inc in range(incarnations):
+            done = [False] * ring_len
+            starts.append(len(trace))
+            req_after.append(len(trace))          # the master's request at the (re)start
+            pending = deque([(1 % ring_len, token)])
+            while pending:
+                r, v = pending.popleft()
+                trace.append((r, v))
+                succ = (r + 1) % ring_len
+                if v > 0:
+                    if r == 0:
+                        req_after.append(len(trace))
+                    pending.append((succ, v - 1))
+                else:
+                    done[r] = True
+                    if not done[succ]:
+                        pending.append((succ, 0))
+            assert all(done)
+        rings.append({"trace": trace, "requests": len(req_after), "request_after": req_after,
+                      "incarnation_starts": starts})
     return rings
 
 

@@ -105,3 +105,25 @@ def test_fork_tree_closed_form():
         assert r["spawned"] == 2 ** (n + 1) - 2
         assert r["messages"] == 3 * (2 ** n - 1) + 2 ** n == 2 ** (n + 2) - 3
         assert r["live_after"] == 0
+
+
+def test_rings_recreated_closed_form():
+    # every incarnation repeats the single-incarnation run; requests add up
+    L, T, R = 128, 1000, 4
+    one = actors.simulate_rings(1, L, T)[0]
+    r = actors.simulate_rings(2, L, T, incarnations=R)[1]
+    assert r["incarnation_starts"] == [k * (T + L) for k in range(R)]
+    assert len(r["trace"]) == R * (T + L)
+    for k in range(R):
+        assert r["trace"][k * (T + L):(k + 1) * (T + L)] == one["trace"]
+        assert r["trace"][k * (T + L)] == (1, T)      # a fresh ring starts at member 1
+    assert r["requests"] == R * one["requests"] == 32
+    assert r["request_after"] == [k * (T + L) + x for k in range(R) for x in one["request_after"]]
+
+
+def test_rings_recreated_small_by_hand():
+    # ring of 2, token 1, two incarnations: a1:1, a0:0, a1:0 | a1:1, a0:0, a1:0
+    r = actors.simulate_rings(1, 2, 1, incarnations=2)[0]
+    assert r["trace"] == [(1, 1), (0, 0), (1, 0)] * 2
+    assert r["incarnation_starts"] == [0, 3]
+    assert r["requests"] == 2 and r["request_after"] == [0, 3]
