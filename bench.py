@@ -72,6 +72,9 @@ def parse_args(argv=None):
     ap.add_argument("--factor-split", type=int, default=0,
                     help="factor, ring, serve: split large factor batches over idle teams, up to this many "
                          "segments (0: off)")
+    ap.add_argument("--gemm-items", type=int, default=None, help="gemm: work items per CTA round (with --no-autotune)")
+    ap.add_argument("--ring-incarnations", type=int, default=4,
+                    help="ring: also run the rings re-created this many times on the device (0: skip)")
     ap.add_argument("--fork-n", type=int, default=20, help="spawn: recursion counter n (2^(n+1) - 2 spawns per step)")
     ap.add_argument("--mandel-iters", default="120,1200", help="mandel: maximum iterations to run (comma list)")
     ap.add_argument("--mandel-shapes", default="single,image,row",
@@ -523,6 +526,8 @@ def run_gemm(args):
                                               runtime_kwargs={"mailbox_capacity": 64}, log=_note)
             line["config"].setdefault("autotune", {})[name] = {
                 "best": sched, "measured": [[c, round(1e3 * t, 3)] for c, t in table]}
+        if args.gemm_items is not None:
+            sched["gemm_items_per_round"] = args.gemm_items
         _note(f"gemm {name}: persistent {sched}")
         with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=wl.n_actors, mailbox_capacity=64, **sched) as rt:
             for _ in range(wl.n_actors):
@@ -672,11 +677,77 @@ def run_ring(args):
                 out[label]["per_message_launch"] = {"ms": 1e3 * tp, "msgs_per_s": msgs / tp, "launches": launches,
                                                     "speedup_persistent": tp / t,
                                                     "timing": "host wall clock around the sends and caf_gpu_sync"}
+    if args.ring_incarnations > 0:
+        out["recreated"] = _ring_recreated(args, wl, C)
+    lat = C.measure_latency()
+    for v in out.values():
+        v["hop_in_handoffs"] = v["ns_per_hop"] / lat["handoff_ns"]
+        v["hop_in_l2_round_trips"] = v["ns_per_hop"] / lat["load_acquire_ns"]
     print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "token rings (64 x 128, token 1000) + "
                       "8 factorization requests per ring, captured CUDA graph", "steps": args.steps,
-                      "factor_split": args.factor_split,
+                      "factor_split": args.factor_split, "latency_probe_ns": lat,
                       "results": out, "value": out["mixed"]["msgs_per_s"]}))
     return 0
+
+
+def _ring_recreated(args, wl, C):
+    """The mixed workload with every ring re-created on the device: each master
+    spawns its 127 members from the device actor pool, runs the ring, and
+    spawns the next incarnation once all have terminated, args.ring_incarnations
+    times; 8 factorization requests per incarnation.  One CUDA graph per step."""
+    import torch
+    R, L, I = wl.n_rings, wl.ring_len, args.ring_incarnations
+    rounds = wl.n.shape[1]
+    big = W.config4(n_rings=R * I)
+    n = big.n.reshape(R, rounds * I)
+    with C.Runtime(max_actors=2 * R, scheduler=_sched(args), factor_split=args.factor_split,
+                   fork_pool=R * (L - 1)) as rt:
+        d_n = torch.from_numpy(n.astype(np.uint64).reshape(-1).copy()).cuda()
+        d_rep = torch.zeros(R * rounds * I * 32, dtype=torch.uint8, device="cuda")
+        masters = []
+        for r in range(R):
+            worker = rt.spawn(C.FACTOR_U64, mailbox_capacity=16)
+            masters.append(rt.spawn(C.RING_TOKEN, mailbox_capacity=4, flags=C.ACTOR_MASTER | C.ACTOR_RECREATE,
+                                    worker=worker, factor_n=d_n.data_ptr() + r * rounds * I * 8,
+                                    factor_count=rounds * I,
+                                    factor_replies=d_rep.data_ptr() + r * rounds * I * 32, ring_len=L, incarnations=I))
+        m = np.zeros(R, C.DMSG_DTYPE)
+        m["actor"] = np.array(masters, np.uint32) - 1
+        m["kind"] = C.RING_TOKEN | (C.MSG_START << 16)
+        m["u64"] = wl.token
+        d_m = torch.from_numpy(m.view(np.uint8).copy()).cuda()
+        d_r = torch.zeros(R * 32, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        rt.graph_begin()
+        rt.reset_actors()
+        rt.request_batch_device(d_m.data_ptr(), R, d_r.data_ptr())
+        g = rt.graph_end()
+        stream = torch.cuda.ExternalStream(rt.stream())
+        for _ in range(args.warmup):
+            rt.graph_launch(g)
+        rt.stream_sync()
+        rt.stats()
+        times = []
+        for _ in range(args.steps):
+            e0, e1 = _events(stream)
+            e0.record(stream)
+            rt.graph_launch(g)
+            e1.record(stream)
+            rt.stream_sync()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        st = rt.stats()
+        rt.graph_destroy(g)
+        rep_ = d_rep.cpu().numpy().view(C.DREPLY_DTYPE).reshape(R, rounds * I)
+        if not (np.all(rep_["status"] == 0) and np.array_equal(rep_["r0"] * rep_["r1"], n.astype(np.uint64))):
+            raise SystemExit("bench: ring recreated: factor replies wrong")
+        if st["device_spawns"] != args.steps * R * (L - 1) * I:
+            raise SystemExit(f"bench: ring recreated: spawned {st['device_spawns']}")
+    t = float(np.mean(times))
+    hops = (L + wl.token) * I
+    msgs = R * (hops + 1 + I) + R * rounds * I        # tokens, START, end-of-incarnation notices, factors
+    return {"ms_per_step": 1e3 * t, "timing_stats": timing_stats(times, msgs), "msgs_per_s": msgs / t,
+            "ns_per_hop": 1e9 * t / hops, "messages": msgs, "incarnations": I,
+            "device_spawns_per_step": R * (L - 1) * I, "spawns_per_s": R * (L - 1) * I / t}
 
 
 def run_serve(args):

@@ -46,6 +46,8 @@ extern "C" {
 #define CAF_GPU_EWAITLIMIT (-6)  /* a bounded device wait expired; see caf_gpu_error_word      */
 #define CAF_GPU_ESTATE     (-7)  /* unknown or already-consumed handle, or runtime misuse      */
 #define CAF_GPU_ECUDA      (-8)  /* a CUDA call failed (no GPU, launch failure, ...)           */
+#define CAF_GPU_EBOUNDS    (-9)  /* validation: the device refused an out-of-range index, or a */
+                                 /* guard region after a device array was overwritten        */
 
 /* ---- kernel ids = message kinds (an actor accepts exactly one kind) ----- */
 #define CAF_GPU_FACTOR_U64          1u  /* u64 n -> (p, q), p <= q                   */
@@ -126,7 +128,24 @@ extern "C" {
 #define CAF_GPU_MSG_START  0x1u    /* RING_TOKEN: start the ring at this master   */
 
 /* ---- actor flags -------------------------------------------------------- */
-#define CAF_GPU_ACTOR_MASTER 0x1u  /* RING_TOKEN: ring master (emits factor requests) */
+#define CAF_GPU_ACTOR_MASTER   1u    /* RING_TOKEN: ring master (emits factor requests)          */
+#define CAF_GPU_ACTOR_RECREATE 2u    /* RING_TOKEN master: creates its ring on the device, anew  */
+                                     /* for each of cfg.incarnations runs (see below)            */
+/* A re-creating ring master (MASTER | RECREATE) is the paper's mixed-benchmark
+ * ring master whose ring "is re-created 4 times" (Sec. 5, "Mixed Operations
+ * Under Work Load").  It is spawned by the host with cfg.ring_len (actors per
+ * ring, master included, 2..65536), cfg.incarnations (1..255), its factor
+ * worker and factor arrays; cfg.next is ignored.  A START message with token
+ * v makes it spawn ring_len - 1 member actors on the device (from the FORK
+ * actor pool, made at this spawn if absent), run the ring with token v, and,
+ * when every member has terminated, spawn the next incarnation's members,
+ * until cfg.incarnations have run; then it terminates.  Members terminate as
+ * in a plain ring and their records return to the pool.  Factor requests go
+ * out at each incarnation's start and per token v > 0 the master receives
+ * (factor_count must cover them all).  A START that reaches a master whose
+ * ring is running gets CAF_GPU_REPLY_REJECTED.  Spawn it before recording any
+ * CUDA graph (ESTATE after one).  Persistent backend only.  Token values are
+ * at most 2^31 - 1. */
 
 typedef struct caf_gpu_runtime caf_gpu_runtime;   /* opaque */
 typedef uint64_t caf_gpu_actor;                   /* opaque actor id, 0 = invalid */
@@ -172,6 +191,8 @@ typedef struct {
     uint32_t factor_count;          /* RING_TOKEN master: entries in factor_n                  */
     const uint64_t *factor_n;       /* RING_TOKEN master: device array, n sent at round k      */
     void *factor_replies;           /* RING_TOKEN master: device caf_gpu_dreply[factor_count]  */
+    uint32_t ring_len;              /* RECREATE master: actors per ring, master included       */
+    uint32_t incarnations;          /* RECREATE master: rings it creates, one after another    */
 } caf_gpu_actor_cfg;
 
 /* A message.  Copied at the call (call-by-value, Sec. 3.3); GEMM operands
@@ -401,6 +422,38 @@ int caf_gpu_measure_mul_rates(double *rates);
  * frees, a small buffer; needs no runtime.  CAF_GPU_EINVAL for a null
  * pointer, CAF_GPU_ECUDA on a CUDA error. */
 int caf_gpu_measure_fp32_rate(double *ops_per_s);
+
+/* Measured latencies, on the current device, of the memory operations a
+ * mailbox hop is built from (a token passed along a ring of actors, Sec. 5,
+ * "Mixed Operations Under Work Load", is a chain of such dependent steps):
+ * ns[0] = a returning atomic add (dependent chain, one thread: one L2 round
+ * trip), ns[1] = an acquire load of a line held in L2 (dependent chain),
+ * ns[2] = a relaxed store followed by fence.sc.gpu, ns[3] = a one-way flag
+ * handoff between two SMs (release store, acquire polling; half a ping-pong
+ * round trip).  ns: host array of 4 doubles.  Runs two short kernels on the
+ * current device (the ping-pong as a cooperative launch of two CTAs on two
+ * SMs, every wait bounded) and allocates, then frees, small buffers; needs no
+ * runtime.  CAF_GPU_EINVAL for a null pointer, CAF_GPU_ECUDA on a CUDA error
+ * or a wait that gave up. */
+int caf_gpu_measure_latency(double *ns);
+
+/* Arena canaries.  Every device array of the runtime is followed by a guard
+ * region that no kernel writes; this call reads them all back and sets
+ * *corrupted to the number whose bytes changed (0 when memory is intact).  The
+ * same check runs in caf_gpu_runtime_destroy, which then returns
+ * CAF_GPU_EBOUNDS.  Not while recording a graph (ESTATE).  The paper has no
+ * counterpart: it is the library's own memory-safety check. */
+int caf_gpu_check_guards(caf_gpu_runtime *rt, uint32_t *corrupted);
+
+/* Fault-injection test hook, host side only (no device fault is made):
+ * what = 1: point the mailbox of actor `arg` (a caf_gpu_actor) past the end of
+ * the slot pool; the next message to it must be refused by the validation-mode
+ * bounds check (CAF_GPU_EBOUNDS from the call that waits for it), with nothing
+ * read or written out of range.  Needs validation_mode (EINVAL otherwise); the
+ * actor stays unusable.  what = 2: overwrite one byte of guard region `arg`
+ * (0-based), which caf_gpu_check_guards then reports.  EINVAL for anything
+ * else. */
+int caf_gpu_debug_inject(caf_gpu_runtime *rt, uint32_t what, uint64_t arg);
 
 /* Clear the device error word after a reported bounded-wait expiry. */
 int caf_gpu_clear_error(caf_gpu_runtime *rt);

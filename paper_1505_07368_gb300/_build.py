@@ -8,7 +8,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcafgpu.so")
-SOURCES = ["runtime.cu", "drain.cu", "gemm.cu", "factor_static.cu", "mulrate.cu", "mandel.cu"]
+SOURCES = ["runtime.cu", "drain.cu", "gemm.cu", "factor_static.cu", "mulrate.cu", "mandel.cu", "latency.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -73,19 +73,28 @@ def workload_key(gpu: str, n_actors: int, n: np.ndarray, max_factor_n: int) -> s
 
 
 def tune_factor(actor_idx: np.ndarray, n: np.ndarray, n_actors: int, max_factor_n: int,
-                candidates=None, runtime_kwargs=None, use_cache: bool = True, log=None):
+                candidates=None, runtime_kwargs=None, use_cache: bool = True, log=None, timed_run=None,
+                gpu_name=None):
     """Pick the fastest (factor_batch, factor_warps, ctas_per_sm) for this workload.
 
     Returns (best_cfg, table) where table lists (cfg, seconds) for every candidate
-    measured (empty when the cached choice was used)."""
-    import torch
+    measured (empty when the cached choice was used).  `timed_run(cand) ->
+    (seconds, signature)` replaces the GPU run (tests stub it on the host)."""
     candidates = candidates or DEFAULT_CANDIDATES
+    if gpu_name is None:
+        import torch
+        gpu_name = torch.cuda.get_device_name()
+    key = workload_key(gpu_name, n_actors, n, max_factor_n)
+    if timed_run is None:
+        timed_run = _factor_run(actor_idx, n, n_actors, max_factor_n, runtime_kwargs)
+    return _tune(key, candidates, timed_run, use_cache, log)
+
+
+def _factor_run(actor_idx, n, n_actors, max_factor_n, runtime_kwargs):
+    """The GPU timed run of one candidate: one device batch after a warm-up;
+    the signature is every reply (status, r0, r1)."""
+    import torch
     runtime_kwargs = dict(runtime_kwargs or {})
-    gpu = torch.cuda.get_device_name()
-    key = workload_key(gpu, n_actors, n, max_factor_n)
-    cache = _load_cache() if use_cache else {}
-    if key in cache:
-        return cache[key]["best"], []
     count = n.size
     m = np.zeros(count, C.DMSG_DTYPE)
     m["actor"] = actor_idx
@@ -94,9 +103,8 @@ def tune_factor(actor_idx: np.ndarray, n: np.ndarray, n_actors: int, max_factor_
     m["tag"] = np.arange(count)
     d_msgs = torch.from_numpy(m.view(np.uint8).copy()).cuda()
     d_rep = torch.zeros(count * C.DREPLY_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
-    table = []
-    ref = None
-    for cand in candidates:
+
+    def run(cand):
         kw = dict(runtime_kwargs)
         kw.update(cand)
         with C.Runtime(max_factor_n=max_factor_n, max_actors=n_actors, **kw) as rt:
@@ -113,25 +121,17 @@ def tune_factor(actor_idx: np.ndarray, n: np.ndarray, n_actors: int, max_factor_
             rt.stream_sync()
             secs = e0.elapsed_time(e1) / 1e3
             rep = d_rep.cpu().numpy().view(C.DREPLY_DTYPE)
-            res = (rep["status"].copy(), rep["r0"].copy(), rep["r1"].copy())
-        if ref is None:
-            ref = res
-        ok = all(np.array_equal(a, b) for a, b in zip(res, ref))
-        table.append((cand, secs if ok else float("inf")))
-        if log:
-            log(f"autotune {cand}: {secs * 1e3:.1f} ms{'' if ok else ' (results differ: rejected)'}")
-    best = min(table, key=lambda x: x[1])[0]
-    if use_cache:
-        cache = _load_cache()
-        cache[key] = {"best": best, "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
-                      "table": [[c, s] for c, s in table]}
-        _store_cache(cache)
-    return best, table
+            sig = rep["status"].tobytes() + rep["r0"].tobytes() + rep["r1"].tobytes()
+        return secs, sig
+
+    return run
 
 
 def _tune(key: str, candidates, run, use_cache: bool, log):
     """Time `run(candidate) -> (seconds, signature)` for every candidate; keep
-    the fastest whose signature equals the first candidate's."""
+    the fastest whose signature equals the first candidate's (a candidate
+    whose results differ is rejected, however fast)."""
+    key += "|cands=" + hashlib.sha1(json.dumps(candidates, sort_keys=True).encode()).hexdigest()[:12]
     cache = _load_cache() if use_cache else {}
     if key in cache:
         return cache[key]["best"], []
@@ -154,19 +154,33 @@ def _tune(key: str, candidates, run, use_cache: bool, log):
 
 
 def tune_gemm(kind: int, actor_idx: np.ndarray, desc: np.ndarray, outs, n_actors: int, candidates=None,
-              runtime_kwargs=None, use_cache: bool = True, log=None):
+              runtime_kwargs=None, use_cache: bool = True, log=None, timed_run=None, gpu_name=None):
     """Pick the fastest GEMM drain schedule (items per round, messages per claim)
     for one device batch of GEMM messages of `kind` (BF16 or split).
 
     desc: caf_gpu_gemm_desc records (host numpy, GEMM_DESC_DTYPE) whose C
     pointers lie in the device tensor `outs`; actor_idx: receiving actor index
-    per message.  Returns (best_cfg, table)."""
-    import torch
+    per message.  `timed_run(cand) -> (seconds, signature)` replaces the GPU run
+    (tests stub it on the host).  Returns (best_cfg, table)."""
     candidates = candidates or GEMM_CANDIDATES
-    runtime_kwargs = dict(runtime_kwargs or {})
     count = desc.size
     h = hashlib.sha1(np.ascontiguousarray(desc["n"]).tobytes() + np.ascontiguousarray(actor_idx).tobytes())
-    key = f"{torch.cuda.get_device_name()}|gemm{kind}|actors={n_actors}|msgs={count}|{h.hexdigest()[:16]}"
+    if gpu_name is None:
+        import torch
+        gpu_name = torch.cuda.get_device_name()
+    key = f"{gpu_name}|gemm{kind}|actors={n_actors}|msgs={count}|{h.hexdigest()[:16]}"
+    if timed_run is None:
+        timed_run = _gemm_run(kind, actor_idx, desc, outs, n_actors, runtime_kwargs)
+    return _tune(key, candidates, timed_run, use_cache, log)
+
+
+def _gemm_run(kind, actor_idx, desc, outs, n_actors, runtime_kwargs):
+    """The GPU timed run of one GEMM candidate; the signature is the replies
+    and a float64 checksum of every C (bit-identical across schedules: a
+    tile's arithmetic does not depend on which CTA runs it or when)."""
+    import torch
+    runtime_kwargs = dict(runtime_kwargs or {})
+    count = desc.size
     d_desc = torch.from_numpy(desc.view(np.uint8).copy()).cuda()
     m = np.zeros(count, C.DMSG_DTYPE)
     m["actor"] = actor_idx
@@ -198,4 +212,4 @@ def tune_gemm(kind: int, actor_idx: np.ndarray, desc: np.ndarray, outs, n_actors
             sig = (rep["status"].tobytes(), rep["r1"].tobytes(), float(outs.sum(dtype=torch.float64).item()))
         return secs, sig
 
-    return _tune(key, candidates, run, use_cache, log)
+    return run

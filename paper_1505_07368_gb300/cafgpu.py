@@ -18,13 +18,14 @@ import numpy as np
 from . import _build
 
 # ---- constants (caf_gpu.h) ------------------------------------------------
-OK, EINVAL, ENOMEM, EAGAIN, ETIMEDOUT, EDEAD, EWAITLIMIT, ESTATE, ECUDA = 0, -1, -2, -3, -4, -5, -6, -7, -8
+OK, EINVAL, ENOMEM, EAGAIN, ETIMEDOUT, EDEAD, EWAITLIMIT, ESTATE, ECUDA, EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 FACTOR_U64, GEMM_BF16, GEMM_SPLIT_BF16X3, RING_TOKEN, SINK, SOURCE, MANDELBROT, FORK = 1, 2, 3, 4, 5, 6, 7, 8
 BACKEND_PERSISTENT, BACKEND_PER_MESSAGE_LAUNCH = 0, 1
 SCHED_GLOBAL, SCHED_STEAL = 0, 1
 REPLY_OK, REPLY_NOFACTOR, REPLY_DEAD, REPLY_REJECTED = 0, 1, 2, 3
 MSG_START = 1
 ACTOR_MASTER = 1
+ACTOR_RECREATE = 2
 
 DMSG_DTYPE = np.dtype([("actor", "<u4"), ("kind", "<u4"), ("sender", "<u4"), ("sender_seq", "<u4"),
                        ("u64", "<u8"), ("tag", "<u8")])
@@ -60,7 +61,8 @@ class ActorCfg(ctypes.Structure):
     _fields_ = [("mailbox_capacity", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("next", ctypes.c_uint64), ("worker", ctypes.c_uint64), ("init_state", ctypes.c_int32),
                 ("factor_count", ctypes.c_uint32), ("factor_n", ctypes.c_void_p),
-                ("factor_replies", ctypes.c_void_p)]
+                ("factor_replies", ctypes.c_void_p), ("ring_len", ctypes.c_uint32),
+                ("incarnations", ctypes.c_uint32)]
 
 
 class Msg(ctypes.Structure):
@@ -114,9 +116,10 @@ EXPORTS = [
     "caf_gpu_request_batch_device", "caf_gpu_sync", "caf_gpu_stream_sync", "caf_gpu_set_backend",
     "caf_gpu_reset_actors", "caf_gpu_actor_state", "caf_gpu_stats_read", "caf_gpu_read_log",
     "caf_gpu_stream", "caf_gpu_mark", "caf_gpu_prime_table", "caf_gpu_debug_wait_expiry", "caf_gpu_clear_error",
-    "caf_gpu_measure_mul_rates", "caf_gpu_measure_fp32_rate", "caf_gpu_sink_totals",
+    "caf_gpu_measure_mul_rates", "caf_gpu_measure_fp32_rate", "caf_gpu_measure_latency", "caf_gpu_sink_totals",
     "caf_gpu_graph_begin", "caf_gpu_graph_end", "caf_gpu_graph_launch", "caf_gpu_graph_destroy",
-    "caf_gpu_serve_run", "caf_gpu_factor_static", "caf_gpu_strerror",
+    "caf_gpu_serve_run", "caf_gpu_factor_static", "caf_gpu_check_guards", "caf_gpu_debug_inject",
+    "caf_gpu_strerror",
 ]
 FACTOR_STATIC_MAX = 4096
 
@@ -156,6 +159,7 @@ def load(build: bool = True):
         "caf_gpu_debug_wait_expiry": [vp, u64],
         "caf_gpu_measure_mul_rates": [vp],
         "caf_gpu_measure_fp32_rate": [vp],
+        "caf_gpu_measure_latency": [vp],
         "caf_gpu_sink_totals": [vp, u64, P(u64), P(u64)],
         "caf_gpu_clear_error": [vp],
         "caf_gpu_mark": [vp],
@@ -165,6 +169,8 @@ def load(build: bool = True):
         "caf_gpu_graph_launch": [vp, vp],
         "caf_gpu_graph_destroy": [vp],
         "caf_gpu_serve_run": [vp, vp, u32, P(ServeCfg), vp, P(ServeStats)],
+        "caf_gpu_check_guards": [vp, P(u32)],
+        "caf_gpu_debug_inject": [vp, u32, u64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -190,6 +196,14 @@ def measure_fp32_rate() -> float:
     out = ctypes.c_double()
     _check(load().caf_gpu_measure_fp32_rate(ctypes.byref(out)), "caf_gpu_measure_fp32_rate")
     return out.value
+
+
+def measure_latency() -> dict:
+    """Measured latencies (ns): returning L2 atomic, L2 acquire load, store +
+    fence.sc, and one-way flag handoff between two SMs."""
+    out = (ctypes.c_double * 4)()
+    _check(load().caf_gpu_measure_latency(out), "caf_gpu_measure_latency")
+    return {"atomic_ns": out[0], "load_acquire_ns": out[1], "store_fence_sc_ns": out[2], "handoff_ns": out[3]}
 
 
 def factor_static(d_n: int, count: int, d_replies: int, stream: int = 0) -> int:
@@ -242,12 +256,22 @@ class Runtime:
     # -- actors -------------------------------------------------------------
     def spawn(self, kernel_id: int, mailbox_capacity: int = 0, flags: int = 0, next: int = 0,
               worker: int = 0, init_state: int = 0, factor_n: int = 0, factor_count: int = 0,
-              factor_replies: int = 0) -> int:
+              factor_replies: int = 0, ring_len: int = 0, incarnations: int = 0) -> int:
         c = ActorCfg(mailbox_capacity, flags, next, worker, init_state, factor_count, factor_n or None,
-                     factor_replies or None)
+                     factor_replies or None, ring_len, incarnations)
         out = ctypes.c_uint64()
         _check(self.L.caf_gpu_spawn(self.h, kernel_id, ctypes.byref(c), ctypes.byref(out)), "caf_gpu_spawn")
         return out.value
+
+    def check_guards(self) -> int:
+        """Guard regions after the device arrays whose bytes changed (0: intact)."""
+        out = ctypes.c_uint32()
+        _check(self.L.caf_gpu_check_guards(self.h, ctypes.byref(out)), "caf_gpu_check_guards")
+        return out.value
+
+    def debug_inject(self, what: int, arg: int) -> int:
+        """Host-side fault injection for tests (returns the status code)."""
+        return self.L.caf_gpu_debug_inject(self.h, what, arg)
 
     def actor_state(self, actor: int):
         lc = ctypes.c_uint32()

@@ -63,21 +63,16 @@ __device__ __forceinline__ void st_release_sys(uint64_t *p, uint64_t v) {
 __device__ __forceinline__ void st_relaxed_sys(uint64_t *p, uint64_t v) {
     asm volatile("st.relaxed.sys.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-// Acquire-release compare-and-swap and release exchange of a 32-bit word
-// (gpu scope): the actor-state handshake between a claim that parks an actor
-// and a producer that wakes it, so the head the claim published is visible
-// to whoever claims the actor next.
+// Acquire-release compare-and-swap of a 32-bit word (gpu scope): the
+// actor-state handshake between a claim that parks an actor (a release store
+// of WAITING) and a producer that wakes or claims it, so the head the claim
+// published is visible to whoever claims the actor next.
 __device__ __forceinline__ uint32_t cas_acq_rel_gpu(uint32_t *p, uint32_t expect, uint32_t desired) {
     uint32_t old;
     asm volatile("atom.acq_rel.gpu.global.cas.b32 %0, [%1], %2, %3;"
                  : "=r"(old)
                  : "l"(p), "r"(expect), "r"(desired)
                  : "memory");
-    return old;
-}
-__device__ __forceinline__ uint32_t exch_release_gpu(uint32_t *p, uint32_t v) {
-    uint32_t old;
-    asm volatile("atom.release.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
     return old;
 }
 __device__ __forceinline__ uint32_t cas_u32(uint32_t *p, uint32_t expect, uint32_t desired) {

@@ -55,6 +55,27 @@ __device__ __forceinline__ void fail(const DrainParams &P, uint32_t code, uint32
     atomicExch(reinterpret_cast<unsigned int *>(&P.ctl->exit_flag), 1u);
 }
 
+// A work item names an existing job record and one of its tiles, pack panels
+// or bands.
+__device__ bool work_item_ok(const DrainParams &P, uint32_t item);
+
+// Validation mode: indices taken from queues, messages and records are checked
+// against their arrays before they are used.  A failed check records
+// kErrBounds (the site, the index and the limit) and the kernel unwinds as
+// after an expired wait; nothing out of range is read or written.
+__device__ __forceinline__ bool actor_ok(const DrainParams &P, uint32_t a) {
+    return a < P.n_actors || (P.fork_pool && a - P.fork_base < P.fork_pool);
+}
+__device__ __noinline__ void bounds_fail(const DrainParams &P, uint32_t site, uint64_t idx, uint64_t lim) {
+    fail(P, kErrBounds, site, idx, lim);
+}
+// Actor `a` and its whole mailbox lie inside the actor table and slot pool.
+__device__ __forceinline__ bool mailbox_ok(const DrainParams &P, uint32_t a) {
+    if (!actor_ok(P, a)) return false;
+    const ActorDesc *A = &P.actors[a];
+    return A->slot_base + (uint64_t)A->cap_mask < P.n_slots;
+}
+
 __device__ __forceinline__ void heartbeat(const DrainParams &P) {
     *((volatile uint64_t *)&P.ctl->heartbeat) = globaltimer();
 }
@@ -115,6 +136,13 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
     const uint32_t lane = lane_id();
     const uint32_t vmask = __ballot_sync(FULL, valid);
     if (!vmask) return true;
+    if (P.validation) {
+        const bool bad = valid && !mailbox_ok(P, a);
+        if (__any_sync(FULL, bad)) {
+            if (bad) bounds_fail(P, 40, a, P.n_slots);
+            return false;
+        }
+    }
     if (lane == 0) add_u64(&P.ctl->ingested, __popc(vmask));
     __syncwarp();
     const uint32_t key = valid ? a : 0xFFFFFFFFu;
@@ -176,16 +204,18 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
 // Park or re-queue an actor after its claim (warp-collective; lane 0 acts).
 // The warp barrier orders every lane's slot reads before lane 0's release
 // store of the new head: a producer that sees that head (acquire) may
-// overwrite those slots.  The exchange to WAITING is a release as well, so a
+// overwrite those slots.  The store of WAITING is a release as well, so a
 // producer whose acquire-CAS wakes the actor passes the head on to the next
-// claim through the ready queue.
-__device__ void release_actor(const DrainParams &P, uint32_t a, uint64_t new_head) {
+// claim through the ready queue.  `done`: 1 if the caller knows the actor has
+// terminated, 0 if it knows it has not, -1 to read its state.
+__device__ void release_actor(const DrainParams &P, uint32_t a, uint64_t new_head, int done = -1) {
     __syncwarp();
     if (lane_id() == 0) {
         ActorDesc *A = &P.actors[a];
         st_release_gpu(&A->head, new_head);
-        if (*((volatile uint32_t *)&A->state) != kDone) {
-            exch_release_gpu(&A->state, kWaiting);
+        if (done < 0) done = *((volatile uint32_t *)&A->state) == kDone;
+        if (!done) {
+            st_release_gpu(&A->state, kWaiting);
             asm volatile("fence.sc.gpu;" ::: "memory");
             if (ld_relaxed_gpu(&A->tail) != new_head &&
                 cas_u32(&A->state, kWaiting, kReady) == kWaiting) {
@@ -194,6 +224,25 @@ __device__ void release_actor(const DrainParams &P, uint32_t a, uint64_t new_hea
         }
     }
     __syncwarp();
+}
+
+// Validation mode: record the handling of `take` messages of actor `a` (lane i
+// holds message i) in the log, in handling order (warp-collective).
+__device__ void log_rows(const DrainParams &P, uint32_t a, uint32_t take, const MsgData &m) {
+    const uint32_t lane = lane_id();
+    uint64_t base = 0;
+    if (lane == 0) base = add_u64(&P.ctl->log_count, take);
+    base = __shfl_sync(FULL, base, 0);
+    if (lane < take && base + lane < P.log_capacity) {
+        LogRow *r = &P.log[base + lane];
+        r->actor = a;
+        r->sender = m.sender;
+        r->sender_seq = m.sender_seq;
+        r->kind = m.kind;
+        r->stamp = base + lane;
+        r->tag = m.tag;
+        r->value = m.payload;
+    }
 }
 
 // Dequeue from the claimed actor: of the next `want` (<= 32) tickets, take
@@ -205,6 +254,10 @@ __device__ void release_actor(const DrainParams &P, uint32_t a, uint64_t new_hea
 __device__ uint32_t warp_dequeue(const DrainParams &P, uint32_t a, uint64_t head, uint32_t want,
                                  MsgData &m) {
     const uint32_t lane = lane_id();
+    if (P.validation && !mailbox_ok(P, a)) {
+        if (lane == 0) bounds_fail(P, 41, a, P.n_slots);
+        return 0;
+    }
     ActorDesc *A = &P.actors[a];
     const uint64_t t = head + lane;
     Slot *s = &P.slots[A->slot_base + (t & A->cap_mask)];
@@ -233,21 +286,7 @@ __device__ uint32_t warp_dequeue(const DrainParams &P, uint32_t a, uint64_t head
         m.kind = s->kind;
         m.reply_token = s->reply_token;
     }
-    if (P.validation) {
-        uint64_t base = 0;
-        if (lane == 0) base = add_u64(&P.ctl->log_count, take);
-        base = __shfl_sync(FULL, base, 0);
-        if (lane < take && base + lane < P.log_capacity) {
-            LogRow *r = &P.log[base + lane];
-            r->actor = a;
-            r->sender = m.sender;
-            r->sender_seq = m.sender_seq;
-            r->kind = m.kind;
-            r->stamp = base + lane;
-            r->tag = m.tag;
-            r->value = m.payload;
-        }
-    }
+    if (P.validation) log_rows(P, a, take, m);
     return take;
 }
 
@@ -422,6 +461,7 @@ __device__ void group_produce_split(const DrainParams &P, GroupShared &G, TableT
 // a message's bound is no divisor below its square root.)
 constexpr uint32_t kSweepPrimes = 4;   // chunks (primes per lane) tested per step
 static_assert((kTile / 32) % (kSweepPrimes * kConsumerWarps) == 0, "a tile splits into steps for any team size");
+
 // kSplit: the drain splits batches (the stream carries tile indices); else
 // the sequential stream of group_produce, whose end is G.final_tile.
 template <bool kSplit>
@@ -490,26 +530,51 @@ __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableT
             // teammates' hits (lane j: message j), read now and applied after
             // this tile so the load's latency overlaps the tests; a stale
             // value only costs tests
+            // (other segments of a split batch record theirs in the same slots)
+            const bool shared_found = wpb > 1 || (kSplit && segs > 1);
             uint32_t fv = 0xFFFFFFFFu;
-            if (wpb > 1 && lane < kFactorKMax) fv = ld_relaxed_gpu(&B->found[lane]);
+            if (shared_found && lane < kFactorKMax) fv = ld_relaxed_gpu(&B->found[lane]);
             const uint32_t tbase = smem_u32(&ring[st]);
             uint32_t tile_tests = 0;
             // kSweepPrimes chunks per step, u + q wpb (kTile / 32 is a multiple
             // of kSweepPrimes * wpb); one copy of the body: the test switch is
-            // large, and an unrolled tile loop overflows the instruction cache
-#pragma unroll 1
-            for (uint32_t u = r; u < kTile / 32 && s.k > 0; u += kSweepPrimes * wpb) {
-                const uint32_t c0 = start + u * 32;
+            // large, and an unrolled tile loop overflows the instruction cache.
+            // The held messages are read-only inside the step loop: a step
+            // with a hit, or one that reaches the next bound, leaves the loop
+            // and is finished outside it, so the loop carries no register
+            // moves for the held slots.
+            const uint32_t ustep = kSweepPrimes * wpb;
+            uint32_t u = r;
+            while (u < kTile / 32 && s.k > 0) {
                 uint32_t pp[kSweepPrimes], pi[kSweepPrimes], pl[kSweepPrimes];
+                const uint32_t k_now = (uint32_t)s.k;
+                uint32_t steps = 0;
+                bool hit = false, stop = false;
+#pragma unroll 1
+                for (;;) {
 #pragma unroll
-                for (uint32_t q = 0; q < kSweepPrimes; ++q) {
-                    const uint32_t off = ((u + q * wpb) * 32 + lane) * 4;
-                    pp[q] = lds_u32(tbase + off);
-                    pi[q] = lds_u32(tbase + kTile * 4 + off);
-                    pl[q] = lds_u32(tbase + 2 * kTile * 4 + off);
+                    for (uint32_t q = 0; q < kSweepPrimes; ++q) {
+                        const uint32_t off = ((u + q * wpb) * 32 + lane) * 4;
+                        pp[q] = lds_u32(tbase + off);
+                        pi[q] = lds_u32(tbase + kTile * 4 + off);
+                        pl[q] = lds_u32(tbase + 2 * kTile * 4 + off);
+                    }
+                    ++steps;
+                    hit = __any_sync(FULL, sweep_chunks<kSweepPrimes>(s, pp, pi, pl));
+                    // the next step starts at c1 + 32 wpb
+                    const uint32_t c1 = start + u * 32 + (kSweepPrimes - 1) * 32 * wpb;
+                    if (hit || c1 + 32 * wpb >= next_drop) {
+                        stop = true;
+                        break;
+                    }
+                    u += ustep;
+                    if (u >= kTile / 32) break;
                 }
-                tile_tests += (uint32_t)s.k * 32u * kSweepPrimes;
-                if (__any_sync(FULL, sweep_chunks<kSweepPrimes>(s, pp, pi, pl))) {
+                tile_tests += steps * k_now * 32u * kSweepPrimes;
+                if (!stop) break;
+                // finish step u: its hits, then its bound check
+                const uint32_t c0 = start + u * 32;
+                if (hit) {
                     uint32_t h[kSweepPrimes], hh = 0;
 #pragma unroll
                     for (uint32_t q = 0; q < kSweepPrimes; ++q) {
@@ -529,17 +594,17 @@ __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableT
                     sweep_remove_mask(s, any);
                 }
                 const uint32_t c1 = c0 + (kSweepPrimes - 1) * 32 * wpb;
-                // the next step starts at c1 + 32 * wpb
                 if (s.k > 0 && c1 + 32 * wpb >= next_drop) {
                     const uint32_t rm = __ballot_sync(FULL, held_value(s, pbv) <= c1 + 32 * wpb);
                     sweep_remove_mask(s, rm);
                     next_drop = s.k > 0 ? sweep_min_bound(s, pbv) : 0xFFFFFFFFu;
                 }
+                u += ustep;
             }
             tests += tile_tests;
             // drop messages a teammate has factored below the next tile: this
             // warp's remaining primes cannot give a smaller divisor
-            if (wpb > 1 && s.k > 0) {
+            if (shared_found && s.k > 0) {
                 const uint32_t rm = __ballot_sync(FULL, held_value(s, fv) < start + kTile);
                 if (rm) {
                     sweep_remove_mask(s, rm);
@@ -680,84 +745,304 @@ __device__ bool ring_emit_factor(const DrainParams &P, uint32_t a) {
     return warp_enqueue(P, valid, worker, m);
 }
 
-__device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v, uint32_t *handoff) {
+// A message handed from one ring actor's run straight to the next actor's,
+// without going through a mailbox (all lanes hold the same copy).
+struct Carry {
+    bool has;
+    MsgData m;
+    uint64_t head;     // the receiver's mailbox position when it was claimed (its mailbox was empty)
+};
+
+// Send token v from ring actor `a` to its successor.  Direct handoff: if the
+// successor is waiting with an empty mailbox, this warp claims it (CAS
+// WAITING -> RUNNING) and carries the token to its run instead of writing a
+// mailbox slot -- no ticket, no slot round trip, no wake handshake.  With an
+// empty mailbox the token is the successor's next message in any order, and
+// per-sender order holds because this actor's earlier tokens to it are all
+// handled.  Otherwise the token goes through the mailbox (warp_enqueue), and
+// a successor this call wakes is returned in *handoff to run next.
+// In a ring that a RECREATE master creates, a token of value 0 carries its
+// origin (the actor id + 1 in the payload's high word), and its tag names the
+// ring, the incarnation and the receiver's position: master + 1 in bits 0..31,
+// the incarnation in bits 32..39, the position in bits 40..63.
+__device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v, uint32_t *handoff, Carry *carry,
+                             uint32_t origin1 = 0) {
     ActorDesc *A = &P.actors[a];
     const uint32_t next = A->next;
     MsgData m{};
-    m.payload = (uint64_t)(uint32_t)v;
+    m.payload = (uint64_t)(uint32_t)v | ((uint64_t)origin1 << 32);
     m.kind = kToken;
     m.sender = 0x80000000u | a;
     m.sender_seq = (uint32_t)v;
-    const bool send = lane_id() == 0;
-    if (lane_id() == 0) add_u64(&P.ctl->device_sends, 1);
-    return warp_enqueue(P, send, next, m, handoff);
+    if (A->flags & (kActorRecreate | kActorLink)) {
+        const bool master = (A->flags & kActorRecreate) != 0;
+        const uint32_t pos = master ? 0u : A->ring_pos;
+        const uint32_t recv = pos + 1 == A->ring_len ? 0u : pos + 1;
+        m.tag = (uint64_t)((master ? a : A->ring_master) + 1) | ((uint64_t)(A->ring_inc & 0xFFu) << 32) |
+                ((uint64_t)recv << 40);
+    }
+    const uint32_t lane = lane_id();
+    if (lane == 0) add_u64(&P.ctl->device_sends, 1);
+    if (carry && !carry->has && next != a) {
+        bool direct = false;
+        uint64_t h = 0;
+        if (lane == 0) {
+            ActorDesc *N = &P.actors[next];
+            if (cas_acq_rel_gpu(&N->state, kWaiting, kRunning) == kWaiting) {
+                // claimed: its head is final (the last holder released it before
+                // parking, and the CAS acquired that).  A message whose ticket
+                // this read misses is found by this claim's release, which
+                // re-queues the actor; with messages already waiting the token
+                // goes behind them, after returning the actor to WAITING
+                // (the mailbox path's wake then schedules it).
+                const uint64_t t = ld_relaxed_gpu(&N->tail);
+                h = ld_relaxed_gpu(&N->head);
+                if (t == h) direct = true;
+                else st_release_gpu(&N->state, kWaiting);
+            }
+            if (direct) add_u64(&P.ctl->ingested, 1);
+        }
+        if (__shfl_sync(FULL, direct, 0)) {
+            carry->has = true;
+            carry->m = m;
+            carry->head = __shfl_sync(FULL, h, 0);
+            *handoff = next;
+            return true;
+        }
+    }
+    return warp_enqueue(P, lane == 0, next, m, handoff);
 }
 
-// Run the claimed ring actor `a`; returns the successor this warp woke (to be
-// run next by the same warp) or kNone.
-__device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a) {
+// RECREATE master `a` (claimed by this warp): spawn the ring_len - 1 members
+// of its next incarnation from the device actor pool (warp-collective).
+// Member i (position i + 1) gets the next member as successor, the last one
+// the master; the master's successor becomes member 0.  The records are
+// complete before the caller's first send reaches any of them.
+__device__ uint32_t fork_take_id(const DrainParams &P);
+
+__device__ bool ring_spawn(const DrainParams &P, uint32_t a) {
+    const uint32_t lane = lane_id();
+    ActorDesc *A = &P.actors[a];
+    const uint32_t L = A->ring_len, nl = L - 1, inc = A->ring_inc;
+    const int32_t init = A->init_state;
+    uint32_t prev_last = kNone, first = kNone;
+    for (uint32_t c0 = 0; c0 < nl; c0 += 32) {
+        const uint32_t i = c0 + lane;
+        uint32_t id = kNone;
+        if (i < nl) id = fork_take_id(P);
+        if (__any_sync(FULL, i < nl && id == kNone)) return false;   // the expired wait is recorded
+        const uint32_t succ = __shfl_down_sync(FULL, id, 1);
+        if (i < nl) {
+            ActorDesc *M = &P.actors[id];
+            M->kind = kToken;
+            M->flags = kActorLink;
+            M->next = i + 1 == nl ? a : (lane < 31 ? succ : kNone);   // kNone: patched by the next chunk
+            M->worker = kNone;
+            M->factor_count = 0;
+            M->round = 0;
+            M->user_state = init;
+            M->init_state = init;
+            M->ring_master = a;
+            M->ring_len = L;
+            M->ring_pos = i + 1;
+            M->ring_inc = inc;
+            M->ring_live = 0;
+            *((volatile uint32_t *)&M->state) = kWaiting;
+        }
+        if (c0 > 0 && lane == 0) P.actors[prev_last].next = id;
+        const uint32_t last_lane = nl - 1 - c0 < 31 ? nl - 1 - c0 : 31u;
+        prev_last = __shfl_sync(FULL, id, last_lane);
+        if (c0 == 0) first = __shfl_sync(FULL, id, 0);
+    }
+    if (lane == 0) {
+        A->next = first;
+        A->ring_live = nl;
+        add_u64(&P.ctl->device_spawns, nl);
+    }
+    __threadfence();
+    __syncwarp();
+    return true;
+}
+
+// RECREATE master `a`, its running incarnation over (every member has
+// terminated): true if another incarnation is to run (its index is advanced),
+// false if the master terminates now (warp-collective; lane 0 writes).
+__device__ bool ring_incarnation_over(const DrainParams &P, uint32_t a) {
+    ActorDesc *A = &P.actors[a];
+    const bool more = A->ring_inc + 1 < A->fork_token;
+    if (lane_id() == 0) {
+        if (more) {
+            A->ring_inc += 1;
+        } else {
+            A->ring_live = 0;
+            *((volatile uint32_t *)&A->state) = kDone;
+        }
+    }
+    __syncwarp();
+    return more;
+}
+
+// Run the claimed ring actor `a`: first the message carried to it (`carry`,
+// from its predecessor's run on this warp), then its mailbox.  Returns the
+// successor this warp woke or claimed (to be run next by the same warp) or
+// kNone; a token carried to that successor is left in `carry`.  With
+// `direct` false every forward goes through the mailbox.
+__device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carry, bool direct) {
     const uint32_t lane = lane_id();
     uint32_t handoff = kNone;
     ActorDesc *A = &P.actors[a];
-    if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
-    __syncwarp();
-    uint64_t head = *((volatile uint64_t *)&A->head);
-    const uint64_t tail = ld_acquire_gpu(&A->tail);
-    uint64_t take = tail - head;
-    // tail counts tickets a sender may not have published yet; a ticket at or
-    // past head + capacity waits for room that this claim only releases at
-    // its end, so a claim never goes past one mailbox's worth
-    if (take > (uint64_t)A->cap_mask + 1) take = (uint64_t)A->cap_mask + 1;
-    if (P.max_claim && take > P.max_claim) take = P.max_claim;
+    const bool carried = carry.has;
+    uint64_t head, take;
+    if (carried) {
+        // claimed by the predecessor's forward with an empty mailbox: later
+        // messages are left to this claim's release, which re-queues the actor
+        head = carry.head;
+        take = 0;
+    } else {
+        if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
+        __syncwarp();
+        head = *((volatile uint64_t *)&A->head);
+        const uint64_t tail = ld_acquire_gpu(&A->tail);
+        take = tail - head;
+        // tail counts tickets a sender may not have published yet; a ticket at or
+        // past head + capacity waits for room that this claim only releases at
+        // its end, so a claim never goes past one mailbox's worth
+        if (take > (uint64_t)A->cap_mask + 1) take = (uint64_t)A->cap_mask + 1;
+        if (P.max_claim && take > P.max_claim) take = P.max_claim;
+    }
     if (lane == 0) add_u64(&P.ctl->claims, 1);
-    for (uint64_t i = 0; i < take; ++i) {
+    Carry out{};
+    out.has = false;
+    // a ring that a RECREATE master creates: the 0 stops by its origin, and a
+    // member that terminates returns its record to the pool after this run
+    const bool recreated = (A->flags & (kActorRecreate | kActorLink)) != 0;
+    const bool is_master = (A->flags & kActorRecreate) != 0;
+    bool link_ended = false;
+    bool ended = false;        // the actor is DONE (found so, or terminated here)
+    for (uint64_t i = 0; i < take + (carried ? 1 : 0); ++i) {
         MsgData m{};
-        if (warp_dequeue(P, a, head, 1, m) == 0) return kNone;
-        m.payload = __shfl_sync(FULL, m.payload, 0);
-        m.kind = __shfl_sync(FULL, m.kind, 0);
-        m.reply_addr = __shfl_sync(FULL, m.reply_addr, 0);
-        m.reply_token = __shfl_sync(FULL, m.reply_token, 0);
-        m.tag = __shfl_sync(FULL, m.tag, 0);
-        head += 1;
+        if (carried && i == 0) {
+            m = carry.m;
+            if (P.validation) log_rows(P, a, 1, m);
+        } else {
+            if (warp_dequeue(P, a, head, 1, m) == 0) return kNone;
+            m.payload = __shfl_sync(FULL, m.payload, 0);
+            m.kind = __shfl_sync(FULL, m.kind, 0);
+            m.reply_addr = __shfl_sync(FULL, m.reply_addr, 0);
+            m.reply_token = __shfl_sync(FULL, m.reply_token, 0);
+            m.tag = __shfl_sync(FULL, m.tag, 0);
+            head += 1;
+        }
         const int32_t v = (int32_t)(uint32_t)m.payload;
-        const bool dead = __shfl_sync(FULL, *((volatile uint32_t *)&A->state) == kDone, 0);
+        // a carried message's receiver was WAITING when it was claimed
+        const bool dead = (carried && i == 0) ? false
+                                              : __shfl_sync(FULL, *((volatile uint32_t *)&A->state) == kDone, 0);
+        ended |= dead;
         bool ok = true;
+        bool rejected = false;
+        Carry *cp = direct ? &out : nullptr;
         if (dead) {
             if (lane == 0) write_reply(m.reply_addr, 2, 0, 0, m.tag, m.reply_token);
+        } else if (is_master && ((m.kind >> 16) & (kMsgStart | kMsgRingDone))) {
+            // a RECREATE master starts its first incarnation on START (unless
+            // a ring is running) and the next one when the running one's
+            // members have all terminated, until incarnations in all have run
+            const bool start = ((m.kind >> 16) & kMsgStart) != 0;
+            bool run_next = false;
+            if (start) {
+                rejected = A->ring_live != 0;
+                if (!rejected && lane == 0) {
+                    A->sink_count = (uint64_t)(uint32_t)v;
+                    A->ring_inc = 0;
+                }
+                run_next = !rejected;
+            } else {
+                run_next = ring_incarnation_over(P, a);
+                ended = !run_next;
+            }
+            __syncwarp();
+            if (run_next) {
+                const int32_t v0 = (int32_t)(uint32_t)A->sink_count;
+                ok = ring_spawn(P, a) && ring_emit_factor(P, a) && ring_forward(P, a, v0, &handoff, cp);
+            }
         } else if ((m.kind >> 16) & kMsgStart) {
-            ok = ring_emit_factor(P, a) && ring_forward(P, a, v, &handoff);
+            ok = ring_emit_factor(P, a) && ring_forward(P, a, v, &handoff, cp);
         } else if (v > 0) {
-            ok = ring_emit_factor(P, a) && ring_forward(P, a, v - 1, &handoff);
+            ok = ring_emit_factor(P, a) && ring_forward(P, a, v - 1, &handoff, cp);
+        } else if (recreated) {
+            // the 0 went once around from its origin: stop before reaching it
+            // again (the same actors as "unless the successor has terminated",
+            // without reading a successor's record, which may already serve a
+            // new actor)
+            const uint32_t origin1 = (uint32_t)(m.payload >> 32) ? (uint32_t)(m.payload >> 32) : a + 1;
+            if (!is_master && lane == 0) *((volatile uint32_t *)&A->state) = kDone;
+            link_ended = !is_master;
+            ended |= !is_master;
+            if (A->next + 1 != origin1) {
+                ok = ring_forward(P, a, 0, &handoff, cp, origin1);
+            } else if (!is_master) {
+                // the 0 stops here: every other actor of the incarnation has
+                // terminated, so tell the master (a send of this message, so
+                // counted before the message completes)
+                MsgData d{};
+                d.kind = kToken | (kMsgRingDone << 16);
+                d.sender = 0x80000000u | a;
+                if (lane == 0) add_u64(&P.ctl->device_sends, 1);
+                ok = warp_enqueue(P, lane == 0, A->ring_master, d);
+            } else if (ring_incarnation_over(P, a)) {
+                // the master is the last to terminate: start the next incarnation
+                const int32_t v0 = (int32_t)(uint32_t)A->sink_count;
+                ok = ring_spawn(P, a) && ring_emit_factor(P, a) && ring_forward(P, a, v0, &handoff, cp);
+            } else {
+                ended = true;
+            }
         } else {
             if (lane == 0) *((volatile uint32_t *)&A->state) = kDone;
+            ended = true;
             uint32_t succ_state = 0;
             if (lane == 0) succ_state = *((volatile uint32_t *)&P.actors[A->next].state);
             succ_state = __shfl_sync(FULL, succ_state, 0);
-            if (succ_state != kDone) ok = ring_forward(P, a, 0, &handoff);
+            if (succ_state != kDone) ok = ring_forward(P, a, 0, &handoff, cp);
         }
         if (!ok) return kNone;
-        if (!dead && lane == 0) {
+        if (rejected) {
+            if (lane == 0) write_reply(m.reply_addr, 3, 0, 0, m.tag, m.reply_token);
+        } else if (!dead && lane == 0 && !((m.kind >> 16) & kMsgRingDone)) {
             A->user_state = v;
             write_reply(m.reply_addr, 0, (uint64_t)(uint32_t)v, 0, m.tag, m.reply_token);
         }
         __syncwarp();
         if (lane == 0) {
-            __threadfence();
+            // everything this message did (its sends counted in ingested)
+            // is ordered before it counts as completed
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
             add_u64(&P.ctl->messages, 1);
             add_u64(&P.ctl->completed, 1);
         }
     }
-    release_actor(P, a, head);
+    release_actor(P, a, head, ended ? 1 : 0);
+    carry = out;
+    if (link_ended && lane == 0) {
+        // the claim is released and nothing more is sent to a terminated
+        // member: its record goes back to the pool
+        __threadfence();
+        if (!q_push(&P.ctl->forkq, P.forkq, a, P.wait_limit_ns)) fail(P, kErrWaitQueue, 35);
+    }
+    __syncwarp();
     return handoff;
 }
 
 // Claim a ring actor and keep running the actors its messages wake, up to a
 // bound, after which the next one goes back to the ready queue.
+// A carried token cannot go back to the ready queue, so the last run of a
+// chain forwards through the mailbox.
 __device__ void claim_ring(const DrainParams &P, uint32_t a) {
     constexpr int kMaxChain = 1 << 14;
     uint32_t cur = a;
-    for (int i = 0; cur != kNone && i < kMaxChain && !exit_requested(P.ctl); ++i) {
-        cur = run_ring_actor(P, cur);
+    Carry carry{};
+    carry.has = false;
+    for (int i = 0; cur != kNone && i < kMaxChain && ((i & 7) != 0 || !exit_requested(P.ctl)); ++i) {
+        cur = run_ring_actor(P, cur, carry, i + 1 < kMaxChain);
         if ((i & 255) == 0 && lane_id() == 0) heartbeat(P);
     }
     if (cur != kNone && lane_id() == 0 && !ready_push(P, cur))
@@ -963,6 +1248,8 @@ __device__ __noinline__ void run_fork(const DrainParams &P, uint32_t a) {
                 c = fork_take_id(P);
                 if (c != kNone) {
                     ActorDesc *C = &P.actors[c];
+                    C->kind = kFork;      // the record may have served a ring member
+                    C->flags = 0;
                     C->next = a;
                     C->user_state = 0;
                     C->sink_sum = 0;
@@ -1041,6 +1328,11 @@ __device__ __forceinline__ bool message_ok(const DrainParams &P, uint32_t a, uin
     if ((kind & 0xFFFFu) != A->kind) { *why = 3; return false; }
     if (*((volatile const uint32_t *)&A->state) == kDone) { *why = 2; return false; }
     if ((kind & 0xFFFFu) == kFactor && payload > P.max_n) { *why = 3; return false; }
+    // a token is a 31-bit value; the end-of-incarnation notice comes only from the device
+    if ((kind & 0xFFFFu) == kToken && (payload > 0x7FFFFFFFull || ((kind >> 16) & kMsgRingDone))) {
+        *why = 3;
+        return false;
+    }
     if ((kind & 0xFFFFu) == kFork) {
         // a start message whose tree fits the pool; results come only from children
         if (((kind >> 16) & kMsgResult) || payload > kForkMaxN || (2ull << payload) - 2 > P.fork_pool) {
@@ -1220,6 +1512,16 @@ __device__ __forceinline__ uint8_t *job_scratch(const DrainParams &P, uint32_t j
 __device__ __forceinline__ bool job_free(const DrainParams &P, uint32_t j) {
     return job_small(j) ? q_push(&P.ctl->jobq, P.jobq, j, P.wait_limit_ns)
                         : q_push(&P.ctl->jobq_large, P.jobq_large, j, P.wait_limit_ns);
+}
+
+__device__ bool work_item_ok(const DrainParams &P, uint32_t item) {
+    const uint32_t j = item >> 16;
+    if (item & kPackItemFlag) {
+        if (j >= kGemmJobs) return false;
+        return (item & 63u) < (P.jobs[j].n + kGemmBN - 1) / kGemmBN;
+    }
+    if (item & kMandelItemFlag) return j < kMandelJobs && (item & (kMandelItemFlag - 1u)) < P.mjobs[j].bands;
+    return j < kGemmJobs && (item & 0xFFFFu) < P.jobs[j].tiles;
 }
 
 // Claim a GEMM actor: take up to 32 messages (as many as there are free job
@@ -1594,6 +1896,10 @@ __device__ uint32_t find_batch(const DrainParams &P, uint32_t &rng) {
             if (pr <= 0) item = kNone;
         }
         item = __shfl_sync(FULL, item, 0);
+        if (item != kNone && P.validation && (item & 0xFFFFFFu) >= P.n_batches) {
+            if (lane == 0) bounds_fail(P, 43, item, P.n_batches);
+            return kNone;
+        }
         if (item != kNone) return item;
     }
     for (int attempt = 0; attempt < 4; ++attempt) {
@@ -1607,6 +1913,10 @@ __device__ uint32_t find_batch(const DrainParams &P, uint32_t &rng) {
         got = __shfl_sync(FULL, got, 0);
         if (!got) return kNone;
         a = __shfl_sync(FULL, a, 0);
+        if (P.validation && !actor_ok(P, a)) {
+            if (lane == 0) bounds_fail(P, 42, a, P.n_actors);
+            return kNone;
+        }
         const uint32_t kind = P.actors[a].kind;
         if (kind == kFactor) {
             uint32_t b = 0;
@@ -1621,6 +1931,11 @@ __device__ uint32_t find_batch(const DrainParams &P, uint32_t &rng) {
                 // no batch record free: leave the actor READY for later
                 if (lane == 0 && !ready_push(P, a)) fail(P, kErrWaitQueue, 7);
                 __syncwarp();
+                return kNone;
+            }
+            b = __shfl_sync(FULL, b, 0);
+            if (P.validation && b >= P.n_batches) {
+                if (lane == 0) bounds_fail(P, 44, b, P.n_batches);
                 return kNone;
             }
             const uint32_t r = claim_factor<kSplit>(P, a, __shfl_sync(FULL, b, 0));
@@ -1785,6 +2100,10 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
                 if (kGemm && pr == 0) pr = q_try_pop(&ctl->packq, P.packq, &item, P.wait_limit_ns);
                 if (pr < 0) fail(P, kErrWaitQueue, 24);
                 if (pr <= 0) item = kNone;
+            }
+            if (P.validation && item != kNone && !work_item_ok(P, item)) {
+                bounds_fail(P, 45, item, 0);
+                item = kNone;
             }
             const uint32_t got = __ballot_sync(FULL, item != kNone);
             if (item != kNone) G.items[__popc(got & ((1u << lane) - 1u))] = item;
@@ -2018,6 +2337,8 @@ __global__ void k_reset_actors(ActorDesc *actors, uint32_t n_actors) {
         A->user_state = A->init_state;
         A->round = 0;
         A->head = A->tail;
+        A->ring_inc = 0;
+        A->ring_live = 0;
     } else if (A->kind == kSink) {
         A->sink_count = 0;
         A->sink_sum = 0;
@@ -2198,23 +2519,21 @@ static cudaError_t drain_attr() {
     return e;
 }
 
-cudaError_t drain_occupancy(bool gemm, int *ctas_per_sm) {
+// Resident CTAs per SM of the instantiation launch_drain runs for (gemm, split).
+cudaError_t drain_occupancy(bool gemm, bool split, int *ctas_per_sm) {
     cudaError_t e = drain_attr();
     if (e != cudaSuccess) return e;
-    // the split instantiations have the same launch bounds and shared memory
-    int split_fit = 0;
-    cudaError_t e2;
-    if (gemm) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain<true, false>, kThreads, kDrainSmemMixed);
-        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&split_fit, k_drain<true, true>, kThreads, kDrainSmemMixed);
-    } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain<false, false>, kThreads,
-                                                          kDrainSmemFactor);
-        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&split_fit, k_drain<false, true>, kThreads,
-                                                           kDrainSmemFactor);
-    }
-    if (e == cudaSuccess && e2 == cudaSuccess && split_fit < *ctas_per_sm) *ctas_per_sm = split_fit;
-    return e != cudaSuccess ? e : e2;
+    if (gemm && split)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain<true, true>, kThreads,
+                                                             kDrainSmemMixed);
+    if (gemm)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain<true, false>, kThreads,
+                                                             kDrainSmemMixed);
+    if (split)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain<false, true>, kThreads,
+                                                             kDrainSmemFactor);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_drain<false, false>, kThreads,
+                                                         kDrainSmemFactor);
 }
 
 cudaError_t launch_drain(const DrainParams &p, unsigned grid, cudaStream_t stream) {

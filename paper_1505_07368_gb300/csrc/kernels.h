@@ -10,7 +10,7 @@ namespace cafgpu {
 
 cudaError_t launch_drain(const DrainParams &p, unsigned grid, cudaStream_t stream);
 // CTAs of the drain kernel that fit on one SM at once (GEMM layout or not).
-cudaError_t drain_occupancy(bool gemm, int *ctas_per_sm);
+cudaError_t drain_occupancy(bool gemm, bool split, int *ctas_per_sm);
 cudaError_t launch_reset_ctl(DevCtl *ctl, cudaStream_t stream);
 cudaError_t launch_mark(DevCtl *ctl, cudaStream_t stream);
 cudaError_t launch_factor_one(uint64_t n, const uint32_t *primes, const uint32_t *pinv,

@@ -168,11 +168,14 @@ enum : uint32_t { kWaiting = 0, kReady = 1, kRunning = 2, kDone = 3 };
 // kinds (mirror caf_gpu.h)
 enum : uint32_t { kFactor = 1, kGemmBf16 = 2, kGemmSplit = 3, kToken = 4, kSink = 5, kSource = 6, kMandel = 7,
                   kFork = 8 };
-enum : uint32_t { kMsgStart = 1, kMsgResult = 2 };
+enum : uint32_t { kMsgStart = 1, kMsgResult = 2, kMsgRingDone = 4 };
+// RECREATE ring masters: at most this many members and incarnations
+constexpr uint32_t kRingMaxLen = 1u << 16;
+constexpr uint32_t kRingMaxIncarnations = 255;
 // FORK: the largest recursion counter (2^n and 2^(n+1) - 2 fit in 32 bits)
 constexpr uint32_t kForkMaxN = 30;
 constexpr uint32_t kForkSlots = 4;         // mailbox of a pool actor: a start and two results
-enum : uint32_t { kActorMaster = 1 };
+enum : uint32_t { kActorMaster = 1, kActorRecreate = 2, kActorLink = 4 };
 
 // error codes in DevCtl::error_word (low byte) -- high bits carry the site
 enum : uint32_t {
@@ -185,6 +188,7 @@ enum : uint32_t {
     kErrStall = 7,         // no progress anywhere while messages were in flight
     kErrWaitTable = 8,     // a prime-table bulk copy did not complete
     kErrNoCompletion = 9,  // messages in flight but none completed for kCompletionLimitNs
+    kErrBounds = 10,       // validation mode: an index outside its array was refused
 };
 constexpr uint64_t kCompletionLimitNs = 30ull * 1000 * 1000 * 1000;
 
@@ -223,11 +227,12 @@ struct ActorDesc {                 // 128 bytes
     uint32_t flags;
     uint64_t slot_base;            // first Slot of this actor's ring
     uint64_t head;                 // consumer position (written by the claim holder only)
-    uint64_t sink_count;           // SINK: messages handled (claim holder only); FORK: actors spawned below
+    uint64_t sink_count;           // SINK: messages handled (claim holder only); FORK: actors spawned below;
+                                   // RECREATE ring master: the START token each incarnation begins with
     uint64_t sink_sum;             // SINK: sum of their values; FORK: children's results so far
     uint64_t fork_reply;           // FORK root: reply record of the running computation
-    uint32_t fork_token;           // FORK root: its reply token
-    uint32_t pad_a;
+    uint32_t fork_token;           // FORK root: its reply token; RECREATE ring master: incarnations in all
+    uint32_t ring_master;          // ring link (spawned by a RECREATE master): its master
     uint64_t tail;                 // producer ticket (atomic add)
     int32_t user_state;            // TOKEN: last token; FORK: results still awaited
     uint32_t next;                 // TOKEN: ring successor; FORK: parent (kNone for a root)
@@ -237,7 +242,10 @@ struct ActorDesc {                 // 128 bytes
     uint64_t factor_replies;       // ring master: reply records (device)
     int32_t init_state;
     uint32_t round;                // ring master: next factor request index
-    uint64_t pad_b[2];
+    uint32_t ring_len;             // RECREATE master and its links: actors per ring, master included
+    uint32_t ring_pos;             // ring link: its position in the ring (the master is 0)
+    uint32_t ring_inc;             // RECREATE master: index of the running incarnation; link: its incarnation
+    uint32_t ring_live;            // RECREATE master: members per incarnation while its rings run, else 0
 };
 static_assert(sizeof(ActorDesc) == 128, "ActorDesc is 128 bytes");
 
@@ -408,6 +416,7 @@ struct DrainParams {
     QCell *segq;
     uint32_t split;
     uint32_t n_batches;            // batch records (those not in freeq are in use)
+    uint64_t n_slots;              // mailbox slots, the pool's included (validation-mode checks)
 };
 constexpr uint32_t kLocalQueueCap = 4096;     // ready actors per CTA queue
 constexpr uint32_t kLocalQueueSlack = 1024;   // room kept for the CTA's concurrent pushes (9 warps x 32 wakes)

@@ -50,6 +50,8 @@ T load_acquire(const T *p) {
 
 struct caf_gpu_runtime {
     caf_gpu_runtime_cfg cfg{};
+    // guard regions after the device arrays: (allocation base, guard start)
+    std::vector<std::pair<void *, uint8_t *>> guards;
     int device = 0;
     int n_sms = 0;
     cudaStream_t stream = nullptr;
@@ -173,6 +175,7 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.forkq = rt->d_forkq;
     p.segq = rt->d_segq;
     p.split = rt->cfg.factor_split;
+    p.n_slots = rt->n_slots + (uint64_t)kForkSlots * rt->fork_pool;
     p.n_batches = rt->n_batches;
     p.localq_hdr = rt->d_localq_hdr;
     p.localq = rt->d_localq;
@@ -189,6 +192,55 @@ DrainParams make_params(caf_gpu_runtime *rt) {
 
 unsigned drain_grid(caf_gpu_runtime *rt) { return rt->gemm_enabled ? rt->grid_mixed : rt->grid_factor; }
 
+// Host status for a nonzero device error word: a refused out-of-range index
+// (validation mode) or an expired bounded wait.
+int device_error(uint32_t word) { return (word & 0xFFu) == kErrBounds ? CAF_GPU_EBOUNDS : CAF_GPU_EWAITLIMIT; }
+
+// Device arrays are allocated with a guard region of kGuardBytes after them,
+// filled with kGuardByte.  No kernel writes there; check_guards reads every
+// guard back, so a write past the end of an array shows up as a changed
+// guard (the runtime's arena canaries).
+constexpr uint64_t kGuardBytes = 256;
+constexpr uint8_t kGuardByte = 0xA5;
+
+cudaError_t guarded_malloc(caf_gpu_runtime *rt, void **p, uint64_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes + kGuardBytes);
+    if (e != cudaSuccess) return e;
+    uint8_t *g = static_cast<uint8_t *>(*p) + bytes;
+    e = cudaMemset(g, kGuardByte, kGuardBytes);
+    if (e != cudaSuccess) return e;
+    rt->guards.emplace_back(*p, g);
+    return cudaSuccess;
+}
+template <class T>
+cudaError_t guarded_malloc(caf_gpu_runtime *rt, T **p, uint64_t bytes) {
+    return guarded_malloc(rt, reinterpret_cast<void **>(p), bytes);
+}
+
+// Forget the guard of an allocation about to be freed.
+void drop_guard(caf_gpu_runtime *rt, void *base) {
+    for (size_t i = 0; i < rt->guards.size(); ++i)
+        if (rt->guards[i].first == base) {
+            rt->guards.erase(rt->guards.begin() + (long)i);
+            return;
+        }
+}
+
+// Guards whose bytes changed (-1 if they cannot be read).
+int check_guards(caf_gpu_runtime *rt) {
+    int bad = 0;
+    uint8_t h[kGuardBytes];
+    for (auto &g : rt->guards) {
+        if (cudaMemcpy(h, g.second, kGuardBytes, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+        for (uint64_t i = 0; i < kGuardBytes; ++i)
+            if (h[i] != kGuardByte) {
+                ++bad;
+                break;
+            }
+    }
+    return bad;
+}
+
 int init_queue(caf_gpu_runtime *rt, QCell **cells, uint32_t cap, QueueHdr *hdr_dev,
                const std::vector<uint32_t> &initial) {
     std::vector<QCell> h(cap);
@@ -201,7 +253,7 @@ int init_queue(caf_gpu_runtime *rt, QCell **cells, uint32_t cap, QueueHdr *hdr_d
         h[i].seq = i + 1;
         h[i].val = initial[i];
     }
-    CK(cudaMalloc(cells, sizeof(QCell) * cap));
+    CK(guarded_malloc(rt, cells, sizeof(QCell) * cap));
     CK(cudaMemcpy(*cells, h.data(), sizeof(QCell) * cap, cudaMemcpyHostToDevice));
     QueueHdr q{};
     q.enq = initial.size();
@@ -266,6 +318,9 @@ int check_msg(caf_gpu_runtime *rt, caf_gpu_actor to, const caf_gpu_msg *m, uint3
     }
     if (m->kind == kSource && m->u64 > 0xFFFFFFFFull) return CAF_GPU_EINVAL;
     if (m->kind == kToken) {
+        // token values fit 31 bits; a re-creating master runs in the drain only
+        if (m->u64 > 0x7FFFFFFFull) return CAF_GPU_EINVAL;
+        if ((d.flags & kActorRecreate) && rt->backend != CAF_GPU_BACKEND_PERSISTENT) return CAF_GPU_EINVAL;
         uint32_t state = 0;
         if (cudaMemcpy(&state, &rt->d_actors[a].state, sizeof(state), cudaMemcpyDeviceToHost) != cudaSuccess)
             return CAF_GPU_ECUDA;
@@ -385,7 +440,7 @@ int submit_locked(caf_gpu_runtime *rt, uint32_t a, const caf_gpu_msg *m, uint64_
         if (r) return r;
         const uint64_t t0 = now_ns();
         while (t - load_acquire(&rt->hctl->ring_consumed) >= cap) {
-            if (rt->hctl->error_word) return CAF_GPU_EWAITLIMIT;
+            if (rt->hctl->error_word) return device_error(rt->hctl->error_word);
             if (now_ns() - t0 > rt->cfg.wait_limit_ns) return CAF_GPU_EAGAIN;
             kick_locked(rt);
             std::this_thread::yield();
@@ -489,8 +544,9 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     // every drain CTA must be resident at once (router and ingress warps are
     // waited on by the others), so the grid never exceeds the occupancy limit
     int fit = 0, fit_mixed = 0;
-    CK(drain_occupancy(false, &fit));
-    CK(drain_occupancy(true, &fit_mixed));
+    const bool split = c.factor_split > 1;   // launch_drain's instantiation choice
+    CK(drain_occupancy(false, split, &fit));
+    CK(drain_occupancy(true, split, &fit_mixed));
     if (fit < 1 || fit_mixed < 1) return CAF_GPU_ECUDA;
     rt->grid_factor = (unsigned)rt->n_sms * std::min<uint32_t>(c.ctas_per_sm, (uint32_t)fit);
     rt->grid_mixed = (unsigned)rt->n_sms * std::min<uint32_t>(c.ctas_per_sm, (uint32_t)fit_mixed);
@@ -507,13 +563,13 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     // device arena
     CK(cudaMalloc(&rt->d_ctl, sizeof(DevCtl)));
     CK(cudaMemset(rt->d_ctl, 0, sizeof(DevCtl)));
-    CK(cudaMalloc(&rt->d_actors, sizeof(ActorDesc) * (size_t)c.max_actors));
+    CK(guarded_malloc(rt, &rt->d_actors, sizeof(ActorDesc) * (size_t)c.max_actors));
     CK(cudaMemset(rt->d_actors, 0, sizeof(ActorDesc) * (size_t)c.max_actors));
     rt->n_slots = (uint64_t)c.max_actors * c.mailbox_capacity;
-    CK(cudaMalloc(&rt->d_slots, sizeof(Slot) * rt->n_slots));
+    CK(guarded_malloc(rt, &rt->d_slots, sizeof(Slot) * rt->n_slots));
     CK(cudaMemset(rt->d_slots, 0, sizeof(Slot) * rt->n_slots));
     rt->n_batches = std::max<uint32_t>(4096, 2u * rt->grid_factor * kConsumerWarps);
-    CK(cudaMalloc(&rt->d_batches, sizeof(FactorBatch) * rt->n_batches));
+    CK(guarded_malloc(rt, &rt->d_batches, sizeof(FactorBatch) * rt->n_batches));
     CK(cudaMemset(rt->d_batches, 0, sizeof(FactorBatch) * rt->n_batches));
     rt->readyq_cap = next_pow2((uint64_t)c.max_actors + 1);
     rt->freeq_cap = next_pow2((uint64_t)rt->n_batches + 1);
@@ -540,22 +596,22 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     if ((r = init_queue(rt, &rt->d_segq, (uint32_t)next_pow2((uint64_t)rt->n_batches * kSplitMax + 1),
                         &rt->d_ctl->segq, none)))
         return r;
-    CK(cudaMalloc(&rt->d_jobs, sizeof(GemmJob) * kGemmJobs));
+    CK(guarded_malloc(rt, &rt->d_jobs, sizeof(GemmJob) * kGemmJobs));
     CK(cudaMemset(rt->d_jobs, 0, sizeof(GemmJob) * kGemmJobs));
     std::vector<uint32_t> mjobs(kMandelJobs);
     for (uint32_t i = 0; i < kMandelJobs; ++i) mjobs[i] = i;
     if ((r = init_queue(rt, &rt->d_mjobq, next_pow2((uint64_t)kMandelJobs + 1), &rt->d_ctl->mjobq, mjobs))) return r;
-    CK(cudaMalloc(&rt->d_mjobs, sizeof(MandelJob) * kMandelJobs));
+    CK(guarded_malloc(rt, &rt->d_mjobs, sizeof(MandelJob) * kMandelJobs));
     CK(cudaMemset(rt->d_mjobs, 0, sizeof(MandelJob) * kMandelJobs));
     if (c.validation_mode) {
-        CK(cudaMalloc(&rt->d_log, sizeof(LogRow) * (size_t)c.log_capacity));
+        CK(guarded_malloc(rt, &rt->d_log, sizeof(LogRow) * (size_t)c.log_capacity));
         CK(cudaMemset(rt->d_log, 0, sizeof(LogRow) * (size_t)c.log_capacity));
     }
     if (c.scheduler == CAF_GPU_SCHED_STEAL) {
         // one queue per CTA of the larger grid; cell i of a queue starts free for position i
         const uint32_t nq = std::max(rt->grid_factor, rt->grid_mixed);
         CK(cudaMalloc(&rt->d_localq_hdr, sizeof(QueueHdr) * nq));
-        CK(cudaMalloc(&rt->d_localq, sizeof(QCell) * (size_t)nq * kLocalQueueCap));
+        CK(guarded_malloc(rt, &rt->d_localq, sizeof(QCell) * (size_t)nq * kLocalQueueCap));
         std::vector<QueueHdr> hdr(nq);
         for (auto &h : hdr) {
             memset(&h, 0, sizeof(h));
@@ -618,7 +674,7 @@ int sync_persistent(caf_gpu_runtime *rt) {
         }
         CK(cudaStreamSynchronize(rt->stream));
         __atomic_store_n(&rt->hctl->stop, 0u, __ATOMIC_RELEASE);
-        if (rt->hctl->error_word) return CAF_GPU_EWAITLIMIT;
+        if (rt->hctl->error_word) return device_error(rt->hctl->error_word);
         std::lock_guard<std::mutex> g(rt->mu);
         if (load_acquire(&rt->hctl->ring_consumed) == rt->ring_tail) return 0;
     }
@@ -637,6 +693,7 @@ const char *caf_gpu_strerror(int code) {
         case CAF_GPU_ETIMEDOUT: return "timed out";
         case CAF_GPU_EDEAD: return "actor has terminated";
         case CAF_GPU_EWAITLIMIT: return "a bounded device wait expired";
+        case CAF_GPU_EBOUNDS: return "validation check: out-of-range index or overwritten guard";
         case CAF_GPU_ESTATE: return "unknown or consumed handle / invalid state";
         case CAF_GPU_ECUDA: return "CUDA error";
         default: return "unknown error";
@@ -660,8 +717,39 @@ int caf_gpu_runtime_destroy(caf_gpu_runtime *rt) {
     if (!rt) return CAF_GPU_EINVAL;
     int r = caf_gpu_sync(rt);
     cudaStreamSynchronize(rt->stream);
+    const int bad = check_guards(rt);
     free_runtime(rt);
-    return r == CAF_GPU_EWAITLIMIT ? 0 : r;
+    if (bad > 0) return CAF_GPU_EBOUNDS;
+    return (r == CAF_GPU_EWAITLIMIT || r == CAF_GPU_EBOUNDS) ? 0 : r;
+}
+
+int caf_gpu_debug_inject(caf_gpu_runtime *rt, uint32_t what, uint64_t arg) {
+    if (!rt || rt->capturing) return CAF_GPU_EINVAL;
+    int r = caf_gpu_sync(rt);   // no drain runs while a record changes
+    if (r) return r;
+    std::lock_guard<std::mutex> g(rt->mu);
+    if (what == 1) {
+        if (!rt->cfg.validation_mode || arg == 0 || arg > rt->n_actors) return CAF_GPU_EINVAL;
+        const uint64_t past = rt->n_slots + (uint64_t)kForkSlots * rt->fork_pool;
+        CK(cudaMemcpy(&rt->d_actors[arg - 1].slot_base, &past, sizeof(past), cudaMemcpyHostToDevice));
+        return 0;
+    }
+    if (what == 2) {
+        if (arg >= rt->guards.size()) return CAF_GPU_EINVAL;
+        const uint8_t x = (uint8_t)~kGuardByte;
+        CK(cudaMemcpy(rt->guards[arg].second, &x, 1, cudaMemcpyHostToDevice));
+        return 0;
+    }
+    return CAF_GPU_EINVAL;
+}
+
+int caf_gpu_check_guards(caf_gpu_runtime *rt, uint32_t *corrupted) {
+    if (!rt || !corrupted) return CAF_GPU_EINVAL;
+    if (rt->capturing) return CAF_GPU_ESTATE;
+    const int bad = check_guards(rt);
+    if (bad < 0) return CAF_GPU_ECUDA;
+    *corrupted = (uint32_t)bad;
+    return 0;
 }
 
 // The FORK actor pool (first FORK spawn): grow the actor table by the pool's
@@ -679,14 +767,14 @@ int make_fork_pool(caf_gpu_runtime *rt) {
     // on any failure, free what this call made; the runtime keeps its old table
     auto fail_with = [&](int code) {
         cudaGetLastError();
-        cudaFree(actors);
-        cudaFree(slots);
-        cudaFree(forkq);
-        cudaFree(readyq);
+        for (void *p : {(void *)actors, (void *)slots, (void *)forkq, (void *)readyq}) {
+            if (p) drop_guard(rt, p);
+            cudaFree(p);
+        }
         return code;
     };
-    if (cudaMalloc(&actors, sizeof(ActorDesc) * n_act) != cudaSuccess) return fail_with(CAF_GPU_ENOMEM);
-    if (cudaMalloc(&slots, sizeof(Slot) * n_slots) != cudaSuccess) return fail_with(CAF_GPU_ENOMEM);
+    if (guarded_malloc(rt, &actors, sizeof(ActorDesc) * n_act) != cudaSuccess) return fail_with(CAF_GPU_ENOMEM);
+    if (guarded_malloc(rt, &slots, sizeof(Slot) * n_slots) != cudaSuccess) return fail_with(CAF_GPU_ENOMEM);
     if (cudaMemcpyAsync(actors, rt->d_actors, sizeof(ActorDesc) * base, cudaMemcpyDeviceToDevice, rt->setup) !=
             cudaSuccess ||
         cudaMemcpyAsync(slots, rt->d_slots, sizeof(Slot) * rt->n_slots, cudaMemcpyDeviceToDevice, rt->setup) !=
@@ -706,9 +794,10 @@ int make_fork_pool(caf_gpu_runtime *rt) {
     int r = init_queue(rt, &forkq, forkq_cap, &rt->d_ctl->forkq, ids);
     if (r) return fail_with(r);
     if ((r = init_queue(rt, &readyq, readyq_cap, &rt->d_ctl->readyq, {}))) return fail_with(r);
-    cudaFree(rt->d_readyq);
-    cudaFree(rt->d_actors);
-    cudaFree(rt->d_slots);
+    for (void *p : {(void *)rt->d_readyq, (void *)rt->d_actors, (void *)rt->d_slots}) {
+        drop_guard(rt, p);
+        cudaFree(p);
+    }
     rt->d_readyq = readyq;
     rt->readyq_cap = readyq_cap;
     rt->d_forkq = forkq;
@@ -722,7 +811,17 @@ int make_fork_pool(caf_gpu_runtime *rt) {
 int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_cfg *cfg, caf_gpu_actor *out) {
     if (!rt || !out) return CAF_GPU_EINVAL;
     if (kernel_id < kFactor || kernel_id > kFork) return CAF_GPU_EINVAL;
-    if (kernel_id == kFork && !rt->fork_pool) {
+    const bool recreate = kernel_id == kToken && cfg && (cfg->flags & kActorRecreate);
+    if (recreate) {
+        // a ring master that creates its ring on the device: its members come
+        // from the device actor pool
+        if (!(cfg->flags & kActorMaster) || cfg->ring_len < 2 || cfg->ring_len > kRingMaxLen ||
+            cfg->incarnations < 1 || cfg->incarnations > kRingMaxIncarnations)
+            return CAF_GPU_EINVAL;
+        if ((uint64_t)cfg->ring_len - 1 > rt->cfg.fork_pool) return CAF_GPU_EINVAL;
+    }
+    if (cfg && (cfg->flags & ~(uint32_t)(kActorMaster | kActorRecreate))) return CAF_GPU_EINVAL;
+    if ((kernel_id == kFork || recreate) && !rt->fork_pool) {
         int r = caf_gpu_sync(rt);   // stops the running drain: it holds the old table addresses
         if (r) return r;
         std::lock_guard<std::mutex> g(rt->mu);
@@ -740,12 +839,12 @@ int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_c
         std::lock_guard<std::mutex> g(rt->mu);
         if (kernel_id == kMandel) rt->mandel_enabled = true;
         if (gemm_kind && !rt->d_pack_small) {
-            if (cudaMalloc(&rt->d_pack_small, kPackSmallBytes * kGemmJobsSmall) != cudaSuccess) {
+            if (guarded_malloc(rt, &rt->d_pack_small, kPackSmallBytes * kGemmJobsSmall) != cudaSuccess) {
                 cudaGetLastError();
                 rt->d_pack_small = nullptr;
                 return CAF_GPU_ENOMEM;
             }
-            if (cudaMalloc(&rt->d_pack_large, kPackLargeBytes * kGemmJobsLarge) != cudaSuccess) {
+            if (guarded_malloc(rt, &rt->d_pack_large, kPackLargeBytes * kGemmJobsLarge) != cudaSuccess) {
                 cudaGetLastError();
                 cudaFree(rt->d_pack_small);
                 rt->d_pack_small = rt->d_pack_large = nullptr;
@@ -768,8 +867,14 @@ int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_c
     d.flags = c.flags;
     d.slot_base = rt->slots_used;
     if (kernel_id == kToken) {
-        if (c.next == 0 || c.next > rt->cfg.max_actors) return CAF_GPU_EINVAL;
-        d.next = (uint32_t)(c.next - 1);
+        if (recreate) {
+            d.next = kNone;                        // its successor is made on the device
+            d.ring_len = c.ring_len;
+            d.fork_token = c.incarnations;         // incarnations in all
+        } else {
+            if (c.next == 0 || c.next > rt->cfg.max_actors) return CAF_GPU_EINVAL;
+            d.next = (uint32_t)(c.next - 1);
+        }
         if (c.flags & kActorMaster) {
             if (c.worker == 0 || c.worker > rt->n_actors) return CAF_GPU_EINVAL;
             if (rt->actors[c.worker - 1].kind != kFactor) return CAF_GPU_EINVAL;
@@ -878,7 +983,7 @@ int caf_gpu_await(caf_gpu_runtime *rt, caf_gpu_handle h, uint64_t timeout_ns, ca
     const uint64_t t0 = now_ns();
     uint32_t spins = 0;
     while (load_acquire(&rt->replies[slot].done) != gen) {
-        if (load_acquire(&rt->hctl->error_word)) return CAF_GPU_EWAITLIMIT;
+        if (const uint32_t w = load_acquire(&rt->hctl->error_word)) return device_error(w);
         if ((++spins & 255) == 0) {
             int r = kick(rt);
             if (r) return r;
@@ -947,10 +1052,10 @@ int caf_gpu_stream_sync(caf_gpu_runtime *rt) {
     if (!rt) return CAF_GPU_EINVAL;
     if (rt->capturing) return CAF_GPU_ESTATE;
     CK(cudaStreamSynchronize(rt->stream));
-    if (rt->hctl->error_word) return CAF_GPU_EWAITLIMIT;
+    if (rt->hctl->error_word) return device_error(rt->hctl->error_word);
     uint32_t err = 0;
     CK(cudaMemcpy(&err, &rt->d_ctl->error_word, sizeof(err), cudaMemcpyDeviceToHost));
-    return err ? CAF_GPU_EWAITLIMIT : 0;
+    return err ? device_error(err) : 0;
 }
 
 int caf_gpu_set_backend(caf_gpu_runtime *rt, int backend) {
@@ -1135,7 +1240,7 @@ int caf_gpu_serve_run(caf_gpu_runtime *rt, const caf_gpu_serve_req *reqs, uint32
     while (done < count) {
         const uint64_t now = now_ns();
         if (c.timeout_ns && now - t0 > c.timeout_ns) return CAF_GPU_ETIMEDOUT;
-        if (load_acquire(&rt->hctl->error_word)) return CAF_GPU_EWAITLIMIT;
+        if (const uint32_t w = load_acquire(&rt->hctl->error_word)) return device_error(w);
         const double tnow = secs(now);
         while (next < count && reqs[next].t_arrival <= tnow) pending.push_back(next++);
         bool progress = false;
@@ -1282,7 +1387,7 @@ int caf_gpu_debug_wait_expiry(caf_gpu_runtime *rt, uint64_t limit_ns) {
     CK(launch_debug_wait(rt->d_zero, limit_ns, rt->d_ctl, rt->hctl, rt->stream));
     rt->launches += 1;
     CK(cudaStreamSynchronize(rt->stream));
-    return rt->hctl->error_word ? CAF_GPU_EWAITLIMIT : 0;
+    return rt->hctl->error_word ? device_error(rt->hctl->error_word) : 0;
 }
 
 int caf_gpu_clear_error(caf_gpu_runtime *rt) {

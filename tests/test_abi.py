@@ -43,6 +43,7 @@ def test_struct_sizes():
     assert ctypes.sizeof(cafgpu.ServeCfg) == 32
     assert ctypes.sizeof(cafgpu.ServeStats) == 32
     assert ctypes.sizeof(cafgpu.RuntimeCfg) == 96
+    assert ctypes.sizeof(cafgpu.ActorCfg) == 56
     assert ctypes.sizeof(cafgpu.Stats) == 96
 
 
@@ -67,6 +68,7 @@ def test_header_constants_match_binding():
         "FACTOR_U64": cafgpu.FACTOR_U64, "GEMM_BF16": cafgpu.GEMM_BF16,
         "GEMM_SPLIT_BF16X3": cafgpu.GEMM_SPLIT_BF16X3, "RING_TOKEN": cafgpu.RING_TOKEN,
         "SINK": cafgpu.SINK, "SOURCE": cafgpu.SOURCE, "MANDELBROT": cafgpu.MANDELBROT, "FORK": cafgpu.FORK,
+        "ACTOR_MASTER": cafgpu.ACTOR_MASTER, "ACTOR_RECREATE": cafgpu.ACTOR_RECREATE,
         "SCHED_GLOBAL": cafgpu.SCHED_GLOBAL, "SCHED_STEAL": cafgpu.SCHED_STEAL,
         "BACKEND_PERSISTENT": cafgpu.BACKEND_PERSISTENT,
         "BACKEND_PER_MESSAGE_LAUNCH": cafgpu.BACKEND_PER_MESSAGE_LAUNCH,
@@ -74,7 +76,7 @@ def test_header_constants_match_binding():
         "REPLY_DEAD": cafgpu.REPLY_DEAD, "REPLY_REJECTED": cafgpu.REPLY_REJECTED,
         "EINVAL": cafgpu.EINVAL, "ENOMEM": cafgpu.ENOMEM, "EAGAIN": cafgpu.EAGAIN,
         "ETIMEDOUT": cafgpu.ETIMEDOUT, "EDEAD": cafgpu.EDEAD, "EWAITLIMIT": cafgpu.EWAITLIMIT,
-        "ESTATE": cafgpu.ESTATE, "ECUDA": cafgpu.ECUDA,
+        "ESTATE": cafgpu.ESTATE, "ECUDA": cafgpu.ECUDA, "EBOUNDS": cafgpu.EBOUNDS,
     }
     for name, value in want.items():
         assert int(defs[name]) == value, name
