@@ -111,6 +111,14 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t saddr) {
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr) : "memory");
     return v;
 }
+// Shared load at a register address plus a constant byte offset (folded into
+// the instruction).
+template <uint32_t kOff>
+__device__ __forceinline__ uint32_t lds_u32_at(uint32_t saddr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(saddr), "n"(kOff) : "memory");
+    return v;
+}
 // Make barrier initialisation visible to the asynchronous proxy.
 __device__ __forceinline__ void fence_barrier_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

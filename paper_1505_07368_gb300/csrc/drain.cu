@@ -544,6 +544,7 @@ __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableT
             // and is finished outside it, so the loop carries no register
             // moves for the held slots.
             const uint32_t ustep = kSweepPrimes * wpb;
+            const uint32_t qstride = wpb * 32 * 4;      // bytes between a lane's primes of one step
             uint32_t u = r;
             while (u < kTile / 32 && s.k > 0) {
                 uint32_t pp[kSweepPrimes], pi[kSweepPrimes], pl[kSweepPrimes];
@@ -552,12 +553,12 @@ __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableT
                 bool hit = false, stop = false;
 #pragma unroll 1
                 for (;;) {
+                    uint32_t addr = tbase + (u * 32 + lane) * 4;
 #pragma unroll
-                    for (uint32_t q = 0; q < kSweepPrimes; ++q) {
-                        const uint32_t off = ((u + q * wpb) * 32 + lane) * 4;
-                        pp[q] = lds_u32(tbase + off);
-                        pi[q] = lds_u32(tbase + kTile * 4 + off);
-                        pl[q] = lds_u32(tbase + 2 * kTile * 4 + off);
+                    for (uint32_t q = 0; q < kSweepPrimes; ++q, addr += qstride) {
+                        pp[q] = lds_u32_at<0>(addr);
+                        pi[q] = lds_u32_at<kTile * 4>(addr);
+                        pl[q] = lds_u32_at<2 * kTile * 4>(addr);
                     }
                     ++steps;
                     hit = __any_sync(FULL, sweep_chunks<kSweepPrimes>(s, pp, pi, pl));
