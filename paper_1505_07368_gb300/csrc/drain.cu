@@ -459,6 +459,7 @@ __device__ void group_produce_split(const DrainParams &P, GroupShared &G, TableT
 // see tiles past its messages' bounds that another team needs: they are
 // tested only until the bound check drops the messages, and a hit at or past
 // a message's bound is no divisor below its square root.)
+constexpr uint32_t kTopUpTries = 8;    // further actors a factor claim may take messages from
 constexpr uint32_t kSweepPrimes = 4;   // chunks (primes per lane) tested per step
 static_assert((kTile / 32) % (kSweepPrimes * kConsumerWarps) == 0, "a tile splits into steps for any team size");
 
@@ -637,45 +638,62 @@ __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableT
     }
 }
 
-// Claim a factor actor: move up to K messages into batch b.  Returns b when
-// the batch needs a sweep (the caller's team runs it), kNone when every
-// message was answered at once or nothing could be taken.
-template <bool kSplit>
-__device__ uint32_t claim_factor(const DrainParams &P, uint32_t a, uint32_t b) {
+// Claim factor actor `a`: move up to K - c0 of its messages into batch b at
+// positions c0.. (a batch may hold the messages of several actors: replies go
+// to each message's own reply record, and each actor's messages enter in its
+// mailbox order).  Releases the actor; returns the batch's new count.
+__device__ uint32_t claim_factor_take(const DrainParams &P, uint32_t a, uint32_t b, uint32_t c0) {
     const uint32_t lane = lane_id();
     ActorDesc *A = &P.actors[a];
     if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
     __syncwarp();
     const uint64_t head = *((volatile uint64_t *)&A->head);
     const uint64_t tail = ld_acquire_gpu(&A->tail);
-    uint32_t limit = P.factor_k;
+    uint32_t limit = P.factor_k - c0;
     if (P.max_claim && P.max_claim < limit) limit = P.max_claim;
     const uint64_t avail = tail - head;
     const uint32_t want = avail < limit ? (uint32_t)avail : limit;
     MsgData m{};
     const uint32_t take = want ? warp_dequeue(P, a, head, want, m) : 0u;
-    if (take == 0) {
-        release_actor(P, a, head);
+    release_actor(P, a, head + take, 0);
+    if (lane == 0) add_u64(&P.ctl->claims, 1);
+    FactorBatch *B = &P.batches[b];
+    if (lane < take) {
+        const uint32_t i = c0 + lane;
+        const uint64_t n = m.payload;
+        const bool even = (n >= 4) && !(n & 1u);
+        B->n[i] = n;
+        B->pbound[i] = even ? 0 : factor_bound(P.primes, P.nprimes, n);
+        B->found[i] = kNoFactor;
+        B->reply_addr[i] = m.reply_addr;
+        B->reply_token[i] = m.reply_token;
+        B->tag[i] = m.tag;
+    }
+    __syncwarp();
+    return c0 + take;
+}
+
+// Start the sweep of batch b holding `count` messages: record it, split it
+// if it is large (kSplit), or answer it at once when no message needs a sweep.
+// Returns b when the caller's team sweeps it, kNone otherwise.
+template <bool kSplit>
+__device__ uint32_t factor_batch_launch(const DrainParams &P, uint32_t b, uint32_t count) {
+    const uint32_t lane = lane_id();
+    FactorBatch *B = &P.batches[b];
+    if (count == 0) {
         if (lane == 0) q_push(&P.ctl->freeq, P.freeq, b, P.wait_limit_ns);
         return kNone;
     }
-    release_actor(P, a, head + take);
-    FactorBatch *B = &P.batches[b];
+    __threadfence_block();
     uint32_t pb = 0;
     bool even = false;
-    if (lane < take) {
-        const uint64_t n = m.payload;
+    if (lane < count) {
+        const uint64_t n = B->n[lane];
         even = (n >= 4) && !(n & 1u);
-        pb = even ? 0 : factor_bound(P.primes, P.nprimes, n);
-        B->n[lane] = n;
-        B->pbound[lane] = pb;
-        B->found[lane] = kNoFactor;
-        B->reply_addr[lane] = m.reply_addr;
-        B->reply_token[lane] = m.reply_token;
-        B->tag[lane] = m.tag;
+        pb = B->pbound[lane];
     }
-    const uint32_t even_mask = __ballot_sync(FULL, lane < take && even);
-    const uint32_t maxb = __reduce_max_sync(FULL, lane < take ? pb : 0u);
+    const uint32_t even_mask = __ballot_sync(FULL, lane < count && even);
+    const uint32_t maxb = __reduce_max_sync(FULL, lane < count ? pb : 0u);
     // split a large batch over the teams that would otherwise idle: the
     // device's teams against the batch records in use
     uint32_t segs = 1;
@@ -690,12 +708,11 @@ __device__ uint32_t claim_factor(const DrainParams &P, uint32_t a, uint32_t b) {
         if (segs < 2) segs = 1;
     }
     if (lane == 0) {
-        B->count = take;
+        B->count = count;
         B->even_mask = even_mask;
         B->maxbound = maxb;
         B->segs = segs;
         B->items_left = P.factor_w * segs;
-        add_u64(&P.ctl->claims, 1);
     }
     __syncwarp();
     if (maxb == 0) {
@@ -1939,7 +1956,32 @@ __device__ uint32_t find_batch(const DrainParams &P, uint32_t &rng) {
                 if (lane == 0) bounds_fail(P, 44, b, P.n_batches);
                 return kNone;
             }
-            const uint32_t r = claim_factor<kSplit>(P, a, __shfl_sync(FULL, b, 0));
+            uint32_t count = claim_factor_take(P, a, b, 0);
+            // top a partial batch up with the messages of further ready factor
+            // actors, so the teams that share a table stream start with full
+            // batches (an actor of another kind goes back to the ready queue)
+            for (uint32_t extra = 0; extra < kTopUpTries && count < P.factor_k; ++extra) {
+                uint32_t a2 = 0;
+                bool got2 = false;
+                if (lane == 0) {
+                    const int pr = ready_pop(P, &a2, rng);
+                    if (pr < 0) fail(P, kErrWaitQueue, 36);
+                    got2 = pr > 0;
+                }
+                if (!__shfl_sync(FULL, got2, 0)) break;
+                a2 = __shfl_sync(FULL, a2, 0);
+                if (P.validation && !actor_ok(P, a2)) {
+                    if (lane == 0) bounds_fail(P, 46, a2, P.n_actors);
+                    break;
+                }
+                if (P.actors[a2].kind != kFactor) {
+                    if (lane == 0 && !ready_push(P, a2)) fail(P, kErrWaitQueue, 37);
+                    __syncwarp();
+                    break;
+                }
+                count = claim_factor_take(P, a2, b, count);
+            }
+            const uint32_t r = factor_batch_launch<kSplit>(P, b, count);
             if (r != kNone) return r;
         } else if (kind == kToken) {
             claim_ring(P, a);
