@@ -73,6 +73,7 @@ def parse_args(argv=None):
                     help="factor, ring, serve: split large factor batches over idle teams, up to this many "
                          "segments (0: off)")
     ap.add_argument("--gemm-items", type=int, default=None, help="gemm: work items per CTA round (with --no-autotune)")
+    ap.add_argument("--gemm-tile-n", type=int, default=None, help="gemm: BF16 output tile width, 128 or 256 (with --no-autotune)")
     ap.add_argument("--ring-incarnations", type=int, default=4,
                     help="ring: also run the rings re-created this many times on the device (0: skip)")
     ap.add_argument("--fork-n", type=int, default=20, help="spawn: recursion counter n (2^(n+1) - 2 spawns per step)")
@@ -528,6 +529,8 @@ def run_gemm(args):
                 "best": sched, "measured": [[c, round(1e3 * t, 3)] for c, t in table]}
         if args.gemm_items is not None:
             sched["gemm_items_per_round"] = args.gemm_items
+        if args.gemm_tile_n is not None:
+            sched["gemm_tile_n"] = args.gemm_tile_n
         _note(f"gemm {name}: persistent {sched}")
         with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=wl.n_actors, mailbox_capacity=64, **sched) as rt:
             for _ in range(wl.n_actors):

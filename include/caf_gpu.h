@@ -179,6 +179,8 @@ typedef struct {
     uint32_t factor_split;          /* 0 or 1: off; else a large factor batch is split into up */
                                     /* to this many (<= 32) segments that idle teams in other  */
                                     /* CTAs sweep                                               */
+    uint32_t gemm_tile_n;           /* GEMM_BF16 output tile width in the drain: 128 or 256    */
+                                    /* (default 256; split-BF16x3 always uses 128)              */
 } caf_gpu_runtime_cfg;
 
 /* Per-actor configuration for caf_gpu_spawn (may be NULL for defaults). */

@@ -10,7 +10,9 @@ Sec. 6.1 (number of workers, messages per actor run):
 * ``ctas_per_sm``: resident drain CTAs per SM (the worker count);
 * ``gemm_items_per_round``: GEMM work items (pack items and output tiles) a
   CTA takes per round -- consecutive tiles of a round run as one pipeline;
-* ``max_msgs_per_claim``: messages one claim of an actor may take.
+* ``max_msgs_per_claim``: messages one claim of an actor may take;
+* ``gemm_tile_n``: BF16 output tile width, 128 or 256 columns (one N = 256
+  MMA reads two B panels per k block).
 
 ``tune_factor`` and ``tune_gemm`` run one device batch of the caller's
 workload for every candidate setting on the current GPU, keep the fastest,
@@ -39,6 +41,8 @@ GEMM_CANDIDATES = [
     {"gemm_items_per_round": i, "max_msgs_per_claim": c}
     for i in (2, 4, 8) for c in (0, 8)
 ]
+# BF16 also searches the output tile width (split-BF16x3 always uses 128)
+GEMM_CANDIDATES_BF16 = [dict(c, gemm_tile_n=w) for w in (256, 128) for c in GEMM_CANDIDATES]
 
 
 def cache_path() -> str:
@@ -162,7 +166,7 @@ def tune_gemm(kind: int, actor_idx: np.ndarray, desc: np.ndarray, outs, n_actors
     pointers lie in the device tensor `outs`; actor_idx: receiving actor index
     per message.  `timed_run(cand) -> (seconds, signature)` replaces the GPU run
     (tests stub it on the host).  Returns (best_cfg, table)."""
-    candidates = candidates or GEMM_CANDIDATES
+    candidates = candidates or (GEMM_CANDIDATES_BF16 if kind == C.GEMM_BF16 else GEMM_CANDIDATES)
     count = desc.size
     h = hashlib.sha1(np.ascontiguousarray(desc["n"]).tobytes() + np.ascontiguousarray(actor_idx).tobytes())
     if gpu_name is None:

@@ -54,7 +54,8 @@ class RuntimeCfg(ctypes.Structure):
                 ("wait_limit_ns", ctypes.c_uint64), ("idle_exit_ns", ctypes.c_uint64),
                 ("validation_mode", ctypes.c_uint32), ("log_capacity", ctypes.c_uint32),
                 ("cuda_stream", ctypes.c_void_p), ("gemm_items_per_round", ctypes.c_uint32),
-                ("fork_pool", ctypes.c_uint32), ("scheduler", ctypes.c_uint32), ("factor_split", ctypes.c_uint32)]
+                ("fork_pool", ctypes.c_uint32), ("scheduler", ctypes.c_uint32), ("factor_split", ctypes.c_uint32),
+                ("gemm_tile_n", ctypes.c_uint32)]
 
 
 class ActorCfg(ctypes.Structure):

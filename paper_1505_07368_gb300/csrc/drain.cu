@@ -207,12 +207,14 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
 // overwrite those slots.  The store of WAITING is a release as well, so a
 // producer whose acquire-CAS wakes the actor passes the head on to the next
 // claim through the ready queue.  `done`: 1 if the caller knows the actor has
-// terminated, 0 if it knows it has not, -1 to read its state.
-__device__ void release_actor(const DrainParams &P, uint32_t a, uint64_t new_head, int done = -1) {
+// terminated, 0 if it knows it has not, -1 to read its state.  `moved`: false
+// when the claim took no slot (the head keeps its value and needs no store).
+__device__ void release_actor(const DrainParams &P, uint32_t a, uint64_t new_head, int done = -1,
+                              bool moved = true) {
     __syncwarp();
     if (lane_id() == 0) {
         ActorDesc *A = &P.actors[a];
-        st_release_gpu(&A->head, new_head);
+        if (moved) st_release_gpu(&A->head, new_head);
         if (done < 0) done = *((volatile uint32_t *)&A->state) == kDone;
         if (!done) {
             st_release_gpu(&A->state, kWaiting);
@@ -1038,7 +1040,7 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
             add_u64(&P.ctl->completed, 1);
         }
     }
-    release_actor(P, a, head, ended ? 1 : 0);
+    release_actor(P, a, head, ended ? 1 : 0, !carried);
     carry = out;
     if (link_ended && lane == 0) {
         // the claim is released and nothing more is sent to a terminated
@@ -1590,13 +1592,16 @@ __device__ __noinline__ void claim_gemm(const DrainParams &P, uint32_t a) {
     if (lane < take) {
         if (valid) {
             const uint32_t tt = (n + kGemmBN - 1) / kGemmBN;
+            // BF16 jobs run wide tiles: 128 rows x 256 columns (two B panels)
+            // per item, a narrow one for the last column of an odd panel count
+            const bool wide = !split && P.gemm_wide;
             GemmJob *J = &P.jobs[j];
             J->A = d->A;
             J->B = d->B;
             J->C = d->C;
             J->n = n;
-            J->split = split;
-            J->tiles = tt * tt;
+            J->split = split | (wide ? 2u : 0u);
+            J->tiles = wide ? tt * ((tt + 1) / 2) : tt * tt;
             J->done = 0;
             J->packs_left = 2 * tt;
             J->reply_addr = m.reply_addr;
@@ -1635,7 +1640,7 @@ __device__ __noinline__ void drain_gemm_pack(const DrainParams &P, PackedSlots &
     const uint32_t j = item >> 16, x = item & 0xFFFFu;
     GemmJob *J = &P.jobs[j];
     const uint32_t n = J->n;
-    const bool split = J->split != 0;
+    const bool split = (J->split & 1u) != 0;
     const PackGeom g = pack_geom(reinterpret_cast<uint8_t *>(J->pack), n, split);
     const uint32_t panel = x & 63u;
     if ((threadIdx.x >> 5) < kGemmConvWarps) {
@@ -1675,11 +1680,20 @@ struct RunTile {
         const uint32_t item = items[i];
         const GemmJob *J = &P->jobs[item >> 16];
         TileRef r;
-        r.split = J->split != 0;
+        r.split = (J->split & 1u) != 0;
         r.g = pack_geom(reinterpret_cast<uint8_t *>(J->pack), J->n, r.split);
         r.C = reinterpret_cast<float *>(J->C);
-        r.tm = (item & 0xFFFFu) / r.g.t;
-        r.tn = (item & 0xFFFFu) % r.g.t;
+        const uint32_t idx = item & 0xFFFFu;
+        if (J->split & 2u) {
+            const uint32_t tw = (r.g.t + 1) / 2;
+            r.tm = idx / tw;
+            r.tn = 2 * (idx % tw);
+            r.wide = r.tn + 1 < r.g.t;
+        } else {
+            r.tm = idx / r.g.t;
+            r.tn = idx % r.g.t;
+            r.wide = false;
+        }
         return r;
     }
 };
@@ -1701,7 +1715,11 @@ __device__ __noinline__ void drain_gemm_tiles(const DrainParams &P, GroupShared 
         if (!ok) fail(P, kErrGemm, 16, mine[0], count);
         heartbeat(P);
         __threadfence();
-        add_u64(&P.ctl->gemm_tiles, count);
+        uint32_t equiv = 0;   // 128 x 128 output tiles these items cover
+#pragma unroll
+        for (uint32_t i = 0; i < kMaxItemsPerRound; ++i)
+            if (i < count) equiv += RunTile{&P, mine}(i).wide ? 2u : 1u;
+        add_u64(&P.ctl->gemm_tiles, equiv);
 #pragma unroll
         for (uint32_t i = 0; i < kMaxItemsPerRound; ++i) {
             if (i >= count) break;
@@ -1959,8 +1977,17 @@ __device__ uint32_t find_batch(const DrainParams &P, uint32_t &rng) {
             uint32_t count = claim_factor_take(P, a, b, 0);
             // top a partial batch up with the messages of further ready factor
             // actors, so the teams that share a table stream start with full
-            // batches (an actor of another kind goes back to the ready queue)
-            for (uint32_t extra = 0; extra < kTopUpTries && count < P.factor_k; ++extra) {
+            // batches (an actor of another kind goes back to the ready queue).
+            // Only while more actors are ready than teams are idle: with idle
+            // teams, messages spread over teams finish sooner than in one batch.
+            bool topup = false;
+            if (lane == 0 && count < P.factor_k) {
+                const int64_t teams = (int64_t)gridDim.x * (kConsumerWarps / P.factor_w);
+                const int64_t busy = (int64_t)P.n_batches - q_len(&ctl->freeq);
+                topup = q_len(&ctl->readyq) > teams - busy;
+            }
+            topup = __shfl_sync(FULL, topup, 0);
+            for (uint32_t extra = 0; topup && extra < kTopUpTries && count < P.factor_k; ++extra) {
                 uint32_t a2 = 0;
                 bool got2 = false;
                 if (lane == 0) {

@@ -42,6 +42,7 @@ struct PackedSlots {
     uint8_t s[kPackSlots][kPackSlotBytes];
 };
 static_assert(sizeof(PackedSlots) <= kGemmOpsBytes, "packed slots fit the GEMM area");
+static_assert(3 * kPackSlotBlocks * kPackPlane <= kPackSlotBytes, "a wide BF16 slot (A + two B planes) fits");
 
 // Where a message's packed operands live.
 struct PackGeom {
@@ -248,22 +249,28 @@ __device__ __forceinline__ void gemm_pack_b_staged(const float *__restrict__ B, 
 constexpr uint32_t kPackTmemCols = 512;   // two accumulator buffers of 256 columns
 
 // One output tile of a packed message.
+// A wide tile (BF16 only) covers columns 128 tn .. 128 tn + 255: B panels tn
+// and tn + 1, whose k-block planes sit side by side in the slot so that one
+// N = 256 MMA reads both.
 struct TileRef {
     PackGeom g;
     float *C;
     uint32_t tm, tn;
     bool split;
+    bool wide;
 };
 
 // Epilogue of a tile from the accumulator buffer at TMEM column `acc`, one
-// of warps 4..7: TMEM lanes 32 (w % 4).. (rows), all 128 columns; the split
-// form adds columns acc + 128.. to them.  Stores are masked at the edge.
+// of warps 4..7: TMEM lanes 32 (w % 4).. (rows), all 128 columns (256 for a
+// wide tile); the split form adds columns acc + 128.. to them.  Stores are
+// masked at the edge.
 __device__ __forceinline__ void packed_epilogue(const TileRef &t, uint32_t tmem, uint32_t acc) {
     const uint32_t lane = lane_id(), q = (threadIdx.x >> 5) & 3u, n = t.g.n;
     const uint32_t gr = t.tm * kGemmBM + 32 * q + lane;
     float *crow = t.C + (size_t)min(gr, n - 1) * n;
+    const uint32_t cols = t.wide ? 2 * kGemmBN : kGemmBN;
 #pragma unroll 1
-    for (uint32_t cc = 0; cc < kGemmBN; cc += 32) {
+    for (uint32_t cc = 0; cc < cols; cc += 32) {
         uint32_t r[32];
         tmem_ld_32x32(tmem + ((32 * q) << 16) + acc + cc, r);
         if (t.split) {
@@ -332,10 +339,20 @@ __device__ bool gemm_tiles_packed(TileAt tile, uint32_t count, PackedSlots &S, G
                     if (!ok) break;
                 }
                 const uint32_t k0 = i * kPackSlotBlocks, kn = min(kPackSlotBlocks, nb - k0);
-                mbar_arrive_expect_tx(&Bb.pk_full[s], 2 * kn * r.g.blk);
+                mbar_arrive_expect_tx(&Bb.pk_full[s], (r.wide ? 3 : 2) * kn * r.g.blk);
                 bulk_g2s(S.s[s], ab + (size_t)k0 * r.g.blk, kn * r.g.blk, &Bb.pk_full[s]);
-                bulk_g2s(S.s[s] + kPackSlotBlocks * r.g.blk, bb + (size_t)k0 * r.g.blk, kn * r.g.blk,
-                         &Bb.pk_full[s]);
+                uint8_t *sb = S.s[s] + kPackSlotBlocks * r.g.blk;
+                if (r.wide) {
+                    // block b of panels tn and tn + 1, side by side
+                    const uint8_t *bb2 = bb + (size_t)nb * r.g.blk;
+                    for (uint32_t b = 0; b < kn; ++b) {
+                        bulk_g2s(sb + 2 * b * r.g.blk, bb + (size_t)(k0 + b) * r.g.blk, r.g.blk, &Bb.pk_full[s]);
+                        bulk_g2s(sb + (2 * b + 1) * r.g.blk, bb2 + (size_t)(k0 + b) * r.g.blk, r.g.blk,
+                                 &Bb.pk_full[s]);
+                    }
+                } else {
+                    bulk_g2s(sb, bb + (size_t)k0 * r.g.blk, kn * r.g.blk, &Bb.pk_full[s]);
+                }
             }
         }
         // after an expired wait, let the copies in flight land (bounded)
@@ -358,9 +375,16 @@ __device__ bool gemm_tiles_packed(TileAt tile, uint32_t count, PackedSlots &S, G
                 tc_fence_after();
                 const uint32_t kn = min(kPackSlotBlocks, nb - i * kPackSlotBlocks);
                 const uint8_t *sa = S.s[s], *sb = S.s[s] + kPackSlotBlocks * r.g.blk;
-                for (uint32_t b = 0; b < kn; ++b)
-                    gemm_mma_planes(sa + b * r.g.blk, sa + b * r.g.blk + kPackPlane, sb + b * r.g.blk, acc, r.split,
-                                    i == 0 && b == 0);
+                if (r.wide) {
+                    const uint32_t id256 = gemm_idesc(kGemmBM, 2 * kGemmBN);
+                    for (uint32_t b = 0; b < kn; ++b)
+                        tc_mma_f16(acc, smem_desc_sw32(sa + b * r.g.blk), smem_desc_sw32(sb + 2 * b * r.g.blk), id256,
+                                   (i == 0 && b == 0) ? 0u : 1u);
+                } else {
+                    for (uint32_t b = 0; b < kn; ++b)
+                        gemm_mma_planes(sa + b * r.g.blk, sa + b * r.g.blk + kPackPlane, sb + b * r.g.blk, acc,
+                                        r.split, i == 0 && b == 0);
+                }
                 tc_commit(&Bb.pk_empty[s]);
             }
             tc_commit(&Bb.acc_full[bsel]);

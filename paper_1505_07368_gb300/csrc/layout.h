@@ -100,8 +100,8 @@ constexpr uint32_t kDrainSmemMixed = 1024 + kDrainHeader + (kGemmOpsBytes > kTab
 struct alignas(64) GemmJob {
     uint64_t A, B, C;
     uint32_t n;
-    uint32_t split;
-    uint32_t tiles;                // tiles of the output
+    uint32_t split;                // bit 0: split-BF16x3; bit 1: wide tiles (128 x 256, BF16)
+    uint32_t tiles;                // tile items of the output
     uint32_t done;                 // tiles finished (atomic)
     uint64_t reply_addr;
     uint32_t reply_token;
@@ -399,6 +399,8 @@ struct DrainParams {
     uint8_t *pack_large;           // kGemmJobsLarge x kPackLargeBytes (record kGemmJobsSmall + i: i-th)
     uint32_t gemm;
     uint32_t mandel;               // Mandelbrot actors exist: every drain runs work items
+    uint32_t gemm_wide;            // BF16 GEMM jobs run 128 x 256 output tiles
+    uint32_t pad_gw;
     // Mandelbrot job records
     MandelJob *mjobs;
     QCell *mjobq;

@@ -158,6 +158,7 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.factor_w = rt->n_factor_actors ? rt->cfg.factor_warps : 1u;
     p.max_claim = rt->cfg.max_msgs_per_claim;
     p.gemm_items = rt->cfg.gemm_items_per_round;
+    p.gemm_wide = rt->cfg.gemm_tile_n == 256 ? 1u : 0u;
     p.max_n = rt->cfg.max_factor_n;
     p.wait_limit_ns = rt->cfg.wait_limit_ns;
     p.idle_exit_ns = rt->cfg.idle_exit_ns;
@@ -527,6 +528,8 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     if (!c.log_capacity) c.log_capacity = 1u << 20;
     if (!c.gemm_items_per_round) c.gemm_items_per_round = 4;
     if (!c.fork_pool) c.fork_pool = 1u << 21;
+    if (!c.gemm_tile_n) c.gemm_tile_n = 256;
+    if (c.gemm_tile_n != 128 && c.gemm_tile_n != 256) return CAF_GPU_EINVAL;
     if (c.scheduler > CAF_GPU_SCHED_STEAL) return CAF_GPU_EINVAL;
     if (c.factor_split > kSplitMax) return CAF_GPU_EINVAL;
     if ((uint64_t)c.max_actors + c.fork_pool >= (1ull << 31)) return CAF_GPU_EINVAL;

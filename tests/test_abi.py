@@ -42,7 +42,7 @@ def test_struct_sizes():
     assert cafgpu.SERVE_RESULT_DTYPE.itemsize == 48
     assert ctypes.sizeof(cafgpu.ServeCfg) == 32
     assert ctypes.sizeof(cafgpu.ServeStats) == 32
-    assert ctypes.sizeof(cafgpu.RuntimeCfg) == 96
+    assert ctypes.sizeof(cafgpu.RuntimeCfg) == 104
     assert ctypes.sizeof(cafgpu.ActorCfg) == 56
     assert ctypes.sizeof(cafgpu.Stats) == 96
 
@@ -86,7 +86,7 @@ def test_header_constants_match_binding():
     {"factor_warps": 3}, {"factor_batch": 17}, {"ctas_per_sm": 5}, {"mailbox_capacity": 48},
     {"ingress_capacity": 1000}, {"max_factor_n": 1 << 62}, {"gemm_items_per_round": 9},
     {"scheduler": 2}, {"max_actors": (1 << 24) + 1}, {"max_actors": 1 << 20, "fork_pool": (1 << 31) - (1 << 20)},
-    {"factor_split": 33},
+    {"factor_split": 33}, {"gemm_tile_n": 192},
 ])
 def test_bad_runtime_settings_rejected_before_any_cuda_call(bad):
     # the settings are checked before the runtime touches the device, so this

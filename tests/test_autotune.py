@@ -49,3 +49,8 @@ def test_gemm_rejects_a_faster_candidate_with_different_checksum(tmp_path, monke
     assert seen == cands
     assert best == cands[1]
     assert [t for _, t in table] == [0.5, 0.4, float("inf"), 0.45]
+
+
+def test_bf16_search_covers_both_tile_widths():
+    assert {c["gemm_tile_n"] for c in autotune.GEMM_CANDIDATES_BF16} == {128, 256}
+    assert all("gemm_tile_n" not in c for c in autotune.GEMM_CANDIDATES)
