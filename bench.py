@@ -55,7 +55,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--factor-batch", type=int, default=16)
-    ap.add_argument("--factor-warps", type=int, default=4)
+    ap.add_argument("--factor-warps", type=int, default=8)
     ap.add_argument("--ctas-per-sm", type=int, default=2)
     ap.add_argument("--skip-per-message", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")

@@ -30,8 +30,8 @@ constexpr uint32_t kOneThreads = 256;                      // per-message factor
 constexpr uint32_t kFactorKMax = 16;     // messages per factor batch, upper bound
 constexpr uint32_t kRangePrimes = 4096;  // table padding granule
 constexpr uint32_t kNoFactor = 0xFFFFFFFFu;
-constexpr uint32_t kTile = 2048;         // primes per staged table tile (64 chunks of 32)
-constexpr uint32_t kStages = 4;          // tiles in flight per CTA
+constexpr uint32_t kTile = 4096;         // primes per staged table tile (128 chunks of 32)
+constexpr uint32_t kStages = 2;          // tiles in flight per CTA
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kMaxItemsPerRound = 8;   // GEMM work items a drain CTA may take per round
 

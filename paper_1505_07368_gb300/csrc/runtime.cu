@@ -520,7 +520,7 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     if (!c.ingress_capacity) c.ingress_capacity = 65536;
     if (!c.ctas_per_sm) c.ctas_per_sm = 2;
     if (!c.factor_batch) c.factor_batch = 16;
-    if (!c.factor_warps) c.factor_warps = 4;
+    if (!c.factor_warps) c.factor_warps = 8;
     if (!c.max_factor_n) c.max_factor_n = (1ull << 62) - 1;
     if (!c.mem_budget_bytes) c.mem_budget_bytes = 8ull << 30;
     if (!c.wait_limit_ns) c.wait_limit_ns = 200000000ull;
@@ -639,6 +639,7 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     // prime table: odd primes up to floor(sqrt(max_factor_n))
     const uint64_t lim = isqrt_u64(c.max_factor_n);
     rt->prime_limit = lim;
+    static_assert(kRangePrimes + 64 >= kTile, "the last table tile's copy stays inside the padded table");
     CK(build_prime_table(lim, kRangePrimes + 64, &rt->d_primes, &rt->d_pinv, &rt->d_plim, &rt->nprimes,
                          rt->setup));
     rt->launches += 4;
