@@ -163,6 +163,7 @@ typedef struct {
     uint32_t ingress_capacity;      /* host->device ring slots, power of two (65536)          */
     uint32_t ctas_per_sm;           /* persistent CTAs per SM: the worker count (default 2)   */
     uint32_t max_msgs_per_claim;    /* messages one claim of an actor may take; 0 = no limit  */
+                                    /* (GEMM claims ignore it and take up to 32)              */
     uint32_t factor_batch;          /* messages swept together as one batch (<= 16, default 16) */
     uint32_t factor_warps;          /* warps sharing one batch: 1, 2, 4 or 8 (default 8); 1   */
                                     /* while no FACTOR actor exists (every warp claims actors) */

@@ -10,7 +10,8 @@ Sec. 6.1 (number of workers, messages per actor run):
 * ``ctas_per_sm``: resident drain CTAs per SM (the worker count);
 * ``gemm_items_per_round``: GEMM work items (pack items and output tiles) a
   CTA takes per round -- consecutive tiles of a round run as one pipeline;
-* ``max_msgs_per_claim``: messages one claim of an actor may take;
+* ``max_msgs_per_claim``: messages one claim of an actor may take (not
+  applied to GEMM claims, so not searched for them);
 * ``gemm_tile_n``: BF16 output tile width, 128 or 256 columns (one N = 256
   MMA reads two B panels per k block).
 
@@ -37,10 +38,8 @@ DEFAULT_CANDIDATES = [
     {"factor_batch": k, "factor_warps": w, "ctas_per_sm": c}
     for k in (8, 16) for w in (2, 4, 8) for c in (2,)
 ]
-GEMM_CANDIDATES = [
-    {"gemm_items_per_round": i, "max_msgs_per_claim": c}
-    for i in (2, 4, 8) for c in (0, 8)
-]
+# (GEMM claims take no per-claim message limit, so it is not searched)
+GEMM_CANDIDATES = [{"gemm_items_per_round": i} for i in (2, 4, 8)]
 # BF16 also searches the output tile width (split-BF16x3 always uses 128)
 GEMM_CANDIDATES_BF16 = [dict(c, gemm_tile_n=w) for w in (256, 128) for c in GEMM_CANDIDATES]
 
@@ -159,8 +158,8 @@ def _tune(key: str, candidates, run, use_cache: bool, log):
 
 def tune_gemm(kind: int, actor_idx: np.ndarray, desc: np.ndarray, outs, n_actors: int, candidates=None,
               runtime_kwargs=None, use_cache: bool = True, log=None, timed_run=None, gpu_name=None):
-    """Pick the fastest GEMM drain schedule (items per round, messages per claim)
-    for one device batch of GEMM messages of `kind` (BF16 or split).
+    """Pick the fastest GEMM drain schedule (items per round; for BF16 also the
+    tile width) for one device batch of GEMM messages of `kind` (BF16 or split).
 
     desc: caf_gpu_gemm_desc records (host numpy, GEMM_DESC_DTYPE) whose C
     pointers lie in the device tensor `outs`; actor_idx: receiving actor index

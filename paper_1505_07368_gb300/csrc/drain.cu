@@ -1534,6 +1534,32 @@ __device__ __forceinline__ bool job_free(const DrainParams &P, uint32_t j) {
                         : q_push(&P.ctl->jobq_large, P.jobq_large, j, P.wait_limit_ns);
 }
 
+// Read the job fields of tile item `item` (job << 16 | tile index) into `s`
+// and check them: a record inside the table, a size its scratch class holds,
+// the tile count the size gives, and a tile index below it (so the tile lies
+// inside the matrix and its images inside the record's scratch).  The
+// images' address comes from the record index, not from the record.
+__device__ __forceinline__ bool tile_snap(const DrainParams &P, uint32_t item, TileSnap &s) {
+    const uint32_t j = item >> 16, idx = item & 0xFFFFu;
+    s = TileSnap{};
+    if (j >= kGemmJobs) return false;
+    const GemmJob *J = &P.jobs[j];
+    const uint32_t n = J->n, flags = J->split, tiles = J->tiles;
+    const uint64_t C = J->C;
+    s.tiles = tiles;
+    if (n == 0 || n > (job_small(j) ? kPackSmallMaxN : kMaxDrainGemmN) || flags > 3u) return false;
+    const uint32_t t = (n + kGemmBN - 1) / kGemmBN, tw = (flags & 2u) ? (t + 1) / 2 : t;
+    if (tiles != t * tw || idx >= tiles || (flags & 3u) == 3u) return false;
+    s.pack = reinterpret_cast<uint64_t>(job_scratch(P, j));
+    s.C = C;
+    s.n = n;
+    s.split = (uint8_t)(flags & 1u);
+    s.tm = (uint16_t)(idx / tw);
+    s.tn = (uint16_t)((flags & 2u) ? 2 * (idx % tw) : idx % tw);
+    s.wide = (uint8_t)((flags & 2u) && s.tn + 1u < t);
+    return true;
+}
+
 __device__ bool work_item_ok(const DrainParams &P, uint32_t item) {
     const uint32_t j = item >> 16;
     if (item & kPackItemFlag) {
@@ -1557,8 +1583,10 @@ __device__ __noinline__ void claim_gemm(const DrainParams &P, uint32_t a) {
     const uint64_t head = *((volatile uint64_t *)&A->head);
     const uint64_t tail = ld_acquire_gpu(&A->tail);
     uint64_t avail = tail - head;
-    uint32_t want = avail < 32 ? (uint32_t)avail : 32u;
-    if (P.max_claim && P.max_claim < want) want = P.max_claim;
+    // (the runtime's per-claim message limit is not applied here: GEMM
+    // claims of at most 8 messages with 128 x 256 tiles faulted the GPU, for
+    // a cause not yet found)
+    const uint32_t want = avail < 32 ? (uint32_t)avail : 32u;
     if (lane == 0) add_u64(&ctl->claims, 1);
     // read each message's descriptor in place (published slots only), then
     // reserve a job record of its class, so a claim never waits for one
@@ -1606,7 +1634,6 @@ __device__ __noinline__ void claim_gemm(const DrainParams &P, uint32_t a) {
             J->packs_left = 2 * tt;
             J->reply_addr = m.reply_addr;
             J->reply_token = m.reply_token;
-            J->pack = reinterpret_cast<uint64_t>(job_scratch(P, j));
             panels = tt;
         } else {
             write_reply(m.reply_addr, 3, 0, n, m.tag, m.reply_token);
@@ -1641,7 +1668,7 @@ __device__ __noinline__ void drain_gemm_pack(const DrainParams &P, PackedSlots &
     GemmJob *J = &P.jobs[j];
     const uint32_t n = J->n;
     const bool split = (J->split & 1u) != 0;
-    const PackGeom g = pack_geom(reinterpret_cast<uint8_t *>(J->pack), n, split);
+    const PackGeom g = pack_geom(job_scratch(P, j), n, split);
     const uint32_t panel = x & 63u;
     if ((threadIdx.x >> 5) < kGemmConvWarps) {
         const float *src = reinterpret_cast<const float *>((x & 64u) ? J->B : J->A);
@@ -1672,60 +1699,61 @@ __device__ __noinline__ void drain_gemm_pack(const DrainParams &P, PackedSlots &
     }
 }
 
-// Tile i of a run of tile items (item: job << 16 | tile index).
+// Tile i of a run of tile items, from the snapshots taken with the items.
 struct RunTile {
-    const DrainParams *P;
-    const uint32_t *items;
+    const TileSnap *snap;
     __device__ TileRef operator()(uint32_t i) const {
-        const uint32_t item = items[i];
-        const GemmJob *J = &P->jobs[item >> 16];
+        const TileSnap &s = snap[i];
         TileRef r;
-        r.split = (J->split & 1u) != 0;
-        r.g = pack_geom(reinterpret_cast<uint8_t *>(J->pack), J->n, r.split);
-        r.C = reinterpret_cast<float *>(J->C);
-        const uint32_t idx = item & 0xFFFFu;
-        if (J->split & 2u) {
-            const uint32_t tw = (r.g.t + 1) / 2;
-            r.tm = idx / tw;
-            r.tn = 2 * (idx % tw);
-            r.wide = r.tn + 1 < r.g.t;
-        } else {
-            r.tm = idx / r.g.t;
-            r.tn = idx % r.g.t;
-            r.wide = false;
-        }
+        r.split = s.split != 0;
+        r.wide = s.wide != 0;
+        r.g = pack_geom(reinterpret_cast<uint8_t *>(s.pack), s.n, r.split);
+        r.C = reinterpret_cast<float *>(s.C);
+        r.tm = s.tm;
+        r.tn = s.tn;
         return r;
     }
 };
 
-// Run `count` tile items as one pipeline with the whole CTA; for each, the
-// CTA that finishes a job's last tile writes its reply and frees the record.
+// Run `count` tile items (their snapshots: `snap`) as one pipeline with the
+// whole CTA; for each, the CTA that finishes a job's last tile writes its
+// reply and frees the record.
 __device__ __noinline__ void drain_gemm_tiles(const DrainParams &P, GroupShared &G, PackedSlots &slots,
-                                              const uint32_t *items, uint32_t count, GemmCounters &K,
-                                              uint32_t bar_threads) {
-    // `items` is shared memory the producer warp refills for its next round
-    // once the sequence's last barrier has passed: keep this run's ids
-    uint32_t mine[kMaxItemsPerRound];
+                                              const uint32_t *items, const TileSnap *snap, uint32_t count,
+                                              GemmCounters &K, uint32_t bar_threads) {
+    // `items` and `snap` are shared memory the producer warp refills for its
+    // next round once the sequence's last barrier has passed: keep this run's
+    // ids and counts
+    uint32_t mine[kMaxItemsPerRound], tiles_of[kMaxItemsPerRound];
+    uint32_t equiv = 0;   // 128 x 128 output tiles these items cover
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (uint32_t i = 0; i < kMaxItemsPerRound; ++i) mine[i] = i < count ? items[i] : 0u;
-    const bool ok = gemm_tiles_packed(RunTile{&P, items}, count, slots, G.gb, K, P.wait_limit_ns,
+        for (uint32_t i = 0; i < kMaxItemsPerRound; ++i) {
+            mine[i] = i < count ? items[i] : 0u;
+            tiles_of[i] = i < count ? snap[i].tiles : 0u;
+            equiv += i < count ? (snap[i].wide ? 2u : 1u) : 0u;
+        }
+    }
+    const bool ok = gemm_tiles_packed(RunTile{snap}, count, slots, G.gb, K, P.wait_limit_ns,
                                       NamedBarSync{bar_threads});
     items = nullptr;
+    snap = nullptr;
     if (threadIdx.x == 0) {
         if (!ok) fail(P, kErrGemm, 16, mine[0], count);
         heartbeat(P);
         __threadfence();
-        uint32_t equiv = 0;   // 128 x 128 output tiles these items cover
-#pragma unroll
-        for (uint32_t i = 0; i < kMaxItemsPerRound; ++i)
-            if (i < count) equiv += RunTile{&P, mine}(i).wide ? 2u : 1u;
         add_u64(&P.ctl->gemm_tiles, equiv);
 #pragma unroll
         for (uint32_t i = 0; i < kMaxItemsPerRound; ++i) {
             if (i >= count) break;
             const uint32_t j = mine[i] >> 16;
             GemmJob *J = &P.jobs[j];
-            if (atomicAdd(reinterpret_cast<unsigned int *>(&J->done), 1u) == J->tiles - 1) {
+            // the tile count was read before this CTA counted its tile: the
+            // record cannot have been freed and reused in between
+            const uint32_t before = atomicAdd(reinterpret_cast<unsigned int *>(&J->done), 1u);
+            if (before >= tiles_of[i]) {
+                fail(P, kErrGemm, 19, mine[i], before);   // a tile counted twice
+            } else if (before + 1u == tiles_of[i]) {
                 __threadfence();
                 write_reply(J->reply_addr, ok ? 0 : 3, 0, J->n, 0, J->reply_token);
                 __threadfence();
@@ -2175,8 +2203,21 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
                 bounds_fail(P, 45, item, 0);
                 item = kNone;
             }
+            // a tile item's job fields, read once here, right after the pop
+            // that ordered them, and checked (in every mode: a tile outside
+            // its matrix or scratch is refused, not computed)
+            TileSnap sn;
+            const bool is_tile = kGemm && item != kNone && !(item & (kPackItemFlag | kMandelItemFlag));
+            if (is_tile && !tile_snap(P, item, sn)) {
+                bounds_fail(P, 47, item, sn.tiles);
+                item = kNone;
+            }
             const uint32_t got = __ballot_sync(FULL, item != kNone);
-            if (item != kNone) G.items[__popc(got & ((1u << lane) - 1u))] = item;
+            if (item != kNone) {
+                const uint32_t pos = __popc(got & ((1u << lane) - 1u));
+                G.items[pos] = item;
+                if (is_tile) G.snap[pos] = sn;
+            }
             if (lane == 0) {
                 G.exit = ex;
                 G.nitems = __popc(got);
@@ -2219,7 +2260,7 @@ __global__ void __launch_bounds__(kThreads, kGemm ? 1 : 2) k_drain(DrainParams P
                         // consecutive tiles run as one pipeline
                         uint32_t e = i + 1;
                         while (e < ni && !(G.items[e] & (kPackItemFlag | kMandelItemFlag))) ++e;
-                        drain_gemm_tiles(P, G, gslots, &G.items[i], e - i, gk, bar_threads);
+                        drain_gemm_tiles(P, G, gslots, &G.items[i], &G.snap[i], e - i, gk, bar_threads);
                         i = e;
                     }
                 }

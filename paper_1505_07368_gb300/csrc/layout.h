@@ -67,6 +67,21 @@ struct GemmBars {
     uint32_t pad;
 };
 
+// A GEMM tile item's job fields, read once (and checked) by the producer lane
+// that takes the item.  Every role of the tile run -- bulk copies, MMAs,
+// epilogue, the slot and buffer phase counts -- works from this one copy, so
+// all of them agree on the tile's geometry.
+struct TileSnap {
+    uint64_t pack;      // the job record's packed images
+    uint64_t C;         // output (n x n, row-major)
+    uint32_t n;
+    uint32_t tiles;     // the job's tile count: the target of its completion count
+    uint16_t tm, tn;    // output tile row, first column panel
+    uint8_t split, wide;
+    uint16_t pad;
+};
+static_assert(sizeof(TileSnap) == 32, "TileSnap is 32 bytes");
+
 // Per-CTA shared state of the drain: the table ring's barriers, the GEMM
 // barriers, and the group (one factor batch per team of consumer warps).
 // The operand area -- table tiles, or GEMM operand tiles -- follows at
@@ -85,6 +100,7 @@ struct GroupShared {
     uint32_t nitems;
     uint32_t mnext;                      // Mandelbrot bands: next 32-pixel group of the round
     unsigned long long msum[kMaxItemsPerRound];   // Mandelbrot bands: escape counts summed
+    TileSnap snap[kMaxItemsPerRound];             // GEMM tile items: their job fields (items[i] -> snap[i])
 };
 constexpr uint32_t kDrainHeader = 1024;
 static_assert(sizeof(GroupShared) <= kDrainHeader, "drain header fits");
@@ -106,7 +122,7 @@ struct alignas(64) GemmJob {
     uint64_t reply_addr;
     uint32_t reply_token;
     uint32_t packs_left;           // pack items not finished (atomic); the last one queues the tiles
-    uint64_t pack;                 // the record's packed-operand scratch (device)
+    uint64_t pad;                  // (the record's packed-operand scratch follows from its index)
 };
 static_assert(sizeof(GemmJob) == 64, "GemmJob is 64 bytes");
 constexpr uint32_t kMaxDrainGemmN = 4096;   // <= 1024 tiles per job

@@ -209,7 +209,11 @@ cudaError_t guarded_malloc(caf_gpu_runtime *rt, void **p, uint64_t bytes) {
     if (e != cudaSuccess) return e;
     uint8_t *g = static_cast<uint8_t *>(*p) + bytes;
     e = cudaMemset(g, kGuardByte, kGuardBytes);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) {
+        cudaFree(*p);
+        *p = nullptr;
+        return e;
+    }
     rt->guards.emplace_back(*p, g);
     return cudaSuccess;
 }
@@ -850,6 +854,7 @@ int caf_gpu_spawn(caf_gpu_runtime *rt, uint32_t kernel_id, const caf_gpu_actor_c
             }
             if (guarded_malloc(rt, &rt->d_pack_large, kPackLargeBytes * kGemmJobsLarge) != cudaSuccess) {
                 cudaGetLastError();
+                drop_guard(rt, rt->d_pack_small);
                 cudaFree(rt->d_pack_small);
                 rt->d_pack_small = rt->d_pack_large = nullptr;
                 return CAF_GPU_ENOMEM;

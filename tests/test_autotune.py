@@ -37,7 +37,7 @@ def test_factor_rejects_a_faster_candidate_with_different_results(tmp_path, monk
 
 def test_gemm_rejects_a_faster_candidate_with_different_checksum(tmp_path, monkeypatch):
     monkeypatch.setenv("CAFGPU_CACHE_DIR", str(tmp_path))
-    cands = autotune.GEMM_CANDIDATES[:4]
+    cands = autotune.GEMM_CANDIDATES_BF16[:4]
     seen = []
     sig_ok = (b"st", b"n", 123.0)
     sig_bad = (b"st", b"n", 123.5)          # one C differs
@@ -54,3 +54,5 @@ def test_gemm_rejects_a_faster_candidate_with_different_checksum(tmp_path, monke
 def test_bf16_search_covers_both_tile_widths():
     assert {c["gemm_tile_n"] for c in autotune.GEMM_CANDIDATES_BF16} == {128, 256}
     assert all("gemm_tile_n" not in c for c in autotune.GEMM_CANDIDATES)
+    # GEMM claims take no per-claim message limit, so no candidate sets one
+    assert all("max_msgs_per_claim" not in c for c in autotune.GEMM_CANDIDATES_BF16)
