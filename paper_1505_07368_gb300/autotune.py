@@ -15,10 +15,11 @@ Sec. 6.1 (number of workers, messages per actor run):
 * ``gemm_tile_n``: BF16 output tile width, 128 or 256 columns (one N = 256
   MMA reads two B panels per k block).
 
-``tune_factor`` and ``tune_gemm`` run one device batch of the caller's
-workload for every candidate setting on the current GPU, keep the fastest,
-and cache the choice in a JSON file keyed by GPU name and workload
-signature.  The timing is CUDA events on the runtime's stream; every
+``tune_factor`` runs one device batch of the caller's workload for every
+candidate setting on the current GPU, keeps the fastest, and caches the
+choice in a JSON file keyed by GPU name and workload signature.
+``tune_gemm`` applies the same selection to timings its caller supplies;
+its own GPU timing is off (see its docstring).  The timing is CUDA events on the runtime's stream; every
 candidate must reproduce the first one's results (factor replies; GEMM
 replies and a checksum of every C), so a setting that breaks results is
 never chosen.
@@ -164,55 +165,20 @@ def tune_gemm(kind: int, actor_idx: np.ndarray, desc: np.ndarray, outs, n_actors
     desc: caf_gpu_gemm_desc records (host numpy, GEMM_DESC_DTYPE) whose C
     pointers lie in the device tensor `outs`; actor_idx: receiving actor index
     per message.  `timed_run(cand) -> (seconds, signature)` replaces the GPU run
-    (tests stub it on the host).  Returns (best_cfg, table)."""
+    (tests stub it on the host).  Returns (best_cfg, table).
+
+    The GPU timed run (a fresh runtime per candidate) is off: the second
+    candidate's runtime faulted the GPU in its first batch each of the three
+    times it ran (BF16, 128 x 256 tiles, the 4096-message GEMM workload), for
+    a cause not yet found.  Without `timed_run` this raises RuntimeError."""
     candidates = candidates or (GEMM_CANDIDATES_BF16 if kind == C.GEMM_BF16 else GEMM_CANDIDATES)
+    if timed_run is None:
+        raise RuntimeError("GEMM autotuning on the GPU is disabled: a second GEMM runtime per process "
+                           "faulted in its first batch; use the fixed schedules")
     count = desc.size
     h = hashlib.sha1(np.ascontiguousarray(desc["n"]).tobytes() + np.ascontiguousarray(actor_idx).tobytes())
     if gpu_name is None:
         import torch
         gpu_name = torch.cuda.get_device_name()
     key = f"{gpu_name}|gemm{kind}|actors={n_actors}|msgs={count}|{h.hexdigest()[:16]}"
-    if timed_run is None:
-        timed_run = _gemm_run(kind, actor_idx, desc, outs, n_actors, runtime_kwargs)
     return _tune(key, candidates, timed_run, use_cache, log)
-
-
-def _gemm_run(kind, actor_idx, desc, outs, n_actors, runtime_kwargs):
-    """The GPU timed run of one GEMM candidate; the signature is the replies
-    and a float64 checksum of every C (bit-identical across schedules: a
-    tile's arithmetic does not depend on which CTA runs it or when)."""
-    import torch
-    runtime_kwargs = dict(runtime_kwargs or {})
-    count = desc.size
-    d_desc = torch.from_numpy(desc.view(np.uint8).copy()).cuda()
-    m = np.zeros(count, C.DMSG_DTYPE)
-    m["actor"] = actor_idx
-    m["kind"] = kind
-    m["u64"] = d_desc.data_ptr() + np.arange(count, dtype=np.uint64) * C.GEMM_DESC_DTYPE.itemsize
-    m["tag"] = np.arange(count)
-    d_msgs = torch.from_numpy(m.view(np.uint8).copy()).cuda()
-    d_rep = torch.zeros(count * C.DREPLY_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
-
-    def run(cand):
-        kw = dict(runtime_kwargs)
-        kw.update(cand)
-        with C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=n_actors, **kw) as rt:
-            for _ in range(n_actors):
-                rt.spawn(kind)
-            stream = torch.cuda.ExternalStream(rt.stream())
-            torch.cuda.synchronize()
-            rt.request_batch_device(d_msgs.data_ptr(), count, d_rep.data_ptr())   # warm-up
-            rt.stream_sync()
-            outs.zero_()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rt.request_batch_device(d_msgs.data_ptr(), count, d_rep.data_ptr())
-            e1.record(stream)
-            rt.stream_sync()
-            secs = e0.elapsed_time(e1) / 1e3
-            rep = d_rep.cpu().numpy().view(C.DREPLY_DTYPE)
-            sig = (rep["status"].tobytes(), rep["r1"].tobytes(), float(outs.sum(dtype=torch.float64).item()))
-        return secs, sig
-
-    return run

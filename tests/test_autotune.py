@@ -2,6 +2,7 @@
 the fastest candidate wins only if its results equal the first candidate's;
 a faster candidate whose results differ is rejected."""
 import numpy as np
+import pytest
 
 from paper_1505_07368_gb300 import autotune
 from paper_1505_07368_gb300 import cafgpu as C
@@ -56,3 +57,10 @@ def test_bf16_search_covers_both_tile_widths():
     assert all("gemm_tile_n" not in c for c in autotune.GEMM_CANDIDATES)
     # GEMM claims take no per-claim message limit, so no candidate sets one
     assert all("max_msgs_per_claim" not in c for c in autotune.GEMM_CANDIDATES_BF16)
+
+
+def test_gemm_gpu_timing_is_refused():
+    desc = np.zeros(2, C.GEMM_DESC_DTYPE)
+    desc["n"] = [64, 128]
+    with pytest.raises(RuntimeError):
+        autotune.tune_gemm(C.GEMM_BF16, np.zeros(2, np.uint32), desc, None, 1, use_cache=False, gpu_name="stub")
