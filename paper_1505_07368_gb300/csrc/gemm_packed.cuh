@@ -34,15 +34,20 @@ constexpr uint32_t kPackPlane = kGemmPlaneBytes;       // 4 KB: 128 rows x 16 k 
 constexpr uint32_t kPackItemFlag = 0x8000u;            // work item: pack (else tile)
 
 // Operand slots of a packed tile (the drain's GEMM shared-memory area): each
-// holds kPackSlotBlocks consecutive k blocks, the A panel's images first
-// (block b at b * blk), then B^T's (at kPackSlotBlocks * blk + b * blk).  A
-// block image is its hi plane and, for the split form, its lo plane.
+// holds bps consecutive k blocks, the A panel's images first (block b at
+// b * blk), then B^T's (at bps * blk).  A block image is its hi plane and,
+// for the split form, its lo plane.  bps fills the 64 KB slot for the tile's
+// form (kSlotBlocks*): 4 blocks of A and B hi + lo for the split form, 8 of A
+// and B for a narrow BF16 tile, 5 of A and two B panels for a wide one.
 constexpr uint32_t kPackSlotBytes = 2 * kPackSlotBlocks * 2 * kGemmPlaneBytes;   // 64 KB
 struct PackedSlots {
     uint8_t s[kPackSlots][kPackSlotBytes];
 };
+constexpr uint32_t kSlotBlocksSplit = 4, kSlotBlocksNarrow = 8, kSlotBlocksWide = 5;
 static_assert(sizeof(PackedSlots) <= kGemmOpsBytes, "packed slots fit the GEMM area");
-static_assert(3 * kPackSlotBlocks * kPackPlane <= kPackSlotBytes, "a wide BF16 slot (A + two B planes) fits");
+static_assert(kSlotBlocksSplit * 2 * 2 * kPackPlane <= kPackSlotBytes, "a split slot fits");
+static_assert(kSlotBlocksNarrow * 2 * kPackPlane <= kPackSlotBytes, "a narrow BF16 slot fits");
+static_assert(kSlotBlocksWide * 3 * kPackPlane <= kPackSlotBytes, "a wide BF16 slot (A + two B planes) fits");
 
 // Where a message's packed operands live.
 struct PackGeom {
@@ -296,15 +301,20 @@ __device__ __forceinline__ void packed_epilogue(const TileRef &t, uint32_t tmem,
     }
 }
 
-// Slots a tile of `g` streams.
-__device__ __forceinline__ uint32_t packed_slots_of(const PackGeom &g) {
-    return (g.nkb + kPackSlotBlocks - 1) / kPackSlotBlocks;
+// k blocks per slot for tile `r`, and the slots it streams.
+__device__ __forceinline__ uint32_t slot_blocks(const TileRef &r) {
+    return r.split ? kSlotBlocksSplit : (r.wide ? kSlotBlocksWide : kSlotBlocksNarrow);
+}
+__device__ __forceinline__ uint32_t packed_slots_of(const TileRef &r) {
+    const uint32_t bps = slot_blocks(r);
+    return (r.g.nkb + bps - 1) / bps;
 }
 
 // Compute `count` output tiles (tile(i): TileRef of the i-th) as one
 // pipeline over the whole CTA:
-//   * warp 0's lane 0 streams every tile's k blocks into the slot ring (two
-//     bulk copies per slot of kPackSlotBlocks blocks), running ahead into the
+//   * warp 0's lane 0 streams every tile's k blocks into the slot ring (per
+//     slot of slot_blocks(r) blocks: one bulk copy of A's blocks, and one of
+//     B's, or two per block for a wide tile), running ahead into the
 //     next tile while the current one is multiplied;
 //   * warp kGemmConvWarps's lane 0 issues the MMAs, alternating between two
 //     accumulator buffers (TMEM columns 0.. and 256..) so a tile's MMAs can
@@ -330,7 +340,7 @@ __device__ bool gemm_tiles_packed(TileAt tile, uint32_t count, PackedSlots &S, G
         uint32_t u = K.pk_uses;
         for (uint32_t t = 0; t < count && ok; ++t) {
             const TileRef r = tile(t);
-            const uint32_t nb = r.g.nkb, ns = packed_slots_of(r.g);
+            const uint32_t nb = r.g.nkb, bps = slot_blocks(r), ns = packed_slots_of(r);
             const uint8_t *ab = r.g.a + (size_t)r.tm * nb * r.g.blk, *bb = r.g.b + (size_t)r.tn * nb * r.g.blk;
             for (uint32_t i = 0; i < ns; ++i, ++u) {
                 const uint32_t s = u % kPackSlots;
@@ -338,10 +348,10 @@ __device__ bool gemm_tiles_packed(TileAt tile, uint32_t count, PackedSlots &S, G
                     ok = gemm_wait(&Bb.pk_empty[s], (u / kPackSlots - 1u) & 1u, limit_ns);
                     if (!ok) break;
                 }
-                const uint32_t k0 = i * kPackSlotBlocks, kn = min(kPackSlotBlocks, nb - k0);
+                const uint32_t k0 = i * bps, kn = min(bps, nb - k0);
                 mbar_arrive_expect_tx(&Bb.pk_full[s], (r.wide ? 3 : 2) * kn * r.g.blk);
                 bulk_g2s(S.s[s], ab + (size_t)k0 * r.g.blk, kn * r.g.blk, &Bb.pk_full[s]);
-                uint8_t *sb = S.s[s] + kPackSlotBlocks * r.g.blk;
+                uint8_t *sb = S.s[s] + bps * r.g.blk;
                 if (r.wide) {
                     // block b of panels tn and tn + 1, side by side
                     const uint8_t *bb2 = bb + (size_t)nb * r.g.blk;
@@ -362,7 +372,8 @@ __device__ bool gemm_tiles_packed(TileAt tile, uint32_t count, PackedSlots &S, G
         uint32_t u = K.pk_uses, tt = K.tiles;
         for (uint32_t t = 0; t < count && ok; ++t, ++tt) {
             const TileRef r = tile(t);
-            const uint32_t nb = r.g.nkb, ns = packed_slots_of(r.g), bsel = tt & 1u, acc = Bb.tmem + bsel * 256u;
+            const uint32_t nb = r.g.nkb, bps = slot_blocks(r), ns = packed_slots_of(r), bsel = tt & 1u,
+                           acc = Bb.tmem + bsel * 256u;
             if (tt >= 2) {
                 ok = gemm_wait(&Bb.acc_empty[bsel], ((tt >> 1) - 1u) & 1u, limit_ns);
                 if (!ok) break;
@@ -373,8 +384,8 @@ __device__ bool gemm_tiles_packed(TileAt tile, uint32_t count, PackedSlots &S, G
                 ok = gemm_wait(&Bb.pk_full[s], (u / kPackSlots) & 1u, limit_ns);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t kn = min(kPackSlotBlocks, nb - i * kPackSlotBlocks);
-                const uint8_t *sa = S.s[s], *sb = S.s[s] + kPackSlotBlocks * r.g.blk;
+                const uint32_t kn = min(bps, nb - i * bps);
+                const uint8_t *sa = S.s[s], *sb = S.s[s] + bps * r.g.blk;
                 if (r.wide) {
                     const uint32_t id256 = gemm_idesc(kGemmBM, 2 * kGemmBN);
                     for (uint32_t b = 0; b < kn; ++b)
@@ -411,7 +422,7 @@ __device__ bool gemm_tiles_packed(TileAt tile, uint32_t count, PackedSlots &S, G
     if (warp == 0 || warp == kGemmConvWarps) __syncwarp();
     // every thread advances the phase counters the same way
     uint32_t slots = 0;
-    for (uint32_t t = 0; t < count; ++t) slots += packed_slots_of(tile(t).g);
+    for (uint32_t t = 0; t < count; ++t) slots += packed_slots_of(tile(t));
     K.pk_uses += slots;
     K.tiles += count;
     // the next sequence's MMAs overwrite the buffers, and a pack item may
