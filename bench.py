@@ -72,7 +72,7 @@ def parse_args(argv=None):
                     help="ready-actor scheduler (factor, ring, mailbox, spawn): one global queue or work stealing")
     ap.add_argument("--factor-split", type=int, default=0,
                     help="factor, ring, serve: split large factor batches over idle teams, up to this many "
-                         "segments (0: off)")
+                         "segments (0: the runtime's automatic choice, small device batches only; 1: off)")
     ap.add_argument("--gemm-items", type=int, default=None, help="gemm: work items per CTA round (default: the fixed schedule)")
     ap.add_argument("--gemm-tile-n", type=int, default=None, help="gemm: BF16 output tile width, 128 or 256 (default: the fixed schedule)")
     ap.add_argument("--ring-incarnations", type=int, default=4,

@@ -177,9 +177,11 @@ typedef struct {
     uint32_t gemm_items_per_round;  /* GEMM work items a drain CTA takes per round, 1..8 (4)   */
     uint32_t fork_pool;             /* FORK actors the device may hold at once (2^21)          */
     uint32_t scheduler;             /* ready actors: CAF_GPU_SCHED_* (global queue)            */
-    uint32_t factor_split;          /* 0 or 1: off; else a large factor batch is split into up */
-                                    /* to this many (<= 32) segments that idle teams in other  */
-                                    /* CTAs sweep                                               */
+    uint32_t factor_split;          /* S > 1: a large factor batch is split into up to S       */
+                                    /* (<= 32) segments that idle teams in other CTAs sweep;   */
+                                    /* 1: never split; 0 (default): a device batch with fewer  */
+                                    /* messages than the drain's teams take (K each) splits    */
+                                    /* with S = 32, other launches do not split                */
     uint32_t gemm_tile_n;           /* GEMM_BF16 output tile width in the drain: 128 or 256    */
                                     /* (default 256; split-BF16x3 always uses 128)              */
 } caf_gpu_runtime_cfg;

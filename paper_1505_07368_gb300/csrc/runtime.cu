@@ -175,7 +175,8 @@ DrainParams make_params(caf_gpu_runtime *rt) {
     p.mjobq = rt->d_mjobq;
     p.forkq = rt->d_forkq;
     p.segq = rt->d_segq;
-    p.split = rt->cfg.factor_split;
+    // factor_split 0 (automatic): no split unless a launch chooses it
+    p.split = rt->cfg.factor_split == 0 ? 1u : rt->cfg.factor_split;
     p.n_slots = rt->n_slots + (uint64_t)kForkSlots * rt->fork_pool;
     p.n_batches = rt->n_batches;
     p.localq_hdr = rt->d_localq_hdr;
@@ -550,10 +551,18 @@ int create_impl(const caf_gpu_runtime_cfg *user, caf_gpu_runtime *rt) {
     CK(cudaDeviceGetAttribute(&rt->n_sms, cudaDevAttrMultiProcessorCount, rt->device));
     // every drain CTA must be resident at once (router and ingress warps are
     // waited on by the others), so the grid never exceeds the occupancy limit
+    // (with factor_split 0 a launch may run either instantiation: take both)
     int fit = 0, fit_mixed = 0;
     const bool split = c.factor_split > 1;   // launch_drain's instantiation choice
     CK(drain_occupancy(false, split, &fit));
     CK(drain_occupancy(true, split, &fit_mixed));
+    if (c.factor_split == 0) {
+        int fs = 0, fms = 0;
+        CK(drain_occupancy(false, true, &fs));
+        CK(drain_occupancy(true, true, &fms));
+        fit = std::min(fit, fs);
+        fit_mixed = std::min(fit_mixed, fms);
+    }
     if (fit < 1 || fit_mixed < 1) return CAF_GPU_ECUDA;
     rt->grid_factor = (unsigned)rt->n_sms * std::min<uint32_t>(c.ctas_per_sm, (uint32_t)fit);
     rt->grid_mixed = (unsigned)rt->n_sms * std::min<uint32_t>(c.ctas_per_sm, (uint32_t)fit_mixed);
@@ -1038,6 +1047,14 @@ int caf_gpu_request_batch_device(caf_gpu_runtime *rt, const caf_gpu_dmsg *d_msgs
     p.batch_replies = reinterpret_cast<Reply *>(d_replies);
     p.batch_count = count;
     p.n_routers = std::min<uint32_t>(drain_grid(rt) * kConsumerWarps, 128);
+    // factor_split 0: a batch smaller than the teams can take (K messages
+    // each) leaves teams idle, so it runs the split instantiation, whose idle
+    // teams take segments of the large factorizations (factor-only drains;
+    // the GEMM layout keeps its one instantiation)
+    if (rt->cfg.factor_split == 0 && rt->n_factor_actors && !rt->gemm_enabled) {
+        const uint64_t teams = (uint64_t)drain_grid(rt) * (kConsumerWarps / p.factor_w);
+        if ((uint64_t)count < teams * rt->cfg.factor_batch) p.split = kSplitMax;
+    }
     CK(launch_reset_ctl(rt->d_ctl, rt->stream));
     CK(launch_drain(p, drain_grid(rt), rt->stream));
     rt->launches += 2;
