@@ -939,6 +939,7 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
     const bool is_master = (A->flags & kActorRecreate) != 0;
     bool link_ended = false;
     bool ended = false;        // the actor is DONE (found so, or terminated here)
+    uint64_t handled = 0;      // messages handled, counted as completed after the release
     for (uint64_t i = 0; i < take + (carried ? 1 : 0); ++i) {
         MsgData m{};
         if (carried && i == 0) {
@@ -1032,15 +1033,17 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
             write_reply(m.reply_addr, 0, (uint64_t)(uint32_t)v, 0, m.tag, m.reply_token);
         }
         __syncwarp();
-        if (lane == 0) {
-            // everything this message did (its sends counted in ingested)
-            // is ordered before it counts as completed
-            asm volatile("fence.acq_rel.gpu;" ::: "memory");
-            add_u64(&P.ctl->messages, 1);
-            add_u64(&P.ctl->completed, 1);
-        }
+        ++handled;
     }
     release_actor(P, a, head, ended ? 1 : 0, !carried);
+    if (lane == 0 && handled) {
+        // everything these messages did (their sends counted in ingested) is
+        // ordered before they count as completed: by the release's fence.sc,
+        // or, for an actor that ended (no release fence), by this fence
+        if (ended) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        add_u64(&P.ctl->messages, handled);
+        add_u64(&P.ctl->completed, handled);
+    }
     carry = out;
     if (link_ended && lane == 0) {
         // the claim is released and nothing more is sent to a terminated
