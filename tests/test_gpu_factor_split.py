@@ -98,3 +98,22 @@ def test_split_setting_checked():
     with pytest.raises(C.CafGpuError) as e:
         C.Runtime(max_factor_n=(1 << 32) - 1, max_actors=4, factor_split=33)
     assert e.value.code == C.EINVAL
+
+
+@pytest.mark.parametrize("setting,split", [(0, True), (1, False)])
+def test_automatic_split_of_a_small_device_batch(setting, split):
+    """factor_split 0 (the default) splits the batches of a device batch that
+    is smaller than the drain's teams can take; 1 never splits.  One message
+    with factors in [2^30, 2^31): unsplit, one team of 8 warps sweeps it (8
+    factor items); split, more segments do.  The reply is exact either way."""
+    n, p, q = W.semiprimes(W.primes_uniform(W.stream_key(4245, 1), 2, 1 << 30, 1 << 31))
+    with C.Runtime(max_actors=4, factor_split=setting) as rt:
+        a = rt.spawn(C.FACTOR_U64)
+        rt.stats()
+        rep = device_batch(rt, np.array([a - 1], np.uint32), C.FACTOR_U64, n)
+        st = rt.stats()
+    assert rep["status"][0] == C.REPLY_OK and rep["r0"][0] == p[0] and rep["r1"][0] == q[0]
+    if split:
+        assert st["factor_items"] > 8
+    else:
+        assert st["factor_items"] == 8
