@@ -292,6 +292,45 @@ __device__ uint32_t warp_dequeue(const DrainParams &P, uint32_t a, uint64_t head
     return take;
 }
 
+// Wide dequeue (outside validation mode): of the next `want` (<= 128)
+// tickets, take the run of consecutive published slots starting at `head`;
+// lane i reads slots head + i + 32 j (j < 4), so one round of loads covers
+// 128 slots.  Returns the number taken, 0 if the slot at head is not
+// published yet (the caller then takes the waiting 32-wide path).  m[j] holds
+// slot head + i + 32 j for i + 32 j below the count.
+__device__ uint32_t warp_dequeue4(const DrainParams &P, uint32_t a, uint64_t head, uint32_t want,
+                                  MsgData (&m)[4]) {
+    const uint32_t lane = lane_id();
+    ActorDesc *A = &P.actors[a];
+    const Slot *s[4];
+    bool pub[4];
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) {
+        const uint64_t t = head + lane + 32 * j;
+        s[j] = &P.slots[A->slot_base + (t & A->cap_mask)];
+        pub[j] = lane + 32 * j < want && ld_acquire_gpu(&s[j]->seq) == t + 1;
+    }
+    uint32_t take = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) {
+        const uint32_t pm = __ballot_sync(FULL, pub[j]);
+        if (take == 32 * j) take += (pm == FULL) ? 32u : (uint32_t)(__ffs(~pm) - 1);
+    }
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) {
+        if (lane + 32 * j < take) {
+            m[j].payload = s[j]->payload;
+            m[j].reply_addr = s[j]->reply_addr;
+            m[j].tag = s[j]->tag;
+            m[j].sender = s[j]->sender;
+            m[j].sender_seq = s[j]->sender_seq;
+            m[j].kind = s[j]->kind;
+            m[j].reply_token = s[j]->reply_token;
+        }
+    }
+    return take;
+}
+
 // ---------------------------------------------------------------------------
 // Factorization batches
 // ---------------------------------------------------------------------------
@@ -1107,6 +1146,29 @@ __device__ __noinline__ void run_sink(const DrainParams &P, uint32_t a) {
     if (lane == 0) add_u64(&P.ctl->claims, 1);
     uint64_t count = A->sink_count, sum = A->sink_sum, handled = 0;
     while (left > 0) {
+        // up to 128 messages per round of loads (the 32-wide dequeue in
+        // validation mode, for its log, and to wait for an unpublished head)
+        if (!P.validation && left > 32) {
+            MsgData mw[4];
+            const uint32_t got = warp_dequeue4(P, a, head, left < 128 ? (uint32_t)left : 128u, mw);
+            if (got > 32) {
+                uint64_t v = 0;
+#pragma unroll
+                for (uint32_t j = 0; j < 4; ++j) {
+                    const uint32_t i = lane + 32 * j;
+                    if (i < got) {
+                        v += mw[j].payload;
+                        write_reply(mw[j].reply_addr, 0, count + i + 1, mw[j].payload, mw[j].tag, mw[j].reply_token);
+                    }
+                }
+                sum += warp_sum_u64(v);
+                count += got;
+                handled += got;
+                head += got;
+                left -= got;
+                continue;
+            }
+        }
         MsgData m{};
         const uint32_t got = warp_dequeue(P, a, head, left < 32 ? (uint32_t)left : 32u, m);
         if (got == 0) break;

@@ -166,6 +166,26 @@ def test_n_to_1_sources_into_one_sink():
     assert errs == []
 
 
+def test_n_to_1_totals_without_validation_mode():
+    """The N:1 experiment outside validation mode, where a SINK takes up to
+    128 messages per round of loads: every message counted exactly once, and
+    the sink's totals and the sources' replies match the oracle's."""
+    counts = [900 + 131 * i for i in range(40)]
+    with C.Runtime(max_factor_n=MAX32, max_actors=64, mailbox_capacity=4096) as rt:
+        sink = rt.spawn(C.SINK)
+        srcs = [rt.spawn(C.SOURCE, next=sink, mailbox_capacity=4) for _ in counts]
+        msgs = (C.Msg * len(srcs))()
+        for i, c in enumerate(counts):
+            msgs[i] = C.Runtime.msg(C.SOURCE, u64=c, tag=i)
+        h = rt.request_batch(np.array(srcs, np.uint64), msgs)
+        rep = rt.await_batch(h, timeout_ns=60_000_000_000)
+        rt.sync()
+        count, total = rt.sink_totals(sink)
+    assert np.all(rep["status"] == 0) and list(rep["r0"]) == counts
+    _, _, _, _, totals = A.source_streams([(s - 1, c, sink - 1) for s, c in zip(srcs, counts)])
+    assert (count, total) == totals[sink - 1]
+
+
 def test_sink_request_replies_count_in_handling_order():
     """Host requests to a SINK: replies are (position in the sink's handling
     order, value), positions 1..N in FIFO order of one sender."""
