@@ -160,6 +160,7 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
     for (;;) {
         // acquire: pairs with the consumer's release of head, so the slot's
         // previous message has been read before this write replaces it
+        bool published = false;
         if (pending && t - ld_acquire_gpu(&A->head) <= mask) {
             Slot *s = &P.slots[A->slot_base + (t & mask)];
             s->payload = m.payload;
@@ -171,16 +172,25 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
             s->reply_token = m.reply_token;
             st_release_gpu(&s->seq, t + 1);
             pending = false;
+            published = true;
         }
-        __syncwarp();
-        // wake the receiver (fence: Dekker pattern with release_actor)
-        asm volatile("fence.sc.gpu;" ::: "memory");
+        // wake a receiver to which this round published (fence: Dekker
+        // pattern with release_actor).  A round that published nothing has
+        // nothing to wake for: its lanes wait for room in a full mailbox,
+        // whose receiver is ready or running.  The state is read first and
+        // only a WAITING receiver is CASed: either this read sees WAITING, or
+        // the receiver's release sees the tail these tickets advanced.
+        __syncwarp();   // every lane's slot writes before the leader's state check
+        const uint32_t pubm = __ballot_sync(FULL, published);
         bool qok = true;
         bool woke = false;
-        if (valid && (int)lane == leader) {
-            if (cas_acq_rel_gpu(&A->state, kWaiting, kReady) == kWaiting) {
-                if (handoff) woke = true;
-                else qok = ready_push(P, a);
+        if (pubm) {
+            asm volatile("fence.sc.gpu;" ::: "memory");
+            if (valid && (int)lane == leader && (pubm & peers) && ld_relaxed_gpu(&A->state) == kWaiting) {
+                if (cas_acq_rel_gpu(&A->state, kWaiting, kReady) == kWaiting) {
+                    if (handoff) woke = true;
+                    else qok = ready_push(P, a);
+                }
             }
         }
         if (handoff) {
@@ -292,42 +302,45 @@ __device__ uint32_t warp_dequeue(const DrainParams &P, uint32_t a, uint64_t head
     return take;
 }
 
-// Wide dequeue (outside validation mode): of the next `want` (<= 128)
+// SINK `a`'s wide take (outside validation mode): of the next `want` (<= 128)
 // tickets, take the run of consecutive published slots starting at `head`;
 // lane i reads slots head + i + 32 j (j < 4), so one round of loads covers
-// 128 slots.  Returns the number taken, 0 if the slot at head is not
-// published yet (the caller then takes the waiting 32-wide path).  m[j] holds
-// slot head + i + 32 j for i + 32 j below the count.
-__device__ uint32_t warp_dequeue4(const DrainParams &P, uint32_t a, uint64_t head, uint32_t want,
-                                  MsgData (&m)[4]) {
+// 128 slots.  Each taken message is handled as the SINK's (count + its
+// position + 1)-th: its reply is written and its value added to the lane's
+// *vsum.  Returns the number taken, 0 if the slot at head is not published
+// yet (the caller then takes the waiting 32-wide path).
+__device__ __noinline__ uint32_t sink_take_wide(const DrainParams &P, uint32_t a, uint64_t head, uint32_t want,
+                                                uint64_t count, uint64_t *vsum) {
     const uint32_t lane = lane_id();
-    ActorDesc *A = &P.actors[a];
-    const Slot *s[4];
-    bool pub[4];
-#pragma unroll
-    for (uint32_t j = 0; j < 4; ++j) {
-        const uint64_t t = head + lane + 32 * j;
-        s[j] = &P.slots[A->slot_base + (t & A->cap_mask)];
-        pub[j] = lane + 32 * j < want && ld_acquire_gpu(&s[j]->seq) == t + 1;
-    }
+    const ActorDesc *A = &P.actors[a];
+    const uint64_t base = A->slot_base, cmask = A->cap_mask;
     uint32_t take = 0;
 #pragma unroll
     for (uint32_t j = 0; j < 4; ++j) {
-        const uint32_t pm = __ballot_sync(FULL, pub[j]);
+        const uint64_t t = head + lane + 32 * j;
+        const bool pub = lane + 32 * j < want && ld_acquire_gpu(&P.slots[base + (t & cmask)].seq) == t + 1;
+        const uint32_t pm = __ballot_sync(FULL, pub);
         if (take == 32 * j) take += (pm == FULL) ? 32u : (uint32_t)(__ffs(~pm) - 1);
     }
+    // the four slots' values and reply addresses in one round of loads
+    uint64_t x[4], ra[4];
 #pragma unroll
     for (uint32_t j = 0; j < 4; ++j) {
-        if (lane + 32 * j < take) {
-            m[j].payload = s[j]->payload;
-            m[j].reply_addr = s[j]->reply_addr;
-            m[j].tag = s[j]->tag;
-            m[j].sender = s[j]->sender;
-            m[j].sender_seq = s[j]->sender_seq;
-            m[j].kind = s[j]->kind;
-            m[j].reply_token = s[j]->reply_token;
+        const uint32_t i = lane + 32 * j;
+        const Slot *sl = &P.slots[base + ((head + i) & cmask)];
+        x[j] = i < take ? sl->payload : 0;
+        ra[j] = i < take ? sl->reply_addr : 0;
+    }
+    uint64_t v = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) {
+        v += x[j];
+        if (ra[j]) {
+            const Slot *sl = &P.slots[base + ((head + lane + 32 * j) & cmask)];
+            write_reply(ra[j], 0, count + lane + 32 * j + 1, x[j], sl->tag, sl->reply_token);
         }
     }
+    *vsum = v;
     return take;
 }
 
@@ -1149,18 +1162,9 @@ __device__ __noinline__ void run_sink(const DrainParams &P, uint32_t a) {
         // up to 128 messages per round of loads (the 32-wide dequeue in
         // validation mode, for its log, and to wait for an unpublished head)
         if (!P.validation && left > 32) {
-            MsgData mw[4];
-            const uint32_t got = warp_dequeue4(P, a, head, left < 128 ? (uint32_t)left : 128u, mw);
-            if (got > 32) {
-                uint64_t v = 0;
-#pragma unroll
-                for (uint32_t j = 0; j < 4; ++j) {
-                    const uint32_t i = lane + 32 * j;
-                    if (i < got) {
-                        v += mw[j].payload;
-                        write_reply(mw[j].reply_addr, 0, count + i + 1, mw[j].payload, mw[j].tag, mw[j].reply_token);
-                    }
-                }
+            uint64_t v = 0;
+            const uint32_t got = sink_take_wide(P, a, head, left < 128 ? (uint32_t)left : 128u, count, &v);
+            if (got > 0) {   // handled (replies written): 0 only when head is unpublished
                 sum += warp_sum_u64(v);
                 count += got;
                 handled += got;
