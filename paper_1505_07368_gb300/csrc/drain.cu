@@ -163,13 +163,10 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
         bool published = false;
         if (pending && t - ld_acquire_gpu(&A->head) <= mask) {
             Slot *s = &P.slots[A->slot_base + (t & mask)];
+            // the slot's fields in three stores (bytes 8, 16..31, 32..47)
             s->payload = m.payload;
-            s->reply_addr = m.reply_addr;
-            s->tag = m.tag;
-            s->sender = m.sender;
-            s->sender_seq = m.sender_seq;
-            s->kind = m.kind;
-            s->reply_token = m.reply_token;
+            *reinterpret_cast<ulonglong2 *>(&s->reply_addr) = make_ulonglong2(m.reply_addr, m.tag);
+            *reinterpret_cast<uint4 *>(&s->sender) = make_uint4(m.sender, m.sender_seq, m.kind, m.reply_token);
             st_release_gpu(&s->seq, t + 1);
             pending = false;
             published = true;
@@ -291,12 +288,14 @@ __device__ uint32_t warp_dequeue(const DrainParams &P, uint32_t a, uint64_t head
     const uint32_t take = (pm == FULL) ? 32u : (uint32_t)(__ffs(~pm) - 1);
     if (lane < take) {
         m.payload = s->payload;
-        m.reply_addr = s->reply_addr;
-        m.tag = s->tag;
-        m.sender = s->sender;
-        m.sender_seq = s->sender_seq;
-        m.kind = s->kind;
-        m.reply_token = s->reply_token;
+        const ulonglong2 rt = *reinterpret_cast<const ulonglong2 *>(&s->reply_addr);
+        const uint4 sk = *reinterpret_cast<const uint4 *>(&s->sender);
+        m.reply_addr = rt.x;
+        m.tag = rt.y;
+        m.sender = sk.x;
+        m.sender_seq = sk.y;
+        m.kind = sk.z;
+        m.reply_token = sk.w;
     }
     if (P.validation) log_rows(P, a, take, m);
     return take;

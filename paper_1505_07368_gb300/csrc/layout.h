@@ -277,6 +277,8 @@ struct Slot {                      // 64 bytes
     uint64_t pad[2];
 };
 static_assert(sizeof(Slot) == 64, "Slot is 64 bytes");
+static_assert(offsetof(Slot, reply_addr) % 16 == 0 && offsetof(Slot, sender) % 16 == 0,
+              "reply_addr..tag and sender..reply_token are 16-byte vectors");
 
 // Reply record, same layout as caf_gpu_dreply (32 bytes).
 struct Reply {
