@@ -691,39 +691,136 @@ __device__ void group_consume(const DrainParams &P, GroupShared &G, const TableT
     }
 }
 
-// Claim factor actor `a`: move up to K - c0 of its messages into batch b at
-// positions c0.. (a batch may hold the messages of several actors: replies go
-// to each message's own reply record, and each actor's messages enter in its
-// mailbox order).  Releases the actor; returns the batch's new count.
-__device__ uint32_t claim_factor_take(const DrainParams &P, uint32_t a, uint32_t b, uint32_t c0) {
+// Claim factor actor `a`: move up to cap - pos of its messages into a group
+// of batch records, message q of the group at slot q % K of record q / K
+// (lane r of `recs` holds the group's record r).  A batch may hold the
+// messages of several actors: replies go to each message's own reply record,
+// and each actor's messages enter in its mailbox order.  Releases the actor;
+// returns the group's new message count.
+__device__ uint32_t claim_factor_take(const DrainParams &P, uint32_t a, uint32_t recs, uint32_t pos,
+                                      uint32_t cap) {
     const uint32_t lane = lane_id();
+    const uint32_t K = P.factor_k;
     ActorDesc *A = &P.actors[a];
     if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
     __syncwarp();
     const uint64_t head = *((volatile uint64_t *)&A->head);
     const uint64_t tail = ld_acquire_gpu(&A->tail);
-    uint32_t limit = P.factor_k - c0;
+    uint32_t limit = cap - pos;
     if (P.max_claim && P.max_claim < limit) limit = P.max_claim;
+    // at most one mailbox's worth: a sender holding a ticket past head + capacity
+    // publishes only after this claim has released the head
+    if (A->cap_mask < limit - 1) limit = A->cap_mask + 1;
     const uint64_t avail = tail - head;
     const uint32_t want = avail < limit ? (uint32_t)avail : limit;
-    MsgData m{};
-    const uint32_t take = want ? warp_dequeue(P, a, head, want, m) : 0u;
-    release_actor(P, a, head + take, 0);
-    if (lane == 0) add_u64(&P.ctl->claims, 1);
-    FactorBatch *B = &P.batches[b];
-    if (lane < take) {
-        const uint32_t i = c0 + lane;
-        const uint64_t n = m.payload;
-        const bool even = (n >= 4) && !(n & 1u);
-        B->n[i] = n;
-        B->pbound[i] = even ? 0 : factor_bound(P.primes, P.nprimes, n);
-        B->found[i] = kNoFactor;
-        B->reply_addr[i] = m.reply_addr;
-        B->reply_token[i] = m.reply_token;
-        B->tag[i] = m.tag;
+    uint32_t took = 0;
+    while (took < want) {
+        const uint32_t w = min(want - took, 32u);
+        MsgData m{};
+        const uint32_t take = warp_dequeue(P, a, head + took, w, m);
+        const uint32_t q = pos + took + lane;
+        const uint32_t rec = __shfl_sync(FULL, recs, min(q / K, 31u));
+        if (lane < take) {
+            FactorBatch *B = &P.batches[rec];
+            const uint32_t i = q % K;
+            const uint64_t n = m.payload;
+            const bool even = (n >= 4) && !(n & 1u);
+            B->n[i] = n;
+            B->pbound[i] = even ? 0 : factor_bound(P.primes, P.nprimes, n);
+            B->found[i] = kNoFactor;
+            B->reply_addr[i] = m.reply_addr;
+            B->reply_token[i] = m.reply_token;
+            B->tag[i] = m.tag;
+        }
+        took += take;
+        if (take < w) break;
     }
+    release_actor(P, a, head + took, 0);
+    if (lane == 0) add_u64(&P.ctl->claims, 1);
     __syncwarp();
-    return c0 + take;
+    return pos + took;
+}
+
+// Reorder the `count` messages of a claim's group of records by n, so that
+// each batch holds messages of similar size.  A batch is swept until its
+// last message is decided, and the smallest factor of a number tends to grow
+// with the number, so batches of similar n leave fewer slots idle.  Lane e %
+// 32 ranks messages e (ties by position), all fields are read, and after the
+// warp barrier each is written to the slot of its rank (found is still
+// kNoFactor everywhere).
+constexpr uint32_t kGroupRecords = 8;     // batch records one factor claim may fill
+constexpr uint32_t kGroupMessages = 128;  // messages one factor claim may take
+__device__ __noinline__ void factor_group_sort(const DrainParams &P, uint32_t recs, uint32_t count) {
+    const uint32_t lane = lane_id();
+    const uint32_t K = P.factor_k;
+    constexpr int J = kGroupMessages / 32;
+    uint64_t key[J];
+    uint32_t rank[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const uint32_t e = lane + 32u * j;
+        const uint32_t rec = __shfl_sync(FULL, recs, min(e / K, 31u));
+        key[j] = e < count ? P.batches[rec].n[e % K] : ~0ull;
+        rank[j] = 0;
+    }
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) {
+        if (32u * jj >= count) break;
+        for (uint32_t src = 0; src < 32; ++src) {
+            const uint64_t kf = __shfl_sync(FULL, key[jj], src);
+            const uint32_t f = src + 32u * jj;
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const uint32_t e = lane + 32u * j;
+                rank[j] += (f < count && (kf < key[j] || (kf == key[j] && f < e))) ? 1u : 0u;
+            }
+        }
+    }
+    // move the fields one at a time: each pass reads all its values before
+    // the warp barrier and writes them after it
+    uint32_t dst[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const uint32_t e = lane + 32u * j;
+        const uint32_t r = e < count ? rank[j] : 0u;
+        dst[j] = __shfl_sync(FULL, recs, min(r / K, 31u)) * kFactorKMax + r % K;
+    }
+    auto slot_of = [&](uint32_t e) {
+        return __shfl_sync(FULL, recs, min(e / K, 31u)) * kFactorKMax + e % K;
+    };
+#pragma unroll 1
+    for (int f = 0; f < 5; ++f) {
+        uint64_t v[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const uint32_t e = lane + 32u * j;
+            const uint32_t src = slot_of(e);
+            const FactorBatch *B = &P.batches[src / kFactorKMax];
+            const uint32_t i = src % kFactorKMax;
+            v[j] = key[j];
+            if (e < count) {
+                if (f == 1) v[j] = B->pbound[i];
+                else if (f == 2) v[j] = B->reply_addr[i];
+                else if (f == 3) v[j] = B->reply_token[i];
+                else if (f == 4) v[j] = B->tag[i];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const uint32_t e = lane + 32u * j;
+            if (e < count) {
+                FactorBatch *B = &P.batches[dst[j] / kFactorKMax];
+                const uint32_t i = dst[j] % kFactorKMax;
+                if (f == 0) B->n[i] = v[j];
+                else if (f == 1) B->pbound[i] = (uint32_t)v[j];
+                else if (f == 2) B->reply_addr[i] = v[j];
+                else if (f == 3) B->reply_token[i] = (uint32_t)v[j];
+                else B->tag[i] = v[j];
+            }
+        }
+        __syncwarp();
+    }
 }
 
 // Start the sweep of batch b holding `count` messages: record it, split it
@@ -2015,12 +2112,104 @@ __device__ __noinline__ void drain_mandel_bands(const DrainParams &P, GroupShare
 // A team leader looks for a factor batch to sweep: pop ready actors, claim
 // factor actors into a fresh batch record, and run ring-token actors on the
 // way (a few at most, so the group forms quickly).
+// Claim factor actor `a` (popped from the ready queue, kind checked) into
+// batch records.  While more actors are ready than teams are idle, the claim
+// fills a group of up to kGroupRecords records: messages of `a`, then of up to
+// kTopUpTries further ready factor actors, reordered by n (factor_group_sort).
+// The caller's team sweeps the group's last batch; the others go to the
+// queue of batches waiting for a team.  Otherwise the claim fills one record
+// from `a` alone.  With no record free the actor stays READY.  Returns the
+// batch the caller's team sweeps, or kNone.
+template <bool kSplit>
+__device__ __noinline__ uint32_t claim_factor_group(const DrainParams &P, uint32_t a, uint32_t rng) {
+    const uint32_t lane = lane_id();
+    DevCtl *ctl = P.ctl;
+    const uint32_t K = P.factor_k;
+    bool topup = false;
+    if (lane == 0) {
+        const int64_t teams = (int64_t)gridDim.x * (kConsumerWarps / P.factor_w);
+        const int64_t busy = (int64_t)P.n_batches - q_len(&ctl->freeq);
+        topup = q_len(&ctl->readyq) > teams - busy;
+    }
+    topup = __shfl_sync(FULL, topup, 0);
+    const uint32_t want = topup ? min(kGroupRecords, kGroupMessages / K) : 1u;
+    uint32_t b = kNone;
+    bool gb = false;
+    if (lane < want) {
+        const int pr = q_try_pop(&ctl->freeq, P.freeq, &b, P.wait_limit_ns);
+        if (pr < 0) fail(P, kErrWaitQueue, 23);
+        gb = pr > 0;
+        if (gb && P.validation && b >= P.n_batches) {
+            bounds_fail(P, 44, b, P.n_batches);
+            gb = false;
+        }
+    }
+    const uint32_t gm = __ballot_sync(FULL, gb);
+    if (gm == 0) {
+        // no batch record free: leave the actor READY for later
+        if (lane == 0 && !ready_push(P, a)) fail(P, kErrWaitQueue, 7);
+        __syncwarp();
+        return kNone;
+    }
+    // lane r < ng holds the group's record r (the records popped, in lane order)
+    const uint32_t ng = __popc(gm);
+    uint32_t m = gm;
+    for (uint32_t i = 0; i < lane && i < ng; ++i) m &= m - 1;
+    const uint32_t recs = __shfl_sync(FULL, b, lane < ng ? (uint32_t)(__ffs(m) - 1) : 0u);
+    const uint32_t cap = ng * K;
+    uint32_t count = claim_factor_take(P, a, recs, 0, cap);
+    // top the group up with the messages of further ready factor actors (an
+    // actor of another kind goes back to the ready queue)
+    for (uint32_t extra = 0; topup && extra < kTopUpTries && count < cap; ++extra) {
+        uint32_t a2 = 0;
+        bool got2 = false;
+        if (lane == 0) {
+            const int pr = ready_pop(P, &a2, rng);
+            if (pr < 0) fail(P, kErrWaitQueue, 36);
+            got2 = pr > 0;
+        }
+        if (!__shfl_sync(FULL, got2, 0)) break;
+        a2 = __shfl_sync(FULL, a2, 0);
+        if (P.validation && !actor_ok(P, a2)) {
+            if (lane == 0) bounds_fail(P, 46, a2, P.n_actors);
+            break;
+        }
+        if (P.actors[a2].kind != kFactor) {
+            if (lane == 0 && !ready_push(P, a2)) fail(P, kErrWaitQueue, 37);
+            __syncwarp();
+            break;
+        }
+        count = claim_factor_take(P, a2, recs, count, cap);
+    }
+    if (ng > 1 && count > K) factor_group_sort(P, recs, count);
+    // launch each record; all but the last launched batch wait in the queue
+    uint32_t mine = kNone;
+    for (uint32_t r = 0; r < ng; ++r) {
+        const uint32_t br = __shfl_sync(FULL, recs, r);
+        const uint32_t cr = count > r * K ? min(count - r * K, K) : 0u;
+        const uint32_t got = factor_batch_launch<kSplit>(P, br, cr);
+        if (got == kNone) continue;
+        if (mine != kNone) {
+            // the record is complete before another team can take it
+            __threadfence();
+            bool ok = true;
+            if (lane == 0) ok = q_push(&ctl->segq, P.segq, mine, P.wait_limit_ns);
+            if (!__shfl_sync(FULL, ok, 0)) {
+                if (lane == 0) fail(P, kErrWaitQueue, 38);
+                return kNone;
+            }
+        }
+        mine = got;
+    }
+    return mine;
+}
+
 template <bool kGemm, bool kSplit>
 __device__ uint32_t find_batch(const DrainParams &P, uint32_t &rng) {
     const uint32_t lane = lane_id();
     DevCtl *ctl = P.ctl;
-    if (kSplit) {
-        // a segment of a split batch waiting for a team comes first
+    {
+        // a batch (or a segment of a split batch) waiting for a team comes first
         uint32_t item = kNone;
         if (lane == 0) {
             const int pr = q_try_pop(&ctl->segq, P.segq, &item, P.wait_limit_ns);
@@ -2051,60 +2240,9 @@ __device__ uint32_t find_batch(const DrainParams &P, uint32_t &rng) {
         }
         const uint32_t kind = P.actors[a].kind;
         if (kind == kFactor) {
-            uint32_t b = 0;
-            bool gb = false;
-            if (lane == 0) {
-                const int pr = q_try_pop(&ctl->freeq, P.freeq, &b, P.wait_limit_ns);
-                if (pr < 0) fail(P, kErrWaitQueue, 23);
-                gb = pr > 0;
-            }
-            gb = __shfl_sync(FULL, gb, 0);
-            if (!gb) {
-                // no batch record free: leave the actor READY for later
-                if (lane == 0 && !ready_push(P, a)) fail(P, kErrWaitQueue, 7);
-                __syncwarp();
-                return kNone;
-            }
-            b = __shfl_sync(FULL, b, 0);
-            if (P.validation && b >= P.n_batches) {
-                if (lane == 0) bounds_fail(P, 44, b, P.n_batches);
-                return kNone;
-            }
-            uint32_t count = claim_factor_take(P, a, b, 0);
-            // top a partial batch up with the messages of further ready factor
-            // actors, so the teams that share a table stream start with full
-            // batches (an actor of another kind goes back to the ready queue).
-            // Only while more actors are ready than teams are idle: with idle
-            // teams, messages spread over teams finish sooner than in one batch.
-            bool topup = false;
-            if (lane == 0 && count < P.factor_k) {
-                const int64_t teams = (int64_t)gridDim.x * (kConsumerWarps / P.factor_w);
-                const int64_t busy = (int64_t)P.n_batches - q_len(&ctl->freeq);
-                topup = q_len(&ctl->readyq) > teams - busy;
-            }
-            topup = __shfl_sync(FULL, topup, 0);
-            for (uint32_t extra = 0; topup && extra < kTopUpTries && count < P.factor_k; ++extra) {
-                uint32_t a2 = 0;
-                bool got2 = false;
-                if (lane == 0) {
-                    const int pr = ready_pop(P, &a2, rng);
-                    if (pr < 0) fail(P, kErrWaitQueue, 36);
-                    got2 = pr > 0;
-                }
-                if (!__shfl_sync(FULL, got2, 0)) break;
-                a2 = __shfl_sync(FULL, a2, 0);
-                if (P.validation && !actor_ok(P, a2)) {
-                    if (lane == 0) bounds_fail(P, 46, a2, P.n_actors);
-                    break;
-                }
-                if (P.actors[a2].kind != kFactor) {
-                    if (lane == 0 && !ready_push(P, a2)) fail(P, kErrWaitQueue, 37);
-                    __syncwarp();
-                    break;
-                }
-                count = claim_factor_take(P, a2, b, count);
-            }
-            const uint32_t r = factor_batch_launch<kSplit>(P, b, count);
+            // (the work-stealing scheduler's victim choice: a fresh draw here)
+            const uint32_t r = claim_factor_group<kSplit>(P, a, rng);
+            rng = rng * 1664525u + 1013904223u;
             if (r != kNone) return r;
         } else if (kind == kToken) {
             claim_ring(P, a);
