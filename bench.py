@@ -45,7 +45,7 @@ WORKLOAD = ("batched factorization actors: 1024 actors, geometric(mean 64) mailb
             "semiprimes with prime factors in [2^24, 2^28), one persistent launch per step")
 L2_FLUSH_BYTES = 256 << 20
 IMAD_PER_SM_CLK = 64          # 32-bit integer multiply(-add) lanes per SM per clock
-FACTOR_DRAM_BYTES_PER_MSG = (119.499094e9 + 13.419008e6) / 32768   # ncu, the factor drain (see its roofline)
+FACTOR_DRAM_BYTES_PER_MSG = (120.189017e9 + 22.784768e6) / 65162   # ncu, the factor drain (see its roofline)
 MULS_PER_TEST = 3             # the Montgomery divisibility test: m0, n + m0*p, m1
 
 
@@ -376,15 +376,15 @@ def run_ours(args):
     peak_tops = sm_count * IMAD_PER_SM_CLK * sm_max * 1e6 / 1e12
     achieved_tops = MULS_PER_TEST * tests_alg / (dev_s / args.steps) / 1e12
     # DRAM traffic per launch: the drain's dram__bytes_read.sum + dram__bytes_write.sum from one
-    # ncu capture of this workload's first 32,768 messages (the current sweep, K=16, W=8, 2
-    # CTAs/SM), scaled by this step's messages: the table stream is one pass per batch, so it
-    # grows with the messages.  Other settings: not captured (null).
+    # ncu capture (one-pass counters) of this workload's full launch with the current sweep (K=16,
+    # W=8, 2 CTAs/SM), per message, times this step's messages.  Other settings: not captured
+    # (null).
     traffic = None
     if (args.factor_batch, args.factor_warps, args.ctas_per_sm, args.factor_split) == (16, 8, 2, 0):
         traffic = FACTOR_DRAM_BYTES_PER_MSG * count
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tmul/s",
                 "frac": achieved_tops / peak_tops, "traffic": traffic,
-                "traffic_basis": "bytes per launch, scaled from a 32,768-message ncu capture" if traffic else None,
+                "traffic_basis": "bytes per launch: ncu capture of the full 65,162-message launch, per message" if traffic else None,
                 "kernel": "k_drain", "algorithmic_tests_per_step": tests_alg,
                 "executed_tests_per_step": st["prime_tests"] / args.steps,
                 "peak_basis": f"{sm_count} SMs (device attribute) x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz (sm_max_mhz of measured)"}

@@ -121,3 +121,26 @@ def test_config2_subsample_certificates():
         assert oracle.check_certificate(int(wl.n[i]), int(rep["r0"][i]), int(rep["r1"][i]), 0)
     sub = np.arange(0, wl.count, 1500)
     _assert_same(rep[sub], wl.n[sub])
+
+
+@pytest.mark.parametrize("ingress", ["live", "device"])
+def test_grouped_claims_with_small_mailboxes(ingress):
+    """Claims that group several batches and sort them by n, with 16-slot mailboxes
+    and more messages per actor than a mailbox holds (a claim takes at most one
+    mailbox's worth), duplicate n values (ties), primes and even numbers."""
+    n_act, per = 384, 40
+    _, p, q = W.semiprimes(W.primes_loguniform(W.stream_key(97, 2), 2 * n_act * per, 1 << 10, 1 << 20))
+    n = (p.astype(np.uint64) * q.astype(np.uint64))[: n_act * per].copy()
+    d = n[3::7].size
+    n[0:7 * d:7] = n[3::7]               # duplicates: equal keys in one claim
+    n[5::11] = W.primes_uniform(W.stream_key(97, 3), n[5::11].size, 1 << 20, 1 << 30)
+    n[9::13] = 2 * (n[9::13] // 2 + 1)
+    actors = np.arange(n.size, dtype=np.int64) % n_act
+    with C.Runtime(max_factor_n=MAX40, max_actors=n_act, mailbox_capacity=16) as rt:
+        ids = [rt.spawn(C.FACTOR_U64) for _ in range(n_act)]
+        if ingress == "live":
+            rep = host_requests(rt, np.asarray(ids, dtype=np.uint64)[actors], C.FACTOR_U64, n)
+        else:
+            rep = device_batch(rt, actors.astype(np.uint32), C.FACTOR_U64, n)
+        assert rt.stats()["error_word"] == 0
+    _assert_same(rep, n)
