@@ -45,7 +45,7 @@ WORKLOAD = ("batched factorization actors: 1024 actors, geometric(mean 64) mailb
             "semiprimes with prime factors in [2^24, 2^28), one persistent launch per step")
 L2_FLUSH_BYTES = 256 << 20
 IMAD_PER_SM_CLK = 64          # 32-bit integer multiply(-add) lanes per SM per clock
-FACTOR_DRAM_BYTES_PER_MSG = (120.189017e9 + 22.784768e6) / 65162   # ncu, the factor drain (see its roofline)
+FACTOR_DRAM_BYTES_PER_MSG = (111.944865e9 + 23.120384e6) / 65162   # ncu, the factor drain (see its roofline)
 MULS_PER_TEST = 3             # the Montgomery divisibility test: m0, n + m0*p, m1
 
 

@@ -748,8 +748,8 @@ __device__ uint32_t claim_factor_take(const DrainParams &P, uint32_t a, uint32_t
 // 32 ranks messages e (ties by position), all fields are read, and after the
 // warp barrier each is written to the slot of its rank (found is still
 // kNoFactor everywhere).
-constexpr uint32_t kGroupRecords = 8;     // batch records one factor claim may fill
-constexpr uint32_t kGroupMessages = 128;  // messages one factor claim may take
+constexpr uint32_t kGroupRecords = 16;    // batch records one factor claim may fill
+constexpr uint32_t kGroupMessages = 256;  // messages one factor claim may take
 __device__ __noinline__ void factor_group_sort(const DrainParams &P, uint32_t recs, uint32_t count) {
     const uint32_t lane = lane_id();
     const uint32_t K = P.factor_k;
