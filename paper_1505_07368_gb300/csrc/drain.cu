@@ -933,8 +933,33 @@ struct Carry {
 // origin (the actor id + 1 in the payload's high word), and its tag names the
 // ring, the incarnation and the receiver's position: master + 1 in bits 0..31,
 // the incarnation in bits 32..39, the position in bits 40..63.
+// Counters of a chain of ring runs, kept in registers (warp-uniform) and
+// added to the device counters every kTallyHops runs and at the chain's end.
+// Only statistics and `completed` wait here: `ingested` is counted at each
+// send, so `completed` can only lag it and never makes the drain look
+// quiescent while a token is in flight.
+struct RingTally {
+    uint32_t done, claims, sends;
+};
+constexpr uint32_t kTallyHops = 32;
+__device__ void ring_tally_flush(const DrainParams &P, RingTally &tl) {
+    if (lane_id() == 0 && (tl.done | tl.claims | tl.sends)) {
+        // everything the counted messages did (their sends counted in
+        // ingested) is ordered before they count as completed
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        if (tl.sends) add_u64(&P.ctl->device_sends, tl.sends);
+        if (tl.claims) add_u64(&P.ctl->claims, tl.claims);
+        if (tl.done) {
+            add_u64(&P.ctl->messages, tl.done);
+            add_u64(&P.ctl->completed, tl.done);
+        }
+    }
+    tl = RingTally{0, 0, 0};
+    __syncwarp();
+}
+
 __device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v, uint32_t *handoff, Carry *carry,
-                             uint32_t origin1 = 0) {
+                             RingTally &tl, uint32_t origin1 = 0) {
     ActorDesc *A = &P.actors[a];
     const uint32_t next = A->next;
     MsgData m{};
@@ -950,7 +975,7 @@ __device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v, uint32
                 ((uint64_t)recv << 40);
     }
     const uint32_t lane = lane_id();
-    if (lane == 0) add_u64(&P.ctl->device_sends, 1);
+    tl.sends += 1;
     if (carry && !carry->has && next != a) {
         bool direct = false;
         uint64_t h = 0;
@@ -1055,7 +1080,7 @@ __device__ bool ring_incarnation_over(const DrainParams &P, uint32_t a) {
 // successor this warp woke or claimed (to be run next by the same warp) or
 // kNone; a token carried to that successor is left in `carry`.  With
 // `direct` false every forward goes through the mailbox.
-__device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carry, bool direct) {
+__device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carry, bool direct, RingTally &tl) {
     const uint32_t lane = lane_id();
     uint32_t handoff = kNone;
     ActorDesc *A = &P.actors[a];
@@ -1078,7 +1103,7 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
         if (take > (uint64_t)A->cap_mask + 1) take = (uint64_t)A->cap_mask + 1;
         if (P.max_claim && take > P.max_claim) take = P.max_claim;
     }
-    if (lane == 0) add_u64(&P.ctl->claims, 1);
+    tl.claims += 1;
     Carry out{};
     out.has = false;
     // a ring that a RECREATE master creates: the 0 stops by its origin, and a
@@ -1132,12 +1157,12 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
             __syncwarp();
             if (run_next) {
                 const int32_t v0 = (int32_t)(uint32_t)A->sink_count;
-                ok = ring_spawn(P, a) && ring_emit_factor(P, a) && ring_forward(P, a, v0, &handoff, cp);
+                ok = ring_spawn(P, a) && ring_emit_factor(P, a) && ring_forward(P, a, v0, &handoff, cp, tl);
             }
         } else if ((m.kind >> 16) & kMsgStart) {
-            ok = ring_emit_factor(P, a) && ring_forward(P, a, v, &handoff, cp);
+            ok = ring_emit_factor(P, a) && ring_forward(P, a, v, &handoff, cp, tl);
         } else if (v > 0) {
-            ok = ring_emit_factor(P, a) && ring_forward(P, a, v - 1, &handoff, cp);
+            ok = ring_emit_factor(P, a) && ring_forward(P, a, v - 1, &handoff, cp, tl);
         } else if (recreated) {
             // the 0 went once around from its origin: stop before reaching it
             // again (the same actors as "unless the successor has terminated",
@@ -1148,7 +1173,7 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
             link_ended = !is_master;
             ended |= !is_master;
             if (A->next + 1 != origin1) {
-                ok = ring_forward(P, a, 0, &handoff, cp, origin1);
+                ok = ring_forward(P, a, 0, &handoff, cp, tl, origin1);
             } else if (!is_master) {
                 // the 0 stops here: every other actor of the incarnation has
                 // terminated, so tell the master (a send of this message, so
@@ -1156,12 +1181,12 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
                 MsgData d{};
                 d.kind = kToken | (kMsgRingDone << 16);
                 d.sender = 0x80000000u | a;
-                if (lane == 0) add_u64(&P.ctl->device_sends, 1);
+                tl.sends += 1;
                 ok = warp_enqueue(P, lane == 0, A->ring_master, d);
             } else if (ring_incarnation_over(P, a)) {
                 // the master is the last to terminate: start the next incarnation
                 const int32_t v0 = (int32_t)(uint32_t)A->sink_count;
-                ok = ring_spawn(P, a) && ring_emit_factor(P, a) && ring_forward(P, a, v0, &handoff, cp);
+                ok = ring_spawn(P, a) && ring_emit_factor(P, a) && ring_forward(P, a, v0, &handoff, cp, tl);
             } else {
                 ended = true;
             }
@@ -1171,7 +1196,7 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
             uint32_t succ_state = 0;
             if (lane == 0) succ_state = *((volatile uint32_t *)&P.actors[A->next].state);
             succ_state = __shfl_sync(FULL, succ_state, 0);
-            if (succ_state != kDone) ok = ring_forward(P, a, 0, &handoff, cp);
+            if (succ_state != kDone) ok = ring_forward(P, a, 0, &handoff, cp, tl);
         }
         if (!ok) return kNone;
         if (rejected) {
@@ -1184,14 +1209,8 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
         ++handled;
     }
     release_actor(P, a, head, ended ? 1 : 0, !carried);
-    if (lane == 0 && handled) {
-        // everything these messages did (their sends counted in ingested) is
-        // ordered before they count as completed: by the release's fence.sc,
-        // or, for an actor that ended (no release fence), by this fence
-        if (ended) asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        add_u64(&P.ctl->messages, handled);
-        add_u64(&P.ctl->completed, handled);
-    }
+    // counted as completed at the chain's next tally flush (after its fence)
+    tl.done += (uint32_t)handled;
     carry = out;
     if (link_ended && lane == 0) {
         // the claim is released and nothing more is sent to a terminated
@@ -1212,10 +1231,13 @@ __device__ void claim_ring(const DrainParams &P, uint32_t a) {
     uint32_t cur = a;
     Carry carry{};
     carry.has = false;
+    RingTally tl{0, 0, 0};
     for (int i = 0; cur != kNone && i < kMaxChain && ((i & 7) != 0 || !exit_requested(P.ctl)); ++i) {
-        cur = run_ring_actor(P, cur, carry, i + 1 < kMaxChain);
+        cur = run_ring_actor(P, cur, carry, i + 1 < kMaxChain, tl);
         if ((i & 255) == 0 && lane_id() == 0) heartbeat(P);
+        if ((uint32_t)(i + 1) % kTallyHops == 0) ring_tally_flush(P, tl);
     }
+    ring_tally_flush(P, tl);
     if (cur != kNone && lane_id() == 0 && !ready_push(P, cur))
         fail(P, kErrWaitQueue, 18);
     __syncwarp();
