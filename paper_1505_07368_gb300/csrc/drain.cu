@@ -935,18 +935,24 @@ struct Carry {
 // the incarnation in bits 32..39, the position in bits 40..63.
 // Counters of a chain of ring runs, kept in registers (warp-uniform) and
 // added to the device counters every kTallyHops runs and at the chain's end.
-// Only statistics and `completed` wait here: `ingested` is counted at each
-// send, so `completed` can only lag it and never makes the drain look
-// quiescent while a token is in flight.
+// Besides statistics, they hold the chain's completions and the ingestion of
+// the tokens it carried directly (sends through a mailbox count `ingested`
+// at once).  A carried token is completed only by the same chain, so the two
+// lag by the same amount, and a flush adds `ingested` before `completed`:
+// the counters never show the drain quiescent while a token is in flight.
 struct RingTally {
-    uint32_t done, claims, sends;
+    uint32_t done, claims, sends, carried;
 };
 constexpr uint32_t kTallyHops = 32;
 __device__ void ring_tally_flush(const DrainParams &P, RingTally &tl) {
-    if (lane_id() == 0 && (tl.done | tl.claims | tl.sends)) {
+    if (lane_id() == 0 && (tl.done | tl.claims | tl.sends | tl.carried)) {
         // everything the counted messages did (their sends counted in
         // ingested) is ordered before they count as completed
         asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        if (tl.carried) {
+            add_u64(&P.ctl->ingested, tl.carried);
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        }
         if (tl.sends) add_u64(&P.ctl->device_sends, tl.sends);
         if (tl.claims) add_u64(&P.ctl->claims, tl.claims);
         if (tl.done) {
@@ -954,7 +960,7 @@ __device__ void ring_tally_flush(const DrainParams &P, RingTally &tl) {
             add_u64(&P.ctl->completed, tl.done);
         }
     }
-    tl = RingTally{0, 0, 0};
+    tl = RingTally{0, 0, 0, 0};
     __syncwarp();
 }
 
@@ -993,9 +999,9 @@ __device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v, uint32
                 if (t == h) direct = true;
                 else st_release_gpu(&N->state, kWaiting);
             }
-            if (direct) add_u64(&P.ctl->ingested, 1);
         }
         if (__shfl_sync(FULL, direct, 0)) {
+            tl.carried += 1;   // ingested at the chain's next tally flush
             carry->has = true;
             carry->m = m;
             carry->head = __shfl_sync(FULL, h, 0);
@@ -1231,7 +1237,7 @@ __device__ void claim_ring(const DrainParams &P, uint32_t a) {
     uint32_t cur = a;
     Carry carry{};
     carry.has = false;
-    RingTally tl{0, 0, 0};
+    RingTally tl{0, 0, 0, 0};
     for (int i = 0; cur != kNone && i < kMaxChain && ((i & 7) != 0 || !exit_requested(P.ctl)); ++i) {
         cur = run_ring_actor(P, cur, carry, i + 1 < kMaxChain, tl);
         if ((i & 255) == 0 && lane_id() == 0) heartbeat(P);
