@@ -217,7 +217,7 @@ __device__ bool warp_enqueue(const DrainParams &P, bool valid, uint32_t a, const
 // terminated, 0 if it knows it has not, -1 to read its state.  `moved`: false
 // when the claim took no slot (the head keeps its value and needs no store).
 __device__ void release_actor(const DrainParams &P, uint32_t a, uint64_t new_head, int done = -1,
-                              bool moved = true) {
+                              bool moved = true, bool head_known = true) {
     __syncwarp();
     if (lane_id() == 0) {
         ActorDesc *A = &P.actors[a];
@@ -226,7 +226,10 @@ __device__ void release_actor(const DrainParams &P, uint32_t a, uint64_t new_hea
         if (!done) {
             st_release_gpu(&A->state, kWaiting);
             asm volatile("fence.sc.gpu;" ::: "memory");
-            if (ld_relaxed_gpu(&A->tail) != new_head &&
+            // (a claim that did not read the head reads it here, beside the
+            // tail: only the claim holder moves it)
+            const uint64_t hd = head_known ? new_head : ld_relaxed_gpu(&A->head);
+            if (ld_relaxed_gpu(&A->tail) != hd &&
                 cas_u32(&A->state, kWaiting, kReady) == kWaiting) {
                 if (!ready_push(P, a)) fail(P, kErrWaitQueue, 3);
             }
@@ -918,21 +921,8 @@ __device__ bool ring_emit_factor(const DrainParams &P, uint32_t a) {
 struct Carry {
     bool has;
     MsgData m;
-    uint64_t head;     // the receiver's mailbox position when it was claimed (its mailbox was empty)
 };
 
-// Send token v from ring actor `a` to its successor.  Direct handoff: if the
-// successor is waiting with an empty mailbox, this warp claims it (CAS
-// WAITING -> RUNNING) and carries the token to its run instead of writing a
-// mailbox slot -- no ticket, no slot round trip, no wake handshake.  With an
-// empty mailbox the token is the successor's next message in any order, and
-// per-sender order holds because this actor's earlier tokens to it are all
-// handled.  Otherwise the token goes through the mailbox (warp_enqueue), and
-// a successor this call wakes is returned in *handoff to run next.
-// In a ring that a RECREATE master creates, a token of value 0 carries its
-// origin (the actor id + 1 in the payload's high word), and its tag names the
-// ring, the incarnation and the receiver's position: master + 1 in bits 0..31,
-// the incarnation in bits 32..39, the position in bits 40..63.
 // Counters of a chain of ring runs, kept in registers (warp-uniform) and
 // added to the device counters every kTallyHops runs and at the chain's end.
 // Besides statistics, they hold the chain's completions and the ingestion of
@@ -964,6 +954,19 @@ __device__ void ring_tally_flush(const DrainParams &P, RingTally &tl) {
     __syncwarp();
 }
 
+// Send token v from ring actor `a` to its successor.  Direct handoff: if the
+// successor is waiting, this warp claims it (CAS WAITING -> RUNNING) and
+// carries the token to its run instead of writing a mailbox slot -- no
+// ticket, no slot round trip, no wake handshake.  Messages already in the
+// successor's mailbox come from other senders (a ring holds one token, so
+// this actor has none there): the successor's release finds them and
+// re-queues it, and messages of different senders have no order to keep.
+// Otherwise the token goes through the mailbox (warp_enqueue), and a
+// successor this call wakes is returned in *handoff to run next.
+// In a ring that a RECREATE master creates, a token of value 0 carries its
+// origin (the actor id + 1 in the payload's high word), and its tag names the
+// ring, the incarnation and the receiver's position: master + 1 in bits 0..31,
+// the incarnation in bits 32..39, the position in bits 40..63.
 __device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v, uint32_t *handoff, Carry *carry,
                              RingTally &tl, uint32_t origin1 = 0) {
     ActorDesc *A = &P.actors[a];
@@ -984,27 +987,19 @@ __device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v, uint32
     tl.sends += 1;
     if (carry && !carry->has && next != a) {
         bool direct = false;
-        uint64_t h = 0;
         if (lane == 0) {
+            // claimed: the token is carried into the successor's run.  Messages
+            // already in its mailbox (from other senders: a ring holds one
+            // token, so this sender has none there) are found by the run's
+            // release, which reads the head beside the tail and re-queues the
+            // actor; messages of different senders have no order to keep.
             ActorDesc *N = &P.actors[next];
-            if (cas_acq_rel_gpu(&N->state, kWaiting, kRunning) == kWaiting) {
-                // claimed: its head is final (the last holder released it before
-                // parking, and the CAS acquired that).  A message whose ticket
-                // this read misses is found by this claim's release, which
-                // re-queues the actor; with messages already waiting the token
-                // goes behind them, after returning the actor to WAITING
-                // (the mailbox path's wake then schedules it).
-                const uint64_t t = ld_relaxed_gpu(&N->tail);
-                h = ld_relaxed_gpu(&N->head);
-                if (t == h) direct = true;
-                else st_release_gpu(&N->state, kWaiting);
-            }
+            direct = cas_acq_rel_gpu(&N->state, kWaiting, kRunning) == kWaiting;
         }
         if (__shfl_sync(FULL, direct, 0)) {
             tl.carried += 1;   // ingested at the chain's next tally flush
             carry->has = true;
             carry->m = m;
-            carry->head = __shfl_sync(FULL, h, 0);
             *handoff = next;
             return true;
         }
@@ -1093,9 +1088,9 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
     const bool carried = carry.has;
     uint64_t head, take;
     if (carried) {
-        // claimed by the predecessor's forward with an empty mailbox: later
-        // messages are left to this claim's release, which re-queues the actor
-        head = carry.head;
+        // claimed by the predecessor's forward: the mailbox's messages are
+        // left to this claim's release, which re-queues the actor
+        head = 0;
         take = 0;
     } else {
         if (lane == 0) *((volatile uint32_t *)&A->state) = kRunning;
@@ -1214,7 +1209,7 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
         __syncwarp();
         ++handled;
     }
-    release_actor(P, a, head, ended ? 1 : 0, !carried);
+    release_actor(P, a, head, ended ? 1 : 0, !carried, !carried);
     // counted as completed at the chain's next tally flush (after its fence)
     tl.done += (uint32_t)handled;
     carry = out;
