@@ -932,8 +932,31 @@ struct Carry {
 // the counters never show the drain quiescent while a token is in flight.
 struct RingTally {
     uint32_t done, claims, sends, carried;
+    uint32_t pend;     // lane i < npend: a carried actor whose release waits for the batch
+    uint32_t npend;
 };
 constexpr uint32_t kTallyHops = 32;
+// Carried runs leave their actor claimed (RUNNING) until kReleaseBatch of
+// them are pending; one warp operation then releases them all: the state
+// stores, one fence.sc, and each actor's head and tail check (re-queueing an
+// actor that messages reached in the meantime: a sender that saw it RUNNING
+// did not wake it).  The protocol is release_actor's, only later.
+constexpr uint32_t kReleaseBatch = 8;
+__device__ void ring_release_pending(const DrainParams &P, RingTally &tl) {
+    if (tl.npend == 0) return;
+    const uint32_t lane = lane_id();
+    __syncwarp();
+    ActorDesc *A = lane < tl.npend ? &P.actors[tl.pend] : nullptr;
+    if (A) st_release_gpu(&A->state, kWaiting);
+    asm volatile("fence.sc.gpu;" ::: "memory");
+    if (A && ld_relaxed_gpu(&A->tail) != ld_relaxed_gpu(&A->head) &&
+        cas_u32(&A->state, kWaiting, kReady) == kWaiting) {
+        if (!ready_push(P, tl.pend)) fail(P, kErrWaitQueue, 3);
+    }
+    tl.npend = 0;
+    tl.pend = kNone;
+    __syncwarp();
+}
 __device__ void ring_tally_flush(const DrainParams &P, RingTally &tl) {
     if (lane_id() == 0 && (tl.done | tl.claims | tl.sends | tl.carried)) {
         // everything the counted messages did (their sends counted in
@@ -950,7 +973,7 @@ __device__ void ring_tally_flush(const DrainParams &P, RingTally &tl) {
             add_u64(&P.ctl->completed, tl.done);
         }
     }
-    tl = RingTally{0, 0, 0, 0};
+    tl.done = tl.claims = tl.sends = tl.carried = 0;
     __syncwarp();
 }
 
@@ -986,6 +1009,8 @@ __device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v, uint32
     const uint32_t lane = lane_id();
     tl.sends += 1;
     if (carry && !carry->has && next != a) {
+        // a successor this chain still holds is released first
+        if (__any_sync(FULL, lane < tl.npend && tl.pend == next)) ring_release_pending(P, tl);
         bool direct = false;
         if (lane == 0) {
             // claimed: the token is carried into the successor's run.  Messages
@@ -1209,7 +1234,13 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
         __syncwarp();
         ++handled;
     }
-    release_actor(P, a, head, ended ? 1 : 0, !carried, !carried);
+    if (carried && !ended) {
+        // released with the chain's next batch
+        if (lane == tl.npend) tl.pend = a;
+        if (++tl.npend == kReleaseBatch) ring_release_pending(P, tl);
+    } else {
+        release_actor(P, a, head, ended ? 1 : 0, !carried, !carried);
+    }
     // counted as completed at the chain's next tally flush (after its fence)
     tl.done += (uint32_t)handled;
     carry = out;
@@ -1232,12 +1263,13 @@ __device__ void claim_ring(const DrainParams &P, uint32_t a) {
     uint32_t cur = a;
     Carry carry{};
     carry.has = false;
-    RingTally tl{0, 0, 0, 0};
+    RingTally tl{0, 0, 0, 0, kNone, 0};
     for (int i = 0; cur != kNone && i < kMaxChain && ((i & 7) != 0 || !exit_requested(P.ctl)); ++i) {
         cur = run_ring_actor(P, cur, carry, i + 1 < kMaxChain, tl);
         if ((i & 255) == 0 && lane_id() == 0) heartbeat(P);
         if ((uint32_t)(i + 1) % kTallyHops == 0) ring_tally_flush(P, tl);
     }
+    ring_release_pending(P, tl);
     ring_tally_flush(P, tl);
     if (cur != kNone && lane_id() == 0 && !ready_push(P, cur))
         fail(P, kErrWaitQueue, 18);
