@@ -1258,6 +1258,38 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
 // bound, after which the next one goes back to the ready queue.
 // A carried token cannot go back to the ready queue, so the last run of a
 // chain forwards through the mailbox.
+// The hop of a plain ring member (no flags) receiving a carried plain token
+// v > 0 that needs no reply: the steps of its run in run_ring_actor (log,
+// forward v - 1, record v, count, release with the chain's next batch)
+// without the general run's dispatch.  Returns false, having done nothing,
+// for any other run.
+__device__ bool ring_fast_hop(const DrainParams &P, uint32_t &cur, Carry &carry, bool direct, RingTally &tl) {
+    const uint32_t lane = lane_id();
+    const uint32_t a = cur;
+    ActorDesc *A = &P.actors[a];
+    const int32_t v = (int32_t)(uint32_t)carry.m.payload;
+    if (!direct || carry.m.kind != kToken || carry.m.reply_addr != 0 || v <= 0 || A->flags != 0 ||
+        A->kind != kToken)
+        return false;
+    tl.claims += 1;
+    if (P.validation) log_rows(P, a, 1, carry.m);
+    Carry out{};
+    out.has = false;
+    uint32_t handoff = kNone;
+    if (!ring_forward(P, a, v - 1, &handoff, &out, tl)) {
+        cur = kNone;
+        return true;
+    }
+    if (lane == 0) A->user_state = v;
+    __syncwarp();
+    tl.done += 1;
+    if (lane == tl.npend) tl.pend = a;
+    if (++tl.npend == kReleaseBatch) ring_release_pending(P, tl);
+    carry = out;
+    cur = handoff;
+    return true;
+}
+
 __device__ void claim_ring(const DrainParams &P, uint32_t a) {
     constexpr int kMaxChain = 1 << 14;
     uint32_t cur = a;
@@ -1265,7 +1297,8 @@ __device__ void claim_ring(const DrainParams &P, uint32_t a) {
     carry.has = false;
     RingTally tl{0, 0, 0, 0, kNone, 0};
     for (int i = 0; cur != kNone && i < kMaxChain && ((i & 7) != 0 || !exit_requested(P.ctl)); ++i) {
-        cur = run_ring_actor(P, cur, carry, i + 1 < kMaxChain, tl);
+        const bool direct = i + 1 < kMaxChain;
+        if (!(carry.has && ring_fast_hop(P, cur, carry, direct, tl))) cur = run_ring_actor(P, cur, carry, direct, tl);
         if ((i & 255) == 0 && lane_id() == 0) heartbeat(P);
         if ((uint32_t)(i + 1) % kTallyHops == 0) ring_tally_flush(P, tl);
     }
