@@ -921,6 +921,10 @@ __device__ bool ring_emit_factor(const DrainParams &P, uint32_t a) {
 struct Carry {
     bool has;
     MsgData m;
+    // the receiver's successor, and whether it is a plain ring member (no
+    // flags), read beside the claim's CAS (neither changes while its ring runs)
+    uint32_t next;
+    bool plain;
 };
 
 // Counters of a chain of ring runs, kept in registers (warp-uniform) and
@@ -991,16 +995,20 @@ __device__ void ring_tally_flush(const DrainParams &P, RingTally &tl) {
 // ring, the incarnation and the receiver's position: master + 1 in bits 0..31,
 // the incarnation in bits 32..39, the position in bits 40..63.
 __device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v, uint32_t *handoff, Carry *carry,
-                             RingTally &tl, uint32_t origin1 = 0) {
+                             RingTally &tl, uint32_t origin1 = 0, uint32_t known_next = kNone,
+                             uint32_t known_flags = kNone) {
+    // (known_next / known_flags: the sender's successor and flags when the
+    // caller has them, so their descriptor line is not read again)
     ActorDesc *A = &P.actors[a];
-    const uint32_t next = A->next;
+    const uint32_t next = known_next != kNone ? known_next : A->next;
+    const uint32_t aflags = known_flags != kNone ? known_flags : A->flags;
     MsgData m{};
     m.payload = (uint64_t)(uint32_t)v | ((uint64_t)origin1 << 32);
     m.kind = kToken;
     m.sender = 0x80000000u | a;
     m.sender_seq = (uint32_t)v;
-    if (A->flags & (kActorRecreate | kActorLink)) {
-        const bool master = (A->flags & kActorRecreate) != 0;
+    if (aflags & (kActorRecreate | kActorLink)) {
+        const bool master = (aflags & kActorRecreate) != 0;
         const uint32_t pos = master ? 0u : A->ring_pos;
         const uint32_t recv = pos + 1 == A->ring_len ? 0u : pos + 1;
         m.tag = (uint64_t)((master ? a : A->ring_master) + 1) | ((uint64_t)(A->ring_inc & 0xFFu) << 32) |
@@ -1012,19 +1020,26 @@ __device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v, uint32
         // a successor this chain still holds is released first
         if (__any_sync(FULL, lane < tl.npend && tl.pend == next)) ring_release_pending(P, tl);
         bool direct = false;
+        uint32_t f = 0;
+        ActorDesc *N = &P.actors[next];
         if (lane == 0) {
             // claimed: the token is carried into the successor's run.  Messages
             // already in its mailbox (from other senders: a ring holds one
             // token, so this sender has none there) are found by the run's
             // release, which reads the head beside the tail and re-queues the
             // actor; messages of different senders have no order to keep.
-            ActorDesc *N = &P.actors[next];
             direct = cas_acq_rel_gpu(&N->state, kWaiting, kRunning) == kWaiting;
+        } else if (lane == 1) {
+            f = N->next;    // read while lane 0's CAS is in flight
+        } else if (lane == 2) {
+            f = (N->flags == 0 && N->kind == kToken) ? 1u : 0u;
         }
         if (__shfl_sync(FULL, direct, 0)) {
             tl.carried += 1;   // ingested at the chain's next tally flush
             carry->has = true;
             carry->m = m;
+            carry->next = __shfl_sync(FULL, f, 1);
+            carry->plain = __shfl_sync(FULL, f, 2) != 0;
             *handoff = next;
             return true;
         }
@@ -1268,15 +1283,13 @@ __device__ bool ring_fast_hop(const DrainParams &P, uint32_t &cur, Carry &carry,
     const uint32_t a = cur;
     ActorDesc *A = &P.actors[a];
     const int32_t v = (int32_t)(uint32_t)carry.m.payload;
-    if (!direct || carry.m.kind != kToken || carry.m.reply_addr != 0 || v <= 0 || A->flags != 0 ||
-        A->kind != kToken)
-        return false;
+    if (!direct || !carry.plain || carry.m.kind != kToken || carry.m.reply_addr != 0 || v <= 0) return false;
     tl.claims += 1;
     if (P.validation) log_rows(P, a, 1, carry.m);
     Carry out{};
     out.has = false;
     uint32_t handoff = kNone;
-    if (!ring_forward(P, a, v - 1, &handoff, &out, tl)) {
+    if (!ring_forward(P, a, v - 1, &handoff, &out, tl, 0, carry.next, 0u)) {
         cur = kNone;
         return true;
     }
