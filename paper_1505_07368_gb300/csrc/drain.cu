@@ -918,13 +918,25 @@ __device__ bool ring_emit_factor(const DrainParams &P, uint32_t a) {
 
 // A message handed from one ring actor's run straight to the next actor's,
 // without going through a mailbox (all lanes hold the same copy).
+// A carried token has no reply record, and its sequence number is its value,
+// so only its payload, tag, sender and kind travel.
 struct Carry {
     bool has;
-    MsgData m;
+    uint64_t payload, tag;
+    uint32_t sender, kind;
     // the receiver's successor, and whether it is a plain ring member (no
     // flags), read beside the claim's CAS (neither changes while its ring runs)
     uint32_t next;
     bool plain;
+    __device__ MsgData msg() const {
+        MsgData m{};
+        m.payload = payload;
+        m.tag = tag;
+        m.sender = sender;
+        m.sender_seq = (uint32_t)payload;
+        m.kind = kind;
+        return m;
+    }
 };
 
 // Counters of a chain of ring runs, kept in registers (warp-uniform) and
@@ -1037,7 +1049,10 @@ __device__ bool ring_forward(const DrainParams &P, uint32_t a, int32_t v, uint32
         if (__shfl_sync(FULL, direct, 0)) {
             tl.carried += 1;   // ingested at the chain's next tally flush
             carry->has = true;
-            carry->m = m;
+            carry->payload = m.payload;
+            carry->tag = m.tag;
+            carry->sender = m.sender;
+            carry->kind = m.kind;
             carry->next = __shfl_sync(FULL, f, 1);
             carry->plain = __shfl_sync(FULL, f, 2) != 0;
             *handoff = next;
@@ -1157,7 +1172,7 @@ __device__ uint32_t run_ring_actor(const DrainParams &P, uint32_t a, Carry &carr
     for (uint64_t i = 0; i < take + (carried ? 1 : 0); ++i) {
         MsgData m{};
         if (carried && i == 0) {
-            m = carry.m;
+            m = carry.msg();
             if (P.validation) log_rows(P, a, 1, m);
         } else {
             if (warp_dequeue(P, a, head, 1, m) == 0) return kNone;
@@ -1282,10 +1297,10 @@ __device__ bool ring_fast_hop(const DrainParams &P, uint32_t &cur, Carry &carry,
     const uint32_t lane = lane_id();
     const uint32_t a = cur;
     ActorDesc *A = &P.actors[a];
-    const int32_t v = (int32_t)(uint32_t)carry.m.payload;
-    if (!direct || !carry.plain || carry.m.kind != kToken || carry.m.reply_addr != 0 || v <= 0) return false;
+    const int32_t v = (int32_t)(uint32_t)carry.payload;
+    if (!direct || !carry.plain || carry.kind != kToken || v <= 0) return false;
     tl.claims += 1;
-    if (P.validation) log_rows(P, a, 1, carry.m);
+    if (P.validation) log_rows(P, a, 1, carry.msg());
     Carry out{};
     out.has = false;
     uint32_t handoff = kNone;
