@@ -2225,17 +2225,14 @@ __device__ __noinline__ void drain_mandel_bands(const DrainParams &P, GroupShare
     }
 }
 
-// A team leader looks for a factor batch to sweep: pop ready actors, claim
-// factor actors into a fresh batch record, and run ring-token actors on the
-// way (a few at most, so the group forms quickly).
 // Claim factor actor `a` (popped from the ready queue, kind checked) into
 // batch records.  While more actors are ready than teams are idle, the claim
 // fills a group of up to kGroupRecords records: messages of `a`, then of up to
 // kTopUpTries further ready factor actors, reordered by n (factor_group_sort).
-// The caller's team sweeps the group's last batch; the others go to the
-// queue of batches waiting for a team.  Otherwise the claim fills one record
-// from `a` alone.  With no record free the actor stays READY.  Returns the
-// batch the caller's team sweeps, or kNone.
+// The caller's team sweeps the group's last batch (the largest n); the
+// others go to the queue of batches waiting for a team.  Otherwise the claim
+// fills one record from `a` alone.  With no record free the actor stays
+// READY.  Returns the batch the caller's team sweeps, or kNone.
 template <bool kSplit>
 __device__ __noinline__ uint32_t claim_factor_group(const DrainParams &P, uint32_t a, uint32_t rng) {
     const uint32_t lane = lane_id();
@@ -2320,6 +2317,9 @@ __device__ __noinline__ uint32_t claim_factor_group(const DrainParams &P, uint32
     return mine;
 }
 
+// A team leader looks for a factor batch to sweep: a batch waiting in the
+// queue first, else pop ready actors, claim factor actors into batch
+// records, and run the other actors on the way (a few at most).
 template <bool kGemm, bool kSplit>
 __device__ uint32_t find_batch(const DrainParams &P, uint32_t &rng) {
     const uint32_t lane = lane_id();
