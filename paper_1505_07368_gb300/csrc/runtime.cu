@@ -810,7 +810,8 @@ int make_fork_pool(caf_gpu_runtime *rt) {
     for (uint32_t i = 0; i < pool; ++i) ids[i] = base + i;
     int r = init_queue(rt, &forkq, forkq_cap, &rt->d_ctl->forkq, ids);
     if (r) return fail_with(r);
-    if ((r = init_queue(rt, &readyq, readyq_cap, &rt->d_ctl->readyq, {}))) return fail_with(r);
+    r = init_queue(rt, &readyq, readyq_cap, &rt->d_ctl->readyq, {});
+    if (r) return fail_with(r);
     for (void *p : {(void *)rt->d_readyq, (void *)rt->d_actors, (void *)rt->d_slots}) {
         drop_guard(rt, p);
         cudaFree(p);
